@@ -1,0 +1,217 @@
+"""CPU FP64 oracle of the crystallization PBE step (Sec. 2.1; SI Sec. S1).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(``paper_2411_00742_gb300``) never imports, links or runs anything here, and
+this package never imports the product path.
+
+The oracle is a plain C program (``pbe_oracle.c``) compiled with
+``-O2 -ffp-contract=off`` and loaded through ctypes; ``mom.py`` holds the
+method-of-moments reference (SI Sec. S1.2), ``exact.py`` an exact-rational
+brute force for tiny grids.
+
+Parity status: every function exported here is pinned by a ``-m "not gpu"``
+test against closed forms, invariants, exact translation, the method of
+moments or exact rational arithmetic (see ``tests/test_oracle_*.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libpbe_oracle.so")
+_SOURCES = [os.path.join(_HERE, "pbe_oracle.c"), os.path.join(_HERE, "pbe_oracle_core.h"),
+            os.path.join(_HERE, "pbe_oracle_adjoint.c")]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no fp contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [s for s in _SOURCES if os.path.exists(s)]
+    if not force and os.path.exists(_LIB_PATH):
+        mtime = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(s) <= mtime for s in srcs):
+            return _LIB_PATH
+    cfiles = [s for s in srcs if s.endswith(".c")]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
+           "-o", tmp] + cfiles + ["-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
+                ("lmax1", ctypes.c_double), ("lmax2", ctypes.c_double),
+                ("fixed_kinetics", ctypes.c_int),
+                ("kg1", ctypes.c_double), ("g1", ctypes.c_double),
+                ("kg2", ctypes.c_double), ("g2", ctypes.c_double),
+                ("kb", ctypes.c_double), ("b", ctypes.c_double),
+                ("cs0", ctypes.c_double), ("cs1", ctypes.c_double), ("cs2", ctypes.c_double),
+                ("T0", ctypes.c_double), ("T1", ctypes.c_double), ("t_cool", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("cfl", ctypes.c_double)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER(Params)
+        lib.orc_psi.restype = ctypes.c_double
+        lib.orc_psi.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.orc_temperature.restype = ctypes.c_double
+        lib.orc_temperature.argtypes = [P, ctypes.c_double]
+        lib.orc_kinetics.argtypes = [P, ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_timestep.restype = ctypes.c_int
+        lib.orc_timestep.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _D]
+        lib.orc_rhs.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_face_fluxes.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, _D]
+        lib.orc_volume.restype = ctypes.c_double
+        lib.orc_volume.argtypes = [P, _D]
+        lib.orc_moments.argtypes = [P, _D, _D]
+        lib.orc_step.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_solve.restype = ctypes.c_long
+        lib.orc_solve.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int, _D, _D]
+        lib.orc_solve_cs.restype = ctypes.c_long
+        lib.orc_solve_cs.argtypes = [P, ctypes.c_int, ctypes.c_double, _D, ctypes.c_double,
+                                     ctypes.c_double, _D, ctypes.c_int, _D, _D]
+        if hasattr(lib, "orc_vjp"):
+            lib.orc_vjp.restype = ctypes.c_long
+            lib.orc_vjp.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
+                                    _D, _D, _D]
+        _lib = lib
+    return _lib
+
+
+def params(problem) -> Params:
+    p = problem
+    n2 = p.ncells[1] if p.ndim == 2 else 1
+    l2 = p.lmax[1] if p.ndim == 2 else 1.0
+    return Params(p.ndim, int(p.ncells[0]), int(n2), float(p.lmax[0]), float(l2),
+                  int(bool(p.fixed_kinetics)),
+                  float(p.kg[0]), float(p.g[0]), float(p.kg[1]), float(p.g[1]),
+                  float(p.kb), float(p.b),
+                  float(p.csat[0]), float(p.csat[1]), float(p.csat[2]),
+                  float(p.T0), float(p.T1), float(p.t_cool), float(p.kappa), float(p.cfl))
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def ncols(problem) -> int:
+    return 6 if problem.ndim == 1 else 12
+
+
+def psi(a: float, b: float) -> float:
+    return _load().orc_psi(float(a), float(b))
+
+
+def temperature(problem, t: float) -> float:
+    P = params(problem)
+    return _load().orc_temperature(ctypes.byref(P), float(t))
+
+
+def kinetics(problem, C: float, t: float):
+    """(G1, G2, B) at concentration C and time t."""
+    P = params(problem)
+    out = np.zeros(3)
+    _load().orc_kinetics(ctypes.byref(P), float(C), float(t), _ptr(out))
+    return tuple(out)
+
+
+def timestep(problem, G1: float, G2: float, t: float, t_next: float):
+    """(dt, t_new, clipped)."""
+    P = params(problem)
+    out = np.zeros(2)
+    c = _load().orc_timestep(ctypes.byref(P), float(G1), float(G2), float(t), float(t_next), _ptr(out))
+    return out[0], out[1], bool(c)
+
+
+def rhs(problem, n, G1: float, G2: float, B: float) -> np.ndarray:
+    P = params(problem)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    L = np.zeros_like(n)
+    _load().orc_rhs(ctypes.byref(P), _ptr(n), float(G1), float(G2), float(B), _ptr(L))
+    return L
+
+
+def face_fluxes(problem, n, G1: float, G2: float = 0.0):
+    P = params(problem)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    if problem.ndim == 1:
+        F = np.zeros(problem.ncells[0] + 1)
+        _load().orc_face_fluxes(ctypes.byref(P), _ptr(n), float(G1), 0.0, _ptr(F), _ptr(F))
+        return F
+    N1, N2 = problem.ncells
+    F1 = np.zeros((N1 + 1, N2))
+    F2 = np.zeros((N1, N2 + 1))
+    _load().orc_face_fluxes(ctypes.byref(P), _ptr(n), float(G1), float(G2), _ptr(F1), _ptr(F2))
+    return F1, F2
+
+
+def volume(problem, n) -> float:
+    P = params(problem)
+    return _load().orc_volume(ctypes.byref(P), _ptr(np.ascontiguousarray(n, dtype=np.float64)))
+
+
+def moments(problem, n) -> np.ndarray:
+    P = params(problem)
+    mu = np.zeros(4 if problem.ndim == 1 else 10)
+    _load().orc_moments(ctypes.byref(P), _ptr(np.ascontiguousarray(n, dtype=np.float64)), _ptr(mu))
+    return mu
+
+
+def step(problem, n, C: float, t: float, t_next: float):
+    """One SSP-RK2 step.  Returns (n_new, dict(dt, C, t, C1, clipped))."""
+    P = params(problem)
+    n = np.array(n, dtype=np.float64, order="C", copy=True)
+    out = np.zeros(5)
+    _load().orc_step(ctypes.byref(P), _ptr(n), float(C), float(t), float(t_next), _ptr(out))
+    return n, dict(dt=out[0], C=out[1], t=out[2], C1=out[3], clipped=bool(out[4]))
+
+
+def solve(problem, n0, C0: float, t0: float, t_out):
+    """March through the output times.  Returns dict(rows, n, C, t, steps).
+
+    rows[j] = (t, mu0..mu3, C) in 1-D and (t, mu00, mu10, mu01, mu20, mu11,
+    mu02, mu30, mu21, mu12, mu03, C) in 2-D."""
+    t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+    if len(t_out) and (t_out[0] < t0 or np.any(np.diff(t_out) <= 0)):
+        raise ValueError("t_out must be increasing and start at or after t0")
+    P = params(problem)
+    n = np.array(n0, dtype=np.float64, order="C", copy=True)
+    rows = np.zeros((len(t_out), ncols(problem)))
+    st = np.zeros(2)
+    steps = _load().orc_solve(ctypes.byref(P), _ptr(n), float(C0), float(t0), _ptr(t_out),
+                              len(t_out), _ptr(rows), _ptr(st))
+    return dict(rows=rows, n=n, C=st[0], t=st[1], steps=int(steps))
+
+
+def solve_cs(problem, which: int, n0, C0: float, t0: float, t_out, h: float = 1e-30):
+    """Complex-step derivative of all output rows w.r.t. kinetic parameter
+    ``which`` (0..5 = kg1, g1, kg2, g2, kb, b).  Returns (rows, drows)."""
+    t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+    P = params(problem)
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    rows = np.zeros((len(t_out), ncols(problem)))
+    drows = np.zeros_like(rows)
+    _load().orc_solve_cs(ctypes.byref(P), int(which), float(h), _ptr(n0), float(C0), float(t0),
+                         _ptr(t_out), len(t_out), _ptr(rows), _ptr(drows))
+    return rows, drows
+
+
+def solve_instance(inst):
+    return solve(inst.problem, inst.n0, inst.C0, inst.t0, inst.t_out)
