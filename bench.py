@@ -1,0 +1,286 @@
+"""Benchmark of the PBE finite-volume solver on GB300.
+
+One benchmark step = one full solve of the 2-D size-and-shape crystallization
+problem (256 x 256 cells on [0, 500]^2 um, Gaussian seed, power-law growth and
+nucleation, cooling 40 -> 20 C over 3600 s, 61 output rows) - the whole hot
+path: kinetics, CFL step, limited fluxes, nucleation inflow, SSP-RK2 update,
+moment reduction and solute balance, repeated to every output time.
+
+Metric: FVM cell-steps/s (cells x SSP-RK2 steps / second) of the fused path,
+with the plain path reported beside it.  ``--impl reference`` times the CPU
+oracle on the same workload instead (the comparison arm).
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+torchrun each rank runs its own replica (the 2-D grid is not sharded).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pbe_inputs as pi  # noqa: E402
+
+METRIC = "FVM cell-steps/s and adjoint grads/s, fused vs plain GPU, at stated FP64 error"
+# algorithmic FP64 operations per cell-step of the 2-D SSP-RK2 step (FMA = 2,
+# division = 1): per stage two faces (difference, sum, division, FMA = 5 each),
+# update (2 differences + 2 FMA = 6), volume moment (FMA = 2); stage 2 adds the
+# Runge-Kutta average (3): 18 + 21 = 39.
+FLOPS_PER_CELL_STEP_2D = 39
+FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64 (2 FMA/clk/SM x 152 SMs x ~2.07 GHz)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload():
+    inst = pi.config_2d(256)
+    return inst, {"workload": "2-D size-and-shape crystallization, 256x256 cells on [0,500]^2 um, "
+                              "full 0-3600 s solve, 61 output rows of (t, mu_pq p+q<=3, C)",
+                  "cells": inst.problem.ncell, "grid": [256, 256], "outputs": len(inst.t_out),
+                  "l2": "state (0.5 MB/array) stays L2-resident inside a solve; a 256 MB buffer is "
+                        "written between timed solves to flush L2"}
+
+
+def _oracle_rate(inst, budget_s: float, min_reps: int = 1):
+    """CPU oracle cell-steps/s on the same workload (single thread)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    reps, cells = 0, 0
+    while True:
+        r = oracle.solve_instance(inst)
+        reps += 1
+        cells += inst.problem.ncell * r["steps"]
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= budget_s:
+            break
+    return cells / el, reps, el, r
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    inst, cfg = _workload()
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.solve_instance(inst)
+    t0 = time.perf_counter()
+    cells = 0
+    for _ in range(args.steps):
+        r = oracle.solve_instance(inst)
+        cells += inst.problem.ncell * r["steps"]
+    el = time.perf_counter() - t0
+    v = cells / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full solves of the 256x256 workload, single thread"},
+            "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_2411_00742_gb300 as P
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    inst, cfg = _workload()
+    cfg["parallelism"] = f"replicas x{ws}" if ws > 1 else "single GPU"
+    n0_dev = torch.as_tensor(inst.n0).to("cuda")
+    nrow, ncol = len(inst.t_out), P.ncols(2)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    import oracle
+    want = oracle.solve_instance(inst)
+
+    def measure(path):
+        g = P.Grid.from_problem(inst.problem, stream=stream, path=path)
+        rows = torch.zeros((nrow, ncol), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.set_state(n0_dev, inst.C0, 0.0)
+                _, steps = g.solve(inst.t_out, out=rows)
+        torch.cuda.synchronize()
+        err = float(np.max(np.abs(rows.cpu().numpy()[:, 1:] - want["rows"][:, 1:]) / np.abs(want["rows"][:, 1:])))
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.set_state(n0_dev, inst.C0, 0.0)
+                _, steps = g.solve(inst.t_out, out=rows)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) * 1e-3)
+        g.close()
+        return sum(times), steps, err
+
+    def e2e(path):
+        g = P.Grid.from_problem(inst.problem, stream=stream, path=path)
+        n0_host = torch.as_tensor(inst.n0).pin_memory()
+        rows_host = torch.zeros((nrow, ncol), dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.set_state(n0_host, inst.C0, 0.0)
+                g.solve(inst.t_out, out=rows_host)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                g.set_state(n0_host, inst.C0, 0.0)
+                _, steps = g.solve(inst.t_out, out=rows_host)
+            el = time.perf_counter() - t0
+        g.close()
+        return inst.problem.ncell * steps * args.steps / el, n0_host.numel() * 8 + nrow * 8, nrow * ncol * 8
+
+    clocks = ClockSampler(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_fused, steps, err_fused = measure("fused")
+    t_plain, steps_p, err_plain = measure("plain")
+    clk = clocks.stop()
+    e2e_rate, h2d, d2h = e2e("fused")
+
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_fused, t_plain], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_fused, t_plain = tt.tolist()
+    cells_per_solve = inst.problem.ncell * steps
+    value = ws * cells_per_solve * args.steps / t_fused
+    plain_value = ws * cells_per_solve * args.steps / t_plain
+    ms = 1e3 * t_fused / args.steps
+    kernel_s = t_fused / args.steps
+    achieved = FLOPS_PER_CELL_STEP_2D * cells_per_solve / kernel_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "ssp_rk2_steps_per_solve": steps,
+        "paths": {"fused": {"value": value, "ms_per_solve": ms, "max_rel_err_vs_oracle": err_fused},
+                  "plain": {"value": plain_value, "ms_per_solve": 1e3 * t_plain / args.steps,
+                            "max_rel_err_vs_oracle": err_plain}},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None,
+                     "kernel": "fused persistent solve (prologue included)",
+                     "note": f"FP64 algorithmic {FLOPS_PER_CELL_STEP_2D} flop/cell-step (division = 1); "
+                             "peak = nominal GB300 FP64"},
+        "e2e": {"value": ws * e2e_rate, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, reps, el, _ = _oracle_rate(inst, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{reps} full solves of the same 256x256 workload ({el:.1f} s), single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

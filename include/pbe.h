@@ -1,0 +1,139 @@
+/*
+ * pbe.h - C ABI of the GB300 (sm_103a) solver for the crystallization
+ * population balance equation (PBE) and its coupled solute balance.
+ *
+ * The model (Sec. 2.1, Eqs. 1-4):
+ *   d n/dt + d(G1 n)/dL1 [+ d(G2 n)/dL2] = 0  on [0, lmax] (1-D) or
+ *   [0, lmax1] x [0, lmax2] (2-D), growth-only transport with nucleation B
+ *   entering the smallest-size cell; solute concentration C follows
+ *   C^{k+1} = C^k - kappa (V(n^{k+1}) - V(n^k)) (Eq. 4) with the crystal
+ *   volume V = sum x^3 n dL (1-D) or sum x1 x2^2 n dL1 dL2 (2-D).
+ * The step (Eq. 3 in semi-discrete form; SI Sec. S1.1): van Leer
+ * flux-limited upwind face fluxes, two-stage SSP Runge-Kutta, CFL time step
+ * dt = cfl / (G1/dL1 + G2/dL2), clipped to land exactly on output times.
+ *
+ * Conventions for every call:
+ *  - returns PBE_OK (0) or a PBE_E* code; pbe_last_error() gives the message
+ *    of the last failure on the calling host thread;
+ *  - a pbe_grid is owned by the library: create with pbe_create_grid, free
+ *    with pbe_destroy_grid; its device buffers live on the CUDA device that
+ *    was current at creation;
+ *  - caller pointers stay owned by the caller; each one is host or device
+ *    memory as the `mem` argument (PBE_MEM_HOST / PBE_MEM_DEVICE) says;
+ *  - work is ordered on the stream given to pbe_set_stream (default: the
+ *    legacy default stream).  Calls that return values to the host
+ *    (pbe_step, pbe_solve, pbe_get_state, pbe_moments with host memory,
+ *    pbe_vjp) synchronize that stream before returning;
+ *  - arrays are float64; a 2-D distribution is row-major n[i * N2 + j],
+ *    i along L1 (first size), j along L2 (second size); cell centres are
+ *    x_i = (i + 1/2) dL.
+ * No call falls back to the CPU: without a usable CUDA device every call
+ * that needs one fails with PBE_ECUDA.
+ */
+#ifndef PBE_H
+#define PBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pbe_status;
+#define PBE_OK 0
+#define PBE_EINVAL 1     /* bad argument (size, pointer, order of times)      */
+#define PBE_ENOMEM 2     /* device or pinned allocation failed                */
+#define PBE_ECUDA 3      /* a CUDA runtime call or launch failed              */
+#define PBE_ENONFINITE 4 /* NaN/Inf appeared in the state or kinetics         */
+#define PBE_ETIMEOUT 5   /* step budget or a bounded device wait ran out      */
+#define PBE_ESTATE 6     /* call out of order (e.g. solve before set_state)   */
+
+#define PBE_MEM_HOST 0
+#define PBE_MEM_DEVICE 1
+
+/* kinetic models */
+#define PBE_KINETICS_POWER_LAW 0 /* G_d = kg[d] s^g[d], B = kb s^b, s = max(C/c*(T) - 1, 0) */
+#define PBE_KINETICS_FIXED 1     /* G_d = kg[d], B = kb, independent of S (tests)           */
+
+/* execution paths of pbe_solve */
+#define PBE_PATH_PLAIN 0 /* two stage kernels per step, device-resident scalars, CUDA graph loop */
+#define PBE_PATH_FUSED 1 /* one persistent kernel for the whole solve                              */
+
+typedef struct pbe_grid pbe_grid;
+
+/* Kinetics, solubility, cooling and scheme parameters (Sec. 2.1, Appendix A;
+ * power-law forms with a polynomial solubility). */
+typedef struct {
+    int kind;          /* PBE_KINETICS_*                                        */
+    double kg[2];      /* growth prefactor per direction, um/s                  */
+    double g[2];       /* growth exponent per direction                         */
+    double kb, b;      /* nucleation prefactor (#/(kg s)) and exponent          */
+    double csat[3];    /* c*(T) = csat[0] + csat[1] T + csat[2] T^2, g/g        */
+    double T0, T1;     /* linear cooling from T0 to T1 (deg C) ...              */
+    double t_cool;     /* ... over t_cool seconds (> 0), constant afterwards    */
+    double kappa;      /* rho_c k_v u: g/g of solute per um^3/kg of crystal     */
+    double cfl;        /* Courant number nu of the CFL step (0 < cfl <= 1)      */
+} pbe_kinetics;
+
+/* Create a grid of ndim (1 or 2) dimensions with ncells[d] >= 1 cells on
+ * [0, lmax[d]].  Allocates the state and work buffers on the current device.
+ * Errors: PBE_EINVAL (ndim, sizes, lmax <= 0), PBE_ENOMEM, PBE_ECUDA. */
+pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, const double* lmax);
+
+/* Free a grid and its device buffers (waits for its stream).  NULL is a no-op. */
+pbe_status pbe_destroy_grid(pbe_grid* g);
+
+/* Order all later work of this grid on `cuda_stream` (a cudaStream_t). */
+pbe_status pbe_set_stream(pbe_grid* g, void* cuda_stream);
+
+/* Select the execution path of pbe_solve (PBE_PATH_PLAIN or PBE_PATH_FUSED).
+ * Both compute the same step; results agree to rounding. */
+pbe_status pbe_set_path(pbe_grid* g, int path);
+
+/* Set the kinetic model (Sec. 2.1 S = c/c*; Appendix A growth law only for
+ * S > 1).  Errors: PBE_EINVAL for kind, cfl not in (0, 1], t_cool <= 0. */
+pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k);
+
+/* Load the state: distribution n (ncell values, `mem` memory), solute
+ * concentration C and time t.  Initial condition of Eqs. (5)-(9). */
+pbe_status pbe_set_state(pbe_grid* g, const double* n, double C, double t, int mem);
+
+/* Read the state back (n may be NULL to read only C and t). */
+pbe_status pbe_get_state(pbe_grid* g, double* n, double* C, double* t, int mem);
+
+/* Advance by one SSP-RK2 step whose length is the CFL step, clipped so the
+ * step ends no later than t_limit (> current t).  *dt_taken (may be NULL)
+ * receives the step length.  Synchronizes the grid's stream. */
+pbe_status pbe_step(pbe_grid* g, double t_limit, double* dt_taken);
+
+/* March from the current state through the increasing output times
+ * t_out[0..n_out) (t_out[0] >= current t; host memory), landing on each
+ * exactly (Fig. 1 loop).  rows receives n_out rows of `ncol` doubles
+ * (ncol = 6 in 1-D: t, mu0, mu1, mu2, mu3, C; ncol = 12 in 2-D: t, mu00,
+ * mu10, mu01, mu20, mu11, mu02, mu30, mu21, mu12, mu03, C), in `mem`
+ * memory.  *steps (may be NULL) receives the number of steps taken.
+ * Moments follow the SI definition of mu_pq by the midpoint rule.
+ * Errors: PBE_EINVAL (times), PBE_ESTATE (no state/kinetics),
+ * PBE_ENONFINITE, PBE_ETIMEOUT (more than the step budget), PBE_ECUDA. */
+pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, int mem,
+                     int64_t* steps);
+
+/* Moments of the current distribution: 4 values (mu0..mu3) in 1-D, 10 in
+ * 2-D in the row order of pbe_solve (SI moment definition, midpoint rule). */
+pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
+
+/* Upper bound on steps per pbe_solve call (default 1e6); exceeding it stops
+ * the solve with PBE_ETIMEOUT. */
+pbe_status pbe_set_max_steps(pbe_grid* g, int64_t max_steps);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* pbe_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int pbe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBE_H */

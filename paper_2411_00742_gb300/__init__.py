@@ -1,0 +1,149 @@
+"""GB300 (sm_103a) solver for the crystallization population balance equation.
+
+The explicit high-resolution finite-volume step (Sec. 2.1, Eq. 3 in
+semi-discrete form, SI Sec. S1.1) with its coupled solute balance (Eq. 4)
+runs entirely in the CUDA kernels of ``libpbe.so``; this package only
+marshals arguments to the C ABI declared in ``include/pbe.h``.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: every call
+raises if the CUDA library or a device is unavailable.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PBE_KINETICS_FIXED, PBE_KINETICS_POWER_LAW, PBE_MEM_DEVICE, PBE_MEM_HOST,
+                   PBE_PATH_FUSED, PBE_PATH_PLAIN, PbeError, Kinetics)
+
+__all__ = ["Grid", "PbeError", "kinetics_struct", "ncols"]
+
+_PATHS = {"plain": PBE_PATH_PLAIN, "fused": PBE_PATH_FUSED}
+
+
+def ncols(ndim: int) -> int:
+    return 6 if ndim == 1 else 12
+
+
+def kinetics_struct(problem) -> Kinetics:
+    """pbe_kinetics from any object with the fields of a problem description
+    (kg, g, kb, b, csat, T0, T1, t_cool, kappa, cfl, fixed_kinetics)."""
+    k = Kinetics()
+    k.kind = PBE_KINETICS_FIXED if getattr(problem, "fixed_kinetics", False) else PBE_KINETICS_POWER_LAW
+    k.kg[0], k.kg[1] = float(problem.kg[0]), float(problem.kg[1])
+    k.g[0], k.g[1] = float(problem.g[0]), float(problem.g[1])
+    k.kb, k.b = float(problem.kb), float(problem.b)
+    for i in range(3):
+        k.csat[i] = float(problem.csat[i])
+    k.T0, k.T1, k.t_cool = float(problem.T0), float(problem.T1), float(problem.t_cool)
+    k.kappa, k.cfl = float(problem.kappa), float(problem.cfl)
+    return k
+
+
+def _buf(x, writable=False):
+    """(pointer, mem flag, keepalive) for a float64 contiguous torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                raise TypeError("expected a contiguous float64 tensor")
+            return ctypes.c_void_p(x.data_ptr()), (PBE_MEM_DEVICE if x.is_cuda else PBE_MEM_HOST), x
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.asarray(x)
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        if writable:
+            raise TypeError("expected a contiguous float64 array")
+        a = np.ascontiguousarray(a, dtype=np.float64)
+    return ctypes.c_void_p(a.ctypes.data), PBE_MEM_HOST, a
+
+
+class Grid:
+    """A PBE grid on the current CUDA device (thin wrapper over pbe_grid)."""
+
+    def __init__(self, ndim: int, ncells, lmax, stream=None):
+        self.lib = _lib.load()
+        self.ndim = int(ndim)
+        self.ncells = tuple(int(v) for v in ncells)
+        nc = (ctypes.c_int64 * 2)(*(list(self.ncells) + [1] * (2 - len(self.ncells))))
+        lm = (ctypes.c_double * 2)(*([float(v) for v in lmax] + [1.0] * (2 - len(lmax))))
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.pbe_create_grid(ctypes.byref(h), self.ndim, nc, lm))
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    @classmethod
+    def from_problem(cls, problem, stream=None, path: str = "plain"):
+        g = cls(problem.ndim, problem.ncells, problem.lmax, stream=stream)
+        g.set_kinetics(problem)
+        g.set_path(path)
+        return g
+
+    @property
+    def ncell(self) -> int:
+        return int(np.prod(self.ncells))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pbe_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        _lib.check(self.lib.pbe_set_stream(self.h, ctypes.c_void_p(int(handle))))
+
+    def set_path(self, path: str):
+        _lib.check(self.lib.pbe_set_path(self.h, _PATHS[path]))
+
+    def set_max_steps(self, n: int):
+        _lib.check(self.lib.pbe_set_max_steps(self.h, int(n)))
+
+    def set_kinetics(self, problem):
+        k = kinetics_struct(problem)
+        _lib.check(self.lib.pbe_set_kinetics(self.h, ctypes.byref(k)))
+
+    def set_state(self, n, C: float, t: float):
+        p, mem, keep = _buf(n)
+        if (keep.numel() if hasattr(keep, "numel") else keep.size) != self.ncell:
+            raise ValueError("state has the wrong number of cells")
+        _lib.check(self.lib.pbe_set_state(self.h, p, float(C), float(t), mem))
+
+    def get_state(self, out=None):
+        """Returns (n, C, t); n is written into ``out`` (tensor/array) or a new numpy array."""
+        if out is None:
+            out = np.zeros(self.ncells)
+        p, mem, keep = _buf(out, writable=True)
+        C, t = ctypes.c_double(), ctypes.c_double()
+        _lib.check(self.lib.pbe_get_state(self.h, p, ctypes.byref(C), ctypes.byref(t), mem))
+        return out, C.value, t.value
+
+    def step(self, t_limit: float) -> float:
+        dt = ctypes.c_double()
+        _lib.check(self.lib.pbe_step(self.h, float(t_limit), ctypes.byref(dt)))
+        return dt.value
+
+    def solve(self, t_out, out=None):
+        """March through the output times; returns (rows, steps)."""
+        t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+        if out is None:
+            out = np.zeros((len(t_out), ncols(self.ndim)))
+        p, mem, keep = _buf(out, writable=True)
+        steps = ctypes.c_int64()
+        _lib.check(self.lib.pbe_solve(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      len(t_out), p, mem, ctypes.byref(steps)))
+        return out, steps.value
+
+    def moments(self, out=None):
+        if out is None:
+            out = np.zeros(4 if self.ndim == 1 else 10)
+        p, mem, keep = _buf(out, writable=True)
+        _lib.check(self.lib.pbe_moments(self.h, p, mem))
+        return out

@@ -1,0 +1,365 @@
+// C ABI of the solver (include/pbe.h): argument checking, device buffers,
+// stream ordering and the solve loop.  All arithmetic runs in the kernels of
+// pbe_plain.cu / pbe_fused.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "pbe_internal.h"
+
+using pbe::Scal;
+
+static thread_local char g_err[512] = "";
+
+static pbe_status fail(pbe_status code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(PBE_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+namespace {
+// Makes the grid's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+cudaMemcpyKind kind_to_device(int mem) { return mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_from_device(int mem) { return mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+void free_grid_buffers(pbe_grid* g)
+{
+    if (g->plain_exec) cudaGraphExecDestroy(g->plain_exec);
+    cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom);
+    cudaFree(g->d_tout); cudaFree(g->d_rows);
+    cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage);
+}
+
+int ncol_of(const pbe_grid* g) { return g->geo.ndim == 1 ? 6 : 12; }
+
+pbe_status ensure_tout_capacity(pbe_grid* g, int n_out)
+{
+    if (n_out <= g->tout_cap) return PBE_OK;
+    int cap = g->tout_cap ? g->tout_cap : 64;
+    while (cap < n_out) cap *= 2;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    cudaFree(g->d_tout); cudaFree(g->d_rows);
+    g->d_tout = nullptr; g->d_rows = nullptr; g->tout_cap = 0;
+    if (g->plain_exec) { cudaGraphExecDestroy(g->plain_exec); g->plain_exec = nullptr; }
+    if (cudaMalloc(&g->d_tout, sizeof(double) * cap) != cudaSuccess ||
+        cudaMalloc(&g->d_rows, sizeof(double) * cap * 12) != cudaSuccess)
+        return fail(PBE_ENOMEM, "cudaMalloc of %d output rows failed", cap);
+    g->tout_cap = cap;
+    return PBE_OK;
+}
+
+// Graph of the plain loop: a conditional while node whose body is the two
+// stage kernels; the last block of stage 2 clears the condition when the
+// solve is done (all output times reached, an error, or the step budget).
+pbe_status build_plain_graph(pbe_grid* g)
+{
+    if (g->plain_exec || g->plain_graph_failed) return PBE_OK;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaStream_t saved = g->stream;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cudaGraphNode_t node;
+    cudaGraph_t body, captured;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        body = cp.conditional.phGraph_out[0];
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        g->stream = cap;
+        cudaError_t le = pbe::launch_plain_step(g, true, h);
+        g->stream = saved;
+        e = cudaStreamEndCapture(cap, &captured);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->plain_exec, graph, 0);
+    if (cap) cudaStreamDestroy(cap);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->plain_exec = nullptr;
+        g->plain_graph_failed = true;  // the host loop below stays available
+        cudaGetLastError();
+    }
+    return PBE_OK;
+}
+
+pbe_status finish_call(pbe_grid* g)
+{
+    CUDA_TRY(cudaMemcpyAsync(g->h_S, g->d_S, sizeof(Scal), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->C_host = g->h_S->C;
+    g->t_host = g->h_S->t;
+    int st = g->h_S->status;
+    if (st == PBE_ENONFINITE) return fail(st, "non-finite value in the state or kinetics at t = %g", g->h_S->t);
+    if (st == PBE_ETIMEOUT) return fail(st, "step budget of %lld steps exhausted at t = %g", g->h_S->max_steps, g->h_S->t);
+    if (st != PBE_OK) return fail(st, "device reported status %d", st);
+    return PBE_OK;
+}
+
+pbe_status run_solve(pbe_grid* g, int n_out)
+{
+    CUDA_TRY(pbe::launch_prologue(g, n_out, g->max_steps, nullptr));
+    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g)) {
+        CUDA_TRY(pbe::launch_fused_solve(g, n_out));
+        return PBE_OK;
+    }
+    build_plain_graph(g);
+    if (g->plain_exec) {
+        CUDA_TRY(cudaGraphLaunch(g->plain_exec, g->stream));
+        return PBE_OK;
+    }
+    // host loop over chunks of steps; stage kernels return at once when done
+    for (long long done_steps = 0;;) {
+        int chunk = 16;
+        for (int k = 0; k < chunk; ++k) CUDA_TRY(pbe::launch_plain_step(g, false, 0));
+        done_steps += chunk;
+        CUDA_TRY(cudaMemcpyAsync(g->h_S, g->d_S, sizeof(Scal), cudaMemcpyDeviceToHost, g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        if (g->h_S->done) break;
+        if (done_steps > g->max_steps + chunk) return fail(PBE_ETIMEOUT, "solve did not finish");
+    }
+    return PBE_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* pbe_last_error(void) { return g_err; }
+
+int pbe_version(void) { return 100; }
+
+pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, const double* lmax)
+{
+    if (!out || !ncells || !lmax) return fail(PBE_EINVAL, "null argument");
+    *out = nullptr;
+    if (ndim != 1 && ndim != 2) return fail(PBE_EINVAL, "ndim must be 1 or 2 (got %d)", ndim);
+    for (int d = 0; d < ndim; ++d) {
+        if (ncells[d] < 1 || ncells[d] > (1LL << 20))
+            return fail(PBE_EINVAL, "ncells[%d] = %lld out of range [1, 2^20]", d, (long long)ncells[d]);
+        if (!(lmax[d] > 0.0) || !std::isfinite(lmax[d]))
+            return fail(PBE_EINVAL, "lmax[%d] must be positive and finite", d);
+    }
+    long long nc = ncells[0] * (ndim == 2 ? ncells[1] : 1);
+    if (nc > (1LL << 31)) return fail(PBE_EINVAL, "grid of %lld cells is too large", nc);
+    pbe_grid* g = new pbe_grid();
+    memset((void*)g, 0, sizeof(*g));
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return fail(PBE_ECUDA, "no CUDA device available");
+    }
+    g->geo.ndim = ndim;
+    g->geo.N1 = (int)ncells[0];
+    g->geo.N2 = ndim == 2 ? (int)ncells[1] : 1;
+    g->geo.d1 = lmax[0] / (double)ncells[0];
+    g->geo.d2 = ndim == 2 ? lmax[1] / (double)ncells[1] : 1.0;
+    g->ncell = (size_t)nc;
+    g->path = PBE_PATH_PLAIN;
+    g->max_steps = 1000000;
+    g->max_blocks = pbe::plain_max_blocks(g->geo);
+    if (g->max_blocks < 1024) g->max_blocks = 1024;
+    bool ok = cudaMalloc(&g->d_n, sizeof(double) * nc) == cudaSuccess &&
+              cudaMalloc(&g->d_n1, sizeof(double) * nc) == cudaSuccess &&
+              cudaMalloc(&g->d_S, sizeof(Scal)) == cudaSuccess &&
+              cudaMalloc(&g->d_part, sizeof(double) * pbe::kMaxMom * g->max_blocks) == cudaSuccess &&
+              cudaMalloc(&g->d_mom, sizeof(double) * pbe::kMaxMom) == cudaSuccess &&
+              cudaMallocHost(&g->h_S, sizeof(Scal)) == cudaSuccess &&
+              cudaMallocHost(&g->h_stage, sizeof(double) * 64) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_grid_buffers(g);
+        delete g;
+        return fail(PBE_ENOMEM, "allocation of grid buffers failed");
+    }
+    if (cudaMemset(g->d_S, 0, sizeof(Scal)) != cudaSuccess ||
+        cudaMemset(g->d_n, 0, sizeof(double) * nc) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        free_grid_buffers(g);
+        delete g;
+        return fail(PBE_ECUDA, "initialising grid buffers failed");
+    }
+    *out = g;
+    return PBE_OK;
+}
+
+pbe_status pbe_destroy_grid(pbe_grid* g)
+{
+    if (!g) return PBE_OK;
+    DeviceGuard dg(g->device);
+    cudaStreamSynchronize(g->stream);
+    free_grid_buffers(g);
+    delete g;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_stream(pbe_grid* g, void* stream)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    g->stream = (cudaStream_t)stream;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_path(pbe_grid* g, int path)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (path != PBE_PATH_PLAIN && path != PBE_PATH_FUSED) return fail(PBE_EINVAL, "unknown path %d", path);
+    g->path = path;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_max_steps(pbe_grid* g, int64_t max_steps)
+{
+    if (!g || max_steps < 1) return fail(PBE_EINVAL, "max_steps must be >= 1");
+    g->max_steps = max_steps;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
+{
+    if (!g || !k) return fail(PBE_EINVAL, "null argument");
+    if (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED)
+        return fail(PBE_EINVAL, "unknown kinetics kind %d", k->kind);
+    if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
+    if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
+    const double vals[] = {k->kg[0], k->kg[1], k->g[0], k->g[1], k->kb, k->b, k->csat[0], k->csat[1],
+                           k->csat[2], k->T0, k->T1, k->t_cool, k->kappa, k->cfl};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(PBE_EINVAL, "non-finite kinetic parameter");
+    if (k->kg[0] < 0 || k->kg[1] < 0 || k->kb < 0) return fail(PBE_EINVAL, "negative rate prefactor");
+    pbe::Kin K;
+    K.kind = k->kind;
+    K.ndim = g->geo.ndim;
+    K.kg1 = k->kg[0]; K.g1 = k->g[0]; K.kg2 = k->kg[1]; K.g2 = k->g[1]; K.kb = k->kb; K.b = k->b;
+    K.cs0 = k->csat[0]; K.cs1 = k->csat[1]; K.cs2 = k->csat[2];
+    K.T0 = k->T0; K.T1 = k->T1; K.t_cool = k->t_cool; K.kappa = k->kappa; K.cfl = k->cfl;
+    g->kin = K;
+    g->has_kin = true;
+    if (g->plain_exec) {  // kinetics are baked into the graph's kernel arguments
+        cudaGraphExecDestroy(g->plain_exec);
+        g->plain_exec = nullptr;
+    }
+    return PBE_OK;
+}
+
+pbe_status pbe_set_state(pbe_grid* g, const double* n, double C, double t, int mem)
+{
+    if (!g || !n) return fail(PBE_EINVAL, "null argument");
+    if (mem != PBE_MEM_HOST && mem != PBE_MEM_DEVICE) return fail(PBE_EINVAL, "bad mem flag");
+    if (!std::isfinite(C) || !std::isfinite(t)) return fail(PBE_EINVAL, "non-finite C or t");
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
+    CUDA_TRY(cudaMemcpyAsync(g->d_n, n, sizeof(double) * g->ncell, kind_to_device(mem), g->stream));
+    CUDA_TRY(pbe::launch_set_scalars(g, C, t));
+    g->C_host = C;
+    g->t_host = t;
+    g->has_state = true;
+    return PBE_OK;
+}
+
+pbe_status pbe_get_state(pbe_grid* g, double* n, double* C, double* t, int mem)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (!g->has_state) return fail(PBE_ESTATE, "no state set");
+    DeviceGuard dg(g->device);
+    if (n) CUDA_TRY(cudaMemcpyAsync(n, g->d_n, sizeof(double) * g->ncell, kind_from_device(mem), g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->h_S, g->d_S, sizeof(Scal), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (C) *C = g->h_S->C;
+    if (t) *t = g->h_S->t;
+    return PBE_OK;
+}
+
+pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, int mem, int64_t* steps)
+{
+    if (!g || !t_out || !rows) return fail(PBE_EINVAL, "null argument");
+    if (n_out < 1) return fail(PBE_EINVAL, "n_out must be >= 1");
+    if (mem != PBE_MEM_HOST && mem != PBE_MEM_DEVICE) return fail(PBE_EINVAL, "bad mem flag");
+    if (!g->has_kin || !g->has_state) return fail(PBE_ESTATE, "set kinetics and state before solving");
+    if (!std::isfinite(t_out[0]) || t_out[0] < g->t_host)
+        return fail(PBE_EINVAL, "t_out[0] = %g precedes the current time %g", t_out[0], g->t_host);
+    for (int j = 1; j < n_out; ++j)
+        if (!(t_out[j] > t_out[j - 1]) || !std::isfinite(t_out[j]))
+            return fail(PBE_EINVAL, "t_out must be strictly increasing and finite (index %d)", j);
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
+    pbe_status st = ensure_tout_capacity(g, n_out);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(g->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, g->stream));
+    st = run_solve(g, n_out);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(rows, g->d_rows, sizeof(double) * n_out * ncol_of(g), kind_from_device(mem), g->stream));
+    st = finish_call(g);
+    if (steps) *steps = g->h_S->steps;
+    return st;
+}
+
+pbe_status pbe_step(pbe_grid* g, double t_limit, double* dt_taken)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (!g->has_kin || !g->has_state) return fail(PBE_ESTATE, "set kinetics and state before stepping");
+    if (!(t_limit > g->t_host) || !std::isfinite(t_limit))
+        return fail(PBE_EINVAL, "t_limit = %g must exceed the current time %g", t_limit, g->t_host);
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
+    pbe_status st = ensure_tout_capacity(g, 1);
+    if (st) return st;
+    g->h_stage[0] = t_limit;
+    CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_stage, sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(pbe::launch_prologue(g, 1, 1, nullptr));
+    CUDA_TRY(pbe::launch_plain_step(g, false, 0));
+    st = finish_call(g);
+    if (dt_taken) *dt_taken = g->h_S->last_dt;
+    if (st == PBE_ETIMEOUT) st = PBE_OK;  // the one-step budget is the point of this call
+    return st;
+}
+
+pbe_status pbe_moments(pbe_grid* g, double* mu, int mem)
+{
+    if (!g || !mu) return fail(PBE_EINVAL, "null argument");
+    if (!g->has_state) return fail(PBE_ESTATE, "no state set");
+    DeviceGuard dg(g->device);
+    CUDA_TRY(pbe::launch_prologue(g, 0, 0, g->d_mom));
+    int nm = g->geo.ndim == 1 ? 4 : 10;
+    CUDA_TRY(cudaMemcpyAsync(mu, g->d_mom, sizeof(double) * nm, kind_from_device(mem), g->stream));
+    if (mem == PBE_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return PBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Host-side state of a grid and the launchers of each execution path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pbe.h"
+#include "pbe_device.cuh"
+
+struct pbe_grid {
+    int device;
+    pbe::Geom geo;
+    pbe::Kin kin;
+    bool has_kin, has_state;
+    int path;
+    cudaStream_t stream;
+    long long max_steps;
+    size_t ncell;
+    double* d_n;        // state n
+    double* d_n1;       // stage-1 buffer
+    pbe::Scal* d_S;     // scalars
+    double* d_part;     // block partials [max_blocks][kMaxMom]
+    double* d_mom;      // moments read-out (kMaxMom doubles)
+    int max_blocks;
+    double* d_tout;     // output times (capacity tout_cap)
+    double* d_rows;     // output rows (capacity tout_cap rows of 12)
+    int tout_cap;
+    pbe::Scal* h_S;     // pinned copy of the scalars
+    double* h_stage;    // pinned staging for small host<->device copies (64 doubles)
+    // plain-path graph: prologue + while-loop over the two stage kernels
+    cudaGraphExec_t plain_exec;
+    bool plain_graph_failed;
+    double C_host, t_host;  // host mirror of the scalar state after the last synchronizing call
+};
+
+namespace pbe {
+
+// number of block partial slots the plain kernels of this grid use
+int plain_max_blocks(const Geom& g);
+
+// Plain path (pbe_plain.cu)
+cudaError_t launch_prologue(pbe_grid* g, int n_out, long long max_steps, double* mom_out);
+cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h);
+cudaError_t launch_set_scalars(pbe_grid* g, double C, double t);
+
+// Fused path (pbe_fused.cu)
+cudaError_t launch_fused_solve(pbe_grid* g, int n_out);
+bool fused_supported(const pbe_grid* g);
+
+}  // namespace pbe

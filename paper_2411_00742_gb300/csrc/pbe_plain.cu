@@ -1,0 +1,298 @@
+// Plain path: one kernel per SSP-RK2 stage.  Each kernel stages a tile of
+// the distribution with its 2-cell upwind / 1-cell downwind halo in shared
+// memory, computes every face value once, updates its cells, and reduces
+// the crystal-volume moment; the last block to finish closes the solute
+// balance (Eq. 4) and evaluates the kinetics of the next stage on the
+// device, so no scalar ever travels to the host between stages.
+#include "pbe_internal.h"
+
+namespace pbe {
+
+constexpr int kNT = 256;      // threads per block
+constexpr int kT1 = 1024;     // 1-D tile (cells per block)
+constexpr int kTI = 16;       // 2-D tile rows (L1)
+constexpr int kTJ = 32;       // 2-D tile columns (L2, contiguous)
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+int plain_max_blocks(const Geom& g)
+{
+    if (g.ndim == 1) return cdiv(g.N1, kT1);
+    return cdiv(g.N1, kTI) * cdiv(g.N2, kTJ);
+}
+
+__global__ void k_set_scalars(Scal* S, double C, double t)
+{
+    S->C = C;
+    S->t = t;
+    S->V0 = 0.0;
+    S->steps = 0;
+    S->done = 1;
+    S->status = 0;
+    S->out_idx = 0;
+    S->n_out = 0;
+    S->counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// moments of the current state; prologue of a solve (or plain read-out)
+// ---------------------------------------------------------------------------
+template <int NDIM>
+__global__ void __launch_bounds__(kNT) k_prologue(const double* __restrict__ n, Scal* S, Kin K, Geom g,
+                                                  double* part, const double* t_out, double* rows,
+                                                  int n_out, long long max_steps, double* mom_out)
+{
+    constexpr int NM = NDIM == 1 ? 4 : 10;
+    __shared__ double sh[kNT / 32 * NM];
+    __shared__ int flag;
+    double m[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) m[k] = 0.0;
+    const int nb = gridDim.x;
+    const long long ncell = (long long)g.N1 * g.N2;
+    for (long long c = (long long)blockIdx.x * kNT + threadIdx.x; c < ncell; c += (long long)nb * kNT) {
+        if (NDIM == 1) {
+            double x = (c + 0.5) * g.d1;
+            double v = n[c] * g.d1;
+            m[0] += v; m[1] += x * v; m[2] += x * x * v; m[3] += x * x * x * v;
+        } else {
+            int i = (int)(c / g.N2), j = (int)(c % g.N2);
+            double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
+            double v = n[c] * g.d1 * g.d2;
+            double x1v = x1 * v, x2v = x2 * v;
+            m[0] += v; m[1] += x1v; m[2] += x2v;
+            m[3] += x1 * x1v; m[4] += x1 * x2v; m[5] += x2 * x2v;
+            m[6] += x1 * x1 * x1v; m[7] += x1 * x1 * x2v; m[8] += x1 * x2 * x2v; m[9] += x2 * x2 * x2v;
+        }
+    }
+    block_sum<kNT, NM>(m, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NM; ++k) part[(size_t)blockIdx.x * kMaxMom + k] = m[k];
+    if (!last_block(&S->counter, nb, &flag)) return;
+    reduce_partials<kNT, NM>(part, nb, m, sh);
+    if (threadIdx.x != 0) return;
+    S->counter = 0u;
+    if (mom_out) {  // read-out only
+        for (int k = 0; k < NM; ++k) mom_out[k] = m[k];
+        return;
+    }
+    const int vidx = NDIM == 1 ? 3 : 8;
+    S->V0 = m[vidx];
+    S->steps = 0;
+    S->status = 0;
+    S->done = 0;
+    S->out_idx = 0;
+    S->n_out = n_out;
+    S->max_steps = max_steps;
+    bool finite = true;
+    for (int k = 0; k < NM; ++k) finite = finite && isfinite(m[k]);
+    if (!finite || !isfinite(S->C) || !isfinite(S->t)) {
+        S->status = PBE_ENONFINITE;
+        S->done = 1;
+        return;
+    }
+    while (S->out_idx < n_out && t_out[S->out_idx] == S->t) {
+        double* row = rows + (size_t)S->out_idx * (NM + 2);
+        row[0] = S->t;
+        for (int k = 0; k < NM; ++k) row[1 + k] = m[k];
+        row[NM + 1] = S->C;
+        S->out_idx += 1;
+    }
+    if (S->out_idx >= n_out) S->done = 1;
+    else prepare_step(S, K, g, t_out);
+}
+
+// ---------------------------------------------------------------------------
+// 1-D stage kernel
+//   STAGE 1: out = in + dt L(in; G_a, B_a)                 (in = n,  out = n1)
+//   STAGE 2: out = old/2 + (in + dt L(in; G_b, B_b))/2     (in = n1, out = old = n)
+// ---------------------------------------------------------------------------
+template <int STAGE>
+__global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, const double* old, double* out,
+                                                 Scal* S, Kin K, Geom g, double* part, const double* t_out,
+                                                 double* rows, int use_cond, cudaGraphConditionalHandle hcond)
+{
+    __shared__ double tile[kT1 + 3];
+    __shared__ double h[kT1 + 1];
+    __shared__ double sh[kNT / 32 * 4];
+    __shared__ int flag;
+    if (S->done) {
+        if (STAGE == 2 && use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hcond, 0);
+        return;
+    }
+    const int N = g.N1;
+    const int i0 = blockIdx.x * kT1;
+    const double dt = S->dt;
+    const double G = STAGE == 1 ? S->G1a : S->G1b;
+    const double B = STAGE == 1 ? S->Ba : S->Bb;
+    const bool moms = STAGE == 2 && S->clipped;
+    const double cG = G * dt / g.d1;
+    for (int k = threadIdx.x; k < kT1 + 3; k += kNT) {
+        int gi = i0 - 2 + k;
+        tile[k] = (gi >= 0 && gi < N) ? in[gi] : 0.0;
+    }
+    __syncthreads();
+    // face f (0..T) lies between cells i0+f-1 (upwind) and i0+f
+    for (int f = threadIdx.x; f <= kT1; f += kNT) {
+        double up = tile[f + 1];
+        h[f] = up + half_psi(up - tile[f], tile[f + 2] - up);
+    }
+    __syncthreads();
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = threadIdx.x; c < kT1; c += kNT) {
+        int i = i0 + c;
+        if (i >= N) break;
+        double v = tile[c + 2] + cG * (h[c] - h[c + 1]);
+        if (i == 0) v += dt * B / g.d1;
+        if (STAGE == 2) v = 0.5 * old[i] + 0.5 * v;
+        out[i] = v;
+        double x = (i + 0.5) * g.d1;
+        double w = v * g.d1;
+        if (moms) { m[0] += w; m[1] += x * w; m[2] += x * x * w; }
+        m[3] += x * x * x * w;
+    }
+    block_sum<kNT, 4>(m, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) part[(size_t)blockIdx.x * kMaxMom + k] = m[k];
+    if (!last_block(&S->counter, gridDim.x, &flag)) return;
+    reduce_partials<kNT, 4>(part, gridDim.x, m, sh);
+    if (threadIdx.x != 0) return;
+    S->counter = 0u;
+    if (STAGE == 1) {
+        finish_stage1(S, K, m[3]);
+    } else {
+        finish_stage2(S, K, g, t_out, rows, m, 4, 3);
+        if (use_cond) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D stage kernel: tile kTI x kTJ cells, both directions at once (unsplit)
+// ---------------------------------------------------------------------------
+template <int STAGE>
+__global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, const double* old, double* out,
+                                                 Scal* S, Kin K, Geom g, double* part, const double* t_out,
+                                                 double* rows, int use_cond, cudaGraphConditionalHandle hcond)
+{
+    constexpr int W = kTJ + 3;
+    __shared__ double tile[(kTI + 3) * W];
+    __shared__ double h1[(kTI + 1) * kTJ];   // faces along L1: local face f between rows f-1 and f
+    __shared__ double h2[kTI * (kTJ + 1)];   // faces along L2
+    __shared__ double sh[kNT / 32 * 10];
+    __shared__ int flag;
+    if (S->done) {
+        if (STAGE == 2 && use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+            cudaGraphSetConditional(hcond, 0);
+        return;
+    }
+    const int N1 = g.N1, N2 = g.N2;
+    const int i0 = blockIdx.y * kTI, j0 = blockIdx.x * kTJ;
+    const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const double dt = S->dt;
+    const double G1 = STAGE == 1 ? S->G1a : S->G1b;
+    const double G2 = STAGE == 1 ? S->G2a : S->G2b;
+    const double B = STAGE == 1 ? S->Ba : S->Bb;
+    const bool moms = STAGE == 2 && S->clipped;
+    const double c1 = G1 * dt / g.d1, c2 = G2 * dt / g.d2;
+    for (int k = threadIdx.x; k < (kTI + 3) * W; k += kNT) {
+        int r = k / W, c = k - r * W;
+        int gi = i0 - 2 + r, gj = j0 - 2 + c;
+        tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? in[(size_t)gi * N2 + gj] : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < (kTI + 1) * kTJ; k += kNT) {
+        int f = k / kTJ, c = k - f * kTJ;
+        double nm2 = tile[f * W + c + 2], up = tile[(f + 1) * W + c + 2], dn = tile[(f + 2) * W + c + 2];
+        h1[k] = up + half_psi(up - nm2, dn - up);
+    }
+    for (int k = threadIdx.x; k < kTI * (kTJ + 1); k += kNT) {
+        int r = k / (kTJ + 1), f = k - r * (kTJ + 1);
+        const double* row = tile + (r + 2) * W;
+        double nm2 = row[f], up = row[f + 1], dn = row[f + 2];
+        h2[k] = up + half_psi(up - nm2, dn - up);
+    }
+    __syncthreads();
+    double m[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) m[k] = 0.0;
+    const double area = g.d1 * g.d2;
+    for (int k = threadIdx.x; k < kTI * kTJ; k += kNT) {
+        int r = k / kTJ, c = k - r * kTJ;
+        int i = i0 + r, j = j0 + c;
+        if (i >= N1 || j >= N2) continue;
+        double v = tile[(r + 2) * W + c + 2] + c1 * (h1[r * kTJ + c] - h1[(r + 1) * kTJ + c]) +
+                   c2 * (h2[r * (kTJ + 1) + c] - h2[r * (kTJ + 1) + c + 1]);
+        if (i == 0 && j == 0) v += dt * B / area;
+        size_t gidx = (size_t)i * N2 + j;
+        if (STAGE == 2) v = 0.5 * old[gidx] + 0.5 * v;
+        out[gidx] = v;
+        double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
+        double w = v * area;
+        double x1w = x1 * w, x2w = x2 * w;
+        m[8] += x1 * x2 * x2w;
+        if (moms) {
+            m[0] += w; m[1] += x1w; m[2] += x2w;
+            m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
+            m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
+        }
+    }
+    block_sum<kNT, 10>(m, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 10; ++k) part[(size_t)bid * kMaxMom + k] = m[k];
+    if (!last_block(&S->counter, nb, &flag)) return;
+    reduce_partials<kNT, 10>(part, nb, m, sh);
+    if (threadIdx.x != 0) return;
+    S->counter = 0u;
+    if (STAGE == 1) {
+        finish_stage1(S, K, m[8]);
+    } else {
+        finish_stage2(S, K, g, t_out, rows, m, 10, 8);
+        if (use_cond) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_set_scalars(pbe_grid* g, double C, double t)
+{
+    k_set_scalars<<<1, 1, 0, g->stream>>>(g->d_S, C, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(pbe_grid* g, int n_out, long long max_steps, double* mom_out)
+{
+    long long ncell = (long long)g->geo.N1 * g->geo.N2;
+    int nb = cdiv(ncell, kNT);
+    if (nb > g->max_blocks) nb = g->max_blocks;
+    if (nb < 1) nb = 1;
+    if (g->geo.ndim == 1)
+        k_prologue<1><<<nb, kNT, 0, g->stream>>>(g->d_n, g->d_S, g->kin, g->geo, g->d_part, g->d_tout,
+                                                 g->d_rows, n_out, max_steps, mom_out);
+    else
+        k_prologue<2><<<nb, kNT, 0, g->stream>>>(g->d_n, g->d_S, g->kin, g->geo, g->d_part, g->d_tout,
+                                                 g->d_rows, n_out, max_steps, mom_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h)
+{
+    const Geom& geo = g->geo;
+    int uc = use_cond ? 1 : 0;
+    if (geo.ndim == 1) {
+        int nb = cdiv(geo.N1, kT1);
+        k_stage1d<1><<<nb, kNT, 0, g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part,
+                                                g->d_tout, g->d_rows, uc, h);
+        k_stage1d<2><<<nb, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
+                                                g->d_tout, g->d_rows, uc, h);
+    } else {
+        dim3 grid(cdiv(geo.N2, kTJ), cdiv(geo.N1, kTI));
+        k_stage2d<1><<<grid, kNT, 0, g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part,
+                                                  g->d_tout, g->d_rows, uc, h);
+        k_stage2d<2><<<grid, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
+                                                  g->d_tout, g->d_rows, uc, h);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pbe

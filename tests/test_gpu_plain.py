@@ -1,0 +1,164 @@
+"""Parity of the plain FP64 CUDA path with the CPU oracle.
+
+Moments mu and concentration C within 1e-10 relative at every output time,
+the distribution within 1e-9 * max(n) in L-inf, the same step count."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import pbe_inputs as pi
+from gpu_helpers import REL_ROWS, assert_n_close, assert_rows_close, compare_instance, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+
+def test_1d_config_every_output_time():
+    compare_instance(pi.config_1d(200))
+
+
+def test_1d_config_host_buffers():
+    compare_instance(pi.config_1d(200), device_buffers=False)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 101, 1023, 1024, 1025, 1999, 2000, 5000])
+def test_1d_ragged_sizes(N):
+    compare_instance(pi.config_1d(N))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 17), (23, 1), (16, 32), (37, 53), (64, 64), (100, 33)])
+def test_2d_ragged_sizes(shape):
+    compare_instance(pi.config_2d(*shape))
+
+
+def test_2d_config_full_size():
+    compare_instance(pi.config_2d(256))
+
+
+def _state_at_every_output(inst):
+    import paper_2411_00742_gb300 as P
+    g = P.Grid.from_problem(inst.problem)
+    g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+    n, C, t = np.array(inst.n0), inst.C0, inst.t0
+    for tk in inst.t_out[1:]:
+        rows, _ = g.solve([tk])
+        ng, Cg, tg = g.get_state()
+        r = oracle.solve(inst.problem, n, C, t, [tk])
+        n, C, t = r["n"], r["C"], r["t"]
+        assert tg == pytest.approx(t, rel=1e-12)
+        assert_n_close(ng, n)
+        assert abs(Cg - C) <= REL_ROWS * abs(C)
+        assert_rows_close(rows, r["rows"])
+    g.close()
+
+
+def test_1d_state_at_every_output_time():
+    _state_at_every_output(pi.config_1d(200))
+
+
+def test_2d_state_at_every_output_time():
+    _state_at_every_output(pi.config_2d(48, 40))
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_single_step_matches_oracle(ndim):
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_1d(300) if ndim == 1 else pi.config_2d(40, 24)
+    g = P.Grid.from_problem(inst.problem)
+    n, C, t = np.array(inst.n0), inst.C0, 0.0
+    g.set_state(n, C, t)
+    for t_lim in [60.0, 120.0, 1000.0, 1500.0, 4000.0]:
+        dt = g.step(t_lim)
+        n, info = oracle.step(inst.problem, n, C, t, t_lim)
+        C, t = info["C"], info["t"]
+        ng, Cg, tg = g.get_state()
+        assert dt == pytest.approx(info["dt"], rel=1e-12)
+        assert tg == pytest.approx(t, rel=1e-12)
+        assert_n_close(ng, n)
+        assert abs(Cg - C) <= REL_ROWS * abs(C)
+    g.close()
+
+
+def test_moments_readout():
+    import paper_2411_00742_gb300 as P
+    for inst in (pi.config_1d(777), pi.config_2d(33, 65)):
+        g = P.Grid.from_problem(inst.problem)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        mu = g.moments()
+        want = oracle.moments(inst.problem, inst.n0)
+        np.testing.assert_allclose(mu, want, rtol=1e-12)
+        g.close()
+
+
+def test_deterministic_bitwise():
+    a = gpu_solve(pi.config_2d(96))
+    b = gpu_solve(pi.config_2d(96))
+    assert np.array_equal(a["rows"], b["rows"]) and np.array_equal(a["n"], b["n"])
+
+
+def test_fixed_growth_translation():
+    p = pi.Problem(ndim=1, ncells=(800,), lmax=(1000.0,), kg=(0.5, 0.0), kb=0.0, cfl=0.45,
+                   fixed_kinetics=True)
+    n0 = pi.gaussian_seed_1d(800, 1000.0, 300.0, 30.0, 1e6)
+    compare_instance(pi.Instance(p, n0, 0.2, 0.0, np.array([0.0, 100.0, 400.0])))
+    p2 = pi.Problem(ndim=2, ncells=(70, 90), lmax=(500.0, 500.0), kg=(0.3, 0.2), kb=5.0, cfl=0.4,
+                    fixed_kinetics=True)
+    n2 = pi.gaussian_seed_2d(70, 90, 500.0, 500.0, (150.0, 100.0), (20.0, 15.0), -0.4, 1e6)
+    compare_instance(pi.Instance(p2, n2, 0.2, 0.0, np.array([50.0, 300.0])))
+
+
+def test_empty_seed_nucleation_only():
+    inst = pi.config_1d(200)
+    inst.n0 = np.zeros(200)
+    compare_instance(inst)
+    inst2 = pi.config_2d(40)
+    inst2.n0 = np.zeros((40, 40))
+    compare_instance(inst2)
+
+
+def test_no_supersaturation_no_change():
+    inst = pi.config_1d(200)
+    p = dataclasses.replace(inst.problem, T1=40.0)   # S stays 1: nothing happens
+    inst = pi.Instance(p, inst.n0, inst.C0, 0.0, inst.t_out)
+    got, _ = compare_instance(inst)
+    assert np.array_equal(got["n"], inst.n0)
+
+
+def test_nonfinite_state_reported():
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_1d(200)
+    g = P.Grid.from_problem(inst.problem)
+    n = inst.n0.copy()
+    n[50] = np.nan
+    g.set_state(n, inst.C0, 0.0)
+    with pytest.raises(P.PbeError) as e:
+        g.solve(inst.t_out)
+    assert e.value.status == 4
+    g.close()
+
+
+def test_step_budget_reported():
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_1d(200)
+    g = P.Grid.from_problem(inst.problem)
+    g.set_max_steps(3)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    with pytest.raises(P.PbeError) as e:
+        g.solve(inst.t_out)
+    assert e.value.status == 5
+    _, _, t = g.get_state()
+    assert t == pytest.approx(180.0)
+    g.close()
+
+
+def test_bad_output_times_rejected():
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_1d(50)
+    g = P.Grid.from_problem(inst.problem)
+    g.set_state(inst.n0, inst.C0, 100.0)
+    with pytest.raises(P.PbeError):
+        g.solve([50.0, 200.0])
+    with pytest.raises(P.PbeError):
+        g.solve([200.0, 150.0])
+    g.close()
