@@ -54,7 +54,7 @@ cudaMemcpyKind kind_from_device(int mem) { return mem == PBE_MEM_DEVICE ? cudaMe
 void free_grid_buffers(pbe_grid* g)
 {
     if (g->plain_exec) cudaGraphExecDestroy(g->plain_exec);
-    cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom);
+    cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom); cudaFree(g->d_bar);
     cudaFree(g->d_tout); cudaFree(g->d_rows);
     cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage);
 }
@@ -200,6 +200,7 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
               cudaMalloc(&g->d_S, sizeof(Scal)) == cudaSuccess &&
               cudaMalloc(&g->d_part, sizeof(double) * pbe::kMaxMom * g->max_blocks) == cudaSuccess &&
               cudaMalloc(&g->d_mom, sizeof(double) * pbe::kMaxMom) == cudaSuccess &&
+              cudaMalloc(&g->d_bar, sizeof(unsigned int) * 2) == cudaSuccess &&
               cudaMallocHost(&g->h_S, sizeof(Scal)) == cudaSuccess &&
               cudaMallocHost(&g->h_stage, sizeof(double) * 64) == cudaSuccess;
     if (!ok) {

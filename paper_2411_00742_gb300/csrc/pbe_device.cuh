@@ -200,10 +200,12 @@ __device__ __forceinline__ void finish_stage2(Scal* S, const Kin& K, const Geom&
         return;
     }
     if (S->clipped) {
-        double* row = rows + (size_t)S->out_idx * (nmom + 2);
-        row[0] = S->t;
-        for (int k = 0; k < nmom; ++k) row[1 + k] = mom[k];
-        row[nmom + 1] = C;
+        if (rows) {  // rows == nullptr: a replica of the scalar chain that must not write
+            double* row = rows + (size_t)S->out_idx * (nmom + 2);
+            row[0] = S->t;
+            for (int k = 0; k < nmom; ++k) row[1 + k] = mom[k];
+            row[nmom + 1] = C;
+        }
         S->out_idx += 1;
     }
     if (S->out_idx >= S->n_out) {

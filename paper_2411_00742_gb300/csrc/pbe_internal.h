@@ -20,6 +20,7 @@ struct pbe_grid {
     pbe::Scal* d_S;     // scalars
     double* d_part;     // block partials [max_blocks][kMaxMom]
     double* d_mom;      // moments read-out (kMaxMom doubles)
+    unsigned int* d_bar; // device-wide barrier of the fused path (count, generation)
     int max_blocks;
     double* d_tout;     // output times (capacity tout_cap)
     double* d_rows;     // output rows (capacity tout_cap rows of 12)

@@ -5,6 +5,7 @@
 // balance (Eq. 4) and evaluates the kinetics of the next stage on the
 // device, so no scalar ever travels to the host between stages.
 #include "pbe_internal.h"
+#include "pbe_tiles.cuh"
 
 namespace pbe {
 
@@ -103,9 +104,9 @@ __global__ void __launch_bounds__(kNT) k_prologue(const double* __restrict__ n, 
 }
 
 // ---------------------------------------------------------------------------
-// 1-D stage kernel
-//   STAGE 1: out = in + dt L(in; G_a, B_a)                 (in = n,  out = n1)
-//   STAGE 2: out = old/2 + (in + dt L(in; G_b, B_b))/2     (in = n1, out = old = n)
+// stage kernels: one tile per block, the last block closes the stage
+//   STAGE 1: n1 = n + dt L(n; G_a, B_a)
+//   STAGE 2: n  = n/2 + (n1 + dt L(n1; G_b, B_b))/2   (in place)
 // ---------------------------------------------------------------------------
 template <int STAGE>
 __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, const double* old, double* out,
@@ -120,37 +121,9 @@ __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, 
         if (STAGE == 2 && use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hcond, 0);
         return;
     }
-    const int N = g.N1;
-    const int i0 = blockIdx.x * kT1;
-    const double dt = S->dt;
-    const double G = STAGE == 1 ? S->G1a : S->G1b;
-    const double B = STAGE == 1 ? S->Ba : S->Bb;
-    const bool moms = STAGE == 2 && S->clipped;
-    const double cG = G * dt / g.d1;
-    for (int k = threadIdx.x; k < kT1 + 3; k += kNT) {
-        int gi = i0 - 2 + k;
-        tile[k] = (gi >= 0 && gi < N) ? in[gi] : 0.0;
-    }
-    __syncthreads();
-    // face f (0..T) lies between cells i0+f-1 (upwind) and i0+f
-    for (int f = threadIdx.x; f <= kT1; f += kNT) {
-        double up = tile[f + 1];
-        h[f] = up + half_psi(up - tile[f], tile[f + 2] - up);
-    }
-    __syncthreads();
+    const StageCoef sc = stage_coef<STAGE>(*S, g);
     double m[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c = threadIdx.x; c < kT1; c += kNT) {
-        int i = i0 + c;
-        if (i >= N) break;
-        double v = tile[c + 2] + cG * (h[c] - h[c + 1]);
-        if (i == 0) v += dt * B / g.d1;
-        if (STAGE == 2) v = 0.5 * old[i] + 0.5 * v;
-        out[i] = v;
-        double x = (i + 0.5) * g.d1;
-        double w = v * g.d1;
-        if (moms) { m[0] += w; m[1] += x * w; m[2] += x * x * w; }
-        m[3] += x * x * x * w;
-    }
+    tile1d<STAGE, false, false, kT1, kNT>(in, old, out, blockIdx.x * kT1, g, sc, m, tile, h);
     block_sum<kNT, 4>(m, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < 4; ++k) part[(size_t)blockIdx.x * kMaxMom + k] = m[k];
@@ -166,18 +139,12 @@ __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, 
     }
 }
 
-// ---------------------------------------------------------------------------
-// 2-D stage kernel: tile kTI x kTJ cells, both directions at once (unsplit)
-// ---------------------------------------------------------------------------
 template <int STAGE>
 __global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, const double* old, double* out,
                                                  Scal* S, Kin K, Geom g, double* part, const double* t_out,
                                                  double* rows, int use_cond, cudaGraphConditionalHandle hcond)
 {
-    constexpr int W = kTJ + 3;
-    __shared__ double tile[(kTI + 3) * W];
-    __shared__ double h1[(kTI + 1) * kTJ];   // faces along L1: local face f between rows f-1 and f
-    __shared__ double h2[kTI * (kTJ + 1)];   // faces along L2
+    __shared__ Tile2DSmem<kTI, kTJ> ts;
     __shared__ double sh[kNT / 32 * 10];
     __shared__ int flag;
     if (S->done) {
@@ -185,57 +152,12 @@ __global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, 
             cudaGraphSetConditional(hcond, 0);
         return;
     }
-    const int N1 = g.N1, N2 = g.N2;
-    const int i0 = blockIdx.y * kTI, j0 = blockIdx.x * kTJ;
     const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-    const double dt = S->dt;
-    const double G1 = STAGE == 1 ? S->G1a : S->G1b;
-    const double G2 = STAGE == 1 ? S->G2a : S->G2b;
-    const double B = STAGE == 1 ? S->Ba : S->Bb;
-    const bool moms = STAGE == 2 && S->clipped;
-    const double c1 = G1 * dt / g.d1, c2 = G2 * dt / g.d2;
-    for (int k = threadIdx.x; k < (kTI + 3) * W; k += kNT) {
-        int r = k / W, c = k - r * W;
-        int gi = i0 - 2 + r, gj = j0 - 2 + c;
-        tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? in[(size_t)gi * N2 + gj] : 0.0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < (kTI + 1) * kTJ; k += kNT) {
-        int f = k / kTJ, c = k - f * kTJ;
-        double nm2 = tile[f * W + c + 2], up = tile[(f + 1) * W + c + 2], dn = tile[(f + 2) * W + c + 2];
-        h1[k] = up + half_psi(up - nm2, dn - up);
-    }
-    for (int k = threadIdx.x; k < kTI * (kTJ + 1); k += kNT) {
-        int r = k / (kTJ + 1), f = k - r * (kTJ + 1);
-        const double* row = tile + (r + 2) * W;
-        double nm2 = row[f], up = row[f + 1], dn = row[f + 2];
-        h2[k] = up + half_psi(up - nm2, dn - up);
-    }
-    __syncthreads();
+    const StageCoef sc = stage_coef<STAGE>(*S, g);
     double m[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) m[k] = 0.0;
-    const double area = g.d1 * g.d2;
-    for (int k = threadIdx.x; k < kTI * kTJ; k += kNT) {
-        int r = k / kTJ, c = k - r * kTJ;
-        int i = i0 + r, j = j0 + c;
-        if (i >= N1 || j >= N2) continue;
-        double v = tile[(r + 2) * W + c + 2] + c1 * (h1[r * kTJ + c] - h1[(r + 1) * kTJ + c]) +
-                   c2 * (h2[r * (kTJ + 1) + c] - h2[r * (kTJ + 1) + c + 1]);
-        if (i == 0 && j == 0) v += dt * B / area;
-        size_t gidx = (size_t)i * N2 + j;
-        if (STAGE == 2) v = 0.5 * old[gidx] + 0.5 * v;
-        out[gidx] = v;
-        double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
-        double w = v * area;
-        double x1w = x1 * w, x2w = x2 * w;
-        m[8] += x1 * x2 * x2w;
-        if (moms) {
-            m[0] += w; m[1] += x1w; m[2] += x2w;
-            m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
-            m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
-        }
-    }
+    tile2d<STAGE, false, false, kTI, kTJ, kNT>(in, old, out, blockIdx.y * kTI, blockIdx.x * kTJ, g, sc, m, ts);
     block_sum<kNT, 10>(m, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < 10; ++k) part[(size_t)bid * kMaxMom + k] = m[k];

@@ -1,0 +1,82 @@
+"""Parity of the fused persistent path (one cooperative launch per solve) with
+the CPU oracle, at the same tolerances as the plain path."""
+import numpy as np
+import pytest
+
+import oracle
+import pbe_inputs as pi
+from gpu_helpers import REL_ROWS, assert_n_close, assert_rows_close, compare_instance, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fused_1d_config():
+    compare_instance(pi.config_1d(200), path="fused")
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 1023, 1024, 1025, 3000, 70001])
+def test_fused_1d_ragged(N):
+    compare_instance(pi.config_1d(N), path="fused")
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 200), (37, 53), (64, 64), (129, 31)])
+def test_fused_2d_ragged(shape):
+    compare_instance(pi.config_2d(*shape), path="fused")
+
+
+def test_fused_2d_full_size():
+    compare_instance(pi.config_2d(256), path="fused")
+
+
+def test_fused_2d_larger_than_one_wave():
+    # more tiles than co-resident blocks: blocks loop over several tiles
+    compare_instance(pi.config_2d(600, 400), path="fused")
+
+
+def test_fused_state_at_every_output_time():
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(48, 40)
+    g = P.Grid.from_problem(inst.problem, path="fused")
+    g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+    n, C, t = np.array(inst.n0), inst.C0, inst.t0
+    for tk in inst.t_out[1:]:
+        rows, _ = g.solve([tk])
+        ng, Cg, tg = g.get_state()
+        r = oracle.solve(inst.problem, n, C, t, [tk])
+        n, C, t = r["n"], r["C"], r["t"]
+        assert_n_close(ng, n)
+        assert abs(Cg - C) <= REL_ROWS * abs(C)
+        assert_rows_close(rows, r["rows"])
+    g.close()
+
+
+def test_fused_matches_plain_closely():
+    a = gpu_solve(pi.config_2d(128), path="plain")
+    b = gpu_solve(pi.config_2d(128), path="fused")
+    assert a["steps"] == b["steps"]
+    np.testing.assert_allclose(b["rows"], a["rows"], rtol=1e-12)
+
+
+def test_fused_deterministic_bitwise():
+    a = gpu_solve(pi.config_2d(200), path="fused")
+    b = gpu_solve(pi.config_2d(200), path="fused")
+    assert np.array_equal(a["rows"], b["rows"]) and np.array_equal(a["n"], b["n"])
+
+
+def test_fused_step_budget_and_nonfinite():
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(64)
+    g = P.Grid.from_problem(inst.problem, path="fused")
+    g.set_max_steps(5)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    with pytest.raises(P.PbeError) as e:
+        g.solve(inst.t_out)
+    assert e.value.status == 5
+    g.set_max_steps(10 ** 6)
+    n = inst.n0.copy()
+    n[10, 10] = np.inf
+    g.set_state(n, inst.C0, 0.0)
+    with pytest.raises(P.PbeError) as e:
+        g.solve(inst.t_out)
+    assert e.value.status == 4
+    g.close()

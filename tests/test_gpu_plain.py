@@ -122,7 +122,9 @@ def test_no_supersaturation_no_change():
     p = dataclasses.replace(inst.problem, T1=40.0)   # S stays 1: nothing happens
     inst = pi.Instance(p, inst.n0, inst.C0, 0.0, inst.t_out)
     got, _ = compare_instance(inst)
-    assert np.array_equal(got["n"], inst.n0)
+    # unchanged up to the halving of odd subnormals in the tail (n/2 + n/2)
+    np.testing.assert_allclose(got["n"], inst.n0, rtol=0, atol=1e-300)
+    assert got["rows"][-1, 5] == inst.C0
 
 
 def test_nonfinite_state_reported():
