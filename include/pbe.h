@@ -126,6 +126,32 @@ pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
  * the solve with PBE_ETIMEOUT. */
 pbe_status pbe_set_max_steps(pbe_grid* g, int64_t max_steps);
 
+/* Solve a 1-D problem without allocating any memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * once running (a fixed-budget real-time loop, a host framework whose
+ * allocator owns all device memory, a process that already holds every byte
+ * it may use).  It does the work of pbe_create_grid + pbe_set_kinetics +
+ * pbe_set_state + pbe_solve on the plain path's arithmetic, with the caller's
+ * buffers for inputs and outputs and a fixed working array built into the
+ * library (about 0.56 MB of device memory per GPU that loads the library,
+ * held until the process exits).
+ *   k        kinetics (host memory)
+ *   ncells   1 <= ncells <= 65536 cells on [0, lmax]; larger grids: PBE_EINVAL
+ *   n        DEVICE memory, ncells doubles: initial distribution in, final out
+ *   C0, t0   initial concentration and time
+ *   t_out    HOST memory, 1 <= n_out <= 4096 increasing times, t_out[0] >= t0
+ *   rows     DEVICE memory, n_out rows of 6 doubles (t, mu0..mu3, C)
+ *   steps    optional (host) number of steps taken
+ *   stream   cudaStream_t the work is ordered on; the call synchronizes it
+ * The first call on each device looks up the working array's device address
+ * (make that first call before any stream capture).  All calls share the
+ * working array: calls that overlap on a GPU race and must be serialized by
+ * the caller.  It calls no cudaMalloc/cudaFree and no allocating library
+ * routine. */
+pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells, double lmax, double* n, double C0,
+                                double t0, const double* t_out, int n_out, double* rows, int64_t* steps,
+                                void* stream);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* pbe_last_error(void);
 

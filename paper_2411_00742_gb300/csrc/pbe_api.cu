@@ -22,6 +22,14 @@ static pbe_status fail(pbe_status code, const char* fmt, ...)
     return code;
 }
 
+// Lets other translation units of the library report an error through
+// pbe_last_error().
+void pbe_set_error_message(int code, const char* msg)
+{
+    (void)code;
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
 #define CUDA_TRY(call)                                                                       \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \
