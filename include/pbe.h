@@ -152,6 +152,56 @@ pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells, double lm
                                 double t0, const double* t_out, int n_out, double* rows, int64_t* steps,
                                 void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched 1-D solves: many independent instances of the 1-D problem, each
+ * with its own grid, kinetics, cooling profile, initial state and
+ * CFL-limited step count, advanced by one persistent launch (replayed as a
+ * CUDA graph) until every instance reaches the shared output times.  The
+ * arithmetic per instance is the 1-D step above (fused-path quotient).
+ * ------------------------------------------------------------------------ */
+typedef struct pbe_batch pbe_batch;
+
+typedef struct {
+    int64_t ncells;     /* 1 <= ncells <= 6144 cells on [0, lmax]           */
+    double lmax;
+    pbe_kinetics kin;   /* per-instance kinetics and scheme (ndim = 1)      */
+    double C0, t0;      /* initial concentration and time                   */
+} pbe_instance;
+
+/* Create a batch of `count` instances (host array).  Distributions are
+ * packed back to back in instance order: instance i occupies cells
+ * [offset[i], offset[i+1]) of the packed state (see pbe_batch_offsets).
+ * Errors: PBE_EINVAL (sizes, parameters), PBE_ENOMEM, PBE_ECUDA. */
+pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count);
+pbe_status pbe_batch_destroy(pbe_batch* b);
+pbe_status pbe_batch_set_stream(pbe_batch* b, void* cuda_stream);
+
+/* offsets[0..count] (host) of each instance in the packed state. */
+pbe_status pbe_batch_offsets(pbe_batch* b, int64_t* offsets);
+
+/* Load the packed distributions (offsets[count] doubles, `mem` memory) and
+ * reset every instance's C and t to its C0 and t0.  Synchronizes. */
+pbe_status pbe_batch_set_state(pbe_batch* b, const double* n_packed, int mem);
+
+/* Read back the packed state, per-instance C and t (any may be NULL). */
+pbe_status pbe_batch_get_state(pbe_batch* b, double* n_packed, double* C, double* t, int mem);
+
+/* Advance every instance through the shared increasing output times
+ * t_out[0..n_out) (host memory; t_out[0] >= every t0).  rows (`mem` memory)
+ * receives count * n_out rows of 6 doubles (t, mu0..mu3, C), instance-major.
+ * *total_steps (host, may be NULL) = steps summed over instances.
+ * Synchronizes.  Errors as pbe_solve, naming the first failing instance. */
+pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double* rows, int mem,
+                           int64_t* total_steps);
+
+/* Instances per block (1, 2, 4 or 8 warps, one instance per warp). */
+pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
+
+/* Time each admissible instances-per-block setting on this batch and these
+ * output times (the state is saved and restored around every trial), keep
+ * the fastest and return it in *chosen (may be NULL). */
+pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int* chosen);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* pbe_last_error(void);
 

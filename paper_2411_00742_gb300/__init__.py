@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (PBE_KINETICS_FIXED, PBE_KINETICS_POWER_LAW, PBE_MEM_DEVICE, PBE_MEM_HOST,
                    PBE_PATH_FUSED, PBE_PATH_PLAIN, PbeError, Kinetics)
 
-__all__ = ["Grid", "PbeError", "kinetics_struct", "ncols"]
+__all__ = ["Grid", "Batch", "PbeError", "kinetics_struct", "ncols"]
 
 _PATHS = {"plain": PBE_PATH_PLAIN, "fused": PBE_PATH_FUSED}
 
@@ -147,3 +147,85 @@ class Grid:
         p, mem, keep = _buf(out, writable=True)
         _lib.check(self.lib.pbe_moments(self.h, p, mem))
         return out
+
+
+class Batch:
+    """Many independent 1-D instances solved by one persistent launch
+    (thin wrapper over pbe_batch)."""
+
+    def __init__(self, problems, C0, t0=None, stream=None):
+        self.lib = _lib.load()
+        n = len(problems)
+        arr = (_lib.Instance * n)()
+        for i, p in enumerate(problems):
+            if p.ndim != 1:
+                raise ValueError("batched solves are 1-D")
+            arr[i].ncells = int(p.ncells[0])
+            arr[i].lmax = float(p.lmax[0])
+            arr[i].kin = kinetics_struct(p)
+            arr[i].C0 = float(C0[i])
+            arr[i].t0 = 0.0 if t0 is None else float(t0[i])
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.pbe_batch_create(ctypes.byref(h), arr, n))
+        self.h = h
+        self.count = n
+        off = (ctypes.c_int64 * (n + 1))()
+        _lib.check(self.lib.pbe_batch_offsets(self.h, off))
+        self.offsets = np.array(off[:], dtype=np.int64)
+        if stream is not None:
+            self.set_stream(stream)
+
+    @property
+    def total_cells(self) -> int:
+        return int(self.offsets[-1])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pbe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        _lib.check(self.lib.pbe_batch_set_stream(self.h, ctypes.c_void_p(int(handle))))
+
+    def pack(self, states):
+        return np.concatenate([np.ascontiguousarray(s, dtype=np.float64).ravel() for s in states])
+
+    def set_state(self, n_packed):
+        p, mem, keep = _buf(n_packed)
+        _lib.check(self.lib.pbe_batch_set_state(self.h, p, mem))
+
+    def get_state(self):
+        n = np.zeros(self.total_cells)
+        C = np.zeros(self.count)
+        t = np.zeros(self.count)
+        _lib.check(self.lib.pbe_batch_get_state(self.h, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(C.ctypes.data),
+                                                ctypes.c_void_p(t.ctypes.data), PBE_MEM_HOST))
+        return [n[self.offsets[i]:self.offsets[i + 1]] for i in range(self.count)], C, t
+
+    def set_config(self, warps_per_block: int):
+        _lib.check(self.lib.pbe_batch_set_config(self.h, int(warps_per_block)))
+
+    def autotune(self, t_out) -> int:
+        t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+        w = ctypes.c_int()
+        _lib.check(self.lib.pbe_batch_autotune(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               len(t_out), ctypes.byref(w)))
+        return w.value
+
+    def solve(self, t_out, out=None):
+        """Returns (rows[count, n_out, 6], total_steps)."""
+        t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+        if out is None:
+            out = np.zeros((self.count, len(t_out), 6))
+        p, mem, keep = _buf(out, writable=True)
+        steps = ctypes.c_int64()
+        _lib.check(self.lib.pbe_batch_solve(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            len(t_out), p, mem, ctypes.byref(steps)))
+        return out, steps.value

@@ -29,6 +29,11 @@ class Kinetics(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("cfl", ctypes.c_double)]
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("ncells", ctypes.c_int64), ("lmax", ctypes.c_double), ("kin", Kinetics),
+                ("C0", ctypes.c_double), ("t0", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -50,6 +55,15 @@ SIGNATURES = {
     "pbe_moments": [_P, _P, _I],
     "pbe_set_max_steps": [_P, _I64],
     "pbe_solve_1d_noalloc": [ctypes.POINTER(Kinetics), _I64, _D, _P, _D, _D, _PD, _I, _P, _PI64, _P],
+    "pbe_batch_create": [ctypes.POINTER(_P), ctypes.POINTER(Instance), _I],
+    "pbe_batch_destroy": [_P],
+    "pbe_batch_set_stream": [_P, _P],
+    "pbe_batch_offsets": [_P, _PI64],
+    "pbe_batch_set_state": [_P, _P, _I],
+    "pbe_batch_get_state": [_P, _P, _P, _P, _I],
+    "pbe_batch_solve": [_P, _PD, _I, _P, _I, _PI64],
+    "pbe_batch_set_config": [_P, _I],
+    "pbe_batch_autotune": [_P, _PD, _I, ctypes.POINTER(_I)],
     "pbe_last_error": [],
     "pbe_version": [],
 }

@@ -198,6 +198,8 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
     g->geo.N2 = ndim == 2 ? (int)ncells[1] : 1;
     g->geo.d1 = lmax[0] / (double)ncells[0];
     g->geo.d2 = ndim == 2 ? lmax[1] / (double)ncells[1] : 1.0;
+    g->geo.inv_d1 = 1.0 / g->geo.d1;
+    g->geo.inv_d2 = 1.0 / g->geo.d2;
     g->ncell = (size_t)nc;
     g->path = PBE_PATH_PLAIN;
     g->max_steps = 1000000;
@@ -278,6 +280,8 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     K.kg1 = k->kg[0]; K.g1 = k->g[0]; K.kg2 = k->kg[1]; K.g2 = k->g[1]; K.kb = k->kb; K.b = k->b;
     K.cs0 = k->csat[0]; K.cs1 = k->csat[1]; K.cs2 = k->csat[2];
     K.T0 = k->T0; K.T1 = k->T1; K.t_cool = k->t_cool; K.kappa = k->kappa; K.cfl = k->cfl;
+    K.lkg1 = std::log(K.kg1); K.lkg2 = std::log(K.kg2); K.lkb = std::log(K.kb);
+    K.inv_tcool = 1.0 / K.t_cool;
     g->kin = K;
     g->has_kin = true;
     if (g->plain_exec) {  // kinetics are baked into the graph's kernel arguments

@@ -17,12 +17,15 @@ struct Kin {
     int kind, ndim;
     double kg1, g1, kg2, g2, kb, b;
     double cs0, cs1, cs2, T0, T1, t_cool, kappa, cfl;
+    double lkg1, lkg2, lkb;   // natural logarithms of kg1, kg2, kb (-inf for 0)
+    double inv_tcool;         // 1 / t_cool
 };
 
 struct Geom {
     int ndim;
     int N1, N2;      // cells along L1 and L2 (N2 = 1 in 1-D)
     double d1, d2;   // cell widths
+    double inv_d1, inv_d2;
 };
 
 // Scalar state of one solve, resident in device memory between kernels.
@@ -216,6 +219,138 @@ __device__ __forceinline__ void finish_stage2(Scal* S, const Kin& K, const Geom&
     } else {
         prepare_step(S, K, g, t_out);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level scalar chain.  On GB300 a dependent FP64 operation takes ~65
+// cycles and pow() several thousand, so the chain between stages is the
+// latency that matters.  The same kinetics are computed with one logarithm
+// pair and three exponentials spread over the lanes of one warp:
+//   s^g = exp(g (ln(C - c*) - ln c*)),  kg s^g = exp(g ln s + ln kg),
+// where C - c* is exact for S near 1.  Every lane of the calling warp must
+// participate with identical arguments; all lanes return identical results.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B)
+{
+    const int lane = threadIdx.x & 31;
+    if (K.kind == PBE_KINETICS_FIXED) {
+        G1 = K.kg1;
+        G2 = (K.ndim == 2) ? K.kg2 : 0.0;
+        B = K.kb;
+        return;
+    }
+    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
+    const double T = K.T0 + (K.T1 - K.T0) * frac;
+    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double d = C - cs;
+    if (!(d > 0.0)) {   // S <= 1: no growth, no nucleation
+        G1 = 0.0; G2 = 0.0; B = 0.0;
+        return;
+    }
+    const double lx = log(lane == 0 ? d : cs);
+    const double L = __shfl_sync(0xffffffffu, lx, 0) - __shfl_sync(0xffffffffu, lx, 1);
+    const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
+    const double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
+    const double e = exp(fma(p, L, q));
+    G1 = __shfl_sync(0xffffffffu, e, 0);
+    G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
+    B = __shfl_sync(0xffffffffu, e, 2);
+}
+
+__device__ __forceinline__ int timestep_fast(const Kin& K, const Geom& g, double G1, double G2, double t,
+                                             double t_next, double& dt, double& t_new)
+{
+    double rate = G1 * g.inv_d1;
+    if (g.ndim == 2) rate = fma(G2, g.inv_d2, rate);
+    const double rem = t_next - t;
+    if (rate > 0.0) {
+        const double dtc = K.cfl / rate;
+        if (dtc < rem) {
+            dt = dtc;
+            t_new = t + dtc;
+            return 0;
+        }
+    }
+    dt = rem;
+    t_new = t_next;
+    return 1;
+}
+
+// Warp versions of prepare_step / finish_stage1 / finish_stage2: called by all
+// lanes of one warp on the same Scal (shared or global); lane 0 writes.
+__device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const Geom& g, const double* t_out)
+{
+    const int lane = threadIdx.x & 31;
+    const double t_next = t_out[S->out_idx];
+    const double C = S->C, t = S->t;
+    double G1, G2, B, dt, t_new;
+    kinetics_warp(K, C, t, G1, G2, B);
+    const int clipped = timestep_fast(K, g, G1, G2, t, t_next, dt, t_new);
+    __syncwarp();
+    if (lane == 0) {
+        S->G1a = G1; S->G2a = G2; S->Ba = B;
+        S->dt = dt; S->t_new = t_new; S->clipped = clipped;
+        if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
+            S->status = PBE_ENONFINITE;
+            S->done = 1;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double V1)
+{
+    const int lane = threadIdx.x & 31;
+    const double C1 = S->C - K.kappa * (V1 - S->V0);
+    double G1, G2, B;
+    kinetics_warp(K, C1, S->t_new, G1, G2, B);
+    __syncwarp();
+    if (lane == 0) {
+        S->C1 = C1;
+        S->G1b = G1; S->G2b = G2; S->Bb = B;
+        if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
+            S->status = PBE_ENONFINITE;
+            S->done = 1;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void finish_stage2_warp(Scal* S, const Kin& K, const Geom& g, const double* t_out,
+                                                   double* rows, const double* mom, int nmom, int vidx)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        const double V2 = mom[vidx];
+        const double C = S->C - K.kappa * (V2 - S->V0);
+        S->t = S->t_new;
+        S->C = C;
+        S->V0 = V2;
+        S->last_dt = S->dt;
+        S->steps += 1;
+        if (!isfinite(V2) || !isfinite(C)) {
+            S->status = PBE_ENONFINITE;
+            S->done = 1;
+        } else {
+            if (S->clipped) {
+                if (rows) {
+                    double* row = rows + (size_t)S->out_idx * (nmom + 2);
+                    row[0] = S->t;
+                    for (int k = 0; k < nmom; ++k) row[1 + k] = mom[k];
+                    row[nmom + 1] = C;
+                }
+                S->out_idx += 1;
+            }
+            if (S->out_idx >= S->n_out) {
+                S->done = 1;
+            } else if (S->steps >= S->max_steps) {
+                S->status = PBE_ETIMEOUT;
+                S->done = 1;
+            }
+        }
+    }
+    __syncwarp();
+    if (!S->done) prepare_step_warp(S, K, g, t_out);
 }
 
 }  // namespace pbe

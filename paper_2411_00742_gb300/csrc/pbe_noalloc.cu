@@ -163,8 +163,11 @@ extern "C" pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells
     K.kg1 = k->kg[0]; K.g1 = k->g[0]; K.kg2 = 0.0; K.g2 = 1.0; K.kb = k->kb; K.b = k->b;
     K.cs0 = k->csat[0]; K.cs1 = k->csat[1]; K.cs2 = k->csat[2];
     K.T0 = k->T0; K.T1 = k->T1; K.t_cool = k->t_cool; K.kappa = k->kappa; K.cfl = k->cfl;
+    K.lkg1 = std::log(K.kg1); K.lkg2 = 0.0; K.lkb = std::log(K.kb);
+    K.inv_tcool = 1.0 / K.t_cool;
     Geom g;
     g.ndim = 1; g.N1 = (int)ncells; g.N2 = 1; g.d1 = lmax / (double)ncells; g.d2 = 1.0;
+    g.inv_d1 = 1.0 / g.d1; g.inv_d2 = 1.0;
 
     // clear the scalar header, then place C0 and t0 and the output times in the scratch
     Scal hs;

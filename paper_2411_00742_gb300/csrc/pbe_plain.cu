@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kNT) k_prologue(const double* __restrict__ n, 
                                                   int n_out, long long max_steps, double* mom_out)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
+    constexpr int VIDX = NDIM == 1 ? 3 : 8;
     __shared__ double sh[kNT / 32 * NM];
     __shared__ int flag;
     double m[NM];
@@ -71,36 +72,41 @@ __global__ void __launch_bounds__(kNT) k_prologue(const double* __restrict__ n, 
         for (int k = 0; k < NM; ++k) part[(size_t)blockIdx.x * kMaxMom + k] = m[k];
     if (!last_block(&S->counter, nb, &flag)) return;
     reduce_partials<kNT, NM>(part, nb, m, sh);
-    if (threadIdx.x != 0) return;
-    S->counter = 0u;
-    if (mom_out) {  // read-out only
-        for (int k = 0; k < NM; ++k) mom_out[k] = m[k];
-        return;
+    if (threadIdx.x >= 32) return;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) m[k] = __shfl_sync(0xffffffffu, m[k], 0);
+    if (threadIdx.x == 0) {
+        S->counter = 0u;
+        if (mom_out) {  // read-out only
+            for (int k = 0; k < NM; ++k) mom_out[k] = m[k];
+        } else {
+            S->V0 = m[VIDX];
+            S->steps = 0;
+            S->status = 0;
+            S->done = 0;
+            S->out_idx = 0;
+            S->n_out = n_out;
+            S->max_steps = max_steps;
+            bool finite = isfinite(S->C) && isfinite(S->t);
+            for (int k = 0; k < NM; ++k) finite = finite && isfinite(m[k]);
+            if (!finite) {
+                S->status = PBE_ENONFINITE;
+                S->done = 1;
+            } else {
+                while (S->out_idx < n_out && t_out[S->out_idx] == S->t) {
+                    double* row = rows + (size_t)S->out_idx * (NM + 2);
+                    row[0] = S->t;
+                    for (int k = 0; k < NM; ++k) row[1 + k] = m[k];
+                    row[NM + 1] = S->C;
+                    S->out_idx += 1;
+                }
+                if (S->out_idx >= n_out) S->done = 1;
+            }
+        }
     }
-    const int vidx = NDIM == 1 ? 3 : 8;
-    S->V0 = m[vidx];
-    S->steps = 0;
-    S->status = 0;
-    S->done = 0;
-    S->out_idx = 0;
-    S->n_out = n_out;
-    S->max_steps = max_steps;
-    bool finite = true;
-    for (int k = 0; k < NM; ++k) finite = finite && isfinite(m[k]);
-    if (!finite || !isfinite(S->C) || !isfinite(S->t)) {
-        S->status = PBE_ENONFINITE;
-        S->done = 1;
-        return;
-    }
-    while (S->out_idx < n_out && t_out[S->out_idx] == S->t) {
-        double* row = rows + (size_t)S->out_idx * (NM + 2);
-        row[0] = S->t;
-        for (int k = 0; k < NM; ++k) row[1 + k] = m[k];
-        row[NM + 1] = S->C;
-        S->out_idx += 1;
-    }
-    if (S->out_idx >= n_out) S->done = 1;
-    else prepare_step(S, K, g, t_out);
+    __syncwarp();
+    if (mom_out || S->done) return;
+    prepare_step_warp(S, K, g, t_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -129,13 +135,15 @@ __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, 
         for (int k = 0; k < 4; ++k) part[(size_t)blockIdx.x * kMaxMom + k] = m[k];
     if (!last_block(&S->counter, gridDim.x, &flag)) return;
     reduce_partials<kNT, 4>(part, gridDim.x, m, sh);
-    if (threadIdx.x != 0) return;
-    S->counter = 0u;
+    if (threadIdx.x >= 32) return;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m[k] = __shfl_sync(0xffffffffu, m[k], 0);
+    if (threadIdx.x == 0) S->counter = 0u;
     if (STAGE == 1) {
-        finish_stage1(S, K, m[3]);
+        finish_stage1_warp(S, K, m[3]);
     } else {
-        finish_stage2(S, K, g, t_out, rows, m, 4, 3);
-        if (use_cond) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
+        finish_stage2_warp(S, K, g, t_out, rows, m, 4, 3);
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
     }
 }
 
@@ -163,13 +171,15 @@ __global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, 
         for (int k = 0; k < 10; ++k) part[(size_t)bid * kMaxMom + k] = m[k];
     if (!last_block(&S->counter, nb, &flag)) return;
     reduce_partials<kNT, 10>(part, nb, m, sh);
-    if (threadIdx.x != 0) return;
-    S->counter = 0u;
+    if (threadIdx.x >= 32) return;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) m[k] = __shfl_sync(0xffffffffu, m[k], 0);
+    if (threadIdx.x == 0) S->counter = 0u;
     if (STAGE == 1) {
-        finish_stage1(S, K, m[8]);
+        finish_stage1_warp(S, K, m[8]);
     } else {
-        finish_stage2(S, K, g, t_out, rows, m, 10, 8);
-        if (use_cond) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
+        finish_stage2_warp(S, K, g, t_out, rows, m, 10, 8);
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
     }
 }
 

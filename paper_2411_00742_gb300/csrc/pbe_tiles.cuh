@@ -142,6 +142,96 @@ __device__ __forceinline__ void tile2d(const double* in, const double* old, doub
     __syncthreads();
 }
 
+// ---- split phases (used by the fused kernel to overlap the face work of the
+// next stage with the scalar chain) -------------------------------------------
+// Load a tile of the stage input with its halo and compute every face value.
+// Runs on the `nthr` threads whose rank within the group is `tid`; `sync`
+// synchronizes exactly those threads.
+template <bool FAST, bool CG, int T, class Sync>
+__device__ __forceinline__ void faces1d(const double* in, int i0, const Geom& g, double* tile, double* h, int tid,
+                                        int nthr, Sync sync)
+{
+    const int N = g.N1;
+    for (int k = tid; k < T + 3; k += nthr) {
+        int gi = i0 - 2 + k;
+        tile[k] = (gi >= 0 && gi < N) ? ld_in<CG>(in + gi) : 0.0;
+    }
+    sync();
+    for (int f = tid; f <= T; f += nthr) h[f] = face_value<FAST>(tile[f], tile[f + 1], tile[f + 2]);
+}
+
+// Update the cells of a tile whose faces are in shared memory (all threads).
+template <int STAGE, int T, int NT>
+__device__ __forceinline__ void cells1d(const double* old, double* out, int i0, const Geom& g, const StageCoef& sc,
+                                        double (&m)[4], const double* tile, const double* h)
+{
+    const int N = g.N1;
+    for (int c = threadIdx.x; c < T; c += NT) {
+        int i = i0 + c;
+        if (i >= N) break;
+        double v = tile[c + 2] + sc.c1 * (h[c] - h[c + 1]);
+        if (i == 0) v += sc.src;
+        if (STAGE == 2) v = 0.5 * old[i] + 0.5 * v;
+        out[i] = v;
+        double x = (i + 0.5) * g.d1;
+        double w = v * g.d1;
+        if (sc.moms) { m[0] += w; m[1] += x * w; m[2] += x * x * w; }
+        m[3] += x * x * x * w;
+    }
+}
+
+template <bool FAST, bool CG, int TI, int TJ, class Sync>
+__device__ __forceinline__ void faces2d(const double* in, int i0, int j0, const Geom& g, Tile2DSmem<TI, TJ>& s,
+                                        int tid, int nthr, Sync sync)
+{
+    constexpr int W = TJ + 3;
+    const int N1 = g.N1, N2 = g.N2;
+    for (int k = tid; k < (TI + 3) * W; k += nthr) {
+        int r = k / W, c = k - r * W;
+        int gi = i0 - 2 + r, gj = j0 - 2 + c;
+        s.tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? ld_in<CG>(in + (size_t)gi * N2 + gj) : 0.0;
+    }
+    sync();
+    for (int k = tid; k < (TI + 1) * TJ; k += nthr) {
+        int f = k / TJ, c = k - f * TJ;
+        s.h1[k] = face_value<FAST>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2], s.tile[(f + 2) * W + c + 2]);
+    }
+    for (int k = tid; k < TI * (TJ + 1); k += nthr) {
+        int r = k / (TJ + 1), f = k - r * (TJ + 1);
+        const double* row = s.tile + (r + 2) * W;
+        s.h2[k] = face_value<FAST>(row[f], row[f + 1], row[f + 2]);
+    }
+}
+
+template <int STAGE, int TI, int TJ, int NT>
+__device__ __forceinline__ void cells2d(const double* old, double* out, int i0, int j0, const Geom& g,
+                                        const StageCoef& sc, double (&m)[10], const Tile2DSmem<TI, TJ>& s)
+{
+    constexpr int W = TJ + 3;
+    const int N1 = g.N1, N2 = g.N2;
+    const double area = g.d1 * g.d2;
+    for (int k = threadIdx.x; k < TI * TJ; k += NT) {
+        int r = k / TJ, c = k - r * TJ;
+        int i = i0 + r, j = j0 + c;
+        if (i >= N1 || j >= N2) continue;
+        double v = s.tile[(r + 2) * W + c + 2] + sc.c1 * (s.h1[r * TJ + c] - s.h1[(r + 1) * TJ + c]) +
+                   sc.c2 * (s.h2[r * (TJ + 1) + c] - s.h2[r * (TJ + 1) + c + 1]);
+        if (i == 0 && j == 0) v += sc.src;
+        size_t gidx = (size_t)i * N2 + j;
+        if (STAGE == 2) v = 0.5 * old[gidx] + 0.5 * v;
+        out[gidx] = v;
+        double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
+        double w = v * area;
+        double x1w = x1 * w, x2w = x2 * w;
+        m[8] += x1 * x2 * x2w;
+        if (sc.moms) {
+            m[0] += w; m[1] += x1w; m[2] += x2w;
+            m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
+            m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
+        }
+    }
+}
+
 template <int STAGE>
 __device__ __forceinline__ StageCoef stage_coef(const Scal& S, const Geom& g)
 {
