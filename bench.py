@@ -217,6 +217,57 @@ def run_gpu(args):
         g.close()
         return inst.problem.ncell * steps * args.steps / el, n0_host.numel() * 8 + nrow * 8, nrow * ncol * 8
 
+    def batch_leg():
+        """4096 independent 1-D instances in one persistent launch (autotuned), vs the
+        plain single-grid path on a sample of the same instances."""
+        insts = pi.batch_1d(4096, seed=2411)
+        b = P.Batch([x.problem for x in insts], [x.C0 for x in insts], stream=stream)
+        packed = torch.as_tensor(b.pack([x.n0 for x in insts])).to("cuda")
+        rows = torch.zeros((len(insts), len(insts[0].t_out), 6), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            b.set_state(packed)
+            wpb = b.autotune(insts[0].t_out)
+            for _ in range(args.warmup):
+                b.set_state(packed)
+                _, bsteps = b.solve(insts[0].t_out, out=rows)
+        torch.cuda.synchronize()
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(max(2, args.steps // 4)):
+                b.set_state(packed)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, bsteps = b.solve(insts[0].t_out, out=rows)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) * 1e-3)
+        bsteps_cells = b.cell_steps()
+        b.close()
+        tb = sum(times) / len(times)
+        # plain single-grid path, instance by instance, on a sample
+        sample = insts[:64]
+        g_cells, g_time = 0, 0.0
+        with torch.cuda.stream(stream):
+            for inst in sample:
+                g = P.Grid.from_problem(inst.problem, stream=stream, path="plain")
+                g.set_state(torch.as_tensor(inst.n0).cuda(), inst.C0, 0.0)
+                g.solve(inst.t_out)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                g.set_state(torch.as_tensor(inst.n0).cuda(), inst.C0, 0.0)
+                e0.record(stream)
+                _, st = g.solve(inst.t_out)
+                e1.record(stream)
+                e1.synchronize()
+                g.close()
+                g_cells += inst.problem.ncell * st
+                g_time += e0.elapsed_time(e1) * 1e-3
+        return {"instances": len(insts), "warps_per_block": wpb, "total_steps": bsteps,
+                "cell_steps": bsteps_cells, "ms_per_solve": 1e3 * tb, "value": bsteps_cells / tb,
+                "unit": "cell-steps/s",
+                "plain_per_instance": {"value": g_cells / g_time, "sample": "first 64 instances, one grid each"}}
+
     clocks = ClockSampler(dev)
     if ws > 1:
         torch.distributed.barrier()
@@ -226,6 +277,7 @@ def run_gpu(args):
     t_plain, steps_p, err_plain = measure("plain")
     clk = clocks.stop()
     e2e_rate, h2d, d2h = e2e("fused")
+    batch = batch_leg() if not args.no_batch else None
 
     if ws > 1:
         import torch.distributed as dist
@@ -253,6 +305,7 @@ def run_gpu(args):
                              "peak = nominal GB300 FP64"},
         "e2e": {"value": ws * e2e_rate, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         # prologue + one persistent kernel per fused solve, timed steps only
+        "batch_1d": batch,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
@@ -275,6 +328,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -194,6 +194,9 @@ pbe_status pbe_batch_get_state(pbe_batch* b, double* n_packed, double* C, double
 pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double* rows, int mem,
                            int64_t* total_steps);
 
+/* Steps taken by each instance in the last pbe_batch_solve (host, count values). */
+pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps);
+
 /* Instances per block (1, 2, 4 or 8 warps, one instance per warp). */
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 

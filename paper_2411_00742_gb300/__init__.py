@@ -209,6 +209,16 @@ class Batch:
                                                 ctypes.c_void_p(t.ctypes.data), PBE_MEM_HOST))
         return [n[self.offsets[i]:self.offsets[i + 1]] for i in range(self.count)], C, t
 
+    def steps(self) -> np.ndarray:
+        """Steps each instance took in the last solve."""
+        st = (ctypes.c_int64 * self.count)()
+        _lib.check(self.lib.pbe_batch_steps(self.h, st))
+        return np.array(st[:], dtype=np.int64)
+
+    def cell_steps(self) -> int:
+        """Sum over instances of cells x steps of the last solve."""
+        return int(np.sum(np.diff(self.offsets) * self.steps()))
+
     def set_config(self, warps_per_block: int):
         _lib.check(self.lib.pbe_batch_set_config(self.h, int(warps_per_block)))
 

@@ -505,6 +505,13 @@ pbe_status pbe_batch_get_state(pbe_batch* b, double* n_packed, double* C, double
     return PBE_OK;
 }
 
+pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps)
+{
+    if (!b || !steps) return bfail(PBE_EINVAL, "null argument");
+    for (int i = 0; i < b->count; ++i) steps[i] = b->h_steps[i];
+    return PBE_OK;
+}
+
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block)
 {
     if (!b) return bfail(PBE_EINVAL, "null batch");
