@@ -26,7 +26,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libpbe_oracle.so")
 _SOURCES = [os.path.join(_HERE, "pbe_oracle.c"), os.path.join(_HERE, "pbe_oracle_core.h"),
-            os.path.join(_HERE, "pbe_oracle_adjoint.c")]
+]
 
 
 def build(force: bool = False) -> str:
@@ -86,10 +86,9 @@ def _load():
         lib.orc_solve_cs.restype = ctypes.c_long
         lib.orc_solve_cs.argtypes = [P, ctypes.c_int, ctypes.c_double, _D, ctypes.c_double,
                                      ctypes.c_double, _D, ctypes.c_int, _D, _D]
-        if hasattr(lib, "orc_vjp"):
-            lib.orc_vjp.restype = ctypes.c_long
-            lib.orc_vjp.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
-                                    _D, _D, _D]
+        lib.orc_vjp.restype = ctypes.c_long
+        lib.orc_vjp.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
+                                _D, _D, _D, _D]
         _lib = lib
     return _lib
 
@@ -215,3 +214,33 @@ def solve_cs(problem, which: int, n0, C0: float, t0: float, t_out, h: float = 1e
 
 def solve_instance(inst):
     return solve(inst.problem, inst.n0, inst.C0, inst.t0, inst.t_out)
+
+
+def vjp(problem, n0, C0: float, t0: float, t_out, drows):
+    """Hand-written discrete adjoint: dL/dtheta (kg1, g1, kg2, g2, kb, b), dL/dn0, dL/dC0
+    for seeds drows = dL/d(rows) (time column ignored)."""
+    t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+    drows = np.ascontiguousarray(drows, dtype=np.float64)
+    assert drows.shape == (len(t_out), ncols(problem))
+    P = params(problem)
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    dth = np.zeros(6)
+    dn0 = np.zeros_like(n0)
+    dC0 = np.zeros(1)
+    _load().orc_vjp(ctypes.byref(P), _ptr(n0), float(C0), float(t0), _ptr(t_out), len(t_out),
+                    _ptr(drows), _ptr(dth), _ptr(dn0), _ptr(dC0))
+    return dth, dn0, dC0[0]
+
+
+def relative_loss(rows, target, cols):
+    """Sum of squared relative errors of the chosen row columns (the parameter
+    estimation objective of Sec. 4.1, Eq. 5, with relative residuals)."""
+    r = (rows[:, cols] - target[:, cols]) / target[:, cols]
+    return float(np.sum(r * r))
+
+
+def relative_loss_seeds(rows, target, cols):
+    """dL/drows of relative_loss."""
+    g = np.zeros_like(rows)
+    g[:, cols] = 2.0 * (rows[:, cols] - target[:, cols]) / target[:, cols] ** 2
+    return g

@@ -173,3 +173,245 @@ long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, do
     free(n); free(rows);
     return steps;
 }
+
+/* ------------------------------------------------------------------ */
+/* Hand-written discrete adjoint of the step (reverse mode through the  */
+/* exact operations of step_r, in reverse order).  Branches follow the  */
+/* forward pass: the limiter derivative is that of the branch taken     */
+/* (strict same-sign test), S <= 1 has zero derivative, and the step    */
+/* length is differentiated through the branch (CFL or output clip)     */
+/* that the forward pass took; the number of steps is that of the       */
+/* forward pass.                                                        */
+/* ------------------------------------------------------------------ */
+
+/* partial derivatives of psi(a, b) = 2ab/(a+b) on its smooth branch */
+static void psi_grad(double a, double b, double* pa, double* pb)
+{
+    if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
+        double qa = b / (a + b), qb = a / (a + b);  /* ratios in (0, 1): no underflow in the tails */
+        *pa = 2.0 * qa * qa;
+        *pb = 2.0 * qb * qb;
+    } else {
+        *pa = 0.0;
+        *pb = 0.0;
+    }
+}
+
+/* One line of cells (N cells, element stride st) of D(n)_i = -(h_{i+1} - h_i)/d,
+ * h_f = n_{f-1} + psi(n_{f-1} - n_{f-2}, n_f - n_{f-1}) / 2 (zero ghosts).
+ * Adds scale * (dD/dn)^T lam to out and returns lam . D(n) = sum_f h_f (lam_f - lam_{f-1}) / d. */
+static double line_adjoint(const double* n, const double* lam, int N, long st, double d, double scale, double* out)
+{
+    double dot = 0.0;
+    for (int f = 0; f <= N; ++f) {
+        double nm2 = (f - 2 >= 0) ? n[(long)(f - 2) * st] : 0.0;
+        double up = (f - 1 >= 0 && f - 1 < N) ? n[(long)(f - 1) * st] : 0.0;
+        double dn = (f < N) ? n[(long)f * st] : 0.0;
+        double a = up - nm2, b = dn - up;
+        double h = up + 0.5 * psi_r(a, b);
+        double lamL = (f - 1 >= 0) ? lam[(long)(f - 1) * st] : 0.0;
+        double lamR = (f < N) ? lam[(long)f * st] : 0.0;
+        double mu = (lamR - lamL) / d;
+        dot += h * mu;
+        double pa, pb;
+        psi_grad(a, b, &pa, &pb);
+        if (f - 2 >= 0) out[(long)(f - 2) * st] += scale * mu * (-0.5 * pa);
+        if (f - 1 >= 0 && f - 1 < N) out[(long)(f - 1) * st] += scale * mu * (1.0 + 0.5 * (pa - pb));
+        if (f < N) out[(long)f * st] += scale * mu * (0.5 * pb);
+    }
+    return dot;
+}
+
+/* out += dt*(G1 dD1/dn + G2 dD2/dn)^T lam; P[0] = lam.D1(n), P[1] = lam.D2(n), P[2] = lam at the inflow cell */
+static void stage_adjoint(const orc_params* p, const double* n, const double* lam, double dt, double G1, double G2,
+                          double* out, double* P)
+{
+    P[0] = P[1] = 0.0;
+    if (p->ndim == 1) {
+        P[0] = line_adjoint(n, lam, p->n1, 1, p->lmax1 / p->n1, dt * G1, out);
+    } else {
+        int N1 = p->n1, N2 = p->n2;
+        double d1 = p->lmax1 / N1, d2 = p->lmax2 / N2;
+        for (int j = 0; j < N2; ++j) P[0] += line_adjoint(n + j, lam + j, N1, N2, d1, dt * G1, out + j);
+        for (int i = 0; i < N1; ++i)
+            P[1] += line_adjoint(n + (size_t)i * N2, lam + (size_t)i * N2, N2, 1, d2, dt * G2, out + (size_t)i * N2);
+    }
+    P[2] = lam[0];
+}
+
+/* weights of the volume moment V = sum w n */
+static void volume_weights(const orc_params* p, double* w)
+{
+    if (p->ndim == 1) {
+        double d = p->lmax1 / p->n1;
+        for (int i = 0; i < p->n1; ++i) {
+            double x = (i + 0.5) * d;
+            w[i] = x * x * x * d;
+        }
+    } else {
+        double d1 = p->lmax1 / p->n1, d2 = p->lmax2 / p->n2;
+        for (int i = 0; i < p->n1; ++i)
+            for (int j = 0; j < p->n2; ++j) {
+                double x1 = (i + 0.5) * d1, x2 = (j + 0.5) * d2;
+                w[(size_t)i * p->n2 + j] = x1 * x2 * x2 * d1 * d2;
+            }
+    }
+}
+
+/* lam += sum_k seed[k] * (weights of moment k) (output row of the moments) */
+static void add_moment_seeds(const orc_params* p, const double* seed, double* lam)
+{
+    if (p->ndim == 1) {
+        double d = p->lmax1 / p->n1;
+        for (int i = 0; i < p->n1; ++i) {
+            double x = (i + 0.5) * d;
+            lam[i] += (seed[0] + seed[1] * x + seed[2] * x * x + seed[3] * x * x * x) * d;
+        }
+    } else {
+        static const int P[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+        static const int Q[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+        double d1 = p->lmax1 / p->n1, d2 = p->lmax2 / p->n2;
+        for (int i = 0; i < p->n1; ++i)
+            for (int j = 0; j < p->n2; ++j) {
+                double x1 = (i + 0.5) * d1, x2 = (j + 0.5) * d2, v = 0.0;
+                for (int k = 0; k < 10; ++k) v += seed[k] * pow(x1, P[k]) * pow(x2, Q[k]);
+                lam[(size_t)i * p->n2 + j] += v * d1 * d2;
+            }
+    }
+}
+
+/* adjoint of (G1, G2, B) = kinetics(C, t): accumulates into *lC, *lt, lth[6] */
+static void kinetics_adjoint(const orc_params* p, double C, double t, double lG1, double lG2, double lB,
+                             double* lC, double* lt, double* lth)
+{
+    if (p->fixed_kinetics) {
+        lth[0] += lG1;
+        if (p->ndim == 2) lth[2] += lG2;
+        lth[4] += lB;
+        return;
+    }
+    double T = temperature_r(p, t);
+    double dTdt = (t < p->t_cool) ? (p->T1 - p->T0) / p->t_cool : 0.0;
+    double cs = p->cs0 + p->cs1 * T + p->cs2 * T * T;
+    double dcs = p->cs1 + 2.0 * p->cs2 * T;
+    double s = C / cs - 1.0;
+    if (!(s > 0.0)) return;
+    double ls = log(s);
+    double s1 = pow(s, p->g1), sb = pow(s, p->b);
+    double G1 = p->kg1 * s1, B = p->kb * sb;
+    double lsum = lG1 * p->g1 * p->kg1 * pow(s, p->g1 - 1.0) + lB * p->b * p->kb * pow(s, p->b - 1.0);
+    lth[0] += lG1 * s1;
+    lth[1] += lG1 * G1 * ls;
+    lth[4] += lB * sb;
+    lth[5] += lB * B * ls;
+    if (p->ndim == 2) {
+        double s2 = pow(s, p->g2), G2 = p->kg2 * s2;
+        lth[2] += lG2 * s2;
+        lth[3] += lG2 * G2 * ls;
+        lsum += lG2 * p->g2 * p->kg2 * pow(s, p->g2 - 1.0);
+    }
+    *lC += lsum / cs;
+    *lt += lsum * (-C * dcs / (cs * cs)) * dTdt;
+}
+
+/* Vector-Jacobian product of a solve.  drows[n_out * ncol]: dL/d(row entries)
+ * (the time column is ignored).  Outputs dL/dtheta[6] (kg1, g1, kg2, g2, kb, b),
+ * and optionally dL/dn0 (ncell) and dL/dC0.  Returns the number of steps. */
+long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const double* t_out, int n_out,
+             const double* drows, double* dtheta, double* dn0, double* dC0)
+{
+    size_t nc = ncells(p);
+    int ncol = ncols(p), nm = ncol - 2;
+    double area = (p->ndim == 1) ? p->lmax1 / p->n1 : (p->lmax1 / p->n1) * (p->lmax2 / p->n2);
+    double d1 = p->lmax1 / p->n1, d2 = (p->ndim == 2) ? p->lmax2 / p->n2 : 1.0;
+    /* forward pass with every step recorded */
+    long cap = 1024;
+    steprec_r* recs = NULL;
+    double* snaps = NULL;
+    double* rows = (double*)malloc((size_t)n_out * ncol * sizeof(double));
+    double* n = (double*)malloc(nc * sizeof(double));
+    long steps;
+    for (;;) {
+        recs = (steprec_r*)malloc(cap * sizeof(steprec_r));
+        snaps = (double*)malloc((size_t)cap * nc * sizeof(double));
+        memcpy(n, n0, nc * sizeof(double));
+        double C = C0, t = t0;
+        ctx_r c = make_ctx_r(p);
+        steps = solve_r(&c, n, &C, &t, t_out, n_out, rows, recs, snaps, cap);
+        if (steps >= 0) break;
+        free(recs); free(snaps);
+        cap *= 4;
+    }
+    double* w = (double*)malloc(nc * sizeof(double));
+    double* lam = (double*)calloc(nc, sizeof(double));
+    double* lam1 = (double*)malloc(nc * sizeof(double));
+    double* lamp = (double*)malloc(nc * sizeof(double));
+    double* n1 = (double*)malloc(nc * sizeof(double));
+    double* L = (double*)malloc(nc * sizeof(double));
+    volume_weights(p, w);
+    double lC = 0.0, lt = 0.0;
+    double lth[6] = {0, 0, 0, 0, 0, 0};
+    for (long k = steps - 1; k >= 0; --k) {
+        const steprec_r* r = &recs[k];
+        if (r->out_index >= 0) {  /* seeds of the output row emitted at the end of this step */
+            const double* sd = drows + (size_t)r->out_index * ncol;
+            add_moment_seeds(p, sd + 1, lam);
+            lC += sd[1 + nm];
+        }
+        const double* nk = snaps + (size_t)k * nc;
+        rhs_r(p, nk, r->G1a, r->G2a, r->Ba, L);
+        for (size_t q = 0; q < nc; ++q) n1[q] = nk[q] + r->dt * L[q];
+        /* C' = C - kappa (V' - V0) */
+        double lV0 = p->kappa * lC;
+        double lCp = lC;
+        for (size_t q = 0; q < nc; ++q) lam[q] += -p->kappa * lC * w[q];
+        /* n' = n/2 + n2/2 */
+        for (size_t q = 0; q < nc; ++q) { lamp[q] = 0.5 * lam[q]; lam[q] = 0.5 * lam[q]; }  /* lam <- lam_n2 */
+        /* n2 = n1 + dt L(n1; b) */
+        double P[3];
+        memcpy(lam1, lam, nc * sizeof(double));
+        stage_adjoint(p, n1, lam, r->dt, r->G1b, r->G2b, lam1, P);
+        double ldt = r->G1b * P[0] + r->G2b * P[1] + r->Bb * P[2] / area;
+        double lG1 = r->dt * P[0], lG2 = r->dt * P[1], lB = r->dt * P[2] / area;
+        /* kinetics at (C1, t') */
+        double lC1 = 0.0, ltn = lt;
+        kinetics_adjoint(p, r->C1, r->t_new, lG1, lG2, lB, &lC1, &ltn, lth);
+        /* C1 = C - kappa (V1 - V0) */
+        lCp += lC1;
+        lV0 += p->kappa * lC1;
+        for (size_t q = 0; q < nc; ++q) lam1[q] += -p->kappa * lC1 * w[q];
+        /* n1 = n + dt L(n; a) */
+        for (size_t q = 0; q < nc; ++q) lamp[q] += lam1[q];
+        stage_adjoint(p, nk, lam1, r->dt, r->G1a, r->G2a, lamp, P);
+        ldt += r->G1a * P[0] + r->G2a * P[1] + r->Ba * P[2] / area;
+        lG1 = r->dt * P[0]; lG2 = r->dt * P[1]; lB = r->dt * P[2] / area;
+        /* V0 = w . n */
+        for (size_t q = 0; q < nc; ++q) lamp[q] += lV0 * w[q];
+        /* step length */
+        double ltp;
+        if (!r->clipped) {
+            ltp = ltn;
+            ldt += ltn;
+            double R = r->G1a / d1 + ((p->ndim == 2) ? r->G2a / d2 : 0.0);
+            double dR = -p->cfl / (R * R) * ldt;
+            lG1 += dR / d1;
+            if (p->ndim == 2) lG2 += dR / d2;
+        } else {
+            ltp = -ldt;
+        }
+        /* kinetics at (C, t) */
+        kinetics_adjoint(p, r->C, r->t, lG1, lG2, lB, &lCp, &ltp, lth);
+        memcpy(lam, lamp, nc * sizeof(double));
+        lC = lCp;
+        lt = ltp;
+    }
+    if (n_out > 0 && t_out[0] == t0) {  /* row emitted from the initial state */
+        add_moment_seeds(p, drows + 1, lam);
+        lC += drows[1 + nm];
+    }
+    for (int q = 0; q < 6; ++q) dtheta[q] = lth[q];
+    if (dn0) memcpy(dn0, lam, nc * sizeof(double));
+    if (dC0) *dC0 = lC;
+    free(recs); free(snaps); free(rows); free(n); free(w); free(lam); free(lam1); free(lamp); free(n1); free(L);
+    return steps;
+}
