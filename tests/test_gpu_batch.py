@@ -66,7 +66,8 @@ def test_batch_edge_sizes_and_kinetics():
 
 @pytest.mark.parametrize("wpb", [1, 2, 8])
 def test_batch_config_independent_bitwise(wpb):
-    insts = pi.batch_1d(40, seed=99)
+    # instances small enough that 8 per block fit in shared memory
+    insts = [x for x in pi.batch_1d(120, seed=99) if x.problem.ncells[0] <= 1500][:40]
     ref = _run_batch(insts, wpb=4)
     got = _run_batch(insts, wpb=wpb)
     assert np.array_equal(ref[0], got[0]) and ref[1] == got[1]
@@ -107,6 +108,15 @@ def test_batch_full_workload_sampled():
         assert np.max(np.abs(n[i] - want["n"])) <= REL_N * np.max(np.abs(want["n"]))
     assert np.all(t == 3600.0)
     assert steps >= 60 * 4096
+
+
+def test_batch_rejects_config_that_does_not_fit():
+    import paper_2411_00742_gb300 as P
+    insts = [pi.config_1d(6000) for _ in range(4)]
+    b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
+    with pytest.raises(P.PbeError):
+        b.set_config(8)
+    b.close()
 
 
 def test_batch_rejects_oversized_instance():
