@@ -122,6 +122,27 @@ pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, 
  * 2-D in the row order of pbe_solve (SI moment definition, midpoint rule). */
 pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
 
+/* Vector-Jacobian product of pbe_solve from the current state: the gradient
+ * that parameter estimation by a gradient method needs (Sec. 4.1, Eq. 5),
+ * computed by the hand-written discrete adjoint of the step (reverse mode
+ * through every operation of the forward scheme, branches as the forward
+ * pass took them: limiter derivative of the branch taken, zero for S <= 1,
+ * the step length through its CFL or output-clip branch; the step count is
+ * that of the forward pass).  Checkpointing: the forward pass keeps the state
+ * every `checkpoint_every` steps; the reverse sweep recomputes each segment.
+ *   t_out, n_out       output times as in pbe_solve (host memory)
+ *   seeds              dL/d(rows): n_out x ncol doubles (`seeds_mem` memory);
+ *                      the time column is ignored
+ *   dL_dtheta          HOST, 6 doubles: d/d(kg[0], g[0], kg[1], g[1], kb, b)
+ *                      (power-law kinetics; with fixed kinetics d/d(kg, kb))
+ *   dL_dn0             optional, ncell doubles (`mem` memory): d/d(initial n)
+ *   dL_dC0             optional HOST double: d/d(initial C)
+ *   rows               optional, the forward rows (`mem` memory)
+ * On return the grid holds the state at the end of the solve.  Allocates
+ * work memory for the checkpoints; synchronizes the stream. */
+pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const double* seeds, int seeds_mem,
+                   int checkpoint_every, double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem);
+
 /* Upper bound on steps per pbe_solve call (default 1e6); exceeding it stops
  * the solve with PBE_ETIMEOUT. */
 pbe_status pbe_set_max_steps(pbe_grid* g, int64_t max_steps);

@@ -41,6 +41,7 @@ int plain_max_blocks(const Geom& g);
 // Plain path (pbe_plain.cu)
 cudaError_t launch_prologue(pbe_grid* g, int n_out, long long max_steps, double* mom_out);
 cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h);
+cudaError_t launch_plain_stage(pbe_grid* g, int stage);
 cudaError_t launch_set_scalars(pbe_grid* g, double C, double t);
 
 // Fused path (pbe_fused.cu)

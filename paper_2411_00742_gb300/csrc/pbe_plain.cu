@@ -207,6 +207,29 @@ cudaError_t launch_prologue(pbe_grid* g, int n_out, long long max_steps, double*
     return cudaGetLastError();
 }
 
+cudaError_t launch_plain_stage(pbe_grid* g, int stage)
+{
+    const Geom& geo = g->geo;
+    if (geo.ndim == 1) {
+        int nb = cdiv(geo.N1, kT1);
+        if (stage == 1)
+            k_stage1d<1><<<nb, kNT, 0, g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part,
+                                                    g->d_tout, g->d_rows, 0, 0);
+        else
+            k_stage1d<2><<<nb, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
+                                                    g->d_tout, g->d_rows, 0, 0);
+    } else {
+        dim3 grid(cdiv(geo.N2, kTJ), cdiv(geo.N1, kTI));
+        if (stage == 1)
+            k_stage2d<1><<<grid, kNT, 0, g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part,
+                                                      g->d_tout, g->d_rows, 0, 0);
+        else
+            k_stage2d<2><<<grid, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
+                                                      g->d_tout, g->d_rows, 0, 0);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h)
 {
     const Geom& geo = g->geo;
