@@ -26,14 +26,16 @@ def ncols(ndim: int) -> int:
     return 6 if ndim == 1 else 12
 
 
-def kinetics_struct(problem) -> Kinetics:
+def kinetics_struct(problem, theta=None) -> Kinetics:
     """pbe_kinetics from any object with the fields of a problem description
-    (kg, g, kb, b, csat, T0, T1, t_cool, kappa, cfl, fixed_kinetics)."""
+    (kg, g, kb, b, csat, T0, T1, t_cool, kappa, cfl, fixed_kinetics);
+    theta = (kg1, g1, kg2, g2, kb, b) overrides the kinetic parameters."""
     k = Kinetics()
     k.kind = PBE_KINETICS_FIXED if getattr(problem, "fixed_kinetics", False) else PBE_KINETICS_POWER_LAW
-    k.kg[0], k.kg[1] = float(problem.kg[0]), float(problem.kg[1])
-    k.g[0], k.g[1] = float(problem.g[0]), float(problem.g[1])
-    k.kb, k.b = float(problem.kb), float(problem.b)
+    if theta is None:
+        theta = (problem.kg[0], problem.g[0], problem.kg[1], problem.g[1], problem.kb, problem.b)
+    th = [float(v) for v in theta]
+    k.kg[0], k.g[0], k.kg[1], k.g[1], k.kb, k.b = th
     for i in range(3):
         k.csat[i] = float(problem.csat[i])
     k.T0, k.T1, k.t_cool = float(problem.T0), float(problem.T1), float(problem.t_cool)
@@ -106,8 +108,8 @@ class Grid:
     def set_max_steps(self, n: int):
         _lib.check(self.lib.pbe_set_max_steps(self.h, int(n)))
 
-    def set_kinetics(self, problem):
-        k = kinetics_struct(problem)
+    def set_kinetics(self, problem, theta=None):
+        k = kinetics_struct(problem, theta)
         _lib.check(self.lib.pbe_set_kinetics(self.h, ctypes.byref(k)))
 
     def set_state(self, n, C: float, t: float):
@@ -140,6 +142,29 @@ class Grid:
         _lib.check(self.lib.pbe_solve(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       len(t_out), p, mem, ctypes.byref(steps)))
         return out, steps.value
+
+    def vjp(self, t_out, seeds, checkpoint_every: int = 64, dn0_out=None, rows_out=None):
+        """Gradient of a scalar loss of the rows of solve(t_out) from the current
+        state, given seeds = dL/drows.  Returns (dL/dtheta[6], dL/dn0 or None, dL/dC0)."""
+        t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+        sp, smem, skeep = _buf(seeds)
+        dth = np.zeros(6)
+        dC0 = ctypes.c_double()
+        mem = PBE_MEM_HOST
+        dn_p = None
+        if dn0_out is not None:
+            dn_p, mem, dkeep = _buf(dn0_out, writable=True)
+        rows_p = None
+        if rows_out is not None:
+            rows_p, rmem, rkeep = _buf(rows_out, writable=True)
+            if dn0_out is not None and rmem != mem:
+                raise ValueError("dn0_out and rows_out must live in the same memory")
+            mem = rmem
+        _lib.check(self.lib.pbe_vjp(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t_out),
+                                    sp, smem, int(checkpoint_every),
+                                    dth.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dn_p,
+                                    ctypes.byref(dC0), rows_p, mem))
+        return dth, dn0_out, dC0.value
 
     def moments(self, out=None):
         if out is None:

@@ -1,0 +1,118 @@
+"""GPU discrete adjoint (pbe_vjp) against the FP64 CPU adjoint of the oracle
+and against central finite differences of the GPU forward path (the
+gradient bar: 1e-6 relative)."""
+import numpy as np
+import pytest
+
+import oracle
+import pbe_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+REL_GRAD = 1e-6
+
+
+def _problem(case):
+    return {"1d": lambda: pi.config_1d(200), "1d_cfl": lambda: pi.config_1d(800),
+            "2d": lambda: pi.config_2d(40), "2d_rect": lambda: pi.config_2d(36, 52),
+            "2d_128": lambda: pi.adjoint_2d(128)}[case]()
+
+
+def _setup(inst):
+    p = inst.problem
+    inst.t_out = pi.loss_times()
+    tgt = oracle.solve(p.with_theta(p.theta * pi.TARGET_FACTOR), inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    cols = [1, 2, 3, 4, 5] if p.ndim == 1 else [1, 2, 3, 9, 11]
+    return p, tgt, cols
+
+
+def _gpu_grad(inst, seeds, K):
+    import torch
+    import paper_2411_00742_gb300 as P
+    g = P.Grid.from_problem(inst.problem)
+    g.set_state(np.ascontiguousarray(inst.n0), inst.C0, 0.0)
+    dn0 = torch.zeros(inst.problem.ncells, dtype=torch.float64, device="cuda")
+    rows = torch.zeros(seeds.shape, dtype=torch.float64, device="cuda")
+    dth, _, dC0 = g.vjp(inst.t_out, seeds, K, dn0_out=dn0, rows_out=rows)
+    _, C, t = g.get_state()
+    g.close()
+    return dth, dn0.cpu().numpy(), dC0, rows.cpu().numpy(), t
+
+
+@pytest.mark.parametrize("case,K", [("1d", 64), ("1d_cfl", 7), ("2d", 64), ("2d_rect", 5), ("2d_128", 64)])
+def test_vjp_matches_cpu_adjoint(case, K):
+    inst = _problem(case)
+    p, tgt, cols = _setup(inst)
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    want, want_dn0, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
+    dth, dn0, dC0, rows, t_end = _gpu_grad(inst, seeds, K)
+    for j in range(6):
+        assert dth[j] == pytest.approx(want[j], rel=REL_GRAD, abs=1e-300), (case, j, dth, want)
+    assert np.max(np.abs(dn0 - want_dn0)) <= REL_GRAD * np.max(np.abs(want_dn0))
+    assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
+    np.testing.assert_allclose(rows[:, 1:], r[:, 1:], rtol=1e-10)
+    assert t_end == pytest.approx(inst.t_out[-1])
+
+
+def test_vjp_checkpoint_interval_does_not_change_result():
+    inst = _problem("2d")
+    p, tgt, cols = _setup(inst)
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    a = _gpu_grad(inst, seeds, 1)
+    b = _gpu_grad(inst, seeds, 64)
+    c = _gpu_grad(inst, seeds, 1000)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(b[0], c[0])
+    assert np.array_equal(a[1], b[1])
+
+
+def test_vjp_matches_central_differences_of_gpu_forward():
+    import paper_2411_00742_gb300 as P
+    inst = _problem("1d_cfl")
+    p, tgt, cols = _setup(inst)
+
+    def loss(theta):
+        g = P.Grid.from_problem(p)
+        g.set_kinetics(p, theta=theta)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        rows, steps = g.solve(inst.t_out)
+        g.close()
+        return oracle.relative_loss(rows, tgt, cols), steps
+
+    g = P.Grid.from_problem(p)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, _ = g.solve(inst.t_out)
+    seeds = oracle.relative_loss_seeds(rows, tgt, cols)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    dth, _, _ = g.vjp(inst.t_out, seeds, 64)
+    g.close()
+    th = p.theta
+    for j in (0, 1, 4, 5):
+        h = 1e-6 * abs(th[j])
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        (Lp, sp), (Lm, sm) = loss(tp), loss(tm)
+        assert sp == sm
+        assert dth[j] == pytest.approx((Lp - Lm) / (2 * h), rel=REL_GRAD), j
+
+
+def test_autograd_function():
+    import torch
+    import paper_2411_00742_gb300 as P
+    from paper_2411_00742_gb300.autograd import PBESolve
+    inst = _problem("2d")
+    p, tgt, cols = _setup(inst)
+    g = P.Grid.from_problem(p)
+    theta = torch.tensor(p.theta, dtype=torch.float64, requires_grad=True)
+    n0 = torch.as_tensor(inst.n0).cuda().requires_grad_(True)
+    rows = PBESolve.apply(theta, n0, g, p, inst.C0, 0.0, inst.t_out, 64)
+    tgt_t = torch.as_tensor(tgt).cuda()
+    L = (((rows[:, cols] - tgt_t[:, cols]) / tgt_t[:, cols]) ** 2).sum()
+    L.backward()
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    want, want_dn0, _ = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, oracle.relative_loss_seeds(r, tgt, cols))
+    np.testing.assert_allclose(theta.grad.numpy(), want, rtol=REL_GRAD)
+    assert np.max(np.abs(n0.grad.cpu().numpy() - want_dn0)) <= REL_GRAD * np.max(np.abs(want_dn0))
+    g.close()
