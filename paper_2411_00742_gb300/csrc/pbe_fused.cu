@@ -8,6 +8,15 @@
 // which do not depend on the kinetics.  Face quotients use the
 // Newton-Raphson form (half_psi_fast).
 //
+// GB300 FP64 notes that shape this kernel: a warp-wide FP64 instruction
+// occupies the SM's FP64 pipe for ~16 cycles whatever its active lanes, and
+// a dependent FP64 operation takes ~65 cycles.  So (a) with one tile per
+// block the moment weights of each thread's cells are computed once and
+// kept in registers, (b) block reductions go through shared memory in two
+// 16-wide levels instead of per-warp butterflies (3x fewer FP64 warp
+// instructions), (c) the cross-block sum reads all partials with one load
+// round and reduces every moment at once.
+//
 // Every wait is bounded: a barrier that does not complete within about one
 // second sets PBE_ETIMEOUT and the kernel returns.
 #include <type_traits>
@@ -17,9 +26,9 @@
 
 namespace pbe {
 
-constexpr int kFNT = 256;     // threads per block
+constexpr int kFNT = 256;     // threads per block (the reductions assume 256)
 constexpr int kFT1 = 1024;    // 1-D tile
-constexpr int kFTI = 8;       // 2-D tile rows
+constexpr int kFTI = 16;      // 2-D tile rows
 constexpr int kFTJ = 32;      // 2-D tile columns
 constexpr long long kBarrierCycles = 2000000000LL;  // ~1 s at 2 GHz
 
@@ -67,29 +76,65 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int& gen, int* fail_sh)
     return *fail_sh == 0;
 }
 
-// Sum of one moment slot over all blocks' partials, by one warp, in a fixed
-// order: lane l sums blocks l, l+32, ... as a balanced tree per chunk of 16,
-// then a butterfly over the lanes (every lane ends with the same value).
-__device__ __forceinline__ double warp_sum_partials(const double* part, int G, int slot)
+// Deterministic block sum of NV values per thread through shared memory:
+// 16 threads per value each sum 16 rows (balanced tree), then one thread per
+// value sums the 16 results.  Result in res[0..NV) (shared).  256 threads.
+template <int NV>
+__device__ __forceinline__ void block_sum_smem(const double (&v)[NV], double* red, double* red2, double* res)
 {
-    const int lane = threadIdx.x & 31;
-    double acc = 0.0;
-    for (int base = 0; base < G; base += 32 * 16) {
-        double v[16];
+    constexpr int S = NV + 1;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int b = base + lane + 32 * k;
-            v[k] = b < G ? __ldcg(part + (size_t)b * kMaxMom + slot) : 0.0;
-        }
+    for (int k = 0; k < NV; ++k) red[threadIdx.x * S + k] = v[k];
+    __syncthreads();
+    const int vv = threadIdx.x & 15, ch = threadIdx.x >> 4;
+    if (vv < NV) {
+        double a[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) a[r] = red[(ch * 16 + r) * S + vv];
 #pragma unroll
         for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
-            for (int k = 0; k < w; ++k) v[k] += v[k + w];
-        acc += v[0];
+            for (int r = 0; r < w; ++r) a[r] += a[r + w];
+        red2[ch * 16 + vv] = a[0];
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double a[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) a[r] = red2[r * 16 + threadIdx.x];
+#pragma unroll
+        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+            for (int r = 0; r < w; ++r) a[r] += a[r + w];
+        res[threadIdx.x] = a[0];
+    }
+    __syncthreads();
+}
+
+// Cross-block sums of NV moment slots (slot[k]) by one warp in a fixed
+// order: lanes read 4 partials per round, tree-sum them, then a butterfly;
+// every lane ends with the totals.
+template <int NV>
+__device__ __forceinline__ void warp_sum_partials(const double* part, int G, const int (&slot)[NV], double (&tot)[NV])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = 0.0;
+    for (int base = 0; base < G; base += 128) {
+        double v[NV][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = base + lane + 32 * q;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k][q] = b < G ? __ldcg(part + (size_t)b * kMaxMom + slot[k]) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] += (v[k][0] + v[k][2]) + (v[k][1] + v[k][3]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
 }
 
 struct GroupSync {  // named barrier over warps 1..7
@@ -112,13 +157,48 @@ struct FusedSmem<2> {
 };
 
 template <int NDIM>
+struct TileShape;
+template <>
+struct TileShape<1> {
+    static constexpr int CELLS = kFT1;
+};
+template <>
+struct TileShape<2> {
+    static constexpr int CELLS = kFTI * kFTJ;
+};
+
+template <int NDIM>
 __device__ __forceinline__ void tile_origin(int t, int tiles_x, int& i0, int& j0)
 {
     if (NDIM == 1) { i0 = t * kFT1; j0 = 0; }
     else { i0 = (t / tiles_x) * kFTI; j0 = (t % tiles_x) * kFTJ; }
 }
 
-// faces of tile t of `in` on threads [tid, tid+nthr) of the block
+// local cell q of this thread in a tile -> (i, j)
+template <int NDIM>
+__device__ __forceinline__ void cell_of(int k, int i0, int j0, int& i, int& j, int& r, int& c)
+{
+    if (NDIM == 1) { r = k; c = 0; i = i0 + k; j = 0; }
+    else { r = k / kFTJ; c = k - r * kFTJ; i = i0 + r; j = j0 + c; }
+}
+
+// moment weights of cell (i, j): x^k dL (1-D), x1^p x2^q dA (2-D, row order)
+template <int NDIM>
+__device__ __forceinline__ void moment_weights(int i, int j, const Geom& g, double* w)
+{
+    if (NDIM == 1) {
+        const double x = (i + 0.5) * g.d1;
+        w[0] = g.d1; w[1] = x * w[0]; w[2] = x * w[1]; w[3] = x * w[2];
+    } else {
+        const double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
+        const double a = g.d1 * g.d2;
+        const double a1 = x1 * a, a2 = x2 * a;
+        w[0] = a; w[1] = a1; w[2] = a2;
+        w[3] = x1 * a1; w[4] = x1 * a2; w[5] = x2 * a2;
+        w[6] = x1 * x1 * a1; w[7] = x1 * x1 * a2; w[8] = x1 * x2 * a2; w[9] = x2 * x2 * a2;
+    }
+}
+
 template <int NDIM, class Sync>
 __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x, const Geom& g, FusedSmem<NDIM>& sm,
                                             int tid, int nthr, Sync sync)
@@ -129,42 +209,47 @@ __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x
     else faces2d<true, true, kFTI, kFTJ>(in, i0, j0, g, sm.t, tid, nthr, sync);
 }
 
-template <int STAGE, int NDIM, int NM>
-__device__ __forceinline__ void fused_cells(const double* old, double* out, int t, int tiles_x, const Geom& g,
-                                            const StageCoef& sc, double (&m)[NM], const FusedSmem<NDIM>& sm)
+// update of cell local index k of tile (i0, j0) from the faces in shared memory
+template <int STAGE, int NDIM>
+__device__ __forceinline__ double cell_update(const double* old, double* out, int k, int i0, int j0, const Geom& g,
+                                              const StageCoef& sc, const FusedSmem<NDIM>& sm, bool& valid, int& i,
+                                              int& j)
 {
-    int i0, j0;
-    tile_origin<NDIM>(t, tiles_x, i0, j0);
-    if constexpr (NDIM == 1) cells1d<STAGE, kFT1, kFNT>(old, out, i0, g, sc, m, sm.tile, sm.h);
-    else cells2d<STAGE, kFTI, kFTJ, kFNT>(old, out, i0, j0, g, sc, m, sm.t);
-}
-
-// One stage over all tiles of this block; the first tile's faces are already
-// in shared memory.  in: stage input, old/out: see tile1d/tile2d.
-template <int STAGE, int NDIM, int NM>
-__device__ __forceinline__ void fused_stage(const double* in, const double* old, double* out, int ntiles, int tiles_x,
-                                            const Geom& g, const StageCoef& sc, double (&m)[NM], FusedSmem<NDIM>& sm)
-{
-    const int G = gridDim.x;
-    for (int t = blockIdx.x; t < ntiles; t += G) {
-        if (t != (int)blockIdx.x) {
-            fused_faces<NDIM>(in, t, tiles_x, g, sm, threadIdx.x, kFNT, BlockSync());
-            __syncthreads();
-        }
-        fused_cells<STAGE, NDIM, NM>(old, out, t, tiles_x, g, sc, m, sm);
-        __syncthreads();
+    int r, c;
+    cell_of<NDIM>(k, i0, j0, i, j, r, c);
+    valid = (NDIM == 1) ? (i < g.N1) : (i < g.N1 && j < g.N2);
+    if (!valid) return 0.0;
+    double v;
+    size_t gidx;
+    if constexpr (NDIM == 1) {
+        v = sm.tile[r + 2] + sc.c1 * (sm.h[r] - sm.h[r + 1]);
+        gidx = i;
+        if (i == 0) v += sc.src;
+    } else {
+        constexpr int W = kFTJ + 3;
+        const auto& s = sm.t;
+        v = s.tile[(r + 2) * W + c + 2] + sc.c1 * (s.h1[r * kFTJ + c] - s.h1[(r + 1) * kFTJ + c]) +
+            sc.c2 * (s.h2[r * (kFTJ + 1) + c] - s.h2[r * (kFTJ + 1) + c + 1]);
+        gidx = (size_t)i * g.N2 + j;
+        if (i == 0 && j == 0) v += sc.src;
     }
+    if (STAGE == 2) v = 0.5 * old[gidx] + 0.5 * v;
+    out[gidx] = v;
+    return v;
 }
 
-template <int NDIM>
-__global__ void __launch_bounds__(kFNT) k_fused(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
-                                                const double* t_out, double* rows, unsigned int* bar, int ntiles,
-                                                int tiles_x)
+template <int NDIM, bool ONE_TILE>
+__global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
+                                                   const double* t_out, double* rows, unsigned int* bar, int ntiles,
+                                                   int tiles_x)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
+    constexpr int CPT = TileShape<NDIM>::CELLS / kFNT;   // cells per thread per tile
     __shared__ Scal s;
-    __shared__ double sh[kFNT / 32 * NM];
+    __shared__ double red[kFNT * (NM + 1)];
+    __shared__ double red2[256];
+    __shared__ double res[NM];
     __shared__ double msum[NM];
     __shared__ int fail;
     __shared__ FusedSmem<NDIM> sm;
@@ -178,64 +263,99 @@ __global__ void __launch_bounds__(kFNT) k_fused(double* n, double* n1, Scal* S, 
     double* my_rows = blockIdx.x == 0 ? rows : nullptr;
     unsigned int gen = 0;
 
+    // moment weights of this thread's cells (one tile per block: fixed for the whole solve)
+    double wgt[ONE_TILE ? CPT : 1][ONE_TILE ? NM : 1];
+    if constexpr (ONE_TILE) {
+        int i0, j0;
+        tile_origin<NDIM>(blockIdx.x, tiles_x, i0, j0);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            int i, j, r, c;
+            cell_of<NDIM>(threadIdx.x + q * kFNT, i0, j0, i, j, r, c);
+            moment_weights<NDIM>(i, j, g, wgt[q]);
+        }
+    }
+
     fused_faces<NDIM>(n, blockIdx.x, tiles_x, g, sm, threadIdx.x, kFNT, BlockSync());
     __syncthreads();
     for (;;) {
-        // ---- stage 1: n1 = n + dt L(n) ----
-        {
-            const StageCoef sc = stage_coef<1>(s, g);
+#pragma unroll 1
+        for (int stage = 1; stage <= 2; ++stage) {
+            const StageCoef sc = stage == 1 ? stage_coef<1>(s, g) : stage_coef<2>(s, g);
+            const double* in = stage == 1 ? n : n1;
+            double* out = stage == 1 ? n1 : n;
             double m[NM];
 #pragma unroll
             for (int k = 0; k < NM; ++k) m[k] = 0.0;
-            fused_stage<1, NDIM, NM>(n, n, n1, ntiles, tiles_x, g, sc, m, sm);
-            double v[1] = {m[VIDX]};
-            block_sum<kFNT, 1>(v, sh);
-            if (threadIdx.x == 0) part1[(size_t)blockIdx.x * kMaxMom + VIDX] = v[0];
-            if (!grid_barrier(bar, gen, &fail)) break;
-            if (warp == 0) {
-                const double V1 = warp_sum_partials(part1, G, VIDX);
-                finish_stage1_warp(&s, K, V1);
-            } else {
-                fused_faces<NDIM>(n1, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, kFNT - 32, GroupSync());
+            for (int t = blockIdx.x; t < ntiles; t += G) {
+                if (t != (int)blockIdx.x) {
+                    fused_faces<NDIM>(in, t, tiles_x, g, sm, threadIdx.x, kFNT, BlockSync());
+                    __syncthreads();
+                }
+                int i0, j0;
+                tile_origin<NDIM>(t, tiles_x, i0, j0);
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    bool valid;
+                    int i, j;
+                    const double v = stage == 1 ? cell_update<1, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, g, sc, sm, valid, i, j)
+                                                : cell_update<2, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, g, sc, sm, valid, i, j);
+                    if (!valid) continue;
+                    double wl[NM];
+                    if constexpr (ONE_TILE) {
+#pragma unroll
+                        for (int k = 0; k < NM; ++k) wl[k] = wgt[q][k];
+                    } else {
+                        moment_weights<NDIM>(i, j, g, wl);
+                    }
+                    if (sc.moms) {
+#pragma unroll
+                        for (int k = 0; k < NM; ++k) m[k] += wl[k] * v;
+                    } else {
+                        m[VIDX] += wl[VIDX] * v;
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            if (s.done) break;
-        }
-        // ---- stage 2: n = n/2 + (n1 + dt L(n1))/2 ----
-        {
-            const StageCoef sc = stage_coef<2>(s, g);
-            double m[NM];
-#pragma unroll
-            for (int k = 0; k < NM; ++k) m[k] = 0.0;
-            fused_stage<2, NDIM, NM>(n1, n, n, ntiles, tiles_x, g, sc, m, sm);
+            double* pp = stage == 1 ? part1 : part2;
             if (sc.moms) {
-                block_sum<kFNT, NM>(m, sh);
-                if (threadIdx.x == 0)
-                    for (int k = 0; k < NM; ++k) part2[(size_t)blockIdx.x * kMaxMom + k] = m[k];
+                block_sum_smem<NM>(m, red, red2, res);
+                if (threadIdx.x < NM) pp[(size_t)blockIdx.x * kMaxMom + threadIdx.x] = res[threadIdx.x];
             } else {
-                double v[1] = {m[VIDX]};
-                block_sum<kFNT, 1>(v, sh);
-                if (threadIdx.x == 0) part2[(size_t)blockIdx.x * kMaxMom + VIDX] = v[0];
+                double v1[1] = {m[VIDX]};
+                block_sum_smem<1>(v1, red, red2, res);
+                if (threadIdx.x == 0) pp[(size_t)blockIdx.x * kMaxMom + VIDX] = res[0];
             }
             if (!grid_barrier(bar, gen, &fail)) break;
             if (warp == 0) {
                 if (sc.moms) {
-                    for (int k = 0; k < NM; ++k) {
-                        const double tot = warp_sum_partials(part2, G, k);
-                        if (threadIdx.x == 0) msum[k] = tot;
+                    int slots[NM];
+#pragma unroll
+                    for (int k = 0; k < NM; ++k) slots[k] = k;
+                    double tot[NM];
+                    warp_sum_partials<NM>(pp, G, slots, tot);
+                    if (threadIdx.x < NM) {
+#pragma unroll
+                        for (int k = 0; k < NM; ++k)
+                            if (threadIdx.x == k) msum[k] = tot[k];
                     }
                 } else {
-                    const double tot = warp_sum_partials(part2, G, VIDX);
-                    if (threadIdx.x == 0) msum[VIDX] = tot;
+                    const int slots[1] = {VIDX};
+                    double tot[1];
+                    warp_sum_partials<1>(pp, G, slots, tot);
+                    if (threadIdx.x == 0) msum[VIDX] = tot[0];
                 }
                 __syncwarp();
-                finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
+                if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
+                else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
             } else {
-                fused_faces<NDIM>(n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, kFNT - 32, GroupSync());
+                // faces of the next stage's input for this block's first tile
+                fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, kFNT - 32, GroupSync());
             }
             __syncthreads();
             if (s.done) break;
         }
+        if (s.done || fail) break;
     }
     if (threadIdx.x == 0 && fail) {
         S->status = PBE_ETIMEOUT;
@@ -264,16 +384,27 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     (void)n_out;
     int tiles_x;
     const int ntiles = fused_tiles(g->geo, &tiles_x);
-    const void* fn = g->geo.ndim == 1 ? (const void*)k_fused<1> : (const void*)k_fused<2>;
-    int occ = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFNT, 0);
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    const bool one = g->geo.ndim == 1 ? true : true;
+    const void* fn_multi = g->geo.ndim == 1 ? (const void*)k_fused<1, false> : (const void*)k_fused<2, false>;
+    const void* fn_one = g->geo.ndim == 1 ? (const void*)k_fused<1, true> : (const void*)k_fused<2, true>;
+    (void)one;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn_one, kFNT, 0);
     if (e != cudaSuccess) return e;
     int G = ntiles;
     if (G > occ * sms) G = occ * sms;
     if (2 * G > g->max_blocks) G = g->max_blocks / 2;
     if (G < 1) G = 1;
+    const void* fn = (G >= ntiles) ? fn_one : fn_multi;
+    if (fn == fn_multi) {
+        int occ2 = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fn_multi, kFNT, 0);
+        if (e != cudaSuccess) return e;
+        if (G > occ2 * sms) G = occ2 * sms;
+    }
     e = cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned int), g->stream);
     if (e != cudaSuccess) return e;
     void* args[] = {&g->d_n, &g->d_n1, &g->d_S, &g->kin, &g->geo, &g->d_part, &g->d_tout, &g->d_rows,
