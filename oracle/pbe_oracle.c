@@ -184,10 +184,15 @@ long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, do
 /* forward pass.                                                        */
 /* ------------------------------------------------------------------ */
 
-/* partial derivatives of psi(a, b) = 2ab/(a+b) on its smooth branch */
+/* partial derivatives of psi(a, b) = 2ab/(a+b) on its smooth branch.
+ * Differences below 2^-959 in magnitude (values far below any physical
+ * density, where the ratio b/(a+b) is decided by rounding of underflowing
+ * tails) count as flat: derivative 0 (the subgradient convention the GPU
+ * adjoint shares). */
+#define PSI_FLAT 1.0316916532478883e-289  /* 2^-959 */
 static void psi_grad(double a, double b, double* pa, double* pb)
 {
-    if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
+    if (((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) && fabs(a) >= PSI_FLAT && fabs(b) >= PSI_FLAT) {
         double qa = b / (a + b), qb = a / (a + b);  /* ratios in (0, 1): no underflow in the tails */
         *pa = 2.0 * qa * qa;
         *pb = 2.0 * qb * qb;

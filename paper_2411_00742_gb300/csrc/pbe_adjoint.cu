@@ -73,9 +73,13 @@ __device__ __forceinline__ FaceAdj face_adj(double nm2, double up, double dn, do
     if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
         const double s = a + b;
         const double qa = b / s, qb = a / s;
-        pa = 2.0 * qa * qa;
-        pb = 2.0 * qb * qb;
         half = a * qa;
+        // differences below 2^-959 count as flat for the derivative (their
+        // ratio is decided by rounding of underflowing tails)
+        if (fabs(a) >= 1.0316916532478883e-289 && fabs(b) >= 1.0316916532478883e-289) {
+            pa = 2.0 * qa * qa;
+            pb = 2.0 * qb * qb;
+        }
     }
     const double mu = (lamR - lamL) * invd;
     FaceAdj r;

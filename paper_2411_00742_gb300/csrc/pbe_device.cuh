@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "pbe.h"
+#include "pbe_math.cuh"
 
 namespace pbe {
 
@@ -247,11 +248,11 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
         G1 = 0.0; G2 = 0.0; B = 0.0;
         return;
     }
-    const double lx = log(lane == 0 ? d : cs);
+    const double lx = pbe_log(lane == 0 ? d : cs);
     const double L = __shfl_sync(0xffffffffu, lx, 0) - __shfl_sync(0xffffffffu, lx, 1);
     const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
     const double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
-    const double e = exp(fma(p, L, q));
+    const double e = pbe_exp(fma(p, L, q));
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
     B = __shfl_sync(0xffffffffu, e, 2);

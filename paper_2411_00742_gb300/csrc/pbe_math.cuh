@@ -1,0 +1,139 @@
+// Short-latency FP64 exp and log for the scalar kinetics chain.
+//
+// On GB300 every dependent FP64 operation costs ~65 cycles, so the latency
+// of the scalar chain between stages is set by the depth of the dependency
+// graph of exp/log.  These are written from the textbook constructions:
+//   exp: Cody-Waite reduction x = k ln2 + r (|r| <= ln2/2, ln2 split in a
+//        high part with trailing zero bits and a low part), exp(r) by its
+//        Taylor polynomial of degree 13 evaluated with Estrin's scheme, and
+//        the scale 2^k written into the exponent field;
+//   log: x = 2^e m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(z),
+//        z = (m-1)/(m+1), by the odd Taylor series of atanh to z^23 (Estrin
+//        in w = z^2), plus e ln2.
+// Relative error is a few units of 2^-53 on the arguments the kinetics use
+// (checked against the C library on the host by the tests).  Arguments
+// outside the handled ranges (non-positive or non-finite log input, exp of
+// |x| > 700) return the IEEE limits of the function.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace pbe {
+
+__host__ __device__ __forceinline__ double pbe_bits_to_double(int64_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+#endif
+}
+
+__host__ __device__ __forceinline__ int64_t pbe_double_to_bits(double d)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(d);
+#else
+    int64_t b;
+    memcpy(&b, &d, sizeof(b));
+    return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double pbe_fma(double a, double b, double c)
+{
+#ifdef __CUDA_ARCH__
+    return __fma_rn(a, b, c);
+#else
+    return __builtin_fma(a, b, c);
+#endif
+}
+
+__host__ __device__ inline double pbe_exp(double x)
+{
+    if (!(x > -700.0)) return x != x ? x : 0.0;   // NaN stays NaN
+    if (x > 700.0) return __builtin_huge_val();
+    const double log2e = 1.4426950408889634;
+    const double ln2_hi = 6.93147180369123816490e-01;   // 0x3fe62e42fee00000
+    const double ln2_lo = 1.90821492927058770002e-10;   // ln2 - ln2_hi
+    const double shifter = 6755399441055744.0;            // 1.5 * 2^52: rounds to an integer
+    const double t = pbe_fma(x, log2e, shifter);
+    const double kd = t - shifter;
+    const int k = (int)(pbe_double_to_bits(t) & 0xffffffff) - (int)(pbe_double_to_bits(shifter) & 0xffffffff);
+    double r = pbe_fma(-kd, ln2_hi, x);
+    r = pbe_fma(-kd, ln2_lo, r);
+    // Taylor coefficients 1/i!, i = 0..13
+    const double c0 = 1.0, c1 = 1.0, c2 = 0.5, c3 = 1.6666666666666666e-01, c4 = 4.1666666666666664e-02,
+                 c5 = 8.3333333333333332e-03, c6 = 1.3888888888888889e-03, c7 = 1.9841269841269841e-04,
+                 c8 = 2.4801587301587302e-05, c9 = 2.7557319223985893e-06, c10 = 2.7557319223985888e-07,
+                 c11 = 2.5052108385441720e-08, c12 = 2.0876756987868100e-09, c13 = 1.6059043836821613e-10;
+    const double r2 = r * r, r4 = r2 * r2, r8 = r4 * r4;
+    const double p01 = pbe_fma(c1, r, c0), p23 = pbe_fma(c3, r, c2), p45 = pbe_fma(c5, r, c4),
+                 p67 = pbe_fma(c7, r, c6), p89 = pbe_fma(c9, r, c8), p1011 = pbe_fma(c11, r, c10),
+                 p1213 = pbe_fma(c13, r, c12);
+    const double q03 = pbe_fma(p23, r2, p01), q47 = pbe_fma(p67, r2, p45), q811 = pbe_fma(p1011, r2, p89);
+    const double q07 = pbe_fma(q47, r4, q03), q813 = pbe_fma(p1213, r4, q811);
+    const double p = pbe_fma(q813, r8, q07);
+    // 2^k split in two factors so that k down to -1074 and up to 1023 stay exact
+    const int k1 = k / 2, k2 = k - k1;
+    const double s1 = pbe_bits_to_double((int64_t)(k1 + 1023) << 52);
+    const double s2 = pbe_bits_to_double((int64_t)(k2 + 1023) << 52);
+    return (p * s1) * s2;
+}
+
+__host__ __device__ inline double pbe_log(double x)
+{
+    if (!(x > 0.0) || x == __builtin_huge_val()) {
+        if (x == 0.0) return -__builtin_huge_val();
+        if (x == __builtin_huge_val()) return x;
+        return (x - x) / (x - x);   // NaN for negative or NaN input
+    }
+    int64_t b = pbe_double_to_bits(x);
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) {                    // subnormal: scale into the normal range
+        x *= 18014398509481984.0;    // 2^54
+        b = pbe_double_to_bits(x);
+        e = (int)((b >> 52) & 0x7ff) - 54;
+    }
+    e -= 1023;
+    double m = pbe_bits_to_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);   // [1, 2)
+    if (m > 1.4142135623730951) {
+        m *= 0.5;
+        e += 1;
+    }
+    const double f = m - 1.0;
+    const double s = 2.0 + f;
+    double z;
+#ifdef __CUDA_ARCH__
+    {
+        double rc;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rc) : "d"(s));
+        rc = pbe_fma(rc, pbe_fma(-s, rc, 1.0), rc);   // one Newton-Raphson step on 1/s
+        const double q0 = f * rc;
+        z = pbe_fma(rc, pbe_fma(-s, q0, f), q0);      // and one on the quotient
+    }
+#else
+    z = f / s;
+#endif
+    const double w = z * z;
+    // 2 atanh(z) = 2 z (1 + w/3 + w^2/5 + ... + w^11/23)
+    const double a0 = 1.0, a1 = 1.0 / 3, a2 = 1.0 / 5, a3 = 1.0 / 7, a4 = 1.0 / 9, a5 = 1.0 / 11, a6 = 1.0 / 13,
+                 a7 = 1.0 / 15, a8 = 1.0 / 17, a9 = 1.0 / 19, a10 = 1.0 / 21, a11 = 1.0 / 23;
+    const double w2 = w * w, w4 = w2 * w2, w8 = w4 * w4;
+    const double p01 = pbe_fma(a1, w, a0), p23 = pbe_fma(a3, w, a2), p45 = pbe_fma(a5, w, a4),
+                 p67 = pbe_fma(a7, w, a6), p89 = pbe_fma(a9, w, a8), p1011 = pbe_fma(a11, w, a10);
+    const double q03 = pbe_fma(p23, w2, p01), q47 = pbe_fma(p67, w2, p45), q811 = pbe_fma(p1011, w2, p89);
+    const double q07 = pbe_fma(q47, w4, q03);
+    const double P = pbe_fma(q811, w8, q07);
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double ed = (double)e;
+    const double two_z = z + z;
+    // e ln2 + 2 z P, with the small terms first
+    return pbe_fma(ed, ln2_hi, pbe_fma(two_z, P, ed * ln2_lo));
+}
+
+}  // namespace pbe
