@@ -268,6 +268,49 @@ def run_gpu(args):
                 "unit": "cell-steps/s",
                 "plain_per_instance": {"value": g_cells / g_time, "sample": "first 64 instances, one grid each"}}
 
+    def adjoint_leg():
+        """Gradients of the relative-error loss (50 loss times, target = kinetics x1.1) with
+        respect to the kinetic parameters: (a) 2-D 128x128 grid, (b) 1-D 500-cell instances.
+        One gradient = forward with checkpoints every 64 steps + reverse sweep."""
+        out = {}
+        for name, inst, cols in (("2d_128x128", pi.adjoint_2d(128), [1, 2, 3, 9, 11]),
+                                 ("1d_500", pi.adjoint_batch_1d(16)[0], [1, 2, 3, 4, 5])):
+            p = inst.problem
+            tgt = oracle.solve(p.with_theta(p.theta * pi.TARGET_FACTOR), inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+            g = P.Grid.from_problem(p, stream=stream)
+            n0d = torch.as_tensor(inst.n0).cuda()
+            seeds = torch.zeros((len(inst.t_out), P.ncols(p.ndim)), dtype=torch.float64, device="cuda")
+            rows = torch.zeros_like(seeds)
+            tgt_t = torch.as_tensor(tgt).cuda()
+            times = []
+            with torch.cuda.stream(stream):
+                for it in range(args.warmup + max(3, args.steps // 2)):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    g.set_state(n0d, inst.C0, 0.0)
+                    e0.record(stream)
+                    g.solve(inst.t_out, out=rows)
+                    sd = torch.zeros_like(rows)
+                    sd[:, cols] = 2.0 * (rows[:, cols] - tgt_t[:, cols]) / tgt_t[:, cols] ** 2
+                    g.set_state(n0d, inst.C0, 0.0)
+                    dth, _, _ = g.vjp(inst.t_out, sd, 64)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if it >= args.warmup:
+                        times.append(e0.elapsed_time(e1) * 1e-3)
+            g.close()
+            tg = sum(times) / len(times)
+            r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+            want, _, _ = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, oracle.relative_loss_seeds(r, tgt, cols))
+            idx = [0, 1, 4, 5] if p.ndim == 1 else list(range(6))
+            err = float(np.max(np.abs(dth[idx] - want[idx]) / np.abs(want[idx])))
+            t0 = time.perf_counter()
+            oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, oracle.relative_loss_seeds(r, tgt, cols))
+            tc = time.perf_counter() - t0
+            out[name] = {"grads_per_s": 1.0 / tg, "ms_per_grad": 1e3 * tg, "max_rel_err_vs_cpu_adjoint": err,
+                         "cpu_adjoint_grads_per_s": 1.0 / tc, "checkpoint_every": 64}
+        return out
+
     clocks = ClockSampler(dev)
     if ws > 1:
         torch.distributed.barrier()
@@ -278,6 +321,7 @@ def run_gpu(args):
     clk = clocks.stop()
     e2e_rate, h2d, d2h = e2e("fused")
     batch = batch_leg() if not args.no_batch else None
+    adjoint = adjoint_leg() if not args.no_adjoint else None
 
     if ws > 1:
         import torch.distributed as dist
@@ -306,6 +350,7 @@ def run_gpu(args):
         "e2e": {"value": ws * e2e_rate, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         # prologue + one persistent kernel per fused solve, timed steps only
         "batch_1d": batch,
+        "adjoint": adjoint,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
@@ -329,6 +374,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
