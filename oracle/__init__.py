@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
                 ("kb", ctypes.c_double), ("b", ctypes.c_double),
                 ("cs0", ctypes.c_double), ("cs1", ctypes.c_double), ("cs2", ctypes.c_double),
                 ("T0", ctypes.c_double), ("T1", ctypes.c_double), ("t_cool", ctypes.c_double),
-                ("kappa", ctypes.c_double), ("cfl", ctypes.c_double)]
+                ("kappa", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("mlp", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -72,6 +73,7 @@ def _load():
         lib.orc_temperature.restype = ctypes.c_double
         lib.orc_temperature.argtypes = [P, ctypes.c_double]
         lib.orc_kinetics.argtypes = [P, ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_kinetics_mlp.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
         lib.orc_timestep.restype = ctypes.c_int
         lib.orc_timestep.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, _D]
@@ -88,21 +90,35 @@ def _load():
                                      ctypes.c_double, _D, ctypes.c_int, _D, _D]
         lib.orc_vjp.restype = ctypes.c_long
         lib.orc_vjp.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
-                                _D, _D, _D, _D]
+                                _D, _D, _D, _D, _D]
         _lib = lib
     return _lib
 
 
-def params(problem) -> Params:
+MLP_NW = 64 * 3 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # learned closure weight count
+_mlp_keep = {}
+
+
+def params(problem, mlp=None) -> Params:
+    """ctypes parameter block; mlp = flat float64 weights of the learned closure
+    (layout W1[64][3], b1, W2[64][64], b2, W3[3][64], b3) or None."""
     p = problem
     n2 = p.ncells[1] if p.ndim == 2 else 1
     l2 = p.lmax[1] if p.ndim == 2 else 1.0
-    return Params(p.ndim, int(p.ncells[0]), int(n2), float(p.lmax[0]), float(l2),
-                  int(bool(p.fixed_kinetics)),
-                  float(p.kg[0]), float(p.g[0]), float(p.kg[1]), float(p.g[1]),
-                  float(p.kb), float(p.b),
-                  float(p.csat[0]), float(p.csat[1]), float(p.csat[2]),
-                  float(p.T0), float(p.T1), float(p.t_cool), float(p.kappa), float(p.cfl))
+    mp = None
+    if mlp is not None:
+        arr = np.ascontiguousarray(mlp, dtype=np.float64)
+        assert arr.size == MLP_NW
+        _mlp_keep[id(arr)] = arr
+        mp = arr.ctypes.data_as(_D)
+    P = Params(p.ndim, int(p.ncells[0]), int(n2), float(p.lmax[0]), float(l2),
+               int(bool(p.fixed_kinetics)),
+               float(p.kg[0]), float(p.g[0]), float(p.kg[1]), float(p.g[1]),
+               float(p.kb), float(p.b),
+               float(p.csat[0]), float(p.csat[1]), float(p.csat[2]),
+               float(p.T0), float(p.T1), float(p.t_cool), float(p.kappa), float(p.cfl), mp)
+    P._keep = arr if mlp is not None else None
+    return P
 
 
 def _ptr(a: np.ndarray):
@@ -182,7 +198,7 @@ def step(problem, n, C: float, t: float, t_next: float):
     return n, dict(dt=out[0], C=out[1], t=out[2], C1=out[3], clipped=bool(out[4]))
 
 
-def solve(problem, n0, C0: float, t0: float, t_out):
+def solve(problem, n0, C0: float, t0: float, t_out, mlp=None):
     """March through the output times.  Returns dict(rows, n, C, t, steps).
 
     rows[j] = (t, mu0..mu3, C) in 1-D and (t, mu00, mu10, mu01, mu20, mu11,
@@ -190,7 +206,7 @@ def solve(problem, n0, C0: float, t0: float, t_out):
     t_out = np.ascontiguousarray(t_out, dtype=np.float64)
     if len(t_out) and (t_out[0] < t0 or np.any(np.diff(t_out) <= 0)):
         raise ValueError("t_out must be increasing and start at or after t0")
-    P = params(problem)
+    P = params(problem, mlp)
     n = np.array(n0, dtype=np.float64, order="C", copy=True)
     rows = np.zeros((len(t_out), ncols(problem)))
     st = np.zeros(2)
@@ -199,11 +215,12 @@ def solve(problem, n0, C0: float, t0: float, t_out):
     return dict(rows=rows, n=n, C=st[0], t=st[1], steps=int(steps))
 
 
-def solve_cs(problem, which: int, n0, C0: float, t0: float, t_out, h: float = 1e-30):
+def solve_cs(problem, which: int, n0, C0: float, t0: float, t_out, h: float = 1e-30, mlp=None):
     """Complex-step derivative of all output rows w.r.t. kinetic parameter
-    ``which`` (0..5 = kg1, g1, kg2, g2, kb, b).  Returns (rows, drows)."""
+    ``which`` (0..5 = kg1, g1, kg2, g2, kb, b; 6 + k = closure weight k).
+    Returns (rows, drows)."""
     t_out = np.ascontiguousarray(t_out, dtype=np.float64)
-    P = params(problem)
+    P = params(problem, mlp)
     n0 = np.ascontiguousarray(n0, dtype=np.float64)
     rows = np.zeros((len(t_out), ncols(problem)))
     drows = np.zeros_like(rows)
@@ -216,20 +233,32 @@ def solve_instance(inst):
     return solve(inst.problem, inst.n0, inst.C0, inst.t0, inst.t_out)
 
 
-def vjp(problem, n0, C0: float, t0: float, t_out, drows):
+def vjp(problem, n0, C0: float, t0: float, t_out, drows, mlp=None):
     """Hand-written discrete adjoint: dL/dtheta (kg1, g1, kg2, g2, kb, b), dL/dn0, dL/dC0
-    for seeds drows = dL/d(rows) (time column ignored)."""
+    (and dL/dweights of the learned closure when mlp is given) for seeds
+    drows = dL/d(rows) (time column ignored)."""
     t_out = np.ascontiguousarray(t_out, dtype=np.float64)
     drows = np.ascontiguousarray(drows, dtype=np.float64)
     assert drows.shape == (len(t_out), ncols(problem))
-    P = params(problem)
+    P = params(problem, mlp)
     n0 = np.ascontiguousarray(n0, dtype=np.float64)
     dth = np.zeros(6)
     dn0 = np.zeros_like(n0)
     dC0 = np.zeros(1)
+    dW = np.zeros(MLP_NW)
     _load().orc_vjp(ctypes.byref(P), _ptr(n0), float(C0), float(t0), _ptr(t_out), len(t_out),
-                    _ptr(drows), _ptr(dth), _ptr(dn0), _ptr(dC0))
+                    _ptr(drows), _ptr(dth), _ptr(dn0), _ptr(dC0), _ptr(dW))
+    if mlp is not None:
+        return dth, dn0, dC0[0], dW
     return dth, dn0, dC0[0]
+
+
+def kinetics_mlp(problem, mlp, C: float, t: float, ratio: float):
+    """(G1, G2, B) of the learned closure at concentration C, time t and moment ratio V/mu0."""
+    P = params(problem, mlp)
+    out = np.zeros(3)
+    _load().orc_kinetics_mlp(ctypes.byref(P), float(C), float(t), float(ratio), _ptr(out))
+    return tuple(out)
 
 
 def relative_loss(rows, target, cols):

@@ -39,46 +39,63 @@ typedef struct {
     double T0, T1, t_cool;
     double kappa;         /* rho_c k_v u */
     double cfl;
+    const double* mlp;    /* learned closure weights (NULL: power law / fixed) */
 } orc_params;
+
+/* Learned kinetics closure (the empirical hybrid model of Sec. 4.2: a network
+ * replaces the growth and nucleation rate expressions inside the solver):
+ * a 3 -> 64 -> 64 -> 3 perceptron with SiLU hidden units.  Inputs (fixed
+ * affine maps): x0 = 4 (S - 1), x1 = (T - 25) / 10, x2 = 1e-6 V / mu0 with V
+ * the volume moment (mu3 in 1-D, mu12 in 2-D).  Outputs: ln G1 = o0 + ln 0.01,
+ * ln G2 = o1 + ln 0.005, ln B = o2 + ln 1e5; G = B = 0 for S <= 1.
+ * Weight layout: W1[64][3], b1[64], W2[64][64], b2[64], W3[3][64], b3[3]. */
+#define MLP_H 64
+#define MLP_NW (MLP_H * 3 + MLP_H + MLP_H * MLP_H + MLP_H + 3 * MLP_H + 3)
 
 /* ---------------- real instance ---------------- */
 typedef struct {
     double dt, C, C1, t, t_new;
     double G1a, G2a, Ba, G1b, G2b, Bb;
+    double r0, r1;  /* moment ratios V/mu0 the closure saw at each stage */
     int clipped, out_index;
 } steprec_r;
 #define SCALAR double
 #define SFX(x) x##_r
 #define RE(x) (x)
 #define SPOW pow
+#define SEXP exp
 #include "pbe_oracle_core.h"
 #undef SCALAR
 #undef SFX
 #undef RE
 #undef SPOW
+#undef SEXP
 
 /* ---------------- complex instance (complex-step derivatives) ---------------- */
 typedef struct {
     double complex dt, C, C1, t, t_new;
     double complex G1a, G2a, Ba, G1b, G2b, Bb;
+    double complex r0, r1;
     int clipped, out_index;
 } steprec_c;
 #define SCALAR double complex
 #define SFX(x) x##_c
 #define RE(x) creal(x)
 #define SPOW cpow
+#define SEXP cexp
 #include "pbe_oracle_core.h"
 #undef SCALAR
 #undef SFX
 #undef RE
 #undef SPOW
+#undef SEXP
 
 static size_t ncells(const orc_params* p) { return (size_t)p->n1 * (p->ndim == 2 ? p->n2 : 1); }
 static int ncols(const orc_params* p) { return p->ndim == 1 ? 6 : 12; }
 
 static ctx_r make_ctx_r(const orc_params* p)
 {
-    ctx_r c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b};
+    ctx_r c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b, p->mlp};
     return c;
 }
 
@@ -93,7 +110,14 @@ double orc_temperature(const orc_params* p, double t) { return temperature_r(p, 
 void orc_kinetics(const orc_params* p, double C, double t, double* out3)
 {
     ctx_r c = make_ctx_r(p);
-    kinetics_r(&c, C, t, out3, out3 + 1, out3 + 2);
+    kinetics_r(&c, C, t, 0.0, out3, out3 + 1, out3 + 2);
+}
+
+/* learned closure at (C, t) with moment ratio V / mu0 */
+void orc_kinetics_mlp(const orc_params* p, double C, double t, double ratio, double* out3)
+{
+    ctx_r c = make_ctx_r(p);
+    kinetics_r(&c, C, t, ratio, out3, out3 + 1, out3 + 2);
 }
 
 /* out2 = {dt, t_new}; returns 1 if clipped at t_next */
@@ -158,9 +182,16 @@ long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, do
 {
     size_t nc = ncells(p);
     int ncol = ncols(p);
-    ctx_c c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b};
+    ctx_c c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b, NULL};
     double complex* slot[6] = {&c.kg1, &c.g1, &c.kg2, &c.g2, &c.kb, &c.b};
-    *slot[which] += I * h;
+    double complex* wc = NULL;
+    if (p->mlp) {
+        wc = (double complex*)malloc(MLP_NW * sizeof(double complex));
+        for (int k = 0; k < MLP_NW; ++k) wc[k] = p->mlp[k];
+        c.w = wc;
+    }
+    if (which < 6) *slot[which] += I * h;
+    else wc[which - 6] += I * h;
     double complex* n = (double complex*)malloc(nc * sizeof(double complex));
     double complex* rows = (double complex*)malloc((size_t)n_out * ncol * sizeof(double complex));
     for (size_t k = 0; k < nc; ++k) n[k] = n0[k];
@@ -170,7 +201,7 @@ long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, do
         rows_re[k] = creal(rows[k]);
         drows[k] = cimag(rows[k]) / h;
     }
-    free(n); free(rows);
+    free(n); free(rows); free(wc);
     return steps;
 }
 
@@ -319,11 +350,93 @@ static void kinetics_adjoint(const orc_params* p, double C, double t, double lG1
     *lt += lsum * (-C * dcs / (cs * cs)) * dTdt;
 }
 
+static double silu_grad(double z)
+{
+    double sg = 1.0 / (1.0 + exp(-z));
+    return sg * (1.0 + z * (1.0 - sg));
+}
+
+/* adjoint of the learned closure at (C, t, ratio): accumulates lC, lt, the
+ * adjoint of the moment ratio, and dL/dweights into dW (layout of the weights) */
+static void mlp_kinetics_adjoint(const orc_params* p, double C, double t, double ratio, double lG1, double lG2,
+                                 double lB, double* lC, double* lt, double* lratio, double* dW)
+{
+    double T = temperature_r(p, t);
+    double dTdt = (t < p->t_cool) ? (p->T1 - p->T0) / p->t_cool : 0.0;
+    double cs = p->cs0 + p->cs1 * T + p->cs2 * T * T;
+    double dcs = p->cs1 + 2.0 * p->cs2 * T;
+    double s = C / cs - 1.0;
+    if (!(s > 0.0)) return;
+    const double* w = p->mlp;
+    const double* W1 = w;
+    const double* b1 = W1 + MLP_H * 3;
+    const double* W2 = b1 + MLP_H;
+    const double* b2 = W2 + MLP_H * MLP_H;
+    const double* W3 = b2 + MLP_H;
+    const double* b3 = W3 + 3 * MLP_H;
+    double* dW1 = dW;
+    double* db1 = dW1 + MLP_H * 3;
+    double* dW2 = db1 + MLP_H;
+    double* db2 = dW2 + MLP_H * MLP_H;
+    double* dW3 = db2 + MLP_H;
+    double* db3 = dW3 + 3 * MLP_H;
+    double x[3] = {4.0 * s, (T - 25.0) / 10.0, 1e-6 * ratio};
+    double z1[MLP_H], a1[MLP_H], z2[MLP_H], a2[MLP_H], o[3];
+    for (int h = 0; h < MLP_H; ++h) {
+        z1[h] = b1[h] + W1[h * 3] * x[0] + W1[h * 3 + 1] * x[1] + W1[h * 3 + 2] * x[2];
+        a1[h] = silu_r(z1[h]);
+    }
+    for (int h = 0; h < MLP_H; ++h) {
+        double z = b2[h];
+        for (int j = 0; j < MLP_H; ++j) z += W2[h * MLP_H + j] * a1[j];
+        z2[h] = z;
+        a2[h] = silu_r(z);
+    }
+    for (int m = 0; m < 3; ++m) {
+        double z = b3[m];
+        for (int h = 0; h < MLP_H; ++h) z += W3[m * MLP_H + h] * a2[h];
+        o[m] = z;
+    }
+    double lo[3] = {lG1 * exp(o[0] + log(0.01)), p->ndim == 2 ? lG2 * exp(o[1] + log(0.005)) : 0.0,
+                    lB * exp(o[2] + log(1e5))};
+    double la2[MLP_H], lz2[MLP_H], la1[MLP_H], lz1[MLP_H], lx[3] = {0, 0, 0};
+    for (int h = 0; h < MLP_H; ++h) la2[h] = 0.0;
+    for (int m = 0; m < 3; ++m) {
+        db3[m] += lo[m];
+        for (int h = 0; h < MLP_H; ++h) {
+            dW3[m * MLP_H + h] += lo[m] * a2[h];
+            la2[h] += W3[m * MLP_H + h] * lo[m];
+        }
+    }
+    for (int h = 0; h < MLP_H; ++h) lz2[h] = la2[h] * silu_grad(z2[h]);
+    for (int j = 0; j < MLP_H; ++j) la1[j] = 0.0;
+    for (int h = 0; h < MLP_H; ++h) {
+        db2[h] += lz2[h];
+        for (int j = 0; j < MLP_H; ++j) {
+            dW2[h * MLP_H + j] += lz2[h] * a1[j];
+            la1[j] += W2[h * MLP_H + j] * lz2[h];
+        }
+    }
+    for (int h = 0; h < MLP_H; ++h) {
+        lz1[h] = la1[h] * silu_grad(z1[h]);
+        db1[h] += lz1[h];
+        for (int k = 0; k < 3; ++k) {
+            dW1[h * 3 + k] += lz1[h] * x[k];
+            lx[k] += W1[h * 3 + k] * lz1[h];
+        }
+    }
+    double lS = 4.0 * lx[0];
+    double lT = lx[1] / 10.0 - lS * C * dcs / (cs * cs);
+    *lC += lS / cs;
+    *lt += lT * dTdt;
+    *lratio += 1e-6 * lx[2];
+}
+
 /* Vector-Jacobian product of a solve.  drows[n_out * ncol]: dL/d(row entries)
  * (the time column is ignored).  Outputs dL/dtheta[6] (kg1, g1, kg2, g2, kb, b),
  * and optionally dL/dn0 (ncell) and dL/dC0.  Returns the number of steps. */
 long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const double* t_out, int n_out,
-             const double* drows, double* dtheta, double* dn0, double* dC0)
+             const double* drows, double* dtheta, double* dn0, double* dC0, double* dmlp)
 {
     size_t nc = ncells(p);
     int ncol = ncols(p), nm = ncol - 2;
@@ -380,7 +493,14 @@ long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const 
         double lG1 = r->dt * P[0], lG2 = r->dt * P[1], lB = r->dt * P[2] / area;
         /* kinetics at (C1, t') */
         double lC1 = 0.0, ltn = lt;
-        kinetics_adjoint(p, r->C1, r->t_new, lG1, lG2, lB, &lC1, &ltn, lth);
+        if (p->mlp) {
+            double lr = 0.0;
+            mlp_kinetics_adjoint(p, r->C1, r->t_new, r->r1, lG1, lG2, lB, &lC1, &ltn, &lr, dmlp);
+            double m0 = mu0_r(p, n1), V1 = volume_r(p, n1);
+            for (size_t q = 0; q < nc; ++q) lam1[q] += (lr / m0) * w[q] - (lr * V1 / (m0 * m0)) * area;
+        } else {
+            kinetics_adjoint(p, r->C1, r->t_new, lG1, lG2, lB, &lC1, &ltn, lth);
+        }
         /* C1 = C - kappa (V1 - V0) */
         lCp += lC1;
         lV0 += p->kappa * lC1;
@@ -405,7 +525,14 @@ long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const 
             ltp = -ldt;
         }
         /* kinetics at (C, t) */
-        kinetics_adjoint(p, r->C, r->t, lG1, lG2, lB, &lCp, &ltp, lth);
+        if (p->mlp) {
+            double lr = 0.0;
+            mlp_kinetics_adjoint(p, r->C, r->t, r->r0, lG1, lG2, lB, &lCp, &ltp, &lr, dmlp);
+            double m0 = mu0_r(p, nk), V0 = volume_r(p, nk);
+            for (size_t q = 0; q < nc; ++q) lamp[q] += (lr / m0) * w[q] - (lr * V0 / (m0 * m0)) * area;
+        } else {
+            kinetics_adjoint(p, r->C, r->t, lG1, lG2, lB, &lCp, &ltp, lth);
+        }
         memcpy(lam, lamp, nc * sizeof(double));
         lC = lCp;
         lt = ltp;

@@ -30,7 +30,34 @@ static SCALAR SFX(psi)(SCALAR a, SCALAR b)
 typedef struct {
     const orc_params* p;
     SCALAR kg1, g1, kg2, g2, kb, b; /* kinetic parameters (differentiable) */
+    const SCALAR* w;                /* learned closure weights, NULL unless p->mlp */
 } SFX(ctx);
+
+static SCALAR SFX(silu)(SCALAR z) { return z / (1.0 + SEXP(-z)); }
+
+/* the closure's perceptron: o = W3 silu(W2 silu(W1 x + b1) + b2) + b3 */
+static void SFX(mlp_forward)(const SCALAR* w, const SCALAR* x, SCALAR* o)
+{
+    const SCALAR* W1 = w;
+    const SCALAR* b1 = W1 + MLP_H * 3;
+    const SCALAR* W2 = b1 + MLP_H;
+    const SCALAR* b2 = W2 + MLP_H * MLP_H;
+    const SCALAR* W3 = b2 + MLP_H;
+    const SCALAR* b3 = W3 + 3 * MLP_H;
+    SCALAR a1[MLP_H], a2[MLP_H];
+    for (int h = 0; h < MLP_H; ++h)
+        a1[h] = SFX(silu)(b1[h] + W1[h * 3] * x[0] + W1[h * 3 + 1] * x[1] + W1[h * 3 + 2] * x[2]);
+    for (int h = 0; h < MLP_H; ++h) {
+        SCALAR z = b2[h];
+        for (int j = 0; j < MLP_H; ++j) z = z + W2[h * MLP_H + j] * a1[j];
+        a2[h] = SFX(silu)(z);
+    }
+    for (int m = 0; m < 3; ++m) {
+        SCALAR z = b3[m];
+        for (int h = 0; h < MLP_H; ++h) z = z + W3[m * MLP_H + h] * a2[h];
+        o[m] = z;
+    }
+}
 
 /* Temperature of the linear cooling profile at time t. */
 static SCALAR SFX(temperature)(const orc_params* p, SCALAR t)
@@ -43,10 +70,26 @@ static SCALAR SFX(temperature)(const orc_params* p, SCALAR t)
  * S = c / c*(T) (Sec. 2.1); growth and nucleation only for S > 1
  * (Appendix A: growth "only applies when S exceeds one").
  * G_m = kg_m (S-1)^g_m, B = kb (S-1)^b. */
-static void SFX(kinetics)(const SFX(ctx)* c, SCALAR C, SCALAR t,
+static void SFX(kinetics)(const SFX(ctx)* c, SCALAR C, SCALAR t, SCALAR ratio,
                           SCALAR* G1, SCALAR* G2, SCALAR* B)
 {
     const orc_params* p = c->p;
+    if (c->w) {  /* learned closure */
+        SCALAR T = SFX(temperature)(p, t);
+        SCALAR csat = p->cs0 + p->cs1 * T + p->cs2 * T * T;
+        SCALAR s = C / csat - 1.0;
+        if (!(RE(s) > 0.0)) {
+            *G1 = 0.0; *G2 = 0.0; *B = 0.0;
+            return;
+        }
+        SCALAR x[3] = {4.0 * s, (T - 25.0) / 10.0, 1e-6 * ratio};
+        SCALAR o[3];
+        SFX(mlp_forward)(c->w, x, o);
+        *G1 = SEXP(o[0] + log(0.01));
+        *G2 = (p->ndim == 2) ? SEXP(o[1] + log(0.005)) : (SCALAR)0.0;
+        *B = SEXP(o[2] + log(1e5));
+        return;
+    }
     if (p->fixed_kinetics) {
         *G1 = c->kg1;
         *G2 = (p->ndim == 2) ? c->kg2 : (SCALAR)0.0;
@@ -159,6 +202,16 @@ static void SFX(rhs)(const orc_params* p, const SCALAR* n, SCALAR G1, SCALAR G2,
     else SFX(rhs2)(p, n, G1, G2, B, L);
 }
 
+/* zeroth moment mu0 = sum n dA */
+static SCALAR SFX(mu0)(const orc_params* p, const SCALAR* n)
+{
+    SCALAR v = 0.0;
+    size_t nc = (size_t)p->n1 * (p->ndim == 2 ? p->n2 : 1);
+    double dA = (p->ndim == 1) ? p->lmax1 / p->n1 : (p->lmax1 / p->n1) * (p->lmax2 / p->n2);
+    for (size_t k = 0; k < nc; ++k) v = v + n[k] * dA;
+    return v;
+}
+
 /* Crystal volume integral of Eq. 2 by the midpoint rule at cell centres
  * x_i = (i + 1/2) dL:  1-D  mu3 = sum x^3 n dL;  2-D  mu12 = sum x1 x2^2 n dL1 dL2. */
 static SCALAR SFX(volume)(const orc_params* p, const SCALAR* n)
@@ -228,17 +281,20 @@ static int SFX(step)(const SFX(ctx)* c, SCALAR* n, SCALAR* work, SCALAR* C, SCAL
     SCALAR G1a, G2a, Ba, G1b, G2b, Bb, dt, t_new;
 
     /* kinetics and time step from the state at the start of the step */
-    SFX(kinetics)(c, *C, *t, &G1a, &G2a, &Ba);
-    int clipped = SFX(timestep)(c, G1a, G2a, *t, t_next, &dt, &t_new);
     SCALAR V0 = SFX(volume)(p, n);
+    SCALAR r0 = c->w ? V0 / SFX(mu0)(p, n) : (SCALAR)0.0;
+    SFX(kinetics)(c, *C, *t, r0, &G1a, &G2a, &Ba);
+    int clipped = SFX(timestep)(c, G1a, G2a, *t, t_next, &dt, &t_new);
 
     /* stage 1: n1 = n + dt L(n); solute balance C1 = C - kappa (V(n1) - V(n)) */
     SFX(rhs)(p, n, G1a, G2a, Ba, L);
     for (size_t k = 0; k < nc; ++k) n1[k] = n[k] + dt * L[k];
-    SCALAR C1 = *C - p->kappa * (SFX(volume)(p, n1) - V0);
+    SCALAR V1 = SFX(volume)(p, n1);
+    SCALAR C1 = *C - p->kappa * (V1 - V0);
+    SCALAR r1 = c->w ? V1 / SFX(mu0)(p, n1) : (SCALAR)0.0;
 
     /* stage 2 with kinetics at (C1, t + dt); n_new = n/2 + (n1 + dt L(n1))/2 */
-    SFX(kinetics)(c, C1, t_new, &G1b, &G2b, &Bb);
+    SFX(kinetics)(c, C1, t_new, r1, &G1b, &G2b, &Bb);
     SFX(rhs)(p, n1, G1b, G2b, Bb, L);
     for (size_t k = 0; k < nc; ++k) n[k] = 0.5 * n[k] + 0.5 * (n1[k] + dt * L[k]);
     SCALAR C_new = *C - p->kappa * (SFX(volume)(p, n) - V0);
@@ -248,6 +304,7 @@ static int SFX(step)(const SFX(ctx)* c, SCALAR* n, SCALAR* work, SCALAR* C, SCAL
         rec->G1a = G1a; rec->G2a = G2a; rec->Ba = Ba;
         rec->G1b = G1b; rec->G2b = G2b; rec->Bb = Bb;
         rec->clipped = clipped;
+        rec->r0 = r0; rec->r1 = r1;
     }
     *C = C_new;
     *t = t_new;
