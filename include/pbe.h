@@ -54,6 +54,7 @@ typedef int pbe_status;
 /* kinetic models */
 #define PBE_KINETICS_POWER_LAW 0 /* G_d = kg[d] s^g[d], B = kb s^b, s = max(C/c*(T) - 1, 0) */
 #define PBE_KINETICS_FIXED 1     /* G_d = kg[d], B = kb, independent of S (tests)           */
+#define PBE_KINETICS_MLP 2       /* learned closure set by pbe_set_closure (plain path)      */
 
 /* execution paths of pbe_solve */
 #define PBE_PATH_PLAIN 0 /* two stage kernels per step, device-resident scalars, CUDA graph loop */
@@ -93,6 +94,18 @@ pbe_status pbe_set_path(pbe_grid* g, int path);
 /* Set the kinetic model (Sec. 2.1 S = c/c*; Appendix A growth law only for
  * S > 1).  Errors: PBE_EINVAL for kind, cfl not in (0, 1], t_cool <= 0. */
 pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k);
+
+/* Weights of the learned kinetics closure (the empirical hybrid model of
+ * Sec. 4.2: a network replaces the growth and nucleation expressions inside
+ * the solver), used when the kinetics kind is PBE_KINETICS_MLP.  A 3 -> 64 ->
+ * 64 -> 3 perceptron with SiLU hidden units: inputs x0 = 4 (S - 1),
+ * x1 = (T - 25)/10, x2 = 1e-6 V/mu0 (V = mu3 in 1-D, mu12 in 2-D); outputs
+ * ln G1 = o0 + ln 0.01, ln G2 = o1 + ln 0.005, ln B = o2 + ln 1e5; G = B = 0
+ * for S <= 1.  w: HOST float array of 4611 values in the layout W1[64][3],
+ * b1[64], W2[64][64], b2[64], W3[3][64], b3[3]; the weight matrices are stored
+ * rounded to bf16 (round to nearest even), the biases in fp32; arithmetic is
+ * fp32.  Solves with the closure run on the plain path. */
+pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count);
 
 /* Load the state: distribution n (ncell values, `mem` memory), solute
  * concentration C and time t.  Initial condition of Eqs. (5)-(9). */
@@ -138,10 +151,14 @@ pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
  *   dL_dn0             optional, ncell doubles (`mem` memory): d/d(initial n)
  *   dL_dC0             optional HOST double: d/d(initial C)
  *   rows               optional, the forward rows (`mem` memory)
+ *   dL_dweights        optional HOST, 4611 doubles: gradient with respect to the
+ *                      learned closure's weights (PBE_KINETICS_MLP; the layout
+ *                      of pbe_set_closure, taken at the stored bf16 values)
  * On return the grid holds the state at the end of the solve.  Allocates
  * work memory for the checkpoints; synchronizes the stream. */
 pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const double* seeds, int seeds_mem,
-                   int checkpoint_every, double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem);
+                   int checkpoint_every, double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem,
+                   double* dL_dweights);
 
 /* Upper bound on steps per pbe_solve call (default 1e6); exceeding it stops
  * the solve with PBE_ETIMEOUT. */

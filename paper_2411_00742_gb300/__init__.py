@@ -14,8 +14,10 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (PBE_KINETICS_FIXED, PBE_KINETICS_POWER_LAW, PBE_MEM_DEVICE, PBE_MEM_HOST,
+from ._lib import (PBE_KINETICS_FIXED, PBE_KINETICS_MLP, PBE_KINETICS_POWER_LAW, PBE_MEM_DEVICE, PBE_MEM_HOST,
                    PBE_PATH_FUSED, PBE_PATH_PLAIN, PbeError, Kinetics)
+
+CLOSURE_SIZE = 64 * 3 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # weights of the learned closure
 
 __all__ = ["Grid", "Batch", "PbeError", "kinetics_struct", "ncols"]
 
@@ -26,7 +28,7 @@ def ncols(ndim: int) -> int:
     return 6 if ndim == 1 else 12
 
 
-def kinetics_struct(problem, theta=None) -> Kinetics:
+def kinetics_struct(problem, theta=None, closure: bool = False) -> Kinetics:
     """pbe_kinetics from any object with the fields of a problem description
     (kg, g, kb, b, csat, T0, T1, t_cool, kappa, cfl, fixed_kinetics);
     theta = (kg1, g1, kg2, g2, kb, b) overrides the kinetic parameters."""
@@ -36,6 +38,8 @@ def kinetics_struct(problem, theta=None) -> Kinetics:
         theta = (problem.kg[0], problem.g[0], problem.kg[1], problem.g[1], problem.kb, problem.b)
     th = [float(v) for v in theta]
     k.kg[0], k.g[0], k.kg[1], k.g[1], k.kb, k.b = th
+    if closure:
+        k.kind = PBE_KINETICS_MLP
     for i in range(3):
         k.csat[i] = float(problem.csat[i])
     k.T0, k.T1, k.t_cool = float(problem.T0), float(problem.T1), float(problem.t_cool)
@@ -108,8 +112,16 @@ class Grid:
     def set_max_steps(self, n: int):
         _lib.check(self.lib.pbe_set_max_steps(self.h, int(n)))
 
-    def set_kinetics(self, problem, theta=None):
-        k = kinetics_struct(problem, theta)
+    def set_closure(self, weights):
+        """Weights of the learned kinetics closure (flat float32, layout W1, b1, W2, b2, W3, b3);
+        the matrices are stored as bf16."""
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        if w.size != CLOSURE_SIZE:
+            raise ValueError(f"the closure has {CLOSURE_SIZE} weights")
+        _lib.check(self.lib.pbe_set_closure(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size))
+
+    def set_kinetics(self, problem, theta=None, closure: bool = False):
+        k = kinetics_struct(problem, theta, closure)
         _lib.check(self.lib.pbe_set_kinetics(self.h, ctypes.byref(k)))
 
     def set_state(self, n, C: float, t: float):
@@ -143,9 +155,11 @@ class Grid:
                                       len(t_out), p, mem, ctypes.byref(steps)))
         return out, steps.value
 
-    def vjp(self, t_out, seeds, checkpoint_every: int = 64, dn0_out=None, rows_out=None):
+    def vjp(self, t_out, seeds, checkpoint_every: int = 64, dn0_out=None, rows_out=None, dweights_out=None):
         """Gradient of a scalar loss of the rows of solve(t_out) from the current
-        state, given seeds = dL/drows.  Returns (dL/dtheta[6], dL/dn0 or None, dL/dC0)."""
+        state, given seeds = dL/drows.  Returns (dL/dtheta[6], dL/dn0 or None, dL/dC0);
+        with the learned closure, dweights_out (float64, CLOSURE_SIZE) receives
+        dL/dweights."""
         t_out = np.ascontiguousarray(t_out, dtype=np.float64)
         sp, smem, skeep = _buf(seeds)
         dth = np.zeros(6)
@@ -163,7 +177,9 @@ class Grid:
         _lib.check(self.lib.pbe_vjp(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t_out),
                                     sp, smem, int(checkpoint_every),
                                     dth.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dn_p,
-                                    ctypes.byref(dC0), rows_p, mem))
+                                    ctypes.byref(dC0), rows_p, mem,
+                                    None if dweights_out is None else
+                                    np.ascontiguousarray(dweights_out).ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return dth, dn0_out, dC0.value
 
     def moments(self, out=None):

@@ -9,7 +9,7 @@ from . import build as _build
 
 PBE_OK, PBE_EINVAL, PBE_ENOMEM, PBE_ECUDA, PBE_ENONFINITE, PBE_ETIMEOUT, PBE_ESTATE = range(7)
 PBE_MEM_HOST, PBE_MEM_DEVICE = 0, 1
-PBE_KINETICS_POWER_LAW, PBE_KINETICS_FIXED = 0, 1
+PBE_KINETICS_POWER_LAW, PBE_KINETICS_FIXED, PBE_KINETICS_MLP = 0, 1, 2
 PBE_PATH_PLAIN, PBE_PATH_FUSED = 0, 1
 
 STATUS_NAMES = {0: "PBE_OK", 1: "PBE_EINVAL", 2: "PBE_ENOMEM", 3: "PBE_ECUDA", 4: "PBE_ENONFINITE",
@@ -54,7 +54,8 @@ SIGNATURES = {
     "pbe_solve": [_P, _PD, _I, _P, _I, _PI64],
     "pbe_moments": [_P, _P, _I],
     "pbe_set_max_steps": [_P, _I64],
-    "pbe_vjp": [_P, _PD, _I, _P, _I, _I, _PD, _P, _PD, _P, _I],
+    "pbe_vjp": [_P, _PD, _I, _P, _I, _I, _PD, _P, _PD, _P, _I, _PD],
+    "pbe_set_closure": [_P, ctypes.POINTER(ctypes.c_float), _I],
     "pbe_solve_1d_noalloc": [ctypes.POINTER(Kinetics), _I64, _D, _P, _D, _D, _PD, _I, _P, _PI64, _P],
     "pbe_batch_create": [ctypes.POINTER(_P), ctypes.POINTER(Instance), _I],
     "pbe_batch_destroy": [_P],

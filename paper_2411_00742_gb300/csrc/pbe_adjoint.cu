@@ -37,7 +37,7 @@ namespace pbe {
 struct AdjS {
     double lC, lt;        // adjoints of C and t at the end of the step being reversed
     double pc[kMaxMom];   // pending: lam_true = lam + sum_k pc[k] W_k
-    double pu;            // pending volume-weight coefficient of u (stage-1 adjoint input)
+    double pu[kMaxMom];   // pending moment-weight coefficients of u (stage-1 adjoint input)
     double lth[6];        // dL/d(kg1, g1, kg2, g2, kb, b)
     double lCprev, lV0, ldt, ltn;
     unsigned int counter;
@@ -105,10 +105,9 @@ __device__ __forceinline__ double lam_at(const double* lam, const AdjS& A, int v
         double p = ndim == 1 ? poly_weights<1>(A.pc, x1, x2, dA) : poly_weights<2>(A.pc, x1, x2, dA);
         return 0.5 * (*lam + p);
     }
-    // STAGE 1: pending volume weight only
-    const double w = ndim == 1 ? x1 * x1 * x1 * dA : x1 * x2 * x2 * dA;
-    return *lam + A.pu * w;
+    // STAGE 1: pending terms of u
     (void)vidx;
+    return *lam + (ndim == 1 ? poly_weights<1>(A.pu, x1, x2, dA) : poly_weights<2>(A.pu, x1, x2, dA));
 }
 
 template <int STAGE>
@@ -321,53 +320,186 @@ __global__ void k_adj_begin(AdjS* A, const Scal* recA, const double* seeds, int 
     *A = a;
 }
 
-// After the stage-2 adjoint: step length and stage-2 kinetics (at C1, t'),
-// then the adjoint of C1 = C - kappa (V(n1) - V(n)).
-__global__ void k_adj_mid(AdjS* A, const Scal* recA, const Scal* recB, Kin K, Geom g, const double* tot)
+// Backward of the learned closure for one evaluation, on 64 threads (one per
+// hidden unit): recomputes the activations from the inputs x, takes the
+// output adjoints lo = dL/d(o), accumulates dL/dweights into dW (fp64, flat
+// layout W1, b1, W2, b2, W3, b3) and returns dL/dx in lx (thread 0).
+__device__ void mlp_backward_block64(const Kin& K, const float x[3], const double lo[3], double* dW, float* sm,
+                                     float lx[3])
 {
-    AdjS a = *A;
+    const int h = threadIdx.x;
+    const __nv_bfloat16* W1 = K.mW;
+    const __nv_bfloat16* W2 = W1 + kMlpH * 3;
+    const __nv_bfloat16* W3 = W2 + kMlpH * kMlpH;
+    const float* b1 = K.mB;
+    const float* b2 = b1 + kMlpH;
+    double* dW1 = dW;
+    double* db1 = dW1 + kMlpH * 3;
+    double* dW2 = db1 + kMlpH;
+    double* db2 = dW2 + kMlpH * kMlpH;
+    double* dW3 = db2 + kMlpH;
+    double* db3 = dW3 + 3 * kMlpH;
+    float* a1s = sm;
+    float* lz2s = sm + kMlpH;
+    float* rs = sm + 2 * kMlpH;   // 3 * 64
+    float z1 = b1[h];
+    z1 = fmaf(__bfloat162float(W1[h * 3]), x[0], z1);
+    z1 = fmaf(__bfloat162float(W1[h * 3 + 1]), x[1], z1);
+    z1 = fmaf(__bfloat162float(W1[h * 3 + 2]), x[2], z1);
+    const float a1 = silu_f(z1);
+    a1s[h] = a1;
+    __syncthreads();
+    float z2 = b2[h];
+    for (int j = 0; j < kMlpH; ++j) z2 = fmaf(__bfloat162float(W2[h * kMlpH + j]), a1s[j], z2);
+    const float a2 = silu_f(z2);
+    float la2 = 0.0f;
+    for (int m = 0; m < 3; ++m) {
+        la2 = fmaf(__bfloat162float(W3[m * kMlpH + h]), (float)lo[m], la2);
+        dW3[m * kMlpH + h] += lo[m] * (double)a2;
+    }
+    if (h < 3) db3[h] += lo[h];
+    const float sg2 = 1.0f / (1.0f + expf(-z2));
+    const float lz2 = la2 * sg2 * (1.0f + z2 * (1.0f - sg2));
+    lz2s[h] = lz2;
+    __syncthreads();
+    for (int j = 0; j < kMlpH; ++j) dW2[h * kMlpH + j] += (double)lz2 * (double)a1s[j];
+    db2[h] += lz2;
+    float la1 = 0.0f;
+    for (int q = 0; q < kMlpH; ++q) la1 = fmaf(__bfloat162float(W2[q * kMlpH + h]), lz2s[q], la1);
+    const float sg1 = 1.0f / (1.0f + expf(-z1));
+    const float lz1 = la1 * sg1 * (1.0f + z1 * (1.0f - sg1));
+    db1[h] += lz1;
+    for (int k = 0; k < 3; ++k) {
+        dW1[h * 3 + k] += (double)lz1 * (double)x[k];
+        rs[h * 3 + k] = __bfloat162float(W1[h * 3 + k]) * lz1;
+    }
+    __syncthreads();
+    if (h == 0) {
+        for (int k = 0; k < 3; ++k) {
+            float v = 0.0f;
+            for (int q = 0; q < kMlpH; ++q) v += rs[q * 3 + k];
+            lx[k] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// dL/d(C, t, ratio) of the closure inputs from dL/dx (thread 0)
+__device__ void mlp_input_adjoint(const Kin& K, double C, double t, const float lx[3], double* lC, double* lt,
+                                  double* lratio)
+{
+    const double frac = (t < K.t_cool) ? t / K.t_cool : 1.0;
+    const double T = K.T0 + (K.T1 - K.T0) * frac;
+    const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) / K.t_cool : 0.0;
+    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double dcs = K.cs1 + 2.0 * K.cs2 * T;
+    const double lS = 4.0 * (double)lx[0];
+    const double lT = (double)lx[1] / 10.0 - lS * C * dcs / (cs * cs);
+    *lC += lS / cs;
+    *lt += lT * dTdt;
+    *lratio += 1e-6 * (double)lx[2];
+}
+
+// After the stage-2 adjoint: step length and stage-2 kinetics (at C1, t'),
+// then the adjoint of C1 = C - kappa (V(n1) - V(n)).  64 threads.
+__global__ void k_adj_mid(AdjS* A, const Scal* recA, const Scal* recB, Kin K, Geom g, const double* tot, int vidx,
+                          double* dW)
+{
+    __shared__ float sm[5 * kMlpH];
+    __shared__ float lx[3];
+    __shared__ double lo[3];
+    __shared__ int run_mlp;
     const double dA = g.ndim == 1 ? g.d1 : g.d1 * g.d2;
     const double P1 = tot[0], P2 = tot[1], P0 = tot[2];
     const double dt = recA->dt;
+    if (threadIdx.x == 0) {
+        lo[0] = dt * P1 * recB->G1b;
+        lo[1] = g.ndim == 2 ? dt * P2 * recB->G2b : 0.0;
+        lo[2] = dt * P0 / dA * recB->Bb;
+        run_mlp = K.kind == PBE_KINETICS_MLP && (recB->G1b > 0.0 || recB->Bb > 0.0);
+    }
+    __syncthreads();
+    if (run_mlp) {
+        float x[3];
+        mlp_inputs(K, recB->C1, recA->t_new, recB->V1 / recB->M1, x);
+        mlp_backward_block64(K, x, lo, dW, sm, lx);
+    }
+    if (threadIdx.x != 0) return;
+    AdjS a = *A;
     a.ldt = recB->G1b * P1 + recB->G2b * P2 + recB->Bb * P0 / dA;
     double lC1 = 0.0, ltn = a.lt;
-    kinetics_adjoint(K, recB->C1, recA->t_new, dt * P1, dt * P2, dt * P0 / dA, &lC1, &ltn, a.lth);
+    for (int k = 0; k < kMaxMom; ++k) a.pu[k] = 0.0;
+    if (K.kind == PBE_KINETICS_MLP) {
+        if (run_mlp) {
+            double lr = 0.0;
+            mlp_input_adjoint(K, recB->C1, recA->t_new, lx, &lC1, &ltn, &lr);
+            a.pu[vidx] += lr / recB->M1;
+            a.pu[0] += -lr * recB->V1 / (recB->M1 * recB->M1);
+        }
+    } else {
+        kinetics_adjoint(K, recB->C1, recA->t_new, dt * P1, dt * P2, dt * P0 / dA, &lC1, &ltn, a.lth);
+    }
     a.ltn = ltn;
     a.lCprev += lC1;
     a.lV0 += K.kappa * lC1;
-    a.pu = -K.kappa * lC1;
+    a.pu[vidx] += -K.kappa * lC1;
     *A = a;
 }
 
 // After the stage-1 adjoint: step length branch, stage-1 kinetics (at C, t),
-// and the pending volume term of lam for the previous step.
-__global__ void k_adj_end(AdjS* A, const Scal* recA, Kin K, Geom g, const double* tot, int vidx)
+// and the pending terms of lam for the previous step.  64 threads.
+__global__ void k_adj_end(AdjS* A, const Scal* recA, Kin K, Geom g, const double* tot, int vidx, double* dW)
 {
-    AdjS a = *A;
+    __shared__ float sm[5 * kMlpH];
+    __shared__ float lx[3];
+    __shared__ double lo[3];
+    __shared__ double sl[4];   // ldt, lG1, lG2, lB after the step-length branch
+    __shared__ int run_mlp;
     const double dA = g.ndim == 1 ? g.d1 : g.d1 * g.d2;
     const double P1 = tot[0], P2 = tot[1], P0 = tot[2];
     const double dt = recA->dt;
-    double ldt = a.ldt + recA->G1a * P1 + recA->G2a * P2 + recA->Ba * P0 / dA;
-    double lG1 = dt * P1, lG2 = dt * P2;
-    const double lB = dt * P0 / dA;
-    double ltp;
-    if (!recA->clipped) {
-        ltp = a.ltn;
-        ldt += a.ltn;
-        double R = recA->G1a / g.d1;
-        if (g.ndim == 2) R = R + recA->G2a / g.d2;
-        const double dR = -K.cfl / (R * R) * ldt;
-        lG1 += dR / g.d1;
-        if (g.ndim == 2) lG2 += dR / g.d2;
-    } else {
-        ltp = -ldt;
+    if (threadIdx.x == 0) {
+        const AdjS& a = *A;
+        double ldt = a.ldt + recA->G1a * P1 + recA->G2a * P2 + recA->Ba * P0 / dA;
+        double lG1 = dt * P1, lG2 = dt * P2;
+        if (!recA->clipped) {
+            ldt += a.ltn;
+            double R = recA->G1a / g.d1;
+            if (g.ndim == 2) R = R + recA->G2a / g.d2;
+            const double dR = -K.cfl / (R * R) * ldt;
+            lG1 += dR / g.d1;
+            if (g.ndim == 2) lG2 += dR / g.d2;
+        }
+        sl[0] = ldt; sl[1] = lG1; sl[2] = lG2; sl[3] = dt * P0 / dA;
+        lo[0] = lG1 * recA->G1a;
+        lo[1] = g.ndim == 2 ? lG2 * recA->G2a : 0.0;
+        lo[2] = sl[3] * recA->Ba;
+        run_mlp = K.kind == PBE_KINETICS_MLP && (recA->G1a > 0.0 || recA->Ba > 0.0);
     }
+    __syncthreads();
+    if (run_mlp) {
+        float x[3];
+        mlp_inputs(K, recA->C, recA->t, recA->V0 / recA->M0, x);
+        mlp_backward_block64(K, x, lo, dW, sm, lx);
+    }
+    if (threadIdx.x != 0) return;
+    AdjS a = *A;
+    double ltp = recA->clipped ? -sl[0] : a.ltn;
     double lC = a.lCprev;
-    kinetics_adjoint(K, recA->C, recA->t, lG1, lG2, lB, &lC, &ltp, a.lth);
+    for (int k = 0; k < kMaxMom; ++k) a.pc[k] = 0.0;
+    if (K.kind == PBE_KINETICS_MLP) {
+        if (run_mlp) {
+            double lr = 0.0;
+            mlp_input_adjoint(K, recA->C, recA->t, lx, &lC, &ltp, &lr);
+            a.pc[vidx] += lr / recA->M0;
+            a.pc[0] += -lr * recA->V0 / (recA->M0 * recA->M0);
+        }
+    } else {
+        kinetics_adjoint(K, recA->C, recA->t, sl[1], sl[2], sl[3], &lC, &ltp, a.lth);
+    }
     a.lC = lC;
     a.lt = ltp;
-    for (int k = 0; k < kMaxMom; ++k) a.pc[k] = 0.0;
-    a.pc[vidx] = a.lV0;
+    a.pc[vidx] += a.lV0;
     *A = a;
 }
 
@@ -439,7 +571,7 @@ pbe_status afail(pbe_status code, const char* fmt, ...)
 
 extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const double* seeds_in, int seeds_mem,
                               int checkpoint_every, double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows,
-                              int mem)
+                              int mem, double* dL_dweights)
 {
     if (!g || !t_out || !seeds_in || !dL_dtheta) return afail(PBE_EINVAL, "null argument");
     if (n_out < 1) return afail(PBE_EINVAL, "n_out must be >= 1");
@@ -457,7 +589,7 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     std::vector<double*> ckpt_n;
     std::vector<Scal*> ckpt_S;
     double *seg_n = nullptr, *seg_n1 = nullptr, *lam = nullptr, *lam2 = nullptr, *u = nullptr, *seeds = nullptr;
-    double *fin_n = nullptr, *apart = nullptr;
+    double *fin_n = nullptr, *apart = nullptr, *dW = nullptr;
     Scal *recA = nullptr, *recB = nullptr, *fin_S = nullptr;
     AdjS* A = nullptr;
     long long total = 0;
@@ -482,6 +614,8 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     ATRY(cudaMalloc(&seeds, sizeof(double) * ncol * n_out));
     ATRY(cudaMalloc(&A, sizeof(AdjS)));
     ATRY(cudaMalloc(&apart, sizeof(double) * kMaxMom * (nb + 1)));
+    ATRY(cudaMalloc(&dW, sizeof(double) * kMlpNW));
+    ATRY(cudaMemsetAsync(dW, 0, sizeof(double) * kMlpNW, st));
     tot = apart + (size_t)nb * kMaxMom;
     ATRY(cudaMemcpyAsync(seeds, seeds_in, sizeof(double) * ncol * n_out,
                          seeds_mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -545,10 +679,10 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
             k_adj_begin<<<1, 1, 0, st>>>(A, recA + q, seeds, ncol, vidx, g->kin.kappa);
             ATRY(cudaGetLastError());
             ATRY(launch_adj_stage(2, g->geo, seg_n1 + q * nc, lam, lam2, u, A, recA + q, recB + q, apart, st));
-            k_adj_mid<<<1, 1, 0, st>>>(A, recA + q, recB + q, g->kin, g->geo, tot);
+            k_adj_mid<<<1, kMlpH, 0, st>>>(A, recA + q, recB + q, g->kin, g->geo, tot, vidx, dW);
             ATRY(cudaGetLastError());
             ATRY(launch_adj_stage(1, g->geo, seg_n + q * nc, u, lam2, nullptr, A, recA + q, recB + q, apart, st));
-            k_adj_end<<<1, 1, 0, st>>>(A, recA + q, g->kin, g->geo, tot, vidx);
+            k_adj_end<<<1, kMlpH, 0, st>>>(A, recA + q, g->kin, g->geo, tot, vidx, dW);
             ATRY(cudaGetLastError());
             std::swap(lam, lam2);
         }
@@ -571,6 +705,7 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     ATRY(cudaStreamSynchronize(st));
     g->C_host = g->h_S->C;
     g->t_host = g->h_S->t;
+    if (dL_dweights) ATRY(cudaMemcpy(dL_dweights, dW, sizeof(double) * kMlpNW, cudaMemcpyDeviceToHost));
     for (int k = 0; k < 6; ++k) dL_dtheta[k] = ha.lth[k];
     if (dL_dC0) *dL_dC0 = ha.lC;
     if (!std::isfinite(ha.lth[0]) || !std::isfinite(ha.lth[1]) || !std::isfinite(ha.lth[4]) || !std::isfinite(ha.lth[5]))
@@ -580,6 +715,6 @@ done:
     for (double* p : ckpt_n) cudaFree(p);
     for (Scal* p : ckpt_S) cudaFree(p);
     cudaFree(seg_n); cudaFree(seg_n1); cudaFree(recA); cudaFree(recB); cudaFree(lam); cudaFree(lam2); cudaFree(u);
-    cudaFree(fin_n); cudaFree(fin_S); cudaFree(seeds); cudaFree(A); cudaFree(apart);
+    cudaFree(fin_n); cudaFree(fin_S); cudaFree(seeds); cudaFree(A); cudaFree(apart); cudaFree(dW);
     return rc;
 }

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <vector>
 
 #include "pbe_internal.h"
 
@@ -145,7 +146,7 @@ pbe_status finish_call(pbe_grid* g)
 pbe_status run_solve(pbe_grid* g, int n_out)
 {
     CUDA_TRY(pbe::launch_prologue(g, n_out, g->max_steps, nullptr));
-    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g)) {
+    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g) && g->kin.kind != PBE_KINETICS_MLP) {
         CUDA_TRY(pbe::launch_fused_solve(g, n_out));
         return PBE_OK;
     }
@@ -265,8 +266,10 @@ pbe_status pbe_set_max_steps(pbe_grid* g, int64_t max_steps)
 pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
 {
     if (!g || !k) return fail(PBE_EINVAL, "null argument");
-    if (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED)
+    if (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED && k->kind != PBE_KINETICS_MLP)
         return fail(PBE_EINVAL, "unknown kinetics kind %d", k->kind);
+    if (k->kind == PBE_KINETICS_MLP && !g->d_mW)
+        return fail(PBE_ESTATE, "set the closure weights (pbe_set_closure) before selecting PBE_KINETICS_MLP");
     if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
     if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
     const double vals[] = {k->kg[0], k->kg[1], k->g[0], k->g[1], k->kb, k->b, k->csat[0], k->csat[1],
@@ -282,12 +285,49 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     K.T0 = k->T0; K.T1 = k->T1; K.t_cool = k->t_cool; K.kappa = k->kappa; K.cfl = k->cfl;
     K.lkg1 = std::log(K.kg1); K.lkg2 = std::log(K.kg2); K.lkb = std::log(K.kb);
     K.inv_tcool = 1.0 / K.t_cool;
+    K.mW = g->d_mW;
+    K.mB = g->d_mB;
     g->kin = K;
     g->has_kin = true;
     if (g->plain_exec) {  // kinetics are baked into the graph's kernel arguments
         cudaGraphExecDestroy(g->plain_exec);
         g->plain_exec = nullptr;
     }
+    return PBE_OK;
+}
+
+pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count)
+{
+    if (!g || !w) return fail(PBE_EINVAL, "null argument");
+    if (count != pbe::kMlpNW) return fail(PBE_EINVAL, "the closure has %d weights (got %d)", pbe::kMlpNW, count);
+    for (int k = 0; k < count; ++k)
+        if (!std::isfinite(w[k])) return fail(PBE_EINVAL, "non-finite closure weight %d", k);
+    DeviceGuard dg(g->device);
+    const int H = pbe::kMlpH;
+    // split the flat layout W1, b1, W2, b2, W3, b3 into bf16 matrices and fp32 biases
+    std::vector<__nv_bfloat16> hw(H * 3 + H * H + 3 * H);
+    std::vector<float> hb(H + H + 3);
+    const float* W1 = w;
+    const float* b1 = W1 + H * 3;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + 3 * H;
+    for (int k = 0; k < H * 3; ++k) hw[k] = __float2bfloat16_rn(W1[k]);
+    for (int k = 0; k < H * H; ++k) hw[H * 3 + k] = __float2bfloat16_rn(W2[k]);
+    for (int k = 0; k < 3 * H; ++k) hw[H * 3 + H * H + k] = __float2bfloat16_rn(W3[k]);
+    for (int k = 0; k < H; ++k) { hb[k] = b1[k]; hb[H + k] = b2[k]; }
+    for (int k = 0; k < 3; ++k) hb[2 * H + k] = b3[k];
+    if (!g->d_mW) {
+        if (cudaMalloc(&g->d_mW, sizeof(__nv_bfloat16) * hw.size()) != cudaSuccess ||
+            cudaMalloc(&g->d_mB, sizeof(float) * hb.size()) != cudaSuccess)
+            return fail(PBE_ENOMEM, "allocating the closure weights failed");
+    }
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    CUDA_TRY(cudaMemcpy(g->d_mW, hw.data(), sizeof(__nv_bfloat16) * hw.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(g->d_mB, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice));
+    g->kin.mW = g->d_mW;
+    g->kin.mB = g->d_mB;
     return PBE_OK;
 }
 

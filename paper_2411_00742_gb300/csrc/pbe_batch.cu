@@ -392,6 +392,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         if (!(p.lmax > 0.0) || !std::isfinite(p.lmax) || !std::isfinite(p.C0) || !std::isfinite(p.t0) ||
             !(k->cfl > 0.0 && k->cfl <= 1.0) || !(k->t_cool > 0.0) ||
             (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED) || k->kg[0] < 0 || k->kb < 0) {
+            // (the learned closure runs on the single-grid plain path only)
             delete b;
             return bfail(PBE_EINVAL, "instance %d: invalid parameters", i);
         }

@@ -3,6 +3,7 @@
 // chain that closes the solute balance between stages.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,7 +21,12 @@ struct Kin {
     double cs0, cs1, cs2, T0, T1, t_cool, kappa, cfl;
     double lkg1, lkg2, lkb;   // natural logarithms of kg1, kg2, kb (-inf for 0)
     double inv_tcool;         // 1 / t_cool
+    const __nv_bfloat16* mW;  // learned closure: W1[64][3], W2[64][64], W3[3][64] (bf16, device)
+    const float* mB;          // and b1[64], b2[64], b3[3] (fp32, device)
 };
+
+constexpr int kMlpH = 64;
+constexpr int kMlpNW = kMlpH * 3 + kMlpH + kMlpH * kMlpH + kMlpH + 3 * kMlpH + 3;  // flat weight count
 
 struct Geom {
     int ndim;
@@ -36,6 +42,8 @@ struct Scal {
     double G1a, G2a, Ba;        // stage-1 kinetics (state at step start)
     double G1b, G2b, Bb;        // stage-2 kinetics (after stage 1)
     double C1;                  // concentration after stage 1
+    double M0;                  // mu0 of the state at the start of the step
+    double V1, M1;              // volume moment and mu0 after stage 1
     double last_dt;             // length of the last completed step
     long long steps, max_steps;
     int clipped, out_idx, n_out, done, status;
@@ -258,6 +266,91 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
     B = __shfl_sync(0xffffffffu, e, 2);
 }
 
+// ---------------------------------------------------------------------------
+// Learned closure (a perceptron replaces the rate expressions: the empirical
+// hybrid model of Sec. 4.2): 3 -> 64 -> 64 -> 3 with SiLU hidden units, bf16
+// weights, fp32 arithmetic and accumulation, one warp (two hidden units per
+// lane).  Inputs x0 = 4 (S - 1), x1 = (T - 25)/10, x2 = 1e-6 V/mu0; outputs
+// ln G1 = o0 + ln 0.01, ln G2 = o1 + ln 0.005, ln B = o2 + ln 1e5.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+
+__device__ __forceinline__ void mlp_forward_warp(const Kin& K, const float x[3], float o[3])
+{
+    const int lane = threadIdx.x & 31;
+    const __nv_bfloat16* W1 = K.mW;
+    const __nv_bfloat16* W2 = W1 + kMlpH * 3;
+    const __nv_bfloat16* W3 = W2 + kMlpH * kMlpH;
+    const float* b1 = K.mB;
+    const float* b2 = b1 + kMlpH;
+    const float* b3 = b2 + kMlpH;
+    float a1[2], z2[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int h = lane + 32 * u;
+        float z = b1[h];
+        z = fmaf(__bfloat162float(W1[h * 3]), x[0], z);
+        z = fmaf(__bfloat162float(W1[h * 3 + 1]), x[1], z);
+        z = fmaf(__bfloat162float(W1[h * 3 + 2]), x[2], z);
+        a1[u] = silu_f(z);
+        z2[u] = b2[h];
+    }
+    for (int j = 0; j < 32; ++j) {
+        const float aj0 = __shfl_sync(0xffffffffu, a1[0], j), aj1 = __shfl_sync(0xffffffffu, a1[1], j);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int h = lane + 32 * u;
+            z2[u] = fmaf(__bfloat162float(W2[h * kMlpH + j]), aj0, z2[u]);
+            z2[u] = fmaf(__bfloat162float(W2[h * kMlpH + j + 32]), aj1, z2[u]);
+        }
+    }
+    const float a20 = silu_f(z2[0]), a21 = silu_f(z2[1]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        float v = __bfloat162float(W3[m * kMlpH + lane]) * a20 + __bfloat162float(W3[m * kMlpH + lane + 32]) * a21;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        o[m] = v + b3[m];
+    }
+}
+
+// closure inputs at (C, t, ratio); returns false when S <= 1
+__device__ __forceinline__ bool mlp_inputs(const Kin& K, double C, double t, double ratio, float x[3])
+{
+    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
+    const double T = K.T0 + (K.T1 - K.T0) * frac;
+    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double s = C / cs - 1.0;
+    if (!(s > 0.0)) return false;
+    x[0] = (float)(4.0 * s);
+    x[1] = (float)((T - 25.0) / 10.0);
+    x[2] = (float)(1e-6 * ratio);
+    return true;
+}
+
+constexpr double kLnG1 = -4.605170185988091;   // ln 0.01
+constexpr double kLnG2 = -5.298317366548036;   // ln 0.005
+constexpr double kLnB = 11.512925464970229;    // ln 1e5
+
+// kinetics with the moment ratio V/mu0 of the state (used by the closure)
+__device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t, double ratio, double& G1,
+                                                double& G2, double& B)
+{
+    if (K.kind != PBE_KINETICS_MLP) {
+        kinetics_warp(K, C, t, G1, G2, B);
+        return;
+    }
+    float x[3], o[3];
+    if (!mlp_inputs(K, C, t, ratio, x)) {
+        G1 = 0.0; G2 = 0.0; B = 0.0;
+        return;
+    }
+    mlp_forward_warp(K, x, o);
+    G1 = pbe_exp((double)o[0] + kLnG1);
+    G2 = (K.ndim == 2) ? pbe_exp((double)o[1] + kLnG2) : 0.0;
+    B = pbe_exp((double)o[2] + kLnB);
+}
+
 __device__ __forceinline__ int timestep_fast(const Kin& K, const Geom& g, double G1, double G2, double t,
                                              double t_next, double& dt, double& t_new)
 {
@@ -285,7 +378,7 @@ __device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const G
     const double t_next = t_out[S->out_idx];
     const double C = S->C, t = S->t;
     double G1, G2, B, dt, t_new;
-    kinetics_warp(K, C, t, G1, G2, B);
+    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B);
     const int clipped = timestep_fast(K, g, G1, G2, t, t_next, dt, t_new);
     __syncwarp();
     if (lane == 0) {
@@ -299,15 +392,17 @@ __device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const G
     __syncwarp();
 }
 
-__device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double V1)
+__device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double V1, double M1 = 1.0)
 {
     const int lane = threadIdx.x & 31;
     const double C1 = S->C - K.kappa * (V1 - S->V0);
     double G1, G2, B;
-    kinetics_warp(K, C1, S->t_new, G1, G2, B);
+    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B);
     __syncwarp();
     if (lane == 0) {
         S->C1 = C1;
+        S->V1 = V1;
+        S->M1 = M1;
         S->G1b = G1; S->G2b = G2; S->Bb = B;
         if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
             S->status = PBE_ENONFINITE;
@@ -327,6 +422,7 @@ __device__ __forceinline__ void finish_stage2_warp(Scal* S, const Kin& K, const 
         S->t = S->t_new;
         S->C = C;
         S->V0 = V2;
+        S->M0 = mom[0];
         S->last_dt = S->dt;
         S->steps += 1;
         if (!isfinite(V2) || !isfinite(C)) {

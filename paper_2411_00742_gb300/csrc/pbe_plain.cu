@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kNT) k_prologue(const double* __restrict__ n, 
             for (int k = 0; k < NM; ++k) mom_out[k] = m[k];
         } else {
             S->V0 = m[VIDX];
+            S->M0 = m[0];
             S->steps = 0;
             S->status = 0;
             S->done = 0;
@@ -127,7 +128,8 @@ __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, 
         if (STAGE == 2 && use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hcond, 0);
         return;
     }
-    const StageCoef sc = stage_coef<STAGE>(*S, g);
+    StageCoef sc = stage_coef<STAGE>(*S, g);
+    if (K.kind == PBE_KINETICS_MLP) sc.moms = true;   // the closure reads mu0 at every stage
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     tile1d<STAGE, false, false, kT1, kNT>(in, old, out, blockIdx.x * kT1, g, sc, m, tile, h);
     block_sum<kNT, 4>(m, sh);
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, 
     for (int k = 0; k < 4; ++k) m[k] = __shfl_sync(0xffffffffu, m[k], 0);
     if (threadIdx.x == 0) S->counter = 0u;
     if (STAGE == 1) {
-        finish_stage1_warp(S, K, m[3]);
+        finish_stage1_warp(S, K, m[3], m[0]);
     } else {
         finish_stage2_warp(S, K, g, t_out, rows, m, 4, 3);
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
@@ -161,7 +163,8 @@ __global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, 
         return;
     }
     const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-    const StageCoef sc = stage_coef<STAGE>(*S, g);
+    StageCoef sc = stage_coef<STAGE>(*S, g);
+    if (K.kind == PBE_KINETICS_MLP) sc.moms = true;   // the closure reads mu0 at every stage
     double m[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) m[k] = 0.0;
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, 
     for (int k = 0; k < 10; ++k) m[k] = __shfl_sync(0xffffffffu, m[k], 0);
     if (threadIdx.x == 0) S->counter = 0u;
     if (STAGE == 1) {
-        finish_stage1_warp(S, K, m[8]);
+        finish_stage1_warp(S, K, m[8], m[0]);
     } else {
         finish_stage2_warp(S, K, g, t_out, rows, m, 10, 8);
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);

@@ -1,0 +1,92 @@
+"""The learned kinetics closure on the GPU (bf16 weights, fp32 arithmetic)
+against the FP64 oracle evaluating the same stored weights.
+
+Tolerances follow from fp32 arithmetic in the 64-wide layers (relative
+rounding ~1e-7 per accumulated product, ~1e-6 on the outputs, which enter the
+rates through exp): rows within 2e-5 relative, weight gradients within 2e-3
+of the largest gradient entry."""
+import numpy as np
+import pytest
+
+import oracle
+import pbe_closure_data as cd
+import pbe_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+REL_ROWS_MLP = 2e-5
+REL_GRAD_MLP = 2e-3
+
+
+def _grid(inst, w):
+    import paper_2411_00742_gb300 as P
+    g = P.Grid.from_problem(inst.problem)
+    g.set_closure(w)
+    g.set_kinetics(inst.problem, closure=True)
+    return g
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_closure_forward_matches_oracle(ndim):
+    inst = pi.config_1d(200) if ndim == 1 else cd.trajectories(1, seed=11, N=48)[0]
+    w = cd.initial_weights(3, 0.2)
+    g = _grid(inst, w)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, steps = g.solve(inst.t_out)
+    g.close()
+    want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=cd.stored_weights(w))
+    assert steps == want["steps"]
+    err = np.max(np.abs(rows[:, 1:] - want["rows"][:, 1:]) / np.abs(want["rows"][:, 1:]))
+    assert err <= REL_ROWS_MLP, err
+
+
+def test_closure_gradients_match_oracle():
+    inst = cd.trajectories(1, seed=12, N=40)[0]
+    w = cd.initial_weights(4, 0.2)
+    ws = cd.stored_weights(w)
+    tgt = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]   # hidden-law truth
+    cols = [1, 2, 3, 9, 11]
+    r = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=ws)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    _, _, _, want = oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds, mlp=ws)
+    g = _grid(inst, w)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    dW = np.zeros(cd.CLOSURE_SIZE)
+    g.vjp(inst.t_out, seeds, 64, dweights_out=dW)
+    g.close()
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(dW - want)) <= REL_GRAD_MLP * scale, np.max(np.abs(dW - want)) / scale
+    # gradient direction agrees closely
+    cos = float(np.dot(dW, want) / (np.linalg.norm(dW) * np.linalg.norm(want)))
+    assert cos > 0.99999
+
+
+def test_closure_gradient_matches_central_differences_on_gpu():
+    import paper_2411_00742_gb300 as P
+    inst = cd.trajectories(1, seed=13, N=32)[0]
+    w = cd.initial_weights(5, 0.2)
+    tgt = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    cols = [1, 2, 3, 9, 11]
+
+    def loss(wv):
+        g = _grid(inst, wv)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        rows, _ = g.solve(inst.t_out)
+        g.close()
+        return oracle.relative_loss(rows, tgt, cols), rows
+
+    L0, rows = loss(w)
+    g = _grid(inst, w)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    dW = np.zeros(cd.CLOSURE_SIZE)
+    g.vjp(inst.t_out, oracle.relative_loss_seeds(rows, tgt, cols), 64, dweights_out=dW)
+    g.close()
+    # biases are stored in fp32 (no bf16 rounding): differentiate through them
+    H = 64
+    for k in (H * 3 + 5, H * 3 + H + H * H + 9, cd.CLOSURE_SIZE - 1, cd.CLOSURE_SIZE - 3):
+        h = 2e-3
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd = (loss(wp)[0] - loss(wm)[0]) / (2 * h)
+        assert dW[k] == pytest.approx(fd, rel=2e-2, abs=1e-6 * np.max(np.abs(dW))), k
