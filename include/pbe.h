@@ -243,6 +243,13 @@ pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
  * the fastest and return it in *chosen (may be NULL). */
 pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int* chosen);
 
+/* One Adam step (the optimizer of the paper's parameter estimation,
+ * Appendix C) on DEVICE arrays of n doubles: moments m, v updated in place,
+ * w -= lr * mhat / (sqrt(vhat) + eps) with bias corrections for step >= 1.
+ * Ordered on `stream`; does not synchronize. */
+pbe_status pbe_adam_update(double* w, const double* grad, double* m, double* v, int n, double lr, double beta1,
+                           double beta2, double eps, int step, void* stream);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* pbe_last_error(void);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "pbe_batch_set_config": [_P, _I],
     "pbe_batch_steps": [_P, _PI64],
     "pbe_batch_autotune": [_P, _PD, _I, ctypes.POINTER(_I)],
+    "pbe_adam_update": [_P, _P, _P, _P, _I, _D, _D, _D, _D, _I, _P],
     "pbe_last_error": [],
     "pbe_version": [],
 }

@@ -1,0 +1,128 @@
+"""Training and evaluation of the learned kinetics closure through the solver.
+
+The closure (a 3-64-64-3 perceptron replacing the growth and nucleation
+expressions, the empirical hybrid model of Sec. 4.2) is trained by gradient
+descent through the differentiable solver: every gradient is one forward
+solve plus the hand-written discrete adjoint (pbe_vjp), which backpropagates
+through the closure inside every stage; the optimizer is Adam (pbe_adam_update)
+on device arrays.  Several solves run concurrently, one per CUDA stream and
+host thread.  This module only orchestrates calls into the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import torch
+
+from . import CLOSURE_SIZE, Grid, _lib
+
+LOSS_COLS_2D = [1, 2, 3, 9, 11]   # mu00, mu10, mu01, mu12, C
+LOSS_COLS_1D = [1, 2, 3, 4, 5]
+
+
+def loss_cols(ndim):
+    return LOSS_COLS_1D if ndim == 1 else LOSS_COLS_2D
+
+
+def relative_loss_and_seeds(rows, target, cols):
+    r = (rows[:, cols] - target[:, cols]) / target[:, cols]
+    seeds = np.zeros_like(rows)
+    seeds[:, cols] = 2.0 * r / target[:, cols]
+    return float(np.sum(r * r)), seeds
+
+
+class _Worker:
+    def __init__(self, problem):
+        self.stream = torch.cuda.Stream()
+        self.grid = Grid.from_problem(problem, stream=self.stream)
+
+    def grad(self, inst, target, weights, cols, checkpoint_every=64):
+        g = self.grid
+        g.set_closure(weights)
+        g.set_kinetics(inst.problem, closure=True)
+        g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+        rows, _ = g.solve(inst.t_out)
+        L, seeds = relative_loss_and_seeds(rows, target, cols)
+        g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+        dW = np.zeros(CLOSURE_SIZE)
+        g.vjp(inst.t_out, seeds, checkpoint_every, dweights_out=dW)
+        return L, dW
+
+    def rows(self, inst, weights=None, problem=None):
+        g = self.grid
+        if weights is not None:
+            g.set_closure(weights)
+            g.set_kinetics(inst.problem, closure=True)
+        else:
+            g.set_kinetics(problem if problem is not None else inst.problem)
+        g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+        rows, _ = g.solve(inst.t_out)
+        return rows
+
+
+class ClosureTrainer:
+    """Adam on the closure weights through the solver's adjoint."""
+
+    def __init__(self, w0, problem_like, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, workers=8):
+        self.lib = _lib.load()
+        self.w = torch.as_tensor(np.asarray(w0, dtype=np.float64)).cuda()
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.step_count = 0
+        self.pool = ThreadPoolExecutor(max_workers=workers)
+        self._local = threading.local()
+        self._problem = problem_like
+        self.workers = []
+        self._lock = threading.Lock()
+
+    def _worker(self):
+        w = getattr(self._local, "w", None)
+        if w is None:
+            w = _Worker(self._problem)
+            self._local.w = w
+            with self._lock:
+                self.workers.append(w)
+        return w
+
+    def weights32(self):
+        return self.w.float().cpu().numpy()
+
+    def batch_grad(self, insts, targets):
+        w32 = self.weights32()
+        cols = loss_cols(insts[0].problem.ndim)
+        res = list(self.pool.map(lambda it: self._worker().grad(it[0], it[1], w32, cols), zip(insts, targets)))
+        L = float(np.mean([r[0] for r in res]))
+        g = np.mean([r[1] for r in res], axis=0)
+        return L, g
+
+    def step(self, insts, targets):
+        L, g = self.batch_grad(insts, targets)
+        gt = torch.as_tensor(g).cuda()
+        self.step_count += 1
+        torch.cuda.synchronize()
+        _lib.check(self.lib.pbe_adam_update(ctypes.c_void_p(self.w.data_ptr()), ctypes.c_void_p(gt.data_ptr()),
+                                            ctypes.c_void_p(self.m.data_ptr()), ctypes.c_void_p(self.v.data_ptr()),
+                                            self.w.numel(), self.lr, self.betas[0], self.betas[1], self.eps,
+                                            self.step_count, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        torch.cuda.synchronize()
+        return L
+
+    def rows(self, insts, weights=None, problems=None):
+        w32 = None if weights is None else np.asarray(weights, dtype=np.float32)
+        probs = problems if problems is not None else [None] * len(insts)
+        return list(self.pool.map(lambda it: self._worker().rows(it[0], w32, it[1]), zip(insts, probs)))
+
+    def close(self):
+        self.pool.shutdown()
+        for w in self.workers:
+            w.grid.close()
+
+
+def trajectory_error(rows, target, cols):
+    """Relative RMS error of the chosen columns over all output times."""
+    r = (rows[:, cols] - target[:, cols]) / target[:, cols]
+    return float(np.sqrt(np.mean(r * r)))
