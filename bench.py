@@ -309,6 +309,43 @@ def run_gpu(args):
             tc = time.perf_counter() - t0
             out[name] = {"grads_per_s": 1.0 / tg, "ms_per_grad": 1e3 * tg, "max_rel_err_vs_cpu_adjoint": err,
                          "cpu_adjoint_grads_per_s": 1.0 / tc, "checkpoint_every": 64}
+        # (b') the batched form: 256 instances of 500 cells, one launch (one warp per instance)
+        insts = pi.adjoint_batch_1d(256)
+        b = P.Batch([x.problem for x in insts], [x.C0 for x in insts], stream=stream)
+        packed = b.pack([x.n0 for x in insts])
+        seeds = np.zeros((len(insts), 50, 6))
+        cols = [1, 2, 3, 4, 5]
+        tgts = []
+        for i, inst in enumerate(insts):
+            p = inst.problem
+            tgt = oracle.solve(p.with_theta(p.theta * pi.TARGET_FACTOR), inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+            r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+            seeds[i] = oracle.relative_loss_seeds(r, tgt, cols)
+            tgts.append(tgt)
+        seeds_d = torch.as_tensor(seeds).cuda()
+        times = []
+        with torch.cuda.stream(stream):
+            b.set_state(packed)
+            for it in range(args.warmup + max(3, args.steps // 2)):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dth_b, _ = b.vjp(pi.loss_times(), seeds_d, 64)
+                e1.record(stream)
+                e1.synchronize()
+                if it >= args.warmup:
+                    times.append(e0.elapsed_time(e1) * 1e-3)
+        b.close()
+        tb = sum(times) / len(times)
+        errs = []
+        for i in range(0, 256, 32):
+            inst = insts[i]
+            want, _, _ = oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds[i])
+            errs.append(float(np.max(np.abs(dth_b[i, [0, 1, 4, 5]] - want[[0, 1, 4, 5]]) / np.abs(want[[0, 1, 4, 5]]))))
+        out["batch_1d_256x500"] = {"grads_per_s": 256 / tb, "ms_per_batch": 1e3 * tb,
+                                   "max_rel_err_vs_cpu_adjoint_sampled": max(errs), "checkpoint_every": 64,
+                                   "single_instance_path_grads_per_s": out["1d_500"]["grads_per_s"],
+                                   "cpu_adjoint_grads_per_s": out["1d_500"]["cpu_adjoint_grads_per_s"]}
         return out
 
     clocks = ClockSampler(dev)

@@ -238,6 +238,18 @@ pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps);
 /* Instances per block (1, 2, 4 or 8 warps, one instance per warp). */
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 
+/* Gradients of a loss of every instance's output rows (the batched form of
+ * pbe_vjp: the same hand-written discrete adjoint, one warp per instance, the
+ * forward with checkpoints every `checkpoint_every` steps and the reverse
+ * sweep with recomputation, up to 4096 steps per instance).  Starts from the
+ * batch's current state; seeds: count * n_out rows of 6 doubles (dL/drows,
+ * instance-major, `seeds_mem` memory); dL_dtheta HOST count x 6
+ * (kg1, g1, kg2, g2, kb, b per instance); dL_dC0 optional HOST count;
+ * dL_dn0 optional DEVICE packed state (mem must be PBE_MEM_DEVICE).  The
+ * batch state is left unchanged.  Synchronizes. */
+pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out, const double* seeds, int seeds_mem,
+                         int checkpoint_every, double* dL_dtheta, double* dL_dC0, double* dL_dn0, int mem);
+
 /* Time each admissible instances-per-block setting on this batch and these
  * output times (the state is saved and restored around every trial), keep
  * the fastest and return it in *chosen (may be NULL). */

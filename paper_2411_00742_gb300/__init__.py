@@ -260,6 +260,22 @@ class Batch:
         """Sum over instances of cells x steps of the last solve."""
         return int(np.sum(np.diff(self.offsets) * self.steps()))
 
+    def vjp(self, t_out, seeds, checkpoint_every: int = 64, dn0_out=None):
+        """Per-instance gradients: returns (dL/dtheta [count, 6], dL/dC0 [count]);
+        dn0_out (CUDA float64 packed state) receives dL/dn0 when given."""
+        t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+        sp, smem, skeep = _buf(seeds)
+        dth = np.zeros((self.count, 6))
+        dC0 = np.zeros(self.count)
+        dn_p = None
+        if dn0_out is not None:
+            dn_p, _, dkeep = _buf(dn0_out, writable=True)
+        _lib.check(self.lib.pbe_batch_vjp(self.h, t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t_out),
+                                          sp, smem, int(checkpoint_every),
+                                          dth.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          dC0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dn_p, PBE_MEM_DEVICE))
+        return dth, dC0
+
     def set_config(self, warps_per_block: int):
         _lib.check(self.lib.pbe_batch_set_config(self.h, int(warps_per_block)))
 

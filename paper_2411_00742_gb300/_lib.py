@@ -65,6 +65,7 @@ SIGNATURES = {
     "pbe_batch_get_state": [_P, _P, _P, _P, _I],
     "pbe_batch_solve": [_P, _PD, _I, _P, _I, _PI64],
     "pbe_batch_set_config": [_P, _I],
+    "pbe_batch_vjp": [_P, _PD, _I, _P, _I, _I, _PD, _PD, _P, _I],
     "pbe_batch_steps": [_P, _PI64],
     "pbe_batch_autotune": [_P, _PD, _I, ctypes.POINTER(_I)],
     "pbe_adam_update": [_P, _P, _P, _P, _I, _D, _D, _D, _D, _I, _P],

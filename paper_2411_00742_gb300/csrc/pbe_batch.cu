@@ -24,14 +24,6 @@ void pbe_set_error_message(int code, const char* msg);  // pbe_api.cu
 
 namespace pbe {
 
-struct BatchInst {
-    Kin K;
-    Geom g;
-    long long offset;   // first cell in the packed state
-    int rows;           // ceil(N / 32)
-    int pad;
-};
-
 constexpr int kMaxBatchCells = 6144;   // largest instance accepted (shared-memory resident)
 
 // buffer layout per instance (cell i at index i + 2, two zero ghosts below)
@@ -503,6 +495,22 @@ pbe_status pbe_batch_get_state(pbe_batch* b, double* n_packed, double* C, double
     if (C) BTRY(cudaMemcpyAsync(C, b->d_C, sizeof(double) * b->count, kd, b->stream));
     if (t) BTRY(cudaMemcpyAsync(t, b->d_t, sizeof(double) * b->count, kd, b->stream));
     BTRY(cudaStreamSynchronize(b->stream));
+    return PBE_OK;
+}
+
+// accessor for the batched adjoint (pbe_batch_adjoint.cu); not part of the public header
+pbe_status pbe_batch_internal_view(pbe_batch* b, const void** inst, const int** order, int* count, double** state,
+                                   double** C, double** t, int* np_max, int* device, void** stream)
+{
+    *inst = b->d_inst;
+    *order = b->d_order;
+    *count = b->count;
+    *state = b->d_state;
+    *C = b->d_C;
+    *t = b->d_t;
+    *np_max = b->np_max;
+    *device = b->device;
+    *stream = (void*)b->stream;
     return PBE_OK;
 }
 

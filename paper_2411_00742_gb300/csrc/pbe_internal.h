@@ -37,6 +37,15 @@ struct pbe_grid {
 
 namespace pbe {
 
+// one instance of a batch (device descriptor)
+struct BatchInst {
+    Kin K;
+    Geom g;
+    long long offset;   // first cell in the packed state
+    int rows;           // ceil(N / 32)
+    int pad;
+};
+
 // number of block partial slots the plain kernels of this grid use
 int plain_max_blocks(const Geom& g);
 

@@ -123,3 +123,37 @@ def test_autograd_function():
     supp = inst.n0 > 1e-3 * inst.n0.max()
     assert np.max(np.abs(n0.grad.cpu().numpy() - want_dn0)[supp]) <= REL_GRAD * np.max(np.abs(want_dn0))
     g.close()
+
+
+@pytest.mark.parametrize("K", [64, 9])
+def test_batched_vjp_matches_cpu_adjoint(K):
+    """The batched adjoint (one warp per instance) against the CPU adjoint,
+    instance by instance: 1-D instances with 500 cells and sampled kinetics
+    (the gradient batch workload), plus mixed sizes."""
+    import torch
+    import paper_2411_00742_gb300 as P
+    insts = pi.adjoint_batch_1d(20) + [x for x in pi.batch_1d(8, seed=77, t_out=pi.loss_times())]
+    insts.append(pi.config_1d(33))
+    insts[-1].t_out = pi.loss_times()
+    b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
+    b.set_state(b.pack([x.n0 for x in insts]))
+    cols = [1, 2, 3, 4, 5]
+    seeds = np.zeros((len(insts), 50, 6))
+    wants = []
+    for i, inst in enumerate(insts):
+        p = inst.problem
+        tgt = oracle.solve(p.with_theta(p.theta * pi.TARGET_FACTOR), inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+        r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+        seeds[i] = oracle.relative_loss_seeds(r, tgt, cols)
+        wants.append(oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds[i]))
+    dn0 = torch.zeros(b.total_cells, dtype=torch.float64, device="cuda")
+    dth, dC0 = b.vjp(pi.loss_times(), seeds, K, dn0_out=dn0)
+    dn0 = dn0.cpu().numpy()
+    b.close()
+    for i, (want, wdn0, wdC0) in enumerate(wants):
+        for j in (0, 1, 4, 5):
+            assert dth[i, j] == pytest.approx(want[j], rel=REL_GRAD, abs=1e-300), (i, j)
+        assert dC0[i] == pytest.approx(wdC0, rel=REL_GRAD)
+        mine = dn0[b.offsets[i]:b.offsets[i + 1]]
+        supp = insts[i].n0 > 1e-3 * insts[i].n0.max()
+        assert np.max(np.abs(mine - wdn0)[supp]) <= REL_GRAD * np.max(np.abs(wdn0)), i
