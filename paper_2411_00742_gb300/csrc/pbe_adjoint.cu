@@ -71,8 +71,8 @@ __device__ __forceinline__ FaceAdj face_adj(double nm2, double up, double dn, do
     const double a = up - nm2, b = dn - up;
     double pa = 0.0, pb = 0.0, half = 0.0;
     if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
-        const double s = a + b;
-        const double qa = b / s, qb = a / s;
+        const double rs = 1.0 / (a + b);   // one division per face
+        const double qa = b * rs, qb = a * rs;
         half = a * qa;
         // differences below 2^-959 count as flat for the derivative (their
         // ratio is decided by rounding of underflowing tails)

@@ -123,7 +123,7 @@ __device__ __forceinline__ void adj_stage(const double* nt, const double* lam, c
             const double a = up - nm2, b = dn - up;
             double pa = 0.0, pb = 0.0, half = 0.0;
             if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
-                const double sab = a + b, qa = b / sab, qb = a / sab;
+                const double rs = 1.0 / (a + b), qa = b * rs, qb = a * rs;   // one division per face
                 half = a * qa;
                 if (fabs(a) >= 1.0316916532478883e-289 && fabs(b) >= 1.0316916532478883e-289) {
                     pa = 2.0 * qa * qa;
@@ -407,7 +407,10 @@ extern "C" pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out
     const void* fn = nullptr;
     BATRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     BATRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    if (count < 1) goto out;
     while (wpb > 1 && (size_t)wpb * 10 * npa * sizeof(double) > (size_t)maxsm) wpb /= 2;
+    // few instances per SM: spread them so every SM's FP64 pipe works on some
+    while (wpb > 1 && (count + wpb - 1) / wpb < 2 * sms) wpb /= 2;
     smem = (size_t)wpb * 10 * npa * sizeof(double);
     if (smem > (size_t)maxsm) { rc = bafail(PBE_EINVAL, "instances too large for the batched adjoint"); goto out; }
     fn = wpb == 4 ? (const void*)k_batch_vjp<4> : (wpb == 2 ? (const void*)k_batch_vjp<2> : (const void*)k_batch_vjp<1>);
