@@ -262,6 +262,12 @@ pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int*
 pbe_status pbe_adam_update(double* w, const double* grad, double* m, double* v, int n, double lr, double beta1,
                            double beta2, double eps, int step, void* stream);
 
+/* Limit of every device-wide wait of the fused path (seconds; < 0 restores
+ * the default of about one second).  A wait that runs out ends the solve
+ * with PBE_ETIMEOUT and leaves the context usable; a limit of 0 makes any
+ * wait that does not complete at once run out (used to exercise that path). */
+pbe_status pbe_set_wait_limit(pbe_grid* g, double seconds);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* pbe_last_error(void);
 

@@ -109,6 +109,9 @@ class Grid:
     def set_path(self, path: str):
         _lib.check(self.lib.pbe_set_path(self.h, _PATHS[path]))
 
+    def set_wait_limit(self, seconds: float):
+        _lib.check(self.lib.pbe_set_wait_limit(self.h, float(seconds)))
+
     def set_max_steps(self, n: int):
         _lib.check(self.lib.pbe_set_max_steps(self.h, int(n)))
 

@@ -204,6 +204,7 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
     g->ncell = (size_t)nc;
     g->path = PBE_PATH_PLAIN;
     g->max_steps = 1000000;
+    g->wait_cycles = -1;
     g->max_blocks = pbe::plain_max_blocks(g->geo);
     if (g->max_blocks < 1024) g->max_blocks = 1024;
     bool ok = cudaMalloc(&g->d_n, sizeof(double) * nc) == cudaSuccess &&
@@ -253,6 +254,19 @@ pbe_status pbe_set_path(pbe_grid* g, int path)
     if (!g) return fail(PBE_EINVAL, "null grid");
     if (path != PBE_PATH_PLAIN && path != PBE_PATH_FUSED) return fail(PBE_EINVAL, "unknown path %d", path);
     g->path = path;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_wait_limit(pbe_grid* g, double seconds)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (seconds < 0.0) {
+        g->wait_cycles = -1;
+        return PBE_OK;
+    }
+    int khz = 0;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, g->device) != cudaSuccess || khz <= 0) khz = 2000000;
+    g->wait_cycles = (long long)(seconds * 1e3 * (double)khz);
     return PBE_OK;
 }
 

@@ -30,7 +30,7 @@ constexpr int kFNT = 256;     // threads per block (the reductions assume 256)
 constexpr int kFT1 = 1024;    // 1-D tile
 constexpr int kFTI = 16;      // 2-D tile rows
 constexpr int kFTJ = 32;      // 2-D tile columns
-constexpr long long kBarrierCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr long long kBarrierCycles = 2000000000LL;  // default wait limit: ~1 s at 2 GHz
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
 {
@@ -45,35 +45,82 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v)
 }
 
 // Device-wide barrier over gridDim.x co-resident blocks (cooperative launch).
-// bar[0] counts arrivals, bar[1] is the generation.  Returns false on timeout.
-__device__ bool grid_barrier(unsigned int* bar, unsigned int& gen, int* fail_sh)
+// bar[0] counts arrivals and only grows: the k-th barrier completes when it
+// reaches k * gridDim.x.  Thread 0 arrives with a release add (cumulative
+// over the writes the block barrier ordered before it) and waits with
+// acquire loads.  Returns false when the wait runs past `limit` cycles.
+__device__ __forceinline__ unsigned int atom_add_release(unsigned int* p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ bool grid_barrier(unsigned int* bar, unsigned int& gen, int* fail_sh, long long limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int target = gen + 1u;
+        const unsigned int target = (gen + 1u) * gridDim.x;
         int ok = 1;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar[0], 1u);
-        if (arrived == gridDim.x - 1u) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            st_release(&bar[1], target);
-        } else {
+        const unsigned int arrived = atom_add_release(&bar[0], 1u) + 1u;
+        if (arrived < target) {
             const long long t0 = clock64();
             unsigned int polls = 0;
-            while (ld_acquire(&bar[1]) != target) {
-                if (++polls > 64u) {
-                    if (clock64() - t0 > kBarrierCycles) { ok = 0; break; }
+            const unsigned int spin = limit > 0 ? 64u : 1u;
+            while (ld_acquire(&bar[0]) < target) {
+                if (++polls > spin) {
+                    if (clock64() - t0 > limit) { ok = 0; break; }
                     __nanosleep(20);
                 }
             }
         }
-        __threadfence();
-        gen = target;
+        gen += 1u;
         *fail_sh = !ok;
     }
     __syncthreads();
     return *fail_sh == 0;
+}
+
+// Block sum of one value (256 threads): warp butterflies, then thread 0 adds
+// the eight warp sums as a balanced tree.  Result in *res (shared).
+__device__ __forceinline__ void block_sum1(double v, double* wsum, double* res)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) *res = ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3])) + ((wsum[4] + wsum[5]) + (wsum[6] + wsum[7]));
+    __syncthreads();
+}
+
+// Cross-block sums of all NV slots by one warp: lane l < 3*NV sums slot
+// l % NV over the blocks b = l / NV (mod 3) as balanced trees of 16, then
+// the three lanes of each slot are added in a fixed order; lanes 0..NV-1
+// write the totals to out[].
+template <int NV>
+__device__ __forceinline__ void warp_sum_partials_all(const double* part, int G, double* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int v = lane % NV, ph = lane / NV;
+    double acc = 0.0;
+    if (ph < 3) {
+        for (int base = ph; base < G; base += 3 * 16) {
+            double a[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int b = base + 3 * q;
+                a[q] = b < G ? __ldcg(part + (size_t)b * kMaxMom + v) : 0.0;
+            }
+#pragma unroll
+            for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                for (int q = 0; q < w; ++q) a[q] += a[q + w];
+            acc += a[0];
+        }
+    }
+    const double a1 = __shfl_sync(0xffffffffu, acc, (lane + NV) & 31);
+    const double a2 = __shfl_sync(0xffffffffu, acc, (lane + 2 * NV) & 31);
+    if (lane < NV) out[lane] = (acc + a1) + a2;
 }
 
 // Deterministic block sum of NV values per thread through shared memory:
@@ -241,7 +288,7 @@ __device__ __forceinline__ double cell_update(const double* old, double* out, in
 template <int NDIM, bool ONE_TILE>
 __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
                                                    const double* t_out, double* rows, unsigned int* bar, int ntiles,
-                                                   int tiles_x)
+                                                   int tiles_x, long long wait_limit)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
@@ -322,23 +369,13 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 block_sum_smem<NM>(m, red, red2, res);
                 if (threadIdx.x < NM) pp[(size_t)blockIdx.x * kMaxMom + threadIdx.x] = res[threadIdx.x];
             } else {
-                double v1[1] = {m[VIDX]};
-                block_sum_smem<1>(v1, red, red2, res);
+                block_sum1(m[VIDX], red2, res);
                 if (threadIdx.x == 0) pp[(size_t)blockIdx.x * kMaxMom + VIDX] = res[0];
             }
-            if (!grid_barrier(bar, gen, &fail)) break;
+            if (!grid_barrier(bar, gen, &fail, wait_limit)) break;
             if (warp == 0) {
                 if (sc.moms) {
-                    int slots[NM];
-#pragma unroll
-                    for (int k = 0; k < NM; ++k) slots[k] = k;
-                    double tot[NM];
-                    warp_sum_partials<NM>(pp, G, slots, tot);
-                    if (threadIdx.x < NM) {
-#pragma unroll
-                        for (int k = 0; k < NM; ++k)
-                            if (threadIdx.x == k) msum[k] = tot[k];
-                    }
+                    warp_sum_partials_all<NM>(pp, G, msum);
                 } else {
                     const int slots[1] = {VIDX};
                     double tot[1];
@@ -407,8 +444,9 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     }
     e = cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned int), g->stream);
     if (e != cudaSuccess) return e;
+    long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
     void* args[] = {&g->d_n, &g->d_n1, &g->d_S, &g->kin, &g->geo, &g->d_part, &g->d_tout, &g->d_rows,
-                    &g->d_bar, (void*)&ntiles, &tiles_x};
+                    &g->d_bar, (void*)&ntiles, &tiles_x, &wait_limit};
     return cudaLaunchCooperativeKernel(fn, G, kFNT, args, 0, g->stream);
 }
 

@@ -31,6 +31,7 @@ struct pbe_grid {
     cudaGraphExec_t plain_exec;
     bool plain_graph_failed;
     double C_host, t_host;  // host mirror of the scalar state after the last synchronizing call
+    long long wait_cycles;  // device-wide wait limit of the fused path (-1: default ~1 s)
     __nv_bfloat16* d_mW;    // learned closure weights (bf16) and biases (fp32)
     float* d_mB;
 };

@@ -80,3 +80,24 @@ def test_fused_step_budget_and_nonfinite():
         g.solve(inst.t_out)
     assert e.value.status == 4
     g.close()
+
+
+def test_fused_wait_limit_runs_out_and_context_survives():
+    """Failure detection without a fault: a zero wait limit makes the device-wide
+    barrier give up (status PBE_ETIMEOUT read by the host); the grid and the
+    context stay usable and the next solve with the default limit is exact."""
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(256)
+    g = P.Grid.from_problem(inst.problem, path="fused")
+    g.set_wait_limit(0.0)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    with pytest.raises(P.PbeError) as e:
+        g.solve(inst.t_out)
+    assert e.value.status == 5
+    g.set_wait_limit(-1.0)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, steps = g.solve(inst.t_out)
+    g.close()
+    want = oracle.solve_instance(inst)
+    assert steps == want["steps"]
+    assert_rows_close(rows, want["rows"])
