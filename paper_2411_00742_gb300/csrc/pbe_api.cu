@@ -64,7 +64,7 @@ void free_grid_buffers(pbe_grid* g)
 {
     if (g->plain_exec) cudaGraphExecDestroy(g->plain_exec);
     cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom); cudaFree(g->d_bar);
-    cudaFree(g->d_tout); cudaFree(g->d_rows);
+    cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
     cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage);
 }
 
@@ -76,11 +76,12 @@ pbe_status ensure_tout_capacity(pbe_grid* g, int n_out)
     int cap = g->tout_cap ? g->tout_cap : 64;
     while (cap < n_out) cap *= 2;
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    cudaFree(g->d_tout); cudaFree(g->d_rows);
-    g->d_tout = nullptr; g->d_rows = nullptr; g->tout_cap = 0;
+    cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
+    g->d_tout = nullptr; g->d_rows = nullptr; g->d_rowpart = nullptr; g->tout_cap = 0;
     if (g->plain_exec) { cudaGraphExecDestroy(g->plain_exec); g->plain_exec = nullptr; }
     if (cudaMalloc(&g->d_tout, sizeof(double) * cap) != cudaSuccess ||
-        cudaMalloc(&g->d_rows, sizeof(double) * cap * 12) != cudaSuccess)
+        cudaMalloc(&g->d_rows, sizeof(double) * cap * 12) != cudaSuccess ||
+        cudaMalloc(&g->d_rowpart, sizeof(double) * (size_t)cap * (g->max_blocks / 2 + 1) * 10) != cudaSuccess)
         return fail(PBE_ENOMEM, "cudaMalloc of %d output rows failed", cap);
     g->tout_cap = cap;
     return PBE_OK;

@@ -47,6 +47,7 @@ struct Scal {
     double last_dt;             // length of the last completed step
     long long steps, max_steps;
     int clipped, out_idx, n_out, done, status;
+    int row_first;              // first row a fused solve emitted (its moments are summed afterwards)
     unsigned int counter;       // arrival counter of the last-block reductions
 };
 

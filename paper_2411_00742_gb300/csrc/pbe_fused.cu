@@ -288,7 +288,7 @@ __device__ __forceinline__ double cell_update(const double* old, double* out, in
 template <int NDIM, bool ONE_TILE>
 __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
                                                    const double* t_out, double* rows, unsigned int* bar, int ntiles,
-                                                   int tiles_x, long long wait_limit)
+                                                   int tiles_x, long long wait_limit, double* rowpart)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
@@ -300,9 +300,15 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     __shared__ double msum[NM];
     __shared__ int fail;
     __shared__ FusedSmem<NDIM> sm;
-    if (threadIdx.x == 0) s = *S;
+    if (threadIdx.x == 0) {
+        s = *S;
+        s.row_first = s.out_idx;   // rows before this index came from the prologue
+    }
     __syncthreads();
-    if (s.done) return;
+    if (s.done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->row_first = s.row_first;
+        return;
+    }
     const int G = gridDim.x;
     const int warp = threadIdx.x >> 5;
     double* part1 = part;                        // stage-1 partials [G][kMaxMom]
@@ -365,29 +371,55 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 __syncthreads();
             }
             double* pp = stage == 1 ? part1 : part2;
+            const int row_here = s.out_idx;
+            // only the volume moment is on the critical path; on output steps
+            // the per-thread moments wait in shared memory and are reduced in
+            // the overlap window, the row completed after the solve
             if (sc.moms) {
-                block_sum_smem<NM>(m, red, red2, res);
-                if (threadIdx.x < NM) pp[(size_t)blockIdx.x * kMaxMom + threadIdx.x] = res[threadIdx.x];
-            } else {
-                block_sum1(m[VIDX], red2, res);
-                if (threadIdx.x == 0) pp[(size_t)blockIdx.x * kMaxMom + VIDX] = res[0];
+#pragma unroll
+                for (int k = 0; k < NM; ++k) red[threadIdx.x * (NM + 1) + k] = m[k];
             }
+            block_sum1(m[VIDX], red2, res);
+            if (threadIdx.x == 0) pp[(size_t)blockIdx.x * kMaxMom + VIDX] = res[0];
             if (!grid_barrier(bar, gen, &fail, wait_limit)) break;
             if (warp == 0) {
-                if (sc.moms) {
-                    warp_sum_partials_all<NM>(pp, G, msum);
-                } else {
-                    const int slots[1] = {VIDX};
-                    double tot[1];
-                    warp_sum_partials<1>(pp, G, slots, tot);
-                    if (threadIdx.x == 0) msum[VIDX] = tot[0];
-                }
+                const int slots[1] = {VIDX};
+                double tot[1];
+                warp_sum_partials<1>(pp, G, slots, tot);
+                if (threadIdx.x == 0) msum[VIDX] = tot[0];
                 __syncwarp();
                 if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
                 else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
             } else {
                 // faces of the next stage's input for this block's first tile
                 fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, kFNT - 32, GroupSync());
+                if (sc.moms) {
+                    // two-level sum of the block's moments: 16 threads per moment, then one
+                    GroupSync()();
+                    const int t = threadIdx.x - 32;
+                    if (t < 16 * NM) {
+                        const int v = t >> 4, ch = t & 15;
+                        double a[16];
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) a[r] = red[(ch * 16 + r) * (NM + 1) + v];
+#pragma unroll
+                        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                            for (int r = 0; r < w; ++r) a[r] += a[r + w];
+                        red2[256 - 16 * NM + v * 16 + ch] = a[0];
+                    }
+                    GroupSync()();
+                    if (t < NM) {
+                        double a[16];
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) a[r] = red2[256 - 16 * NM + t * 16 + r];
+#pragma unroll
+                        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                            for (int r = 0; r < w; ++r) a[r] += a[r + w];
+                        rowpart[((size_t)row_here * G + blockIdx.x) * NM + t] = a[0];
+                    }
+                }
             }
             __syncthreads();
             if (s.done) break;
@@ -404,6 +436,19 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     }
 }
 
+// Moments of the rows the fused solve emitted: sums of the per-block partials
+// in block order (one block per row, one thread per moment).
+template <int NDIM>
+__global__ void k_fused_rows(const double* rowpart, int G, const Scal* S, double* rows)
+{
+    constexpr int NM = NDIM == 1 ? 4 : 10;
+    const int r = S->row_first + blockIdx.x;
+    if (r >= S->out_idx || threadIdx.x >= NM) return;
+    double acc = 0.0;
+    for (int b = 0; b < G; ++b) acc += rowpart[((size_t)r * G + b) * NM + threadIdx.x];
+    rows[(size_t)r * (NM + 2) + 1 + threadIdx.x] = acc;
+}
+
 static int fused_tiles(const Geom& g, int* tiles_x)
 {
     if (g.ndim == 1) {
@@ -418,7 +463,6 @@ bool fused_supported(const pbe_grid* g) { return g->d_bar != nullptr; }
 
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
 {
-    (void)n_out;
     int tiles_x;
     const int ntiles = fused_tiles(g->geo, &tiles_x);
     int sms = 0;
@@ -446,8 +490,13 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     if (e != cudaSuccess) return e;
     long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
     void* args[] = {&g->d_n, &g->d_n1, &g->d_S, &g->kin, &g->geo, &g->d_part, &g->d_tout, &g->d_rows,
-                    &g->d_bar, (void*)&ntiles, &tiles_x, &wait_limit};
-    return cudaLaunchCooperativeKernel(fn, G, kFNT, args, 0, g->stream);
+                    &g->d_bar, (void*)&ntiles, &tiles_x, &wait_limit, &g->d_rowpart};
+    e = cudaLaunchCooperativeKernel(fn, G, kFNT, args, 0, g->stream);
+    if (e != cudaSuccess) return e;
+    const int nrows = n_out > 0 ? n_out : 1;
+    if (g->geo.ndim == 1) k_fused_rows<1><<<nrows, 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
+    else k_fused_rows<2><<<nrows, 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
+    return cudaGetLastError();
 }
 
 }  // namespace pbe

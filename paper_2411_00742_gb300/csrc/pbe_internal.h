@@ -24,6 +24,7 @@ struct pbe_grid {
     int max_blocks;
     double* d_tout;     // output times (capacity tout_cap)
     double* d_rows;     // output rows (capacity tout_cap rows of 12)
+    double* d_rowpart;  // fused path: per-row, per-block moment partials (tout_cap x max_blocks/2 x 10)
     int tout_cap;
     pbe::Scal* h_S;     // pinned copy of the scalars
     double* h_stage;    // pinned staging for small host<->device copies (64 doubles)
