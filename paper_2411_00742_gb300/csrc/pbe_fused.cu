@@ -184,8 +184,16 @@ __device__ __forceinline__ void warp_sum_partials(const double* part, int G, con
         for (int k = 0; k < NV; ++k) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
 }
 
-struct GroupSync {  // named barrier over warps 1..7
-    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(kFNT - 32) : "memory"); }
+// In the window after each barrier warp 0 runs the scalar chain, warps 1-3
+// compute the next stage's faces (enough to keep the FP64 pipe busy while
+// leaving issue slots to warp 0's dependent chain), warps 4-7 reduce the
+// deferred output moments.
+constexpr int kFaceWarps = 3;
+struct GroupSync {  // named barrier over the face warps 1..kFaceWarps
+    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(32 * kFaceWarps) : "memory"); }
+};
+struct MomSync {    // named barrier over warps kFaceWarps+1..7
+    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 2, %0;" ::"r"(kFNT - 32 * (kFaceWarps + 1)) : "memory"); }
 };
 struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
@@ -390,35 +398,35 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 __syncwarp();
                 if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
                 else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
-            } else {
+            } else if (warp <= kFaceWarps) {
                 // faces of the next stage's input for this block's first tile
-                fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, kFNT - 32, GroupSync());
-                if (sc.moms) {
-                    // two-level sum of the block's moments: 16 threads per moment, then one
-                    GroupSync()();
-                    const int t = threadIdx.x - 32;
-                    if (t < 16 * NM) {
-                        const int v = t >> 4, ch = t & 15;
-                        double a[16];
+                fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, 32 * kFaceWarps,
+                                  GroupSync());
+            } else if (sc.moms) {
+                // two-level sum of the block's moments: 16 threads per moment, then one
+                constexpr int NT2 = kFNT - 32 * (kFaceWarps + 1);
+                const int t0 = threadIdx.x - 32 * (kFaceWarps + 1);
+                for (int t = t0; t < 16 * NM; t += NT2) {
+                    const int v = t >> 4, ch = t & 15;
+                    double a[16];
 #pragma unroll
-                        for (int r = 0; r < 16; ++r) a[r] = red[(ch * 16 + r) * (NM + 1) + v];
+                    for (int r = 0; r < 16; ++r) a[r] = red[(ch * 16 + r) * (NM + 1) + v];
 #pragma unroll
-                        for (int w = 8; w > 0; w >>= 1)
+                    for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
-                            for (int r = 0; r < w; ++r) a[r] += a[r + w];
-                        red2[256 - 16 * NM + v * 16 + ch] = a[0];
-                    }
-                    GroupSync()();
-                    if (t < NM) {
-                        double a[16];
+                        for (int r = 0; r < w; ++r) a[r] += a[r + w];
+                    red2[256 - 16 * NM + v * 16 + ch] = a[0];
+                }
+                MomSync()();
+                if (t0 < NM) {
+                    double a[16];
 #pragma unroll
-                        for (int r = 0; r < 16; ++r) a[r] = red2[256 - 16 * NM + t * 16 + r];
+                    for (int r = 0; r < 16; ++r) a[r] = red2[256 - 16 * NM + t0 * 16 + r];
 #pragma unroll
-                        for (int w = 8; w > 0; w >>= 1)
+                    for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
-                            for (int r = 0; r < w; ++r) a[r] += a[r + w];
-                        rowpart[((size_t)row_here * G + blockIdx.x) * NM + t] = a[0];
-                    }
+                        for (int r = 0; r < w; ++r) a[r] += a[r + w];
+                    rowpart[((size_t)row_here * G + blockIdx.x) * NM + t0] = a[0];
                 }
             }
             __syncthreads();
