@@ -184,11 +184,11 @@ __device__ __forceinline__ void warp_sum_partials(const double* part, int G, con
         for (int k = 0; k < NV; ++k) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
 }
 
-// In the window after each barrier warp 0 runs the scalar chain, warps 1-3
+// In the window after each barrier warp 0 runs the scalar chain, warps 1-6
 // compute the next stage's faces (enough to keep the FP64 pipe busy while
-// leaving issue slots to warp 0's dependent chain), warps 4-7 reduce the
-// deferred output moments.
-constexpr int kFaceWarps = 3;
+// leaving issue slots to warp 0's dependent chain) and warp 7 reduces the
+// deferred output moments (warp 7).
+constexpr int kFaceWarps = 6;
 struct GroupSync {  // named barrier over the face warps 1..kFaceWarps
     __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(32 * kFaceWarps) : "memory"); }
 };
