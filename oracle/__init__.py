@@ -56,7 +56,9 @@ class Params(ctypes.Structure):
                 ("cs0", ctypes.c_double), ("cs1", ctypes.c_double), ("cs2", ctypes.c_double),
                 ("T0", ctypes.c_double), ("T1", ctypes.c_double), ("t_cool", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("mlp", ctypes.POINTER(ctypes.c_double))]
+                ("mlp", ctypes.POINTER(ctypes.c_double)),
+                ("scheme", ctypes.c_int), ("growth_form", ctypes.c_int), ("solubility_form", ctypes.c_int),
+                ("ea1", ctypes.c_double), ("ea2", ctypes.c_double)]
 
 
 _lib = None
@@ -116,7 +118,9 @@ def params(problem, mlp=None) -> Params:
                float(p.kg[0]), float(p.g[0]), float(p.kg[1]), float(p.g[1]),
                float(p.kb), float(p.b),
                float(p.csat[0]), float(p.csat[1]), float(p.csat[2]),
-               float(p.T0), float(p.T1), float(p.t_cool), float(p.kappa), float(p.cfl), mp)
+               float(p.T0), float(p.T1), float(p.t_cool), float(p.kappa), float(p.cfl), mp,
+               int(getattr(p, "scheme", 0)), int(getattr(p, "growth_form", 0)), int(getattr(p, "solubility_form", 0)),
+               float(getattr(p, "ea", (0.0, 0.0))[0]), float(getattr(p, "ea", (0.0, 0.0))[1]))
     P._keep = arr if mlp is not None else None
     return P
 

@@ -22,12 +22,19 @@ def _kin(problem, C, t):
         return problem.kg[0], (problem.kg[1] if problem.ndim == 2 else 0.0), problem.kb
     frac = t / problem.t_cool if t < problem.t_cool else 1.0
     T = problem.T0 + (problem.T1 - problem.T0) * frac
-    cs = problem.csat[0] + problem.csat[1] * T + problem.csat[2] * T * T
+    if getattr(problem, "solubility_form", 0) == 1:
+        cs = problem.csat[0] * np.exp(problem.csat[1] * T)
+    else:
+        cs = problem.csat[0] + problem.csat[1] * T + problem.csat[2] * T * T
     s = C / cs - 1.0
     if not s > 0.0:
         return 0.0, 0.0, 0.0
-    G2 = problem.kg[1] * s ** problem.g[1] if problem.ndim == 2 else 0.0
-    return problem.kg[0] * s ** problem.g[0], G2, problem.kb * s ** problem.b
+    a1 = a2 = 1.0
+    if getattr(problem, "growth_form", 0) == 1:   # Arrhenius factor of Appendix A
+        a1 = np.exp(-problem.ea[0] / (T + 273.15))
+        a2 = np.exp(-problem.ea[1] / (T + 273.15))
+    G2 = a2 * problem.kg[1] * s ** problem.g[1] if problem.ndim == 2 else 0.0
+    return a1 * problem.kg[0] * s ** problem.g[0], G2, problem.kb * s ** problem.b
 
 
 def _rhs(problem, y, t, L0):

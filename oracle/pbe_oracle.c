@@ -40,6 +40,11 @@ typedef struct {
     double kappa;         /* rho_c k_v u */
     double cfl;
     const double* mlp;    /* learned closure weights (NULL: power law / fixed) */
+    int scheme;           /* 0: SSP-RK2 semi-discrete, unsplit; 1: Eq. 3 (one-step high resolution) with
+                             Godunov dimensional splitting, dt = cfl * min(dL1/G1, dL2/G2) */
+    int growth_form;      /* 0: G = kg s^g; 1: Arrhenius form of Appendix A, G = kg exp(-ea/(T+273.15)) s^g */
+    int solubility_form;  /* 0: c* = cs0 + cs1 T + cs2 T^2; 1: c* = cs0 exp(cs1 T) (Appendix A) */
+    double ea1, ea2;      /* activation temperatures (K) of the Arrhenius form */
 } orc_params;
 
 /* Learned kinetics closure (the empirical hybrid model of Sec. 4.2: a network
@@ -155,9 +160,10 @@ void orc_moments(const orc_params* p, const double* n, double* mu) { moments_r(p
 void orc_step(const orc_params* p, double* n, double C, double t, double t_next, double* out5)
 {
     ctx_r c = make_ctx_r(p);
-    double* work = (double*)malloc(3 * ncells(p) * sizeof(double));
+    double* work = (double*)malloc((3 * ncells(p) + 16) * sizeof(double));
     steprec_r rec;
-    int clipped = step_r(&c, n, work, &C, &t, t_next, &rec);
+    int clipped = p->scheme == 1 ? step_lw_r(&c, n, work, &C, &t, t_next, &rec)
+                                 : step_r(&c, n, work, &C, &t, t_next, &rec);
     out5[0] = rec.dt; out5[1] = C; out5[2] = t; out5[3] = rec.C1; out5[4] = clipped;
     free(work);
 }
@@ -438,6 +444,7 @@ static void mlp_kinetics_adjoint(const orc_params* p, double C, double t, double
 long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const double* t_out, int n_out,
              const double* drows, double* dtheta, double* dn0, double* dC0, double* dmlp)
 {
+    if (p->scheme != 0 || p->growth_form != 0 || p->solubility_form != 0) return -1;  /* adjoint of the SSP-RK2 power-law form only */
     size_t nc = ncells(p);
     int ncol = ncols(p), nm = ncol - 2;
     double area = (p->ndim == 1) ? p->lmax1 / p->n1 : (p->lmax1 / p->n1) * (p->lmax2 / p->n2);

@@ -66,6 +66,13 @@ static SCALAR SFX(temperature)(const orc_params* p, SCALAR t)
     return p->T0 + (p->T1 - p->T0) * frac;
 }
 
+/* Solubility: polynomial, or the exponential c* = a exp(b T) of Appendix A. */
+static SCALAR SFX(solubility)(const orc_params* p, SCALAR T)
+{
+    if (p->solubility_form == 1) return p->cs0 * SEXP(p->cs1 * T);
+    return p->cs0 + p->cs1 * T + p->cs2 * T * T;
+}
+
 /* Kinetics at concentration C and time t.
  * S = c / c*(T) (Sec. 2.1); growth and nucleation only for S > 1
  * (Appendix A: growth "only applies when S exceeds one").
@@ -76,7 +83,7 @@ static void SFX(kinetics)(const SFX(ctx)* c, SCALAR C, SCALAR t, SCALAR ratio,
     const orc_params* p = c->p;
     if (c->w) {  /* learned closure */
         SCALAR T = SFX(temperature)(p, t);
-        SCALAR csat = p->cs0 + p->cs1 * T + p->cs2 * T * T;
+        SCALAR csat = SFX(solubility)(p, T);
         SCALAR s = C / csat - 1.0;
         if (!(RE(s) > 0.0)) {
             *G1 = 0.0; *G2 = 0.0; *B = 0.0;
@@ -97,14 +104,19 @@ static void SFX(kinetics)(const SFX(ctx)* c, SCALAR C, SCALAR t, SCALAR ratio,
         return;
     }
     SCALAR T = SFX(temperature)(p, t);
-    SCALAR csat = p->cs0 + p->cs1 * T + p->cs2 * T * T;
+    SCALAR csat = SFX(solubility)(p, T);
     SCALAR s = C / csat - 1.0;
     if (!(RE(s) > 0.0)) {
         *G1 = 0.0; *G2 = 0.0; *B = 0.0;
         return;
     }
-    *G1 = c->kg1 * SPOW(s, c->g1);
-    *G2 = (p->ndim == 2) ? c->kg2 * SPOW(s, c->g2) : (SCALAR)0.0;
+    SCALAR a1 = 1.0, a2 = 1.0;
+    if (p->growth_form == 1) {  /* Appendix A: kg exp(-kg2 / (T + 273.15)) (S - 1)^kg3 */
+        a1 = SEXP(-p->ea1 / (T + 273.15));
+        a2 = SEXP(-p->ea2 / (T + 273.15));
+    }
+    *G1 = c->kg1 * a1 * SPOW(s, c->g1);
+    *G2 = (p->ndim == 2) ? c->kg2 * a2 * SPOW(s, c->g2) : (SCALAR)0.0;
     *B = c->kb * SPOW(s, c->b);
 }
 
@@ -117,7 +129,14 @@ static int SFX(timestep)(const SFX(ctx)* c, SCALAR G1, SCALAR G2, SCALAR t,
     const orc_params* p = c->p;
     double d1 = p->lmax1 / p->n1;
     SCALAR rate = G1 / d1;
-    if (p->ndim == 2) rate = rate + G2 / (p->lmax2 / p->n2);
+    if (p->ndim == 2) {
+        SCALAR r2 = G2 / (p->lmax2 / p->n2);
+        if (p->scheme == 1) {  /* SI Sec. S1.1: dt = nu min(dL1/G1, dL2/G2) */
+            if (RE(r2) > RE(rate)) rate = r2;
+        } else {
+            rate = rate + r2;
+        }
+    }
     SCALAR rem = t_next - t;
     if (RE(rate) > 0.0) {
         SCALAR dtc = p->cfl / rate;
@@ -311,6 +330,61 @@ static int SFX(step)(const SFX(ctx)* c, SCALAR* n, SCALAR* work, SCALAR* C, SCAL
     return clipped;
 }
 
+/* One sweep of Eq. 3 along a line of N cells with element stride st:
+ * f_i <- f_i - nu (f_i - f_{i-1})
+ *        - nu (1 - nu) / 2 [phi_{i+1/2} (f_{i+1} - f_i) - phi_{i-1/2} (f_i - f_{i-1})],
+ * phi the van Leer limiter of the smoothness ratio (SI Sec. S1.1), zero
+ * ghost cells; line is overwritten, tmp holds N values. */
+static void SFX(lw_line)(SCALAR* line, long st, int N, SCALAR nu, SCALAR* tmp)
+{
+    for (int i = 0; i < N; ++i) {
+        SCALAR fm2 = (i - 2 >= 0) ? line[(long)(i - 2) * st] : (SCALAR)0.0;
+        SCALAR fm1 = (i - 1 >= 0) ? line[(long)(i - 1) * st] : (SCALAR)0.0;
+        SCALAR f0 = line[(long)i * st];
+        SCALAR fp1 = (i + 1 < N) ? line[(long)(i + 1) * st] : (SCALAR)0.0;
+        SCALAR lim_p = SFX(psi)(f0 - fm1, fp1 - f0);    /* phi_{i+1/2} (f_{i+1} - f_i) */
+        SCALAR lim_m = SFX(psi)(fm1 - fm2, f0 - fm1);   /* phi_{i-1/2} (f_i - f_{i-1}) */
+        tmp[i] = f0 - nu * (f0 - fm1) - 0.5 * nu * (1.0 - nu) * (lim_p - lim_m);
+    }
+    for (int i = 0; i < N; ++i) line[(long)i * st] = tmp[i];
+}
+
+/* One time step of the paper's scheme: Eq. 3 along L1, then along L2
+ * (Godunov splitting, Sec. 2.1), nucleation inflow B dt / dA into the
+ * smallest-size cell, then the solute balance of Eq. 4. */
+static int SFX(step_lw)(const SFX(ctx)* c, SCALAR* n, SCALAR* work, SCALAR* C, SCALAR* t, double t_next,
+                        SFX(steprec)* rec)
+{
+    const orc_params* p = c->p;
+    SCALAR G1, G2, B, dt, t_new;
+    SCALAR V0 = SFX(volume)(p, n);
+    SCALAR r0 = c->w ? V0 / SFX(mu0)(p, n) : (SCALAR)0.0;
+    SFX(kinetics)(c, *C, *t, r0, &G1, &G2, &B);
+    int clipped = SFX(timestep)(c, G1, G2, *t, t_next, &dt, &t_new);
+    double d1 = p->lmax1 / p->n1;
+    if (p->ndim == 1) {
+        SFX(lw_line)(n, 1, p->n1, G1 * dt / d1, work);
+        n[0] = n[0] + B * dt / d1;
+    } else {
+        int N1 = p->n1, N2 = p->n2;
+        double d2 = p->lmax2 / N2;
+        for (int j = 0; j < N2; ++j) SFX(lw_line)(n + j, N2, N1, G1 * dt / d1, work);
+        for (int i = 0; i < N1; ++i) SFX(lw_line)(n + (size_t)i * N2, 1, N2, G2 * dt / d2, work);
+        n[0] = n[0] + B * dt / (d1 * d2);
+    }
+    SCALAR C_new = *C - p->kappa * (SFX(volume)(p, n) - V0);
+    if (rec) {
+        rec->dt = dt; rec->C = *C; rec->C1 = *C; rec->t = *t; rec->t_new = t_new;
+        rec->G1a = G1; rec->G2a = G2; rec->Ba = B;
+        rec->G1b = 0.0; rec->G2b = 0.0; rec->Bb = 0.0;
+        rec->clipped = clipped;
+        rec->r0 = r0; rec->r1 = 0.0;
+    }
+    *C = C_new;
+    *t = t_new;
+    return clipped;
+}
+
 /* Output row: t, moments, C. */
 static void SFX(emit)(const orc_params* p, const SCALAR* n, SCALAR C, SCALAR t, SCALAR* row)
 {
@@ -330,13 +404,16 @@ static long SFX(solve)(const SFX(ctx)* c, SCALAR* n, SCALAR* C, SCALAR* t,
     const orc_params* p = c->p;
     size_t nc = (size_t)p->n1 * (p->ndim == 2 ? p->n2 : 1);
     int ncol = (p->ndim == 1) ? 6 : 12;
-    SCALAR* work = (SCALAR*)malloc(3 * nc * sizeof(SCALAR));
+    SCALAR* work = (SCALAR*)malloc((3 * nc + 16) * sizeof(SCALAR));
     long steps = 0;
     for (int j = 0; j < n_out; ++j) {
         while (RE(*t) < t_out[j]) {
             if (recs && steps >= max_recs) { free(work); return -1; }
             if (snaps) memcpy(snaps + (size_t)steps * nc, n, nc * sizeof(SCALAR));
-            SFX(step)(c, n, work, C, t, t_out[j], recs ? recs + steps : NULL);
+            if (p->scheme == 1)
+                SFX(step_lw)(c, n, work, C, t, t_out[j], recs ? recs + steps : NULL);
+            else
+                SFX(step)(c, n, work, C, t, t_out[j], recs ? recs + steps : NULL);
             if (recs) recs[steps].out_index = -1;
             ++steps;
         }

@@ -45,6 +45,10 @@ class Problem:
     kappa: float = KAPPA
     cfl: float = 0.5
     fixed_kinetics: bool = False
+    scheme: int = 0            # 0: SSP-RK2 unsplit; 1: Eq. 3 with Godunov splitting
+    growth_form: int = 0       # 0: kg s^g; 1: Arrhenius kg exp(-ea/(T+273.15)) s^g
+    solubility_form: int = 0   # 0: polynomial csat; 1: csat[0] exp(csat[1] T)
+    ea: tuple = (0.0, 0.0)     # activation temperatures of the Arrhenius form (K)
 
     @property
     def ncell(self) -> int:
@@ -162,3 +166,41 @@ def adjoint_2d(N: int = 128) -> Instance:
 
 def adjoint_batch_1d(count: int = 256, seed: int = 2412) -> list[Instance]:
     return batch_1d(count, seed=seed, N_fixed=500, t_out=loss_times())
+
+
+# ---------------------------------------------------------------------------
+# The paper's own base case (Table 1 and Appendix A, Table A.1): 2-D growth-only
+# batch crystallizer at constant 15 C, exponential solubility, Arrhenius growth,
+# seed normal in both lengths scaled by the seed mass, one-step high-resolution
+# scheme with Godunov splitting at Courant number 0.9.
+# ---------------------------------------------------------------------------
+RHO_C = 1.11e-12            # g / um^3
+KV = math.pi / 4.0          # cylinder
+
+
+def paper_seed_2d(N1: int, N2: int, lmax1: float = 1200.0, lmax2: float = 600.0, mean=(400.0, 250.0),
+                  sd=(30.0, 30.0), seed_mass: float = 1.0) -> np.ndarray:
+    """Normal seed in both lengths, scaled so that rho_c k_v sum x1 x2^2 n dA equals
+    the seed mass (SI Sec. S1.3, scale factor beta)."""
+    d1, d2 = lmax1 / N1, lmax2 / N2
+    x1 = ((np.arange(N1) + 0.5) * d1)[:, None]
+    x2 = ((np.arange(N2) + 0.5) * d2)[None, :]
+    f = np.exp(-0.5 * ((x1 - mean[0]) / sd[0]) ** 2 - 0.5 * ((x2 - mean[1]) / sd[1]) ** 2)
+    mass = RHO_C * KV * float(np.sum(x1 * x2 * x2 * f)) * d1 * d2
+    return f * (seed_mass / mass)
+
+
+def paper_base_case(N1: int = 1200, N2: int | None = None, t_end: float = 3600.0, every: float | None = None) -> Instance:
+    """Table 1 / Table A.1: 1200 x 600 um, 1 um bins at N1 = 1200 (N2 = N1 / 2), T = 15 C,
+    c0 = 8 g/kg, seed mass 1 g (means 400/250 um, sd 30 um), rho_c = 1.11e-12 g/um^3,
+    k_v = pi/4, c* = 3.37 exp(0.036 T) g/kg, G1 = 8.86e6 um/min exp(-2450/(T+273.15)) (S-1)^3.7,
+    G2 = 4.088e5 um/min exp(-2400/(T+273.15)) (S-1)^2.5, no nucleation, Courant number 0.9.
+    Concentration in g/kg and n in # per kg per um^2, so kappa = rho_c k_v.  The simulated
+    time is read as one hour (the table's "1000 [hour]" is garbled)."""
+    N2 = N1 // 2 if N2 is None else N2
+    p = Problem(ndim=2, ncells=(N1, N2), lmax=(1200.0, 600.0), kg=(8.86e6 / 60.0, 4.088e5 / 60.0),
+                g=(3.7, 2.5), kb=0.0, b=2.0, csat=(3.37, 0.036, 0.0), T0=15.0, T1=15.0, t_cool=3600.0,
+                kappa=RHO_C * KV, cfl=0.9, scheme=1, growth_form=1, solubility_form=1, ea=(2450.0, 2400.0))
+    n0 = paper_seed_2d(N1, N2)
+    t_out = np.array([t_end]) if every is None else output_times(t_end, every)
+    return Instance(p, n0, 8.0, 0.0, t_out)
