@@ -56,6 +56,13 @@ typedef int pbe_status;
 #define PBE_KINETICS_FIXED 1     /* G_d = kg[d], B = kb, independent of S (tests)           */
 #define PBE_KINETICS_MLP 2       /* learned closure set by pbe_set_closure (plain path)      */
 
+/* time schemes */
+#define PBE_SCHEME_SSPRK2 0 /* semi-discrete limited fluxes, two-stage SSP Runge-Kutta, both
+                               directions at once, dt = cfl / (G1/dL1 + G2/dL2)           */
+#define PBE_SCHEME_PAPER 1  /* Eq. 3 (one-step high resolution, van Leer limiter) with Godunov
+                               dimensional splitting (L1 sweep then L2 sweep),
+                               dt = cfl min(dL1/G1, dL2/G2) (SI Sec. S1.1); plain path only  */
+
 /* execution paths of pbe_solve */
 #define PBE_PATH_PLAIN 0 /* two stage kernels per step, device-resident scalars, CUDA graph loop */
 #define PBE_PATH_FUSED 1 /* one persistent kernel for the whole solve                              */
@@ -74,6 +81,10 @@ typedef struct {
     double t_cool;     /* ... over t_cool seconds (> 0), constant afterwards    */
     double kappa;      /* rho_c k_v u: g/g of solute per um^3/kg of crystal     */
     double cfl;        /* Courant number nu of the CFL step (0 < cfl <= 1)      */
+    int scheme;        /* PBE_SCHEME_SSPRK2 or PBE_SCHEME_PAPER                  */
+    int growth_form;   /* 0: G = kg s^g; 1: Arrhenius G = kg exp(-ea/(T+273.15)) s^g (Appendix A) */
+    int solubility_form; /* 0: polynomial csat; 1: c* = csat[0] exp(csat[1] T) (Appendix A) */
+    double ea[2];      /* activation temperatures of the Arrhenius form (K)      */
 } pbe_kinetics;
 
 /* Create a grid of ndim (1 or 2) dimensions with ncells[d] >= 1 cells on

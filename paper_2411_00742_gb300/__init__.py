@@ -44,6 +44,11 @@ def kinetics_struct(problem, theta=None, closure: bool = False) -> Kinetics:
         k.csat[i] = float(problem.csat[i])
     k.T0, k.T1, k.t_cool = float(problem.T0), float(problem.T1), float(problem.t_cool)
     k.kappa, k.cfl = float(problem.kappa), float(problem.cfl)
+    k.scheme = int(getattr(problem, "scheme", 0))
+    k.growth_form = int(getattr(problem, "growth_form", 0))
+    k.solubility_form = int(getattr(problem, "solubility_form", 0))
+    ea = getattr(problem, "ea", (0.0, 0.0))
+    k.ea[0], k.ea[1] = float(ea[0]), float(ea[1])
     return k
 
 

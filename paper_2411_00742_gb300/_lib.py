@@ -26,7 +26,9 @@ class Kinetics(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("kg", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
                 ("kb", ctypes.c_double), ("b", ctypes.c_double), ("csat", ctypes.c_double * 3),
                 ("T0", ctypes.c_double), ("T1", ctypes.c_double), ("t_cool", ctypes.c_double),
-                ("kappa", ctypes.c_double), ("cfl", ctypes.c_double)]
+                ("kappa", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("scheme", ctypes.c_int), ("growth_form", ctypes.c_int), ("solubility_form", ctypes.c_int),
+                ("ea", ctypes.c_double * 2)]
 
 
 class Instance(ctypes.Structure):

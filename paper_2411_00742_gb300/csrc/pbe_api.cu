@@ -147,7 +147,8 @@ pbe_status finish_call(pbe_grid* g)
 pbe_status run_solve(pbe_grid* g, int n_out)
 {
     CUDA_TRY(pbe::launch_prologue(g, n_out, g->max_steps, nullptr));
-    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g) && g->kin.kind != PBE_KINETICS_MLP) {
+    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g) && g->kin.kind != PBE_KINETICS_MLP &&
+        g->kin.scheme == PBE_SCHEME_SSPRK2) {
         CUDA_TRY(pbe::launch_fused_solve(g, n_out));
         return PBE_OK;
     }
@@ -287,6 +288,11 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
         return fail(PBE_ESTATE, "set the closure weights (pbe_set_closure) before selecting PBE_KINETICS_MLP");
     if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
     if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
+    if (k->scheme != PBE_SCHEME_SSPRK2 && k->scheme != PBE_SCHEME_PAPER) return fail(PBE_EINVAL, "unknown scheme %d", k->scheme);
+    if ((k->growth_form != 0 && k->growth_form != 1) || (k->solubility_form != 0 && k->solubility_form != 1))
+        return fail(PBE_EINVAL, "unknown growth or solubility form");
+    if (k->scheme == PBE_SCHEME_PAPER && k->kind == PBE_KINETICS_MLP)
+        return fail(PBE_EINVAL, "the learned closure runs with the SSP-RK2 scheme");
     const double vals[] = {k->kg[0], k->kg[1], k->g[0], k->g[1], k->kb, k->b, k->csat[0], k->csat[1],
                            k->csat[2], k->T0, k->T1, k->t_cool, k->kappa, k->cfl};
     for (double v : vals)
@@ -300,6 +306,11 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     K.T0 = k->T0; K.T1 = k->T1; K.t_cool = k->t_cool; K.kappa = k->kappa; K.cfl = k->cfl;
     K.lkg1 = std::log(K.kg1); K.lkg2 = std::log(K.kg2); K.lkb = std::log(K.kb);
     K.inv_tcool = 1.0 / K.t_cool;
+    K.scheme = k->scheme;
+    K.growth_form = k->growth_form;
+    K.solubility_form = k->solubility_form;
+    K.ea1 = k->ea[0];
+    K.ea2 = k->ea[1];
     K.mW = g->d_mW;
     K.mB = g->d_mB;
     g->kin = K;

@@ -383,7 +383,9 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         }
         if (!(p.lmax > 0.0) || !std::isfinite(p.lmax) || !std::isfinite(p.C0) || !std::isfinite(p.t0) ||
             !(k->cfl > 0.0 && k->cfl <= 1.0) || !(k->t_cool > 0.0) ||
-            (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED) || k->kg[0] < 0 || k->kb < 0) {
+            (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED) || k->kg[0] < 0 || k->kb < 0 ||
+            k->scheme != PBE_SCHEME_SSPRK2 || (k->growth_form != 0 && k->growth_form != 1) ||
+            (k->solubility_form != 0 && k->solubility_form != 1)) {
             // (the learned closure runs on the single-grid plain path only)
             delete b;
             return bfail(PBE_EINVAL, "instance %d: invalid parameters", i);
@@ -396,6 +398,9 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         d.K.T0 = k->T0; d.K.T1 = k->T1; d.K.t_cool = k->t_cool; d.K.kappa = k->kappa; d.K.cfl = k->cfl;
         d.K.lkg1 = std::log(k->kg[0]); d.K.lkg2 = -INFINITY; d.K.lkb = std::log(k->kb);
         d.K.inv_tcool = 1.0 / k->t_cool;
+        d.K.growth_form = k->growth_form;
+        d.K.solubility_form = k->solubility_form;
+        d.K.ea1 = k->ea[0];
         d.g.ndim = 1; d.g.N1 = (int)p.ncells; d.g.N2 = 1; d.g.d1 = p.lmax / (double)p.ncells; d.g.d2 = 1.0;
         d.g.inv_d1 = 1.0 / d.g.d1; d.g.inv_d2 = 1.0;
         d.offset = b->offsets[i];

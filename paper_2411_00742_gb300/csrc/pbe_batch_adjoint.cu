@@ -389,6 +389,15 @@ extern "C" pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out
     for (int j = 1; j < n_out; ++j)
         if (!(t_out[j] > t_out[j - 1])) return bafail(PBE_EINVAL, "t_out must increase");
     pbe_batch_internal_view(b, &inst_v, &order, &count, &state, &Cs, &ts, &np_max, &device, &stream_v);
+    {
+        // the batched adjoint differentiates the power-law form (checked on the host copies)
+        std::vector<BatchInst> hi(count);
+        if (cudaMemcpy(hi.data(), inst_v, sizeof(BatchInst) * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bafail(PBE_ECUDA, "reading the batch descriptors failed");
+        for (int i = 0; i < count; ++i)
+            if (hi[i].K.growth_form != 0 || hi[i].K.solubility_form != 0)
+                return bafail(PBE_EINVAL, "instance %d: the batched adjoint needs power-law kinetics", i);
+    }
     cudaStream_t st = (cudaStream_t)stream_v;
     const BatchInst* inst = (const BatchInst*)inst_v;
     const int K = checkpoint_every;

@@ -21,6 +21,9 @@ struct Kin {
     double cs0, cs1, cs2, T0, T1, t_cool, kappa, cfl;
     double lkg1, lkg2, lkb;   // natural logarithms of kg1, kg2, kb (-inf for 0)
     double inv_tcool;         // 1 / t_cool
+    int scheme;               // PBE_SCHEME_*
+    int growth_form, solubility_form;
+    double ea1, ea2;          // Arrhenius activation temperatures (growth_form 1)
     const __nv_bfloat16* mW;  // learned closure: W1[64][3], W2[64][64], W3[3][64] (bf16, device)
     const float* mB;          // and b1[64], b2[64], b3[3] (fp32, device)
 };
@@ -64,14 +67,16 @@ __device__ __forceinline__ void kinetics(const Kin& K, double C, double t, doubl
     }
     double frac = (t < K.t_cool) ? t / K.t_cool : 1.0;
     double T = K.T0 + (K.T1 - K.T0) * frac;
-    double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    double cs = K.solubility_form == 1 ? K.cs0 * exp(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
     double s = C / cs - 1.0;
     if (!(s > 0.0)) {
         G1 = 0.0; G2 = 0.0; B = 0.0;
         return;
     }
-    G1 = K.kg1 * pow(s, K.g1);
-    G2 = (K.ndim == 2) ? K.kg2 * pow(s, K.g2) : 0.0;
+    const double a1 = K.growth_form == 1 ? exp(-K.ea1 / (T + 273.15)) : 1.0;
+    const double a2 = K.growth_form == 1 ? exp(-K.ea2 / (T + 273.15)) : 1.0;
+    G1 = K.kg1 * a1 * pow(s, K.g1);
+    G2 = (K.ndim == 2) ? K.kg2 * a2 * pow(s, K.g2) : 0.0;
     B = K.kb * pow(s, K.b);
 }
 
@@ -80,7 +85,10 @@ __device__ __forceinline__ int timestep(const Kin& K, const Geom& g, double G1, 
                                         double t_next, double& dt, double& t_new)
 {
     double rate = G1 / g.d1;
-    if (g.ndim == 2) rate = rate + G2 / g.d2;
+    if (g.ndim == 2) {
+        const double r2 = G2 / g.d2;
+        rate = K.scheme == PBE_SCHEME_PAPER ? (r2 > rate ? r2 : rate) : rate + r2;
+    }
     double rem = t_next - t;
     if (rate > 0.0) {
         double dtc = K.cfl / rate;
@@ -251,7 +259,7 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
     }
     const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
     const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
     const double d = C - cs;
     if (!(d > 0.0)) {   // S <= 1: no growth, no nucleation
         G1 = 0.0; G2 = 0.0; B = 0.0;
@@ -260,7 +268,8 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
     const double lx = pbe_log(lane == 0 ? d : cs);
     const double L = __shfl_sync(0xffffffffu, lx, 0) - __shfl_sync(0xffffffffu, lx, 1);
     const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
-    const double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
+    double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
+    if (K.growth_form == 1 && lane < 2) q -= (lane == 0 ? K.ea1 : K.ea2) / (T + 273.15);   // Arrhenius factor
     const double e = pbe_exp(fma(p, L, q));
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
@@ -356,7 +365,14 @@ __device__ __forceinline__ int timestep_fast(const Kin& K, const Geom& g, double
                                              double t_next, double& dt, double& t_new)
 {
     double rate = G1 * g.inv_d1;
-    if (g.ndim == 2) rate = fma(G2, g.inv_d2, rate);
+    if (g.ndim == 2) {
+        if (K.scheme == PBE_SCHEME_PAPER) {
+            const double r2 = G2 * g.inv_d2;
+            rate = r2 > rate ? r2 : rate;
+        } else {
+            rate = fma(G2, g.inv_d2, rate);
+        }
+    }
     const double rem = t_next - t;
     if (rate > 0.0) {
         const double dtc = K.cfl / rate;

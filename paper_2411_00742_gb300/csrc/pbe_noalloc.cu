@@ -16,6 +16,7 @@
 // contents of the last call; the scalar header is cleared before each solve.
 // Two calls whose work overlaps on a GPU (different streams, or different
 // host threads) race on it and give wrong results: serialize them.
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -145,6 +146,8 @@ extern "C" pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells
     if (!(lmax > 0.0) || !std::isfinite(lmax)) return fail(PBE_EINVAL, "lmax must be positive and finite");
     if (!std::isfinite(C0) || !std::isfinite(t0)) return fail(PBE_EINVAL, "non-finite C0 or t0");
     if (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED) return fail(PBE_EINVAL, "unknown kinetics kind");
+    if (k->scheme != PBE_SCHEME_SSPRK2 || k->growth_form != 0 || k->solubility_form != 0)
+        return fail(PBE_EINVAL, "this entry point runs the SSP-RK2 scheme with power-law kinetics");
     if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
     if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
     if (!(t_out[0] >= t0) || !std::isfinite(t_out[0])) return fail(PBE_EINVAL, "t_out[0] precedes t0");
@@ -159,6 +162,7 @@ extern "C" pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells
     cudaStream_t st = (cudaStream_t)stream;
 
     Kin K;
+    memset(&K, 0, sizeof(K));
     K.kind = k->kind; K.ndim = 1;
     K.kg1 = k->kg[0]; K.g1 = k->g[0]; K.kg2 = 0.0; K.g2 = 1.0; K.kb = k->kb; K.b = k->b;
     K.cs0 = k->csat[0]; K.cs1 = k->csat[1]; K.cs2 = k->csat[2];
