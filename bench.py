@@ -412,11 +412,11 @@ def run_gpu(args):
                      "note": f"FP64 algorithmic {FLOPS_PER_CELL_STEP_2D} flop/cell-step (division = 1); "
                              "peak = nominal GB300 FP64"},
         "e2e": {"value": ws * e2e_rate, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # prologue + one persistent kernel per fused solve, timed steps only
         "batch_1d": batch,
         "adjoint": adjoint,
         "paper_scheme": paper,
-        "gpu_launches": 2 * args.steps,
+        # per timed fused solve: k_set_scalars, k_prologue, k_fused, k_fused_rows
+        "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

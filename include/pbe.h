@@ -122,6 +122,25 @@ pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count);
  * concentration C and time t.  Initial condition of Eqs. (5)-(9). */
 pbe_status pbe_set_state(pbe_grid* g, const double* n, double C, double t, int mem);
 
+/* Initial condition from a normal seed (SI Sec. S1.3, initial distribution
+ * generation): n = exp(-q/2) at the cell centres, q the squared Mahalanobis
+ * distance of the normal with means mean[ndim] (um), standard deviations
+ * sd[ndim] > 0 (um) and, in 2-D, correlation corr in (-1, 1) (ignored in
+ * 1-D), scaled so that the discrete zeroth moment sum(n) dA equals
+ * total_number (# per kg of solvent).  Sets C = C0 and t = 0.  Host arrays;
+ * synchronizes the grid's stream (the normalisation is read back).  Errors:
+ * PBE_EINVAL (arguments, or a density that underflows at every cell
+ * centre), PBE_ECUDA. */
+pbe_status pbe_init_seed_gaussian(pbe_grid* g, const double* mean, const double* sd, double corr,
+                                  double total_number, double C0);
+
+/* The same normal seed scaled by the seed mass instead (the scale factor
+ * beta of SI Sec. S1.3): rho_kv sum(x1 x2^2 n) dA = seed_mass in 2-D,
+ * rho_kv sum(x^3 n) dL = seed_mass in 1-D, with rho_kv = rho_c k_v in the
+ * mass units of seed_mass per um^3.  Arguments and errors as above. */
+pbe_status pbe_init_seed_gaussian_mass(pbe_grid* g, const double* mean, const double* sd, double corr,
+                                       double seed_mass, double rho_kv, double C0);
+
 /* Read the state back (n may be NULL to read only C and t). */
 pbe_status pbe_get_state(pbe_grid* g, double* n, double* C, double* t, int mem);
 

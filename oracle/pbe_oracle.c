@@ -226,7 +226,7 @@ long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, do
  * density, where the ratio b/(a+b) is decided by rounding of underflowing
  * tails) count as flat: derivative 0 (the subgradient convention the GPU
  * adjoint shares). */
-#define PSI_FLAT 1.0316916532478883e-289  /* 2^-959 */
+#define PSI_FLAT 0x1p-959
 static void psi_grad(double a, double b, double* pa, double* pb)
 {
     if (((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) && fabs(a) >= PSI_FLAT && fabs(b) >= PSI_FLAT) {

@@ -138,6 +138,22 @@ class Grid:
             raise ValueError("state has the wrong number of cells")
         _lib.check(self.lib.pbe_set_state(self.h, p, float(C), float(t), mem))
 
+    def init_seed_gaussian(self, mean, sd, corr: float = 0.0, total_number: float | None = None,
+                           C0: float = 0.0, seed_mass: float | None = None, rho_kv: float | None = None):
+        """Normal seed at the cell centres, scaled to a number of crystals
+        (total_number) or to a seed mass (seed_mass with rho_kv); C = C0, t = 0."""
+        m = (ctypes.c_double * 2)(*[float(v) for v in list(mean)[:2]] + [0.0] * (2 - len(list(mean)[:2])))
+        s = (ctypes.c_double * 2)(*[float(v) for v in list(sd)[:2]] + [1.0] * (2 - len(list(sd)[:2])))
+        if (total_number is None) == (seed_mass is None):
+            raise ValueError("give exactly one of total_number and seed_mass")
+        if seed_mass is None:
+            _lib.check(self.lib.pbe_init_seed_gaussian(self.h, m, s, float(corr), float(total_number), float(C0)))
+        else:
+            if rho_kv is None:
+                raise ValueError("seed_mass needs rho_kv")
+            _lib.check(self.lib.pbe_init_seed_gaussian_mass(self.h, m, s, float(corr), float(seed_mass),
+                                                            float(rho_kv), float(C0)))
+
     def get_state(self, out=None):
         """Returns (n, C, t); n is written into ``out`` (tensor/array) or a new numpy array."""
         if out is None:

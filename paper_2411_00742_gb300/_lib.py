@@ -51,6 +51,8 @@ SIGNATURES = {
     "pbe_set_path": [_P, _I],
     "pbe_set_kinetics": [_P, ctypes.POINTER(Kinetics)],
     "pbe_set_state": [_P, _P, _D, _D, _I],
+    "pbe_init_seed_gaussian": [_P, _PD, _PD, _D, _D, _D],
+    "pbe_init_seed_gaussian_mass": [_P, _PD, _PD, _D, _D, _D, _D],
     "pbe_get_state": [_P, _P, _PD, _PD, _I],
     "pbe_step": [_P, _D, _PD],
     "pbe_solve": [_P, _PD, _I, _P, _I, _PI64],

@@ -71,14 +71,18 @@ __device__ __forceinline__ FaceAdj face_adj(double nm2, double up, double dn, do
     const double a = up - nm2, b = dn - up;
     double pa = 0.0, pb = 0.0, half = 0.0;
     if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
-        const double rs = 1.0 / (a + b);   // one division per face
-        const double qa = b * rs, qb = a * rs;
-        half = a * qa;
-        // differences below 2^-959 count as flat for the derivative (their
-        // ratio is decided by rounding of underflowing tails)
-        if (fabs(a) >= 1.0316916532478883e-289 && fabs(b) >= 1.0316916532478883e-289) {
+        if (fabs(a) >= kPsiFlat && fabs(b) >= kPsiFlat) {
+            // one division per face; |a + b| >= 2^-958, so 1 / (a + b) is finite
+            const double rs = 1.0 / (a + b);
+            const double qa = b * rs, qb = a * rs;
+            half = a * qa;
             pa = 2.0 * qa * qa;
             pb = 2.0 * qb * qb;
+        } else {
+            // differences below 2^-959 count as flat for the derivative (their
+            // ratio is decided by rounding of underflowing tails); the
+            // reciprocal of their sum may overflow, the quotient does not
+            half = a * (b / (a + b));
         }
     }
     const double mu = (lamR - lamL) * invd;

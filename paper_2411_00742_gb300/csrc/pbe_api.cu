@@ -372,6 +372,54 @@ pbe_status pbe_set_state(pbe_grid* g, const double* n, double C, double t, int m
     return PBE_OK;
 }
 
+namespace {
+
+// by_mass = false: scale so that sum(n) dA = total; true: so that
+// rho_kv sum(x1 x2^2 n) dA (x^3 in 1-D) = total
+pbe_status init_seed(pbe_grid* g, const double* mean, const double* sd, double corr, double total, bool by_mass,
+                     double rho_kv, double C0)
+{
+    if (!g || !mean || !sd) return fail(PBE_EINVAL, "null argument");
+    const int nd = g->geo.ndim;
+    for (int d = 0; d < nd; ++d)
+        if (!std::isfinite(mean[d]) || !(sd[d] > 0.0) || !std::isfinite(sd[d]))
+            return fail(PBE_EINVAL, "seed mean must be finite and sd positive (direction %d)", d);
+    if (nd == 2 && !(std::fabs(corr) < 1.0)) return fail(PBE_EINVAL, "correlation must lie in (-1, 1)");
+    if (!(total > 0.0) || !std::isfinite(total)) return fail(PBE_EINVAL, "the seed total must be positive and finite");
+    if (by_mass && (!(rho_kv > 0.0) || !std::isfinite(rho_kv))) return fail(PBE_EINVAL, "rho_kv must be positive");
+    if (!std::isfinite(C0)) return fail(PBE_EINVAL, "non-finite C0");
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
+    g->has_state = false;
+    CUDA_TRY(pbe::launch_seed_pdf(g, mean, sd, nd == 2 ? corr : 0.0, g->d_mom));
+    CUDA_TRY(cudaMemcpyAsync(g->h_stage, g->d_mom, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    const double sum = by_mass ? rho_kv * g->h_stage[1] : g->h_stage[0];
+    if (!(sum > 0.0) || !std::isfinite(sum))
+        return fail(PBE_EINVAL, "the seed has no mass on the grid (its density underflows at every cell centre)");
+    const double scale = nd == 1 ? total / (sum * g->geo.d1) : total / (sum * g->geo.d1 * g->geo.d2);
+    CUDA_TRY(pbe::launch_scale(g, scale));
+    CUDA_TRY(pbe::launch_set_scalars(g, C0, 0.0));
+    g->C_host = C0;
+    g->t_host = 0.0;
+    g->has_state = true;
+    return PBE_OK;
+}
+
+}  // namespace
+
+pbe_status pbe_init_seed_gaussian(pbe_grid* g, const double* mean, const double* sd, double corr,
+                                  double total_number, double C0)
+{
+    return init_seed(g, mean, sd, corr, total_number, false, 0.0, C0);
+}
+
+pbe_status pbe_init_seed_gaussian_mass(pbe_grid* g, const double* mean, const double* sd, double corr,
+                                       double seed_mass, double rho_kv, double C0)
+{
+    return init_seed(g, mean, sd, corr, seed_mass, true, rho_kv, C0);
+}
+
 pbe_status pbe_get_state(pbe_grid* g, double* n, double* C, double* t, int mem)
 {
     if (!g) return fail(PBE_EINVAL, "null grid");

@@ -123,11 +123,13 @@ __device__ __forceinline__ void adj_stage(const double* nt, const double* lam, c
             const double a = up - nm2, b = dn - up;
             double pa = 0.0, pb = 0.0, half = 0.0;
             if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
-                const double rs = 1.0 / (a + b), qa = b * rs, qb = a * rs;   // one division per face
-                half = a * qa;
-                if (fabs(a) >= 1.0316916532478883e-289 && fabs(b) >= 1.0316916532478883e-289) {
+                if (fabs(a) >= kPsiFlat && fabs(b) >= kPsiFlat) {
+                    const double rs = 1.0 / (a + b), qa = b * rs, qb = a * rs;   // one division per face
+                    half = a * qa;
                     pa = 2.0 * qa * qa;
                     pb = 2.0 * qb * qb;
+                } else {
+                    half = a * (b / (a + b));   // flat tail: the reciprocal of a + b may overflow
                 }
             }
             const double mu = (leff[f + 2] - leff[f + 1]) * invd;   // (lam_f - lam_{f-1}) / dL

@@ -103,6 +103,10 @@ __device__ __forceinline__ int timestep(const Kin& K, const Geom& g, double G1, 
     return 1;
 }
 
+// Differences below this magnitude count as flat for the limiter's
+// derivative (their ratio is decided by rounding of underflowing tails).
+constexpr double kPsiFlat = 0x1p-959;
+
 // Half the van Leer limited slope: phi(theta) (n_{i+1} - n_i) / 2 with
 // theta = a / b, a = n_i - n_{i-1}, b = n_{i+1} - n_i (SI Sec. S1.1),
 // i.e. a b / (a + b) when a and b have the same strict sign, else 0.

@@ -56,6 +56,10 @@ cudaError_t launch_prologue(pbe_grid* g, int n_out, long long max_steps, double*
 cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h);
 cudaError_t launch_plain_stage(pbe_grid* g, int stage);
 cudaError_t launch_set_scalars(pbe_grid* g, double C, double t);
+// unscaled Gaussian density at the cell centres into d_n; total_dev[0] = its sum,
+// total_dev[1] = its sum weighted by x^3 (1-D) or x1 x2^2 (2-D)
+cudaError_t launch_seed_pdf(pbe_grid* g, const double* mean, const double* sd, double corr, double* total_dev);
+cudaError_t launch_scale(pbe_grid* g, double a);   // d_n *= a
 
 // Fused path (pbe_fused.cu)
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out);

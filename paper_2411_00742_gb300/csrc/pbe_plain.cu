@@ -338,6 +338,84 @@ __global__ void __launch_bounds__(kNT) k_close1d(const double* __restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
+// Gaussian seed: the density exp(-q/2) sampled at the cell centres (q the
+// squared Mahalanobis distance of the normal with the given means, standard
+// deviations and correlation).  Block sums of the density and of its volume
+// moment weight (x^3 in 1-D, x1 x2^2 in 2-D) go to part[] for the scaling.
+// ---------------------------------------------------------------------------
+template <int NDIM>
+__global__ void __launch_bounds__(kNT) k_seed_pdf(double* n, Geom g, double m1, double m2, double s1, double s2,
+                                                  double rho, double* part)
+{
+    __shared__ double sh[kNT / 32 * 2];
+    const long long ncell = (long long)g.N1 * g.N2;
+    double acc[2] = {0.0, 0.0};
+    for (long long c = (long long)blockIdx.x * kNT + threadIdx.x; c < ncell; c += (long long)gridDim.x * kNT) {
+        double q, wv;
+        if (NDIM == 1) {
+            const double x = (c + 0.5) * g.d1;
+            const double z = (x - m1) / s1;
+            q = z * z;
+            wv = x * x * x;
+        } else {
+            const int i = (int)(c / g.N2), j = (int)(c % g.N2);
+            const double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
+            const double z1 = (x1 - m1) / s1, z2 = (x2 - m2) / s2;
+            q = (z1 * z1 - 2.0 * rho * z1 * z2 + z2 * z2) / (1.0 - rho * rho);
+            wv = x1 * x2 * x2;
+        }
+        const double f = exp(-0.5 * q);
+        n[c] = f;
+        acc[0] += f;
+        acc[1] += wv * f;
+    }
+    block_sum<kNT, 2>(acc, sh);
+    if (threadIdx.x == 0) {
+        part[(size_t)blockIdx.x * kMaxMom] = acc[0];
+        part[(size_t)blockIdx.x * kMaxMom + 1] = acc[1];
+    }
+}
+
+__global__ void __launch_bounds__(kNT) k_seed_total(const double* part, int nb, double* total)
+{
+    __shared__ double sh[kNT / 32 * 2];
+    double v[2];
+    reduce_partials<kNT, 2>(part, nb, v, sh);
+    if (threadIdx.x == 0) {
+        total[0] = v[0];
+        total[1] = v[1];
+    }
+}
+
+__global__ void k_scale(double* n, long long ncell, double a)
+{
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+        n[c] *= a;
+}
+
+cudaError_t launch_seed_pdf(pbe_grid* g, const double* mean, const double* sd, double corr, double* total_dev)
+{
+    const long long ncell = (long long)g->geo.N1 * g->geo.N2;
+    int nb = cdiv(ncell, kNT);
+    if (nb > 1024) nb = 1024;
+    if (g->geo.ndim == 1)
+        k_seed_pdf<1><<<nb, kNT, 0, g->stream>>>(g->d_n, g->geo, mean[0], 0.0, sd[0], 1.0, 0.0, g->d_part);
+    else
+        k_seed_pdf<2><<<nb, kNT, 0, g->stream>>>(g->d_n, g->geo, mean[0], mean[1], sd[0], sd[1], corr, g->d_part);
+    k_seed_total<<<1, kNT, 0, g->stream>>>(g->d_part, nb, total_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(pbe_grid* g, double a)
+{
+    const long long ncell = (long long)g->geo.N1 * g->geo.N2;
+    int nb = cdiv(ncell, kNT);
+    if (nb > 4096) nb = 4096;
+    k_scale<<<nb, kNT, 0, g->stream>>>(g->d_n, ncell, a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_set_scalars(pbe_grid* g, double C, double t)

@@ -157,3 +157,38 @@ def test_batched_vjp_matches_cpu_adjoint(K):
         mine = dn0[b.offsets[i]:b.offsets[i + 1]]
         supp = insts[i].n0 > 1e-3 * insts[i].n0.max()
         assert np.max(np.abs(mine - wdn0)[supp]) <= REL_GRAD * np.max(np.abs(wdn0)), i
+
+
+def _subnormal_tail(inst):
+    """Overwrite the far tail with a halving sequence that runs from 2^-1020
+    into subnormal numbers: neighbouring differences of equal sign whose sum
+    is too small for its reciprocal to be finite."""
+    n0 = inst.n0.copy()
+    k = np.arange(n0.size - 150)
+    n0[150:] = np.ldexp(1.0, -1020) * 0.5 ** k
+    inst.n0 = n0
+    return inst
+
+
+def test_vjp_with_subnormal_tails_matches_cpu_adjoint():
+    import paper_2411_00742_gb300 as P
+    inst = _subnormal_tail(pi.config_1d(200))
+    assert np.any((inst.n0 > 0) & (inst.n0 < np.finfo(np.float64).tiny))
+    p, tgt, cols = _setup(inst)
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    want, want_dn0, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
+    dth, dn0, dC0, rows, _ = _gpu_grad(inst, seeds, 64)
+    assert np.all(np.isfinite(dth)) and np.all(np.isfinite(dn0))
+    for j in (0, 1, 4, 5):
+        assert dth[j] == pytest.approx(want[j], rel=REL_GRAD), j
+    assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
+    # the batched adjoint on the same instance
+    b = P.Batch([p], [inst.C0])
+    b.set_state(b.pack([inst.n0]))
+    bth, bC0 = b.vjp(inst.t_out, seeds[None], 64)
+    b.close()
+    assert np.all(np.isfinite(bth))
+    for j in (0, 1, 4, 5):
+        assert bth[0, j] == pytest.approx(want[j], rel=REL_GRAD), j
+    assert bC0[0] == pytest.approx(want_dC0, rel=REL_GRAD)

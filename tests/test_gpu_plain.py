@@ -164,3 +164,42 @@ def test_bad_output_times_rejected():
     with pytest.raises(P.PbeError):
         g.solve([200.0, 150.0])
     g.close()
+
+
+def test_init_seed_gaussian_matches_the_input_generator():
+    """pbe_init_seed_gaussian / _mass reproduce the seeded inputs (normal
+    seed at cell centres, scaled by number or by seed mass)."""
+    import paper_2411_00742_gb300 as P
+    i1 = pi.config_1d(200)
+    g = P.Grid.from_problem(i1.problem)
+    g.init_seed_gaussian([150.0], [20.0], total_number=1e8, C0=i1.C0)
+    n, C, t = g.get_state()
+    g.close()
+    np.testing.assert_allclose(n, i1.n0, rtol=1e-13, atol=1e-13 * i1.n0.max())
+    assert C == i1.C0 and t == 0.0
+    i2 = pi.config_2d(48, 40)
+    g = P.Grid.from_problem(i2.problem)
+    g.init_seed_gaussian([100.0, 60.0], [15.0, 10.0], corr=0.3, total_number=1e8, C0=i2.C0)
+    n, _, _ = g.get_state()
+    g.close()
+    np.testing.assert_allclose(n, i2.n0, rtol=1e-13, atol=1e-13 * i2.n0.max())
+    # the paper's base case: seed scaled by its mass (1 g)
+    i3 = pi.paper_base_case(120)
+    g = P.Grid.from_problem(i3.problem)
+    g.init_seed_gaussian([400.0, 250.0], [30.0, 30.0], seed_mass=1.0, rho_kv=pi.RHO_C * pi.KV, C0=8.0)
+    n, _, _ = g.get_state()
+    g.close()
+    np.testing.assert_allclose(n, i3.n0, rtol=1e-13, atol=1e-13 * i3.n0.max())
+
+
+def test_init_seed_gaussian_rejects_bad_arguments():
+    import paper_2411_00742_gb300 as P
+    from paper_2411_00742_gb300._lib import PbeError
+    inst = pi.config_2d(16)
+    g = P.Grid.from_problem(inst.problem)
+    for kw in (dict(sd=[0.0, 10.0]), dict(corr=1.0), dict(total_number=-1.0), dict(mean=[1e9, 1e9])):
+        args = dict(mean=[100.0, 60.0], sd=[15.0, 10.0], corr=0.3, total_number=1e8, C0=0.2)
+        args.update(kw)
+        with pytest.raises(PbeError):
+            g.init_seed_gaussian(**args)
+    g.close()
