@@ -155,6 +155,7 @@ pbe_status run_solve(pbe_grid* g, int n_out)
     build_plain_graph(g);
     if (g->plain_exec) {
         CUDA_TRY(cudaGraphLaunch(g->plain_exec, g->stream));
+        CUDA_TRY(pbe::launch_paper_finish(g));
         return PBE_OK;
     }
     // host loop over chunks of steps; stage kernels return at once when done
@@ -167,6 +168,7 @@ pbe_status run_solve(pbe_grid* g, int n_out)
         if (g->h_S->done) break;
         if (done_steps > g->max_steps + chunk) return fail(PBE_ETIMEOUT, "solve did not finish");
     }
+    CUDA_TRY(pbe::launch_paper_finish(g));
     return PBE_OK;
 }
 }  // namespace
@@ -471,6 +473,7 @@ pbe_status pbe_step(pbe_grid* g, double t_limit, double* dt_taken)
     CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_stage, sizeof(double), cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(pbe::launch_prologue(g, 1, 1, nullptr));
     CUDA_TRY(pbe::launch_plain_step(g, false, 0));
+    CUDA_TRY(pbe::launch_paper_finish(g));
     st = finish_call(g);
     if (dt_taken) *dt_taken = g->h_S->last_dt;
     if (st == PBE_ETIMEOUT) st = PBE_OK;  // the one-step budget is the point of this call

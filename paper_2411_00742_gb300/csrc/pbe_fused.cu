@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
     constexpr int CPT = TileShape<NDIM>::CELLS / kFNT;   // cells per thread per tile
     __shared__ Scal s;
+    __shared__ StageCoef scs;   // coefficients of the coming stage (written by thread 0)
     __shared__ double red[kFNT * (NM + 1)];
     __shared__ double red2[256];
     __shared__ double res[NM];
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     if (threadIdx.x == 0) {
         s = *S;
         s.row_first = s.out_idx;   // rows before this index came from the prologue
+        scs = stage_coef_fast<1>(s, g);
     }
     __syncthreads();
     if (s.done) {
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     for (;;) {
 #pragma unroll 1
         for (int stage = 1; stage <= 2; ++stage) {
-            const StageCoef sc = stage == 1 ? stage_coef<1>(s, g) : stage_coef<2>(s, g);
+            const StageCoef sc = scs;
             const double* in = stage == 1 ? n : n1;
             double* out = stage == 1 ? n1 : n;
             double m[NM];
@@ -398,6 +400,9 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 __syncwarp();
                 if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
                 else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
+                // the next stage's coefficients, once per block (the divisions of
+                // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
+                if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
             } else if (warp <= kFaceWarps) {
                 // faces of the next stage's input for this block's first tile
                 fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, 32 * kFaceWarps,

@@ -61,6 +61,13 @@ cudaError_t launch_set_scalars(pbe_grid* g, double C, double t);
 cudaError_t launch_seed_pdf(pbe_grid* g, const double* mean, const double* sd, double corr, double* total_dev);
 cudaError_t launch_scale(pbe_grid* g, double a);   // d_n *= a
 
+// The paper's split scheme in 2-D (pbe_paper.cu): one kernel per step, the
+// state alternating between d_n and d_n1; launch_paper_finish puts it back
+// in d_n after the last step (no launch for other schemes).
+cudaError_t launch_paper_step2d(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h);
+cudaError_t launch_paper_finish(pbe_grid* g);
+int paper_blocks2d(const Geom& g);
+
 // Fused path (pbe_fused.cu)
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out);
 bool fused_supported(const pbe_grid* g);

@@ -187,95 +187,11 @@ __global__ void __launch_bounds__(kNT) k_stage2d(const double* __restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
-// The paper's scheme: Eq. 3 (one-step high-resolution update, van Leer
-// limiter) with Godunov dimensional splitting - one kernel per direction.
-// In flux form with Courant number nu = G dt / dL per direction,
-//   f_i <- f_i - nu (hl_{i+1/2} - hl_{i-1/2}),
-//   hl_{i+1/2} = f_i + (1 - nu) phi(theta_{i+1/2}) (f_{i+1} - f_i) / 2,
-// which is Eq. 3 term by term.  DIR 1 sweeps along L1 (n -> n1), DIR 2 along
-// L2 (n1 -> n) and closes the step: nucleation inflow, moments, the solute
-// balance of Eq. 4 and the next step's kinetics and CFL step (last block).
+// The paper's scheme in 1-D: Eq. 3 (one-step high-resolution update, van
+// Leer limiter); the 2-D split form is in pbe_paper.cu.  With Courant number
+// nu = G dt / dL, f_i <- f_i - nu (h_{i+1/2} - h_{i-1/2}),
+// h_{i+1/2} = f_i + (1 - nu) phi(theta_{i+1/2}) (f_{i+1} - f_i) / 2.
 // ---------------------------------------------------------------------------
-template <int DIR>
-__global__ void __launch_bounds__(kNT) k_sweep2d(const double* __restrict__ in, double* out, Scal* S, Kin K, Geom g,
-                                                 double* part, const double* t_out, double* rows, int use_cond,
-                                                 cudaGraphConditionalHandle hcond)
-{
-    constexpr int W = kTJ + 3;
-    __shared__ Tile2DSmem<kTI, kTJ> ts;
-    __shared__ double sh[kNT / 32 * 10];
-    __shared__ int flag;
-    if (S->done) {
-        if (DIR == 2 && use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-            cudaGraphSetConditional(hcond, 0);
-        return;
-    }
-    const int N1 = g.N1, N2 = g.N2;
-    const int i0 = blockIdx.y * kTI, j0 = blockIdx.x * kTJ;
-    const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-    const double dt = S->dt;
-    const double nu = DIR == 1 ? S->G1a * dt / g.d1 : S->G2a * dt / g.d2;
-    const double om = 1.0 - nu;
-    const bool moms = DIR == 2 && S->clipped;
-    for (int k = threadIdx.x; k < (kTI + 3) * W; k += kNT) {
-        int r = k / W, c = k - r * W;
-        int gi = i0 - 2 + r, gj = j0 - 2 + c;
-        ts.tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? in[(size_t)gi * N2 + gj] : 0.0;
-    }
-    __syncthreads();
-    if (DIR == 1) {
-        for (int k = threadIdx.x; k < (kTI + 1) * kTJ; k += kNT) {
-            int f = k / kTJ, c = k - f * kTJ;
-            const double nm2 = ts.tile[f * W + c + 2], up = ts.tile[(f + 1) * W + c + 2], dn = ts.tile[(f + 2) * W + c + 2];
-            ts.h1[k] = up + om * half_psi(up - nm2, dn - up);
-        }
-    } else {
-        for (int k = threadIdx.x; k < kTI * (kTJ + 1); k += kNT) {
-            int r = k / (kTJ + 1), f = k - r * (kTJ + 1);
-            const double* row = ts.tile + (r + 2) * W;
-            ts.h2[k] = row[f + 1] + om * half_psi(row[f + 1] - row[f], row[f + 2] - row[f + 1]);
-        }
-    }
-    __syncthreads();
-    double m[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) m[k] = 0.0;
-    const double area = g.d1 * g.d2;
-    for (int k = threadIdx.x; k < kTI * kTJ; k += kNT) {
-        int r = k / kTJ, c = k - r * kTJ;
-        int i = i0 + r, j = j0 + c;
-        if (i >= N1 || j >= N2) continue;
-        double v = ts.tile[(r + 2) * W + c + 2];
-        if (DIR == 1) v += nu * (ts.h1[r * kTJ + c] - ts.h1[(r + 1) * kTJ + c]);
-        else v += nu * (ts.h2[r * (kTJ + 1) + c] - ts.h2[r * (kTJ + 1) + c + 1]);
-        if (DIR == 2 && i == 0 && j == 0) v += dt * S->Ba / area;
-        out[(size_t)i * N2 + j] = v;
-        if (DIR == 2) {
-            double x1 = (i + 0.5) * g.d1, x2 = (j + 0.5) * g.d2;
-            double w = v * area;
-            double x1w = x1 * w, x2w = x2 * w;
-            m[8] += x1 * x2 * x2w;
-            if (moms) {
-                m[0] += w; m[1] += x1w; m[2] += x2w;
-                m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
-                m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
-            }
-        }
-    }
-    if (DIR == 1) return;
-    block_sum<kNT, 10>(m, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 10; ++k) part[(size_t)bid * kMaxMom + k] = m[k];
-    if (!last_block(&S->counter, nb, &flag)) return;
-    reduce_partials<kNT, 10>(part, nb, m, sh);
-    if (threadIdx.x >= 32) return;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) m[k] = __shfl_sync(0xffffffffu, m[k], 0);
-    if (threadIdx.x == 0) S->counter = 0u;
-    finish_stage2_warp(S, K, g, t_out, rows, m, 10, 8);
-    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
-}
-
 // 1-D: the sweep (n -> n1), then a close kernel that copies n1 back to n with
 // the nucleation inflow, the moments and the last-block close of the step.
 __global__ void __launch_bounds__(kNT) k_sweep1d(const double* __restrict__ in, double* out, const Scal* S, Geom g)
@@ -476,12 +392,7 @@ cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHa
                                                  g->d_rows, uc, h);
             return cudaGetLastError();
         }
-        dim3 grid(cdiv(geo.N2, kTJ), cdiv(geo.N1, kTI));
-        k_sweep2d<1><<<grid, kNT, 0, g->stream>>>(g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part, g->d_tout,
-                                                  g->d_rows, uc, h);
-        k_sweep2d<2><<<grid, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_S, g->kin, geo, g->d_part, g->d_tout,
-                                                  g->d_rows, uc, h);
-        return cudaGetLastError();
+        return launch_paper_step2d(g, use_cond, h);
     }
     if (geo.ndim == 1) {
         int nb = cdiv(geo.N1, kT1);
