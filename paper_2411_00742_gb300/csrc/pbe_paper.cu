@@ -8,15 +8,17 @@
 // which is Eq. 3 term by term (phi(theta) (f_{i+1} - f_i) = 2ab/(a+b) for
 // a, b of the same strict sign, else 0).
 //
-// Block = 256 threads.  A block holds 64 consecutive columns j0-2 .. j0+61
-// and writes the 61 columns j0 .. j0+60 of 32 rows:
-//   1. L1 sweep (64 columns x 4 row groups of 8 rows): every thread walks
+// Block = 256 threads.  A block holds 128 consecutive columns j0-2 .. j0+125
+// and writes the 125 columns j0 .. j0+124 of 32 rows:
+//   1. L1 sweep (128 columns x 2 row groups of 16 rows): every thread walks
 //      down its column with a register window of the input (2 rows above,
 //      1 below), each face value computed once; the L1-swept values go to
 //      shared memory;
-//   2. L2 sweep along the rows (8 warps x 4 rows, two columns per lane):
-//      the three extra columns are the stencil's halo, recomputed by the
-//      neighbouring block; face values pass between lanes by shuffles;
+//   2. L2 sweep along the rows (8 warps x 4 rows, four columns per lane):
+//      both stencil differences of a face come from the lane itself or the
+//      lane below, face values pass between lanes by shuffles; the three
+//      extra columns are the stencil's halo, recomputed by the neighbouring
+//      block;
 //   3. update, nucleation inflow in the corner cell, the crystal-volume
 //      moment (and every moment on output steps), last-block close of the
 //      step: solute balance (Eq. 4), kinetics and CFL step of the next step.
@@ -24,23 +26,38 @@
 // counter; launch_paper_finish copies it back after the last step.
 //
 // Face quotients use the Newton-Raphson form (half_psi_fast).  On GB300 the
-// step is bound by the FP64 pipe (about 20 FP64 instructions per cell and
-// step against 16 bytes of HBM traffic).
+// step is bound by the FP64 pipe: about 20 FP64 instructions per cell and
+// step (per direction and face: one difference, five for the limited slope,
+// one for the face value; two for the update; one for the volume moment)
+// against 16 bytes of HBM traffic.
 #include "pbe_internal.h"
 #include "pbe_tiles.cuh"
 
 namespace pbe {
 
 constexpr int kPNT = 256;              // threads per block
-constexpr int kPX = 64;                // columns held per block
+constexpr int kPX = 128;               // columns held per block
 constexpr int kPOut = kPX - 3;         // columns written per block
-constexpr int kPG = kPNT / kPX;        // row groups
-constexpr int kPR = 8;                 // rows per row group
+constexpr int kPG = kPNT / kPX;        // row groups of the L1 sweep
+constexpr int kPR = 16;                // rows per row group
 constexpr int kPTI = kPG * kPR;        // rows per block
+constexpr int kPW = kPNT / 32;         // warps
+constexpr int kPRW = kPTI / kPW;       // rows per warp in the L2 sweep
+constexpr int kPC = kPX / 32;          // columns per lane in the L2 sweep
 
 static inline int pdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 int paper_blocks2d(const Geom& g) { return pdiv(g.N2, kPOut) * pdiv(g.N1, kPTI); }
+
+// all ten moments of one cell value into m (order of the output rows)
+__device__ __forceinline__ void add_moments(double (&m)[10], double val, double x1, double x2, double area)
+{
+    const double w = val * area;
+    const double x1w = x1 * w, x2w = x2 * w;
+    m[0] += w; m[1] += x1w; m[2] += x2w;
+    m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
+    m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
+}
 
 __global__ void __launch_bounds__(kPNT) k_lw_step2d(double* na, double* nb, Scal* S, Kin K, Geom g, double* part,
                                                      const double* t_out, double* rows, int use_cond,
@@ -48,7 +65,7 @@ __global__ void __launch_bounds__(kPNT) k_lw_step2d(double* na, double* nb, Scal
 {
     __shared__ __align__(16) double n1s[kPTI][kPX];
     __shared__ double x1s[kPTI];
-    __shared__ double sh[kPNT / 32 * 10];
+    __shared__ double sh[kPW * 10];
     __shared__ int flag;
     if (S->done) {
         if (use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(hcond, 0);
@@ -58,25 +75,24 @@ __global__ void __launch_bounds__(kPNT) k_lw_step2d(double* na, double* nb, Scal
     const double* __restrict__ in = odd ? nb : na;
     double* __restrict__ out = odd ? na : nb;
     const int N1 = g.N1, N2 = g.N2;
-    const int tx = threadIdx.x % kPX, ty = threadIdx.x / kPX;
     const int i0 = blockIdx.y * kPTI, j0 = blockIdx.x * kPOut;
-    const int j = j0 - 2 + tx;
-    const bool jin = j >= 0 && j < N2;
-    const int ra = ty * kPR;
     const double dt = S->dt;
-    const double nu1 = S->G1a * dt / g.d1, om1 = 1.0 - nu1;
-    const double nu2 = S->G2a * dt / g.d2, om2 = 1.0 - nu2;
+    const double nu1 = S->G1a * dt * g.inv_d1, om1 = 1.0 - nu1;
+    const double nu2 = S->G2a * dt * g.inv_d2, om2 = 1.0 - nu2;
     const bool moms = S->clipped != 0;
     if (threadIdx.x < kPTI) x1s[threadIdx.x] = (i0 + threadIdx.x + 0.5) * g.d1;
 
     // 1. L1 sweep down this thread's column: input rows i0+ra-2 .. i0+ra+kPR
-    double v[kPR + 3];
-#pragma unroll
-    for (int q = 0; q < kPR + 3; ++q) {
-        const int i = i0 + ra - 2 + q;
-        v[q] = (jin && i >= 0 && i < N1) ? __ldg(in + (size_t)i * N2 + j) : 0.0;
-    }
     {
+        const int tx = threadIdx.x % kPX, ra = (threadIdx.x / kPX) * kPR;
+        const int j = j0 - 2 + tx;
+        const bool jin = j >= 0 && j < N2;
+        double v[kPR + 3];
+#pragma unroll
+        for (int q = 0; q < kPR + 3; ++q) {
+            const int i = i0 + ra - 2 + q;
+            v[q] = (jin && i >= 0 && i < N1) ? __ldg(in + (size_t)i * N2 + j) : 0.0;
+        }
         double dprev = v[2] - v[1];
         double hup = v[1] + om1 * half_psi_fast(v[1] - v[0], dprev);   // face between rows i-1 and i
 #pragma unroll
@@ -90,57 +106,66 @@ __global__ void __launch_bounds__(kPNT) k_lw_step2d(double* na, double* nb, Scal
     }
     __syncthreads();
 
-    // 2-3. L2 sweep, update and moments: warp w takes rows 4w .. 4w+3, lane l
-    // the columns 2l and 2l+1, so both stencil differences of every face come
-    // from the lane itself or the lane below (no divergent lanes).  Face c
-    // lies between columns c-1 and c; column c is updated from faces c, c+1.
+    // 2-3. L2 sweep, update and moments.  Local face c lies between columns
+    // c-1 and c; column c is updated from faces c and c+1.  Written columns:
+    // local 2 .. kPX-2 (0, 1 and kPX-1 are halo).
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ce = 2 * lane, co = ce + 1;          // local columns of this lane
-    const int je = j0 - 2 + ce, jo = je + 1;       // their grid columns
-    // written columns: local 2 .. kPX-2 (0, 1 and kPX-1 are halo)
-    const bool oute = lane > 0 && je < N2, outo = lane > 0 && co < kPX - 1 && jo < N2;
+    const int c0 = kPC * lane, jb = j0 - 2 + c0;
     const double area = g.d1 * g.d2;
-    const double src = dt * S->Ba / area;
-    const double x2e = (je + 0.5) * g.d2, x2o = (jo + 0.5) * g.d2;
+    double x2[kPC], acc[kPC];
+    bool ok[kPC];
+#pragma unroll
+    for (int k = 0; k < kPC; ++k) {
+        x2[k] = (jb + k + 0.5) * g.d2;
+        acc[k] = 0.0;
+        ok[k] = c0 + k >= 2 && c0 + k <= kPX - 2 && jb + k < N2;
+    }
     double m[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) m[k] = 0.0;
-    double acce = 0.0, acco = 0.0;
+    double v00 = 0.0;
 #pragma unroll
-    for (int q = 0; q < kPTI / (kPNT / 32); ++q) {
-        const int r = warp * (kPTI / (kPNT / 32)) + q, i = i0 + r;
-        const double2 c = *reinterpret_cast<const double2*>(&n1s[r][ce]);
-        const double cl = __shfl_up_sync(0xffffffffu, c.y, 1);      // column ce-1
-        const double de = c.x - cl, dd = c.y - c.x;                  // differences across faces ce, co
-        const double ae = __shfl_up_sync(0xffffffffu, dd, 1);       // across face ce-1
-        const double he = cl + om2 * half_psi_fast(ae, de);         // face ce
-        const double ho = c.x + om2 * half_psi_fast(de, dd);        // face co
-        const double hn = __shfl_down_sync(0xffffffffu, he, 1);     // face co+1
+    for (int q = 0; q < kPRW; ++q) {
+        const int r = warp * kPRW + q, i = i0 + r;
+        const double2 p0 = *reinterpret_cast<const double2*>(&n1s[r][c0]);
+        const double2 p1 = *reinterpret_cast<const double2*>(&n1s[r][c0 + 2]);
+        const double c[kPC] = {p0.x, p0.y, p1.x, p1.y};
+        const double cl = __shfl_up_sync(0xffffffffu, c[kPC - 1], 1);   // column c0-1
+        double d[kPC];
+        d[0] = c[0] - cl;
+#pragma unroll
+        for (int k = 1; k < kPC; ++k) d[k] = c[k] - c[k - 1];
+        const double a0 = __shfl_up_sync(0xffffffffu, d[kPC - 1], 1);  // across face c0-1
+        double h[kPC + 1];
+        h[0] = cl + om2 * half_psi_fast(a0, d[0]);
+#pragma unroll
+        for (int k = 1; k < kPC; ++k) h[k] = c[k - 1] + om2 * half_psi_fast(d[k - 1], d[k]);
+        h[kPC] = __shfl_down_sync(0xffffffffu, h[0], 1);                // face c0+kPC
         if (i >= N1) continue;
-        double ve = c.x + nu2 * (he - ho);
-        const double vo = c.y + nu2 * (ho - hn);
-        if (i == 0 && je == 0) ve += src;
         const size_t row = (size_t)i * N2;
-        if (oute) out[row + je] = ve;
-        if (outo) out[row + jo] = vo;
         const double x1 = x1s[r];
-        if (oute) acce = fma(x1, ve, acce);
-        if (outo) acco = fma(x1, vo, acco);
-        if (moms) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const bool ok = h == 0 ? oute : outo;
-                if (!ok) continue;
-                const double val = h == 0 ? ve : vo, x2 = h == 0 ? x2e : x2o;
-                const double w = val * area;
-                const double x1w = x1 * w, x2w = x2 * w;
-                m[0] += w; m[1] += x1w; m[2] += x2w;
-                m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
-                m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
+        for (int k = 0; k < kPC; ++k) {
+            const double val = c[k] + nu2 * (h[k] - h[k + 1]);
+            if (q == 0 && k == 2) v00 = val;
+            if (ok[k]) {
+                out[row + jb + k] = val;
+                acc[k] = fma(x1, val, acc[k]);
+                if (moms) add_moments(m, val, x1, x2[k], area);
             }
         }
     }
-    m[8] = acce * (x2e * x2e * area) + acco * (x2o * x2o * area);
+    // nucleation inflow B dt / (dL1 dL2) into cell (0, 0): warp 0, lane 0, row 0, local column 2
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        const double src = dt * S->Ba / area;
+        out[0] = v00 + src;
+        acc[2] = fma(x1s[0], src, acc[2]);
+        if (moms) add_moments(m, src, x1s[0], x2[2], area);
+    }
+    m[8] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPC; ++k) m[8] = fma(acc[k], x2[k] * x2[k] * area, m[8]);
+
     const int nbk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (moms) {
         block_sum<kPNT, 10>(m, sh);
