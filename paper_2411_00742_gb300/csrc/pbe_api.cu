@@ -216,7 +216,7 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
               cudaMalloc(&g->d_S, sizeof(Scal)) == cudaSuccess &&
               cudaMalloc(&g->d_part, sizeof(double) * pbe::kMaxMom * g->max_blocks) == cudaSuccess &&
               cudaMalloc(&g->d_mom, sizeof(double) * pbe::kMaxMom) == cudaSuccess &&
-              cudaMalloc(&g->d_bar, sizeof(unsigned int) * 2) == cudaSuccess &&
+              cudaMalloc(&g->d_bar, 512) == cudaSuccess &&
               cudaMallocHost(&g->h_S, sizeof(Scal)) == cudaSuccess &&
               cudaMallocHost(&g->h_stage, sizeof(double) * 64) == cudaSuccess;
     if (!ok) {

@@ -269,7 +269,7 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
         G1 = 0.0; G2 = 0.0; B = 0.0;
         return;
     }
-    const double lx = pbe_log(lane == 0 ? d : cs);
+    const double lx = pbe_log_tab(lane == 0 ? d : cs);
     const double L = __shfl_sync(0xffffffffu, lx, 0) - __shfl_sync(0xffffffffu, lx, 1);
     const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
     double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);

@@ -1,24 +1,28 @@
 // Fused path for one grid: a single persistent cooperative launch runs the
-// whole solve.  Each block owns a fixed set of tiles; the two stages of every
-// step are separated by a device-wide barrier.  After each barrier the block
-// splits: warp 0 sums the per-block moment partials in a fixed order and
-// advances the block's private copy of the scalar chain (solute balance,
-// kinetics, CFL step - identical in every block), while the other warps
-// already load the next stage's input tile and compute its face values,
-// which do not depend on the kinetics.  Face quotients use the
+// whole solve.  Each block owns a fixed set of tiles (2-D: tiles of ti x 32
+// cells, ti chosen so that every SM gets at most one tile when the grid
+// allows); the two stages of every step are separated by a device-wide
+// barrier that also sums the volume moment over the blocks (barrier_sum).
+// After each barrier the block splits: warp 0 advances the block's private
+// copy of the scalar chain (solute balance, kinetics, CFL step, the next
+// stage's coefficients - identical in every block), warps 1-6 already load
+// the next stage's input tile and compute its face values, which do not
+// depend on the kinetics, and on output steps warp 7 reduces the block's
+// moments (summed into the rows after the solve).  Face quotients use the
 // Newton-Raphson form (half_psi_fast).
 //
 // GB300 FP64 notes that shape this kernel: a warp-wide FP64 instruction
 // occupies the SM's FP64 pipe for ~16 cycles whatever its active lanes, and
-// a dependent FP64 operation takes ~65 cycles.  So (a) with one tile per
-// block the moment weights of each thread's cells are computed once and
-// kept in registers, (b) block reductions go through shared memory in two
-// 16-wide levels instead of per-warp butterflies (3x fewer FP64 warp
-// instructions), (c) the cross-block sum reads all partials with one load
-// round and reduces every moment at once.
+// a dependent FP64 operation takes ~65 cycles, so the scalar chain between
+// stages (the critical path on small grids) is kept short: with one tile per
+// block the moment weights of each thread's cells are computed once and kept
+// in registers, the cross-block sum costs no round trip beyond the barrier's
+// own, the stage coefficients are computed once per block, and the kinetics
+// use short-latency exp and table-driven log.
 //
 // Every wait is bounded: a barrier that does not complete within about one
 // second sets PBE_ETIMEOUT and the kernel returns.
+#include <algorithm>
 #include <type_traits>
 
 #include "pbe_internal.h"
@@ -28,160 +32,70 @@ namespace pbe {
 
 constexpr int kFNT = 256;     // threads per block (the reductions assume 256)
 constexpr int kFT1 = 1024;    // 1-D tile
-constexpr int kFTI = 16;      // 2-D tile rows
+constexpr int kFTI = 16;      // largest 2-D tile height (the launch picks ti <= kFTI)
 constexpr int kFTJ = 32;      // 2-D tile columns
 constexpr long long kBarrierCycles = 2000000000LL;  // default wait limit: ~1 s at 2 GHz
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v)
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Device-wide barrier over gridDim.x co-resident blocks (cooperative launch).
-// bar[0] counts arrivals and only grows: the k-th barrier completes when it
-// reaches k * gridDim.x.  Thread 0 arrives with a release add (cumulative
-// over the writes the block barrier ordered before it) and waits with
-// acquire loads.  Returns false when the wait runs past `limit` cycles.
-__device__ __forceinline__ unsigned int atom_add_release(unsigned int* p, unsigned int v)
-{
-    unsigned int old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
     return old;
 }
 
-__device__ bool grid_barrier(unsigned int* bar, unsigned int& gen, int* fail_sh, long long limit)
+// Device-wide barrier over the co-resident blocks of the cooperative launch
+// that also sums one value over the blocks, exactly and independently of the
+// arrival order (so every block, on every run, gets the same total): each
+// block adds its value rounded to an integer multiple q of the unit u (a
+// power of two), as (q << 10) + 1, to a 64-bit accumulator with a release
+// add (cumulative over the writes the block barrier ordered before it), and
+// waits with acquire loads.  The low 10 bits count the arrivals of the
+// stage, the rest sums q (integer addition is associative; the accumulator
+// wraps modulo 2^64, differences stay exact).  Stages alternate between two
+// accumulators (a block cannot reach stage s+2 before every block has read
+// stage s).  Thread 0 only; returns false when the wait runs past `limit`
+// cycles.
+constexpr int kAccStride = 16;   // the two accumulators lie 128 bytes apart
+__device__ bool barrier_sum(unsigned long long* acc, unsigned long long& base, double v, double inv_u, double u,
+                            unsigned int nblocks, long long limit, double& total)
 {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int target = (gen + 1u) * gridDim.x;
-        int ok = 1;
-        const unsigned int arrived = atom_add_release(&bar[0], 1u) + 1u;
-        if (arrived < target) {
-            const long long t0 = clock64();
-            unsigned int polls = 0;
-            const unsigned int spin = limit > 0 ? 64u : 1u;
-            while (ld_acquire(&bar[0]) < target) {
-                if (++polls > spin) {
-                    if (clock64() - t0 > limit) { ok = 0; break; }
-                    __nanosleep(20);
-                }
+    const long long q = llrint(v * inv_u);
+    atom_add_release_u64(acc, ((unsigned long long)q << 10) + 1ull);
+    unsigned long long x = ld_acquire_u64(acc);
+    if (((x - base) & 1023ull) != nblocks) {
+        const long long t0 = clock64();
+        const unsigned int spin = limit > 0 ? 64u : 1u;
+        for (unsigned int polls = 0;;) {
+            x = ld_acquire_u64(acc);
+            if (((x - base) & 1023ull) == nblocks) break;
+            if (++polls > spin) {
+                if (clock64() - t0 > limit) return false;
+                __nanosleep(20);
             }
         }
-        gen += 1u;
-        *fail_sh = !ok;
     }
-    __syncthreads();
-    return *fail_sh == 0;
+    const long long sq = (long long)(x - base - nblocks) >> 10;
+    base = x;
+    total = (double)sq * u;
+    return true;
 }
 
-// Block sum of one value (256 threads): warp butterflies, then thread 0 adds
-// the eight warp sums as a balanced tree.  Result in *res (shared).
-__device__ __forceinline__ void block_sum1(double v, double* wsum, double* res)
+// Block sum of one value (256 threads) for thread 0 only: warp butterflies,
+// then thread 0 adds the eight warp sums as a balanced tree.
+__device__ __forceinline__ double block_sum1_t0(double v, double* wsum)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x == 0) *res = ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3])) + ((wsum[4] + wsum[5]) + (wsum[6] + wsum[7]));
-    __syncthreads();
-}
-
-// Cross-block sums of all NV slots by one warp: lane l < 3*NV sums slot
-// l % NV over the blocks b = l / NV (mod 3) as balanced trees of 16, then
-// the three lanes of each slot are added in a fixed order; lanes 0..NV-1
-// write the totals to out[].
-template <int NV>
-__device__ __forceinline__ void warp_sum_partials_all(const double* part, int G, double* out)
-{
-    const int lane = threadIdx.x & 31;
-    const int v = lane % NV, ph = lane / NV;
-    double acc = 0.0;
-    if (ph < 3) {
-        for (int base = ph; base < G; base += 3 * 16) {
-            double a[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int b = base + 3 * q;
-                a[q] = b < G ? __ldcg(part + (size_t)b * kMaxMom + v) : 0.0;
-            }
-#pragma unroll
-            for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-                for (int q = 0; q < w; ++q) a[q] += a[q + w];
-            acc += a[0];
-        }
-    }
-    const double a1 = __shfl_sync(0xffffffffu, acc, (lane + NV) & 31);
-    const double a2 = __shfl_sync(0xffffffffu, acc, (lane + 2 * NV) & 31);
-    if (lane < NV) out[lane] = (acc + a1) + a2;
-}
-
-// Deterministic block sum of NV values per thread through shared memory:
-// 16 threads per value each sum 16 rows (balanced tree), then one thread per
-// value sums the 16 results.  Result in res[0..NV) (shared).  256 threads.
-template <int NV>
-__device__ __forceinline__ void block_sum_smem(const double (&v)[NV], double* red, double* red2, double* res)
-{
-    constexpr int S = NV + 1;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) red[threadIdx.x * S + k] = v[k];
-    __syncthreads();
-    const int vv = threadIdx.x & 15, ch = threadIdx.x >> 4;
-    if (vv < NV) {
-        double a[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) a[r] = red[(ch * 16 + r) * S + vv];
-#pragma unroll
-        for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-            for (int r = 0; r < w; ++r) a[r] += a[r + w];
-        red2[ch * 16 + vv] = a[0];
-    }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        double a[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) a[r] = red2[r * 16 + threadIdx.x];
-#pragma unroll
-        for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-            for (int r = 0; r < w; ++r) a[r] += a[r + w];
-        res[threadIdx.x] = a[0];
-    }
-    __syncthreads();
-}
-
-// Cross-block sums of NV moment slots (slot[k]) by one warp in a fixed
-// order: lanes read 4 partials per round, tree-sum them, then a butterfly;
-// every lane ends with the totals.
-template <int NV>
-__device__ __forceinline__ void warp_sum_partials(const double* part, int G, const int (&slot)[NV], double (&tot)[NV])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-    for (int base = 0; base < G; base += 128) {
-        double v[NV][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int b = base + lane + 32 * q;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) v[k][q] = b < G ? __ldcg(part + (size_t)b * kMaxMom + slot[k]) : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += (v[k][0] + v[k][2]) + (v[k][1] + v[k][3]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+    return ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3])) + ((wsum[4] + wsum[5]) + (wsum[6] + wsum[7]));
 }
 
 // In the window after each barrier warp 0 runs the scalar chain, warps 1-6
@@ -223,10 +137,10 @@ struct TileShape<2> {
 };
 
 template <int NDIM>
-__device__ __forceinline__ void tile_origin(int t, int tiles_x, int& i0, int& j0)
+__device__ __forceinline__ void tile_origin(int t, int tiles_x, int ti, int& i0, int& j0)
 {
     if (NDIM == 1) { i0 = t * kFT1; j0 = 0; }
-    else { i0 = (t / tiles_x) * kFTI; j0 = (t % tiles_x) * kFTJ; }
+    else { i0 = (t / tiles_x) * ti; j0 = (t % tiles_x) * kFTJ; }
 }
 
 // local cell q of this thread in a tile -> (i, j)
@@ -254,25 +168,50 @@ __device__ __forceinline__ void moment_weights(int i, int j, const Geom& g, doub
     }
 }
 
+// Stage a 2-D tile of ti (<= kFTI) rows with its halo and compute every face
+// value, on the `nthr` threads whose rank in the group is `tid`.
+template <class Sync>
+__device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, int ti, const Geom& g,
+                                             Tile2DSmem<kFTI, kFTJ>& s, int tid, int nthr, Sync sync)
+{
+    constexpr int W = kFTJ + 3;
+    const int N1 = g.N1, N2 = g.N2;
+    for (int k = tid; k < (ti + 3) * W; k += nthr) {
+        const int r = k / W, c = k - r * W;
+        const int gi = i0 - 2 + r, gj = j0 - 2 + c;
+        s.tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? __ldcg(in + (size_t)gi * N2 + gj) : 0.0;
+    }
+    sync();
+    for (int k = tid; k < (ti + 1) * kFTJ; k += nthr) {
+        const int f = k / kFTJ, c = k - f * kFTJ;
+        s.h1[k] = face_value<true>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2], s.tile[(f + 2) * W + c + 2]);
+    }
+    for (int k = tid; k < ti * (kFTJ + 1); k += nthr) {
+        const int r = k / (kFTJ + 1), f = k - r * (kFTJ + 1);
+        const double* row = s.tile + (r + 2) * W;
+        s.h2[k] = face_value<true>(row[f], row[f + 1], row[f + 2]);
+    }
+}
+
 template <int NDIM, class Sync>
-__device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x, const Geom& g, FusedSmem<NDIM>& sm,
-                                            int tid, int nthr, Sync sync)
+__device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x, int ti, const Geom& g,
+                                            FusedSmem<NDIM>& sm, int tid, int nthr, Sync sync)
 {
     int i0, j0;
-    tile_origin<NDIM>(t, tiles_x, i0, j0);
+    tile_origin<NDIM>(t, tiles_x, ti, i0, j0);
     if constexpr (NDIM == 1) faces1d<true, true, kFT1>(in, i0, g, sm.tile, sm.h, tid, nthr, sync);
-    else faces2d<true, true, kFTI, kFTJ>(in, i0, j0, g, sm.t, tid, nthr, sync);
+    else faces2d_rows(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
 }
 
 // update of cell local index k of tile (i0, j0) from the faces in shared memory
 template <int STAGE, int NDIM>
-__device__ __forceinline__ double cell_update(const double* old, double* out, int k, int i0, int j0, const Geom& g,
+__device__ __forceinline__ double cell_update(const double* old, double* out, int k, int i0, int j0, int ti, const Geom& g,
                                               const StageCoef& sc, const FusedSmem<NDIM>& sm, bool& valid, int& i,
                                               int& j)
 {
     int r, c;
     cell_of<NDIM>(k, i0, j0, i, j, r, c);
-    valid = (NDIM == 1) ? (i < g.N1) : (i < g.N1 && j < g.N2);
+    valid = (NDIM == 1) ? (i < g.N1) : (r < ti && i < g.N1 && j < g.N2);
     if (!valid) return 0.0;
     double v;
     size_t gidx;
@@ -296,7 +235,7 @@ __device__ __forceinline__ double cell_update(const double* old, double* out, in
 template <int NDIM, bool ONE_TILE>
 __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
                                                    const double* t_out, double* rows, unsigned int* bar, int ntiles,
-                                                   int tiles_x, long long wait_limit, double* rowpart)
+                                                   int tiles_x, int ti, long long wait_limit, double* rowpart)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
@@ -305,7 +244,6 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     __shared__ StageCoef scs;   // coefficients of the coming stage (written by thread 0)
     __shared__ double red[kFNT * (NM + 1)];
     __shared__ double red2[256];
-    __shared__ double res[NM];
     __shared__ double msum[NM];
     __shared__ int fail;
     __shared__ FusedSmem<NDIM> sm;
@@ -321,16 +259,28 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     }
     const int G = gridDim.x;
     const int warp = threadIdx.x >> 5;
-    double* part1 = part;                        // stage-1 partials [G][kMaxMom]
-    double* part2 = part + (size_t)G * kMaxMom;  // stage-2 partials
     double* my_rows = blockIdx.x == 0 ? rows : nullptr;
+    // the volume moment is summed across blocks in fixed point (barrier_sum):
+    // unit u = 2^(E-52) with 2^E above twice the largest volume moment the
+    // solute balance allows, V0 + C / kappa (crystals grow only while S > 1),
+    // so that an error of u in V moves C by about 2^-52 C
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(bar);
+    unsigned long long acc_base0 = 0ull, acc_base1 = 0ull;
+    double u, inv_u;
+    {
+        double vmax = 2.0 * (s.V0 + (K.kappa > 0.0 ? s.C / K.kappa : 0.0));
+        if (!(vmax > 0.0) || !isfinite(vmax)) vmax = 1.0;
+        const int E = ilogb(vmax) + 1;
+        u = ldexp(1.0, E - 52);
+        inv_u = ldexp(1.0, 52 - E);
+    }
     unsigned int gen = 0;
 
     // moment weights of this thread's cells (one tile per block: fixed for the whole solve)
     double wgt[ONE_TILE ? CPT : 1][ONE_TILE ? NM : 1];
     if constexpr (ONE_TILE) {
         int i0, j0;
-        tile_origin<NDIM>(blockIdx.x, tiles_x, i0, j0);
+        tile_origin<NDIM>(blockIdx.x, tiles_x, ti, i0, j0);
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             int i, j, r, c;
@@ -339,7 +289,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
         }
     }
 
-    fused_faces<NDIM>(n, blockIdx.x, tiles_x, g, sm, threadIdx.x, kFNT, BlockSync());
+    fused_faces<NDIM>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
     __syncthreads();
     for (;;) {
 #pragma unroll 1
@@ -352,17 +302,17 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             for (int k = 0; k < NM; ++k) m[k] = 0.0;
             for (int t = blockIdx.x; t < ntiles; t += G) {
                 if (t != (int)blockIdx.x) {
-                    fused_faces<NDIM>(in, t, tiles_x, g, sm, threadIdx.x, kFNT, BlockSync());
+                    fused_faces<NDIM>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
                     __syncthreads();
                 }
                 int i0, j0;
-                tile_origin<NDIM>(t, tiles_x, i0, j0);
+                tile_origin<NDIM>(t, tiles_x, ti, i0, j0);
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     bool valid;
                     int i, j;
-                    const double v = stage == 1 ? cell_update<1, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, g, sc, sm, valid, i, j)
-                                                : cell_update<2, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, g, sc, sm, valid, i, j);
+                    const double v = stage == 1 ? cell_update<1, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, valid, i, j)
+                                                : cell_update<2, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, valid, i, j);
                     if (!valid) continue;
                     double wl[NM];
                     if constexpr (ONE_TILE) {
@@ -380,7 +330,6 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 }
                 __syncthreads();
             }
-            double* pp = stage == 1 ? part1 : part2;
             const int row_here = s.out_idx;
             // only the volume moment is on the critical path; on output steps
             // the per-thread moments wait in shared memory and are reduced in
@@ -389,15 +338,21 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
 #pragma unroll
                 for (int k = 0; k < NM; ++k) red[threadIdx.x * (NM + 1) + k] = m[k];
             }
-            block_sum1(m[VIDX], red2, res);
-            if (threadIdx.x == 0) pp[(size_t)blockIdx.x * kMaxMom + VIDX] = res[0];
-            if (!grid_barrier(bar, gen, &fail, wait_limit)) break;
+            const double vb = block_sum1_t0(m[VIDX], red2);
+            if (threadIdx.x == 0) {
+                double total = 0.0;
+                const int p = (int)(gen & 1u);
+                unsigned long long base = p ? acc_base1 : acc_base0;
+                const bool ok = barrier_sum(acc + p * kAccStride, base, vb, inv_u, u, (unsigned int)G, wait_limit, total);
+                if (p) acc_base1 = base;
+                else acc_base0 = base;
+                msum[VIDX] = total;
+                fail = !ok;
+            }
+            gen += 1u;
+            __syncthreads();
+            if (fail) break;
             if (warp == 0) {
-                const int slots[1] = {VIDX};
-                double tot[1];
-                warp_sum_partials<1>(pp, G, slots, tot);
-                if (threadIdx.x == 0) msum[VIDX] = tot[0];
-                __syncwarp();
                 if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
                 else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
                 // the next stage's coefficients, once per block (the divisions of
@@ -405,7 +360,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
             } else if (warp <= kFaceWarps) {
                 // faces of the next stage's input for this block's first tile
-                fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, g, sm, threadIdx.x - 32, 32 * kFaceWarps,
+                fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x - 32, 32 * kFaceWarps,
                                   GroupSync());
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one
@@ -462,25 +417,36 @@ __global__ void k_fused_rows(const double* rowpart, int G, const Scal* S, double
     rows[(size_t)r * (NM + 2) + 1 + threadIdx.x] = acc;
 }
 
-static int fused_tiles(const Geom& g, int* tiles_x)
+// Tiles of the fused launch: 1-D 1024 cells; 2-D ti x 32 with the smallest
+// ti (4 <= ti <= 16) that gives every co-resident block at most one tile
+// (all SMs busy, fewer cells each), else 16 x 32 tiles looped over.
+static int fused_tiles(const Geom& g, int max_blocks, int* tiles_x, int* ti)
 {
     if (g.ndim == 1) {
         *tiles_x = 1;
+        *ti = 1;
         return (g.N1 + kFT1 - 1) / kFT1;
     }
     *tiles_x = (g.N2 + kFTJ - 1) / kFTJ;
-    return *tiles_x * ((g.N1 + kFTI - 1) / kFTI);
+    *ti = kFTI;
+    if (*tiles_x <= max_blocks) {
+        const int rows_of_tiles = max_blocks / *tiles_x;
+        int t = (g.N1 + rows_of_tiles - 1) / rows_of_tiles;
+        if (t < 4) t = 4;
+        if (t <= kFTI) *ti = t;
+    }
+    return *tiles_x * ((g.N1 + *ti - 1) / *ti);
 }
 
 bool fused_supported(const pbe_grid* g) { return g->d_bar != nullptr; }
 
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
 {
-    int tiles_x;
-    const int ntiles = fused_tiles(g->geo, &tiles_x);
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) return e;
+    int tiles_x, ti;
+    const int ntiles = fused_tiles(g->geo, std::min(sms, g->max_blocks / 2), &tiles_x, &ti);
     const bool one = g->geo.ndim == 1 ? true : true;
     const void* fn_multi = g->geo.ndim == 1 ? (const void*)k_fused<1, false> : (const void*)k_fused<2, false>;
     const void* fn_one = g->geo.ndim == 1 ? (const void*)k_fused<1, true> : (const void*)k_fused<2, true>;
@@ -492,6 +458,7 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     if (G > occ * sms) G = occ * sms;
     if (2 * G > g->max_blocks) G = g->max_blocks / 2;
     if (G < 1) G = 1;
+    if (G > 1000) G = 1000;   // the arrival count of barrier_sum has 10 bits
     const void* fn = (G >= ntiles) ? fn_one : fn_multi;
     if (fn == fn_multi) {
         int occ2 = 0;
@@ -499,11 +466,11 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
         if (e != cudaSuccess) return e;
         if (G > occ2 * sms) G = occ2 * sms;
     }
-    e = cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned int), g->stream);
+    e = cudaMemsetAsync(g->d_bar, 0, 2 * kAccStride * sizeof(unsigned long long), g->stream);
     if (e != cudaSuccess) return e;
     long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
     void* args[] = {&g->d_n, &g->d_n1, &g->d_S, &g->kin, &g->geo, &g->d_part, &g->d_tout, &g->d_rows,
-                    &g->d_bar, (void*)&ntiles, &tiles_x, &wait_limit, &g->d_rowpart};
+                    &g->d_bar, (void*)&ntiles, &tiles_x, &ti, &wait_limit, &g->d_rowpart};
     e = cudaLaunchCooperativeKernel(fn, G, kFNT, args, 0, g->stream);
     if (e != cudaSuccess) return e;
     const int nrows = n_out > 0 ? n_out : 1;

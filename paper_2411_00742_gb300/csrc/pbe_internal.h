@@ -20,7 +20,7 @@ struct pbe_grid {
     pbe::Scal* d_S;     // scalars
     double* d_part;     // block partials [max_blocks][kMaxMom]
     double* d_mom;      // moments read-out (kMaxMom doubles)
-    unsigned int* d_bar; // device-wide barrier of the fused path (count, generation)
+    unsigned int* d_bar; // fused path: 512 bytes of barrier accumulators (two 64-bit words, 128 B apart)
     int max_blocks;
     double* d_tout;     // output times (capacity tout_cap)
     double* d_rows;     // output rows (capacity tout_cap rows of 12)

@@ -10,6 +10,12 @@
 //   log: x = 2^e m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(z),
 //        z = (m-1)/(m+1), by the odd Taylor series of atanh to z^23 (Estrin
 //        in w = z^2), plus e ln2.
+//   log_tab: the table-driven form (Tang's method): x = 2^e m, m in [1, 2),
+//        the top 7 bits of m pick a centre c_j (pbe_log_table.h, written by
+//        gen_log_table.py), log x = e ln2 + ln c_j + log1p(r) with
+//        r = m / c_j - 1 (|r| <= 1/257) and log1p by its Taylor polynomial
+//        to r^7 (Estrin); 7 dependent FP64 operations instead of ~16, at an
+//        absolute (not relative) error of a few 1e-16 near x = 1.
 // Relative error is a few units of 2^-53 on the arguments the kinetics use
 // (checked against the C library on the host by the tests).  Arguments
 // outside the handled ranges (non-positive or non-finite log input, exp of
@@ -20,7 +26,16 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "pbe_log_table.h"
+
 namespace pbe {
+
+#ifdef __CUDACC__
+static __constant__ double c_log_inv[128] = PBE_LOG_TAB_INV;
+static __constant__ double c_log_ln[128] = PBE_LOG_TAB_LN;
+#endif
+static const double h_log_inv[128] = PBE_LOG_TAB_INV;
+static const double h_log_ln[128] = PBE_LOG_TAB_LN;
 
 __host__ __device__ __forceinline__ double pbe_bits_to_double(int64_t b)
 {
@@ -134,6 +149,41 @@ __host__ __device__ inline double pbe_log(double x)
     const double two_z = z + z;
     // e ln2 + 2 z P, with the small terms first
     return pbe_fma(ed, ln2_hi, pbe_fma(two_z, P, ed * ln2_lo));
+}
+
+__host__ __device__ inline double pbe_log_tab(double x)
+{
+    if (!(x > 0.0) || x == __builtin_huge_val()) {
+        if (x == 0.0) return -__builtin_huge_val();
+        if (x == __builtin_huge_val()) return x;
+        return (x - x) / (x - x);   // NaN for negative or NaN input
+    }
+    int64_t b = pbe_double_to_bits(x);
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) {                    // subnormal: scale into the normal range
+        x *= 18014398509481984.0;    // 2^54
+        b = pbe_double_to_bits(x);
+        e = (int)((b >> 52) & 0x7ff) - 54;
+    }
+    e -= 1023;
+    const int j = (int)((b >> 45) & 127);
+    const double m = pbe_bits_to_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);   // [1, 2)
+#ifdef __CUDA_ARCH__
+    const double inv = c_log_inv[j], lnc = c_log_ln[j];
+#else
+    const double inv = h_log_inv[j], lnc = h_log_ln[j];
+#endif
+    const double r = pbe_fma(m, inv, -1.0);
+    // log1p(r) = r + r^2 (c2 + c3 r + c4 r^2 + c5 r^3 + c6 r^4 + c7 r^5), c_k = (-1)^(k+1) / k
+    const double c2 = -0.5, c3 = 1.0 / 3, c4 = -0.25, c5 = 0.2, c6 = -1.0 / 6, c7 = 1.0 / 7;
+    const double r2 = r * r;
+    const double p23 = pbe_fma(c3, r, c2), p45 = pbe_fma(c5, r, c4), p67 = pbe_fma(c7, r, c6);
+    const double r4 = r2 * r2;
+    const double q = pbe_fma(r4, p67, pbe_fma(r2, p45, p23));
+    const double l1p = pbe_fma(r2, q, r);
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double ed = (double)e;
+    return pbe_fma(ed, ln2_hi, lnc) + pbe_fma(ed, ln2_lo, l1p);
 }
 
 }  // namespace pbe

@@ -1,6 +1,7 @@
 """Accuracy of the library's short-latency exp/log (pbe_math.cuh), compiled
 for the host with nvcc and compared with the C library on the ranges the
-kinetics use (argument of exp in [-60, 25], log of [e^-40, e^40])."""
+kinetics use (argument of exp in [-60, 25], log of [e^-40, e^40]), including
+the table-driven log (absolute error bound) at every table entry."""
 import os
 import shutil
 import subprocess
@@ -26,7 +27,19 @@ int main() {
   int special = pbe::pbe_exp(-800.0) == 0.0 && std::isinf(pbe::pbe_exp(800.0)) && std::isinf(pbe::pbe_log(0.0))
                 && std::isnan(pbe::pbe_log(-1.0)) && pbe::pbe_log(1.0) == 0.0 && pbe::pbe_exp(0.0) == 1.0
                 && std::fabs(pbe::pbe_log(4.9e-320) - std::log(4.9e-320)) < 1e-12;
-  printf("%.6e %.6e %.6e %d\n", me, ml, ma, special);
+  // table-driven log: absolute error on [e^-40, e^40] and near 1, special values
+  double mt = 0, mtr = 0;
+  for (int i = 0; i < 400000; ++i) {
+    double y = std::exp(L(rng)); double c = pbe::pbe_log_tab(y), d = std::log(y);
+    mtr = fmax(mtr, fabs(c - d) / fmax(fabs(d), 1.0));
+  }
+  for (int i = 0; i < 200000; ++i) { double y = 1.0 + (i - 100000) * 1e-9; mt = fmax(mt, fabs(pbe::pbe_log_tab(y) - std::log(y))); }
+  for (int k = 0; k < 128; ++k) {   // every table entry at its centre and both ends
+    for (double f : {0.0, 0.5, 0.999999}) { double y = 1.0 + (k + f) / 128.0; mt = fmax(mt, fabs(pbe::pbe_log_tab(y) - std::log(y))); }
+  }
+  int special_t = std::isinf(pbe::pbe_log_tab(0.0)) && std::isnan(pbe::pbe_log_tab(-1.0))
+                  && std::fabs(pbe::pbe_log_tab(1.0)) < 2e-16 && std::fabs(pbe::pbe_log_tab(4.9e-320) - std::log(4.9e-320)) < 1e-12;
+  printf("%.6e %.6e %.6e %d %.6e %.6e %d\n", me, ml, ma, special, mt, mtr, special_t);
   return 0;
 }
 '''
@@ -41,6 +54,11 @@ def test_exp_log_accuracy(tmp_path):
     exe = tmp_path / "m"
     subprocess.run([nvcc, "-O2", "-I", os.path.join(ROOT, "paper_2411_00742_gb300", "csrc"), "-o", str(exe), str(src)],
                    check=True, capture_output=True)
-    me, ml, ma, special = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    me, ml, ma, special, mt, mtr, special_t = subprocess.run([str(exe)], check=True, capture_output=True,
+                                                            text=True).stdout.split()
     assert float(me) < 1e-15 and float(ml) < 1e-15 and float(ma) < 1e-18
     assert special == "1"
+    # table-driven log: absolute error a few 1e-16 where |log x| <= 1 (every table
+    # entry, the neighbourhood of 1), relative error a few 1e-16 where |log x| > 1
+    assert float(mt) < 4e-16 and float(mtr) < 5e-16
+    assert special_t == "1"
