@@ -37,6 +37,12 @@ METRIC = "FVM cell-steps/s and adjoint grads/s, fused vs plain GPU, at stated FP
 # update (2 differences + 2 FMA = 6), volume moment (FMA = 2); stage 2 adds the
 # Runge-Kutta average (3): 18 + 21 = 39.
 FLOPS_PER_CELL_STEP_2D = 39
+# the paper's split scheme (Eq. 3, two sweeps): per direction and cell one
+# difference, one sum, one division, one product, the face value (FMA = 2), the
+# flux difference and the update (FMA = 2) = 9; two directions and the volume
+# moment (FMA = 2): 20 flops; HBM: read and write the state once = 16 bytes
+FLOPS_PER_CELL_STEP_PAPER = 20
+BYTES_PER_CELL_STEP_PAPER = 16
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64 (2 FMA/clk/SM x 152 SMs x ~2.07 GHz)
 L2_FLUSH_BYTES = 256 << 20
 
@@ -368,11 +374,50 @@ def run_gpu(args):
                     times.append(e0.elapsed_time(e1) * 1e-3)
         g.close()
         tp = sum(times) / len(times)
+        rate = inst.problem.ncell * steps / tp
+        achieved = FLOPS_PER_CELL_STEP_PAPER * rate / 1e12
         return {"workload": "paper base case, 6000x3000 bins on 1200x600 um, T = 15 C, 1 h, Eq. 3 + splitting",
                 "steps": steps, "paper_reported_steps": 1339, "s_per_solve": tp,
-                "value": inst.problem.ncell * steps / tp, "unit": "cell-steps/s",
-                "paper_context": "JAX (GPU) on an RTX 4090 in FP64: about 0.4 s for this case "
-                                 "(derived: Sec. 3.2 calls it almost 3x faster than 1.2 s)"}
+                "value": rate, "unit": "cell-steps/s",
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                             "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
+                             "hbm_gbs": BYTES_PER_CELL_STEP_PAPER * rate / 1e9,
+                             "kernel": "k_lw_step2d (one kernel per step, both sweeps)",
+                             "note": f"{FLOPS_PER_CELL_STEP_PAPER} algorithmic FP64 flop/cell-step (division = 1); "
+                                     "peak = nominal GB300 FP64"},
+                "paper_context": "JAX (GPU) on an RTX 4090 in FP64: 'almost 3x as fast' as a 1.2 s MATLAB run "
+                                 "(Sec. 3.2): about 0.4 s read as total time, about 2.3 s read per time step"}
+
+    def scaling_leg():
+        """Grid-size sweep of the 2-D workload (the paper's Fig. 3b analogue): full
+        solves at 512^2, 1024^2 and 2048^2 on the fused and plain paths."""
+        out = []
+        for N in (512, 1024, 2048):
+            sinst = pi.config_2d(N)
+            n0s = torch.as_tensor(sinst.n0).cuda()
+            row = {"grid": [N, N], "cells": N * N}
+            for path in ("fused", "plain"):
+                g = P.Grid.from_problem(sinst.problem, stream=stream, path=path)
+                times, nsteps = [], 0
+                with torch.cuda.stream(stream):
+                    for it in range(3 if N < 2048 else 2):
+                        g.set_state(n0s, sinst.C0, 0.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        _, nsteps = g.solve(sinst.t_out)
+                        e1.record(stream)
+                        e1.synchronize()
+                        if it >= 1:
+                            times.append(e0.elapsed_time(e1) * 1e-3)
+                g.close()
+                t = min(times)
+                rate = N * N * nsteps / t
+                row["steps"] = nsteps
+                row[path] = {"ms_per_solve": 1e3 * t, "value": rate, "unit": "cell-steps/s",
+                             "roofline_frac": FLOPS_PER_CELL_STEP_2D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
+            out.append(row)
+        return out
 
     clocks = ClockSampler(dev)
     if ws > 1:
@@ -386,6 +431,7 @@ def run_gpu(args):
     batch = batch_leg() if not args.no_batch else None
     adjoint = adjoint_leg() if not args.no_adjoint else None
     paper = paper_leg() if not args.no_paper else None
+    scaling = scaling_leg() if not args.no_scaling else None
 
     if ws > 1:
         import torch.distributed as dist
@@ -415,6 +461,7 @@ def run_gpu(args):
         "batch_1d": batch,
         "adjoint": adjoint,
         "paper_scheme": paper,
+        "scaling_2d": scaling,
         # per timed fused solve: k_set_scalars, k_prologue, k_fused, k_fused_rows
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
@@ -441,6 +488,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--no-scaling", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
