@@ -225,9 +225,11 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
         delete g;
         return fail(PBE_ENOMEM, "allocation of grid buffers failed");
     }
-    if (cudaMemset(g->d_S, 0, sizeof(Scal)) != cudaSuccess ||
-        cudaMemset(g->d_n, 0, sizeof(double) * nc) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
+    // per-thread default stream: no device-wide synchronization, so grids can
+    // be created while other threads' solves and graph captures are in flight
+    if (cudaMemsetAsync(g->d_S, 0, sizeof(Scal), cudaStreamPerThread) != cudaSuccess ||
+        cudaMemsetAsync(g->d_n, 0, sizeof(double) * nc, cudaStreamPerThread) != cudaSuccess ||
+        cudaStreamSynchronize(cudaStreamPerThread) != cudaSuccess) {
         free_grid_buffers(g);
         delete g;
         return fail(PBE_ECUDA, "initialising grid buffers failed");
