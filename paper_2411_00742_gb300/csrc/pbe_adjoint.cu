@@ -628,15 +628,17 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     // ---- forward with checkpoints every K steps ----
     if (n_out > g->tout_cap) {
         // grow the grid's output buffers through a regular solve-size request
-        cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
-        g->d_tout = nullptr; g->d_rows = nullptr; g->d_rowpart = nullptr; g->tout_cap = 0;
+        cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart); cudaFreeHost(g->h_tout);
+        g->d_tout = nullptr; g->d_rows = nullptr; g->d_rowpart = nullptr; g->h_tout = nullptr; g->tout_cap = 0;
         if (g->plain_exec) { cudaGraphExecDestroy(g->plain_exec); g->plain_exec = nullptr; }
         ATRY(cudaMalloc(&g->d_tout, sizeof(double) * n_out));
         ATRY(cudaMalloc(&g->d_rows, sizeof(double) * 12 * n_out));
         ATRY(cudaMalloc(&g->d_rowpart, sizeof(double) * (size_t)n_out * (g->max_blocks / 2 + 1) * 10));
+        ATRY(cudaMallocHost(&g->h_tout, sizeof(double) * n_out));
         g->tout_cap = n_out;
     }
     ATRY(cudaMemcpyAsync(g->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, st));
+    g->tout_valid_n = 0;
     ATRY(launch_prologue(g, n_out, g->max_steps, nullptr));
     for (;;) {
         double* cn;

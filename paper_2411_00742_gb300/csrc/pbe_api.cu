@@ -65,7 +65,7 @@ void free_grid_buffers(pbe_grid* g)
     if (g->plain_exec) cudaGraphExecDestroy(g->plain_exec);
     cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom); cudaFree(g->d_bar);
     cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
-    cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage);
+    cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage); cudaFreeHost(g->h_tout);
 }
 
 int ncol_of(const pbe_grid* g) { return g->geo.ndim == 1 ? 6 : 12; }
@@ -76,12 +76,14 @@ pbe_status ensure_tout_capacity(pbe_grid* g, int n_out)
     int cap = g->tout_cap ? g->tout_cap : 64;
     while (cap < n_out) cap *= 2;
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
-    g->d_tout = nullptr; g->d_rows = nullptr; g->d_rowpart = nullptr; g->tout_cap = 0;
+    cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart); cudaFreeHost(g->h_tout);
+    g->d_tout = nullptr; g->d_rows = nullptr; g->d_rowpart = nullptr; g->h_tout = nullptr; g->tout_cap = 0;
+    g->tout_valid_n = 0;
     if (g->plain_exec) { cudaGraphExecDestroy(g->plain_exec); g->plain_exec = nullptr; }
     if (cudaMalloc(&g->d_tout, sizeof(double) * cap) != cudaSuccess ||
         cudaMalloc(&g->d_rows, sizeof(double) * cap * 12) != cudaSuccess ||
-        cudaMalloc(&g->d_rowpart, sizeof(double) * (size_t)cap * (g->max_blocks / 2 + 1) * 10) != cudaSuccess)
+        cudaMalloc(&g->d_rowpart, sizeof(double) * (size_t)cap * (g->max_blocks / 2 + 1) * 10) != cudaSuccess ||
+        cudaMallocHost(&g->h_tout, sizeof(double) * cap) != cudaSuccess)
         return fail(PBE_ENOMEM, "cudaMalloc of %d output rows failed", cap);
     g->tout_cap = cap;
     return PBE_OK;
@@ -452,7 +454,12 @@ pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, 
     if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
     pbe_status st = ensure_tout_capacity(g, n_out);
     if (st) return st;
-    CUDA_TRY(cudaMemcpyAsync(g->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, g->stream));
+    // the output times go to the device only when they changed since the last solve
+    if (n_out != g->tout_valid_n || memcmp(g->h_tout, t_out, sizeof(double) * n_out) != 0) {
+        memcpy(g->h_tout, t_out, sizeof(double) * n_out);
+        CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_tout, sizeof(double) * n_out, cudaMemcpyHostToDevice, g->stream));
+        g->tout_valid_n = n_out;
+    }
     st = run_solve(g, n_out);
     if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(rows, g->d_rows, sizeof(double) * n_out * ncol_of(g), kind_from_device(mem), g->stream));
@@ -473,6 +480,7 @@ pbe_status pbe_step(pbe_grid* g, double t_limit, double* dt_taken)
     if (st) return st;
     g->h_stage[0] = t_limit;
     CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_stage, sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    g->tout_valid_n = 0;
     CUDA_TRY(pbe::launch_prologue(g, 1, 1, nullptr));
     CUDA_TRY(pbe::launch_plain_step(g, false, 0));
     CUDA_TRY(pbe::launch_paper_finish(g));

@@ -26,6 +26,8 @@ struct pbe_grid {
     double* d_rows;     // output rows (capacity tout_cap rows of 12)
     double* d_rowpart;  // fused path: per-row, per-block moment partials (tout_cap x max_blocks/2 x 10)
     int tout_cap;
+    double* h_tout;     // pinned copy of the output times last sent to d_tout (capacity tout_cap)
+    int tout_valid_n;   // number of entries of d_tout equal to h_tout (0: none)
     pbe::Scal* h_S;     // pinned copy of the scalars
     double* h_stage;    // pinned staging for small host<->device copies (64 doubles)
     // plain-path graph: prologue + while-loop over the two stage kernels
