@@ -298,6 +298,17 @@ pbe_status pbe_adam_update(double* w, const double* grad, double* m, double* v, 
  * wait that does not complete at once run out (used to exercise that path). */
 pbe_status pbe_set_wait_limit(pbe_grid* g, double seconds);
 
+/* Device timing of pbe_solve.  With `enable` != 0 every later pbe_solve
+ * records two CUDA events on the grid's stream around the launch that
+ * advances the state (the fused path's persistent kernel; the plain path's
+ * graph or its chunked step launches) - the prologue, the output-row kernel
+ * and the copies stay outside.  pbe_kernel_time writes that duration of the
+ * last solve in milliseconds to the HOST double `ms` (-1 when timing was off
+ * or the solve failed).  Enabling creates the two events; it does not
+ * synchronize. */
+pbe_status pbe_set_timing(pbe_grid* g, int enable);
+pbe_status pbe_kernel_time(pbe_grid* g, double* ms);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* pbe_last_error(void);
 

@@ -120,6 +120,16 @@ class Grid:
     def set_max_steps(self, n: int):
         _lib.check(self.lib.pbe_set_max_steps(self.h, int(n)))
 
+    def set_timing(self, enable: bool = True):
+        """Record CUDA events around the launch that advances the state in every solve."""
+        _lib.check(self.lib.pbe_set_timing(self.h, 1 if enable else 0))
+
+    def kernel_time_ms(self) -> float:
+        """Device time of that launch in the last solve (ms; -1 when not recorded)."""
+        v = ctypes.c_double(-1.0)
+        _lib.check(self.lib.pbe_kernel_time(self.h, ctypes.byref(v)))
+        return v.value
+
     def set_closure(self, weights):
         """Weights of the learned kinetics closure (flat float32, layout W1, b1, W2, b2, W3, b3);
         the matrices are stored as bf16."""

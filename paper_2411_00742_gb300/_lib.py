@@ -59,6 +59,8 @@ SIGNATURES = {
     "pbe_moments": [_P, _P, _I],
     "pbe_set_max_steps": [_P, _I64],
     "pbe_set_wait_limit": [_P, _D],
+    "pbe_set_timing": [_P, _I],
+    "pbe_kernel_time": [_P, _PD],
     "pbe_vjp": [_P, _PD, _I, _P, _I, _I, _PD, _P, _PD, _P, _I, _PD],
     "pbe_set_closure": [_P, ctypes.POINTER(ctypes.c_float), _I],
     "pbe_solve_1d_noalloc": [ctypes.POINTER(Kinetics), _I64, _D, _P, _D, _D, _PD, _I, _P, _PI64, _P],

@@ -66,6 +66,8 @@ void free_grid_buffers(pbe_grid* g)
     cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom); cudaFree(g->d_bar);
     cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
     cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage); cudaFreeHost(g->h_tout);
+    if (g->ev_k0) cudaEventDestroy(g->ev_k0);
+    if (g->ev_k1) cudaEventDestroy(g->ev_k1);
 }
 
 int ncol_of(const pbe_grid* g) { return g->geo.ndim == 1 ? 6 : 12; }
@@ -156,11 +158,14 @@ pbe_status run_solve(pbe_grid* g, int n_out)
     }
     build_plain_graph(g);
     if (g->plain_exec) {
+        if (g->timing) CUDA_TRY(cudaEventRecord(g->ev_k0, g->stream));
         CUDA_TRY(cudaGraphLaunch(g->plain_exec, g->stream));
+        if (g->timing) CUDA_TRY(cudaEventRecord(g->ev_k1, g->stream));
         CUDA_TRY(pbe::launch_paper_finish(g));
         return PBE_OK;
     }
     // host loop over chunks of steps; stage kernels return at once when done
+    if (g->timing) CUDA_TRY(cudaEventRecord(g->ev_k0, g->stream));
     for (long long done_steps = 0;;) {
         int chunk = 16;
         for (int k = 0; k < chunk; ++k) CUDA_TRY(pbe::launch_plain_step(g, false, 0));
@@ -170,6 +175,7 @@ pbe_status run_solve(pbe_grid* g, int n_out)
         if (g->h_S->done) break;
         if (done_steps > g->max_steps + chunk) return fail(PBE_ETIMEOUT, "solve did not finish");
     }
+    if (g->timing) CUDA_TRY(cudaEventRecord(g->ev_k1, g->stream));
     CUDA_TRY(pbe::launch_paper_finish(g));
     return PBE_OK;
 }
@@ -211,6 +217,7 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
     g->path = PBE_PATH_PLAIN;
     g->max_steps = 1000000;
     g->wait_cycles = -1;
+    g->kernel_ms = -1.0;
     g->max_blocks = pbe::plain_max_blocks(g->geo);
     if (g->max_blocks < 1024) g->max_blocks = 1024;
     bool ok = cudaMalloc(&g->d_n, sizeof(double) * nc) == cudaSuccess &&
@@ -460,12 +467,38 @@ pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, 
         CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_tout, sizeof(double) * n_out, cudaMemcpyHostToDevice, g->stream));
         g->tout_valid_n = n_out;
     }
+    g->kernel_ms = -1.0;
     st = run_solve(g, n_out);
     if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(rows, g->d_rows, sizeof(double) * n_out * ncol_of(g), kind_from_device(mem), g->stream));
     st = finish_call(g);
     if (steps) *steps = g->h_S->steps;
+    if (g->timing) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, g->ev_k0, g->ev_k1) == cudaSuccess) g->kernel_ms = ms;
+    }
     return st;
+}
+
+pbe_status pbe_set_timing(pbe_grid* g, int enable)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
+    if (enable && !g->ev_k0) {
+        CUDA_TRY(cudaEventCreate(&g->ev_k0));
+        CUDA_TRY(cudaEventCreate(&g->ev_k1));
+    }
+    g->timing = enable != 0;
+    g->kernel_ms = -1.0;
+    return PBE_OK;
+}
+
+pbe_status pbe_kernel_time(pbe_grid* g, double* ms)
+{
+    if (!g || !ms) return fail(PBE_EINVAL, "null argument");
+    *ms = g->kernel_ms;
+    return PBE_OK;
 }
 
 pbe_status pbe_step(pbe_grid* g, double t_limit, double* dt_taken)

@@ -53,8 +53,8 @@ __device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long
 // Device-wide barrier over the co-resident blocks of the cooperative launch
 // that also sums one value over the blocks, exactly and independently of the
 // arrival order (so every block, on every run, gets the same total): each
-// block adds its value rounded to an integer multiple q of the unit u (a
-// power of two), as (q << 10) + 1, to a 64-bit accumulator with a release
+// block adds its value, an integer multiple q of the unit u (a power of
+// two), as (q << 10) + 1, to a 64-bit accumulator with a release
 // add (cumulative over the writes the block barrier ordered before it), and
 // waits with acquire loads.  The low 10 bits count the arrivals of the
 // stage, the rest sums q (integer addition is associative; the accumulator
@@ -63,10 +63,9 @@ __device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long
 // stage s).  Thread 0 only; returns false when the wait runs past `limit`
 // cycles.
 constexpr int kAccStride = 16;   // the two accumulators lie 128 bytes apart
-__device__ bool barrier_sum(unsigned long long* acc, unsigned long long& base, double v, double inv_u, double u,
+__device__ bool barrier_sum(unsigned long long* acc, unsigned long long& base, long long q, double u,
                             unsigned int nblocks, long long limit, double& total)
 {
-    const long long q = llrint(v * inv_u);
     atom_add_release_u64(acc, ((unsigned long long)q << 10) + 1ull);
     unsigned long long x = ld_acquire_u64(acc);
     if (((x - base) & 1023ull) != nblocks) {
@@ -87,13 +86,19 @@ __device__ bool barrier_sum(unsigned long long* acc, unsigned long long& base, d
     return true;
 }
 
-// Block sum of one value (256 threads) for thread 0 only: warp butterflies,
-// then thread 0 adds the eight warp sums as a balanced tree.
-__device__ __forceinline__ double block_sum1_t0(double v, double* wsum)
+// Block sum of one value (256 threads) in the fixed-point unit of
+// barrier_sum, for thread 0 only: every thread rounds its value to a
+// multiple q of u, each warp adds its q exactly with two 32-bit reductions
+// (the low 26 bits and the rest of q), and thread 0 adds the eight warp
+// sums.  Integer adds leave the FP64 pipe to the other warps and make the
+// sum independent of the order.  |q| < 2^51 (the unit bounds the volume
+// moment by 2^52 u) keeps the reduced high parts inside 32 bits.
+__device__ __forceinline__ long long block_sum_fixed_t0(double v, double inv_u, long long* wsum)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    const long long q = llrint(v * inv_u);
+    const int hs = __reduce_add_sync(0xffffffffu, (int)(q >> 26));
+    const unsigned ls = __reduce_add_sync(0xffffffffu, (unsigned)(q & 0x3ffffffLL));
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (long long)hs * (1LL << 26) + (long long)ls;
     __syncthreads();
     return ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3])) + ((wsum[4] + wsum[5]) + (wsum[6] + wsum[7]));
 }
@@ -338,12 +343,12 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
 #pragma unroll
                 for (int k = 0; k < NM; ++k) red[threadIdx.x * (NM + 1) + k] = m[k];
             }
-            const double vb = block_sum1_t0(m[VIDX], red2);
+            const long long qb = block_sum_fixed_t0(m[VIDX], inv_u, reinterpret_cast<long long*>(red2));
             if (threadIdx.x == 0) {
                 double total = 0.0;
                 const int p = (int)(gen & 1u);
                 unsigned long long base = p ? acc_base1 : acc_base0;
-                const bool ok = barrier_sum(acc + p * kAccStride, base, vb, inv_u, u, (unsigned int)G, wait_limit, total);
+                const bool ok = barrier_sum(acc + p * kAccStride, base, qb, u, (unsigned int)G, wait_limit, total);
                 if (p) acc_base1 = base;
                 else acc_base0 = base;
                 msum[VIDX] = total;
@@ -471,8 +476,10 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
     void* args[] = {&g->d_n, &g->d_n1, &g->d_S, &g->kin, &g->geo, &g->d_part, &g->d_tout, &g->d_rows,
                     &g->d_bar, (void*)&ntiles, &tiles_x, &ti, &wait_limit, &g->d_rowpart};
+    if (g->timing && (e = cudaEventRecord(g->ev_k0, g->stream)) != cudaSuccess) return e;
     e = cudaLaunchCooperativeKernel(fn, G, kFNT, args, 0, g->stream);
     if (e != cudaSuccess) return e;
+    if (g->timing && (e = cudaEventRecord(g->ev_k1, g->stream)) != cudaSuccess) return e;
     const int nrows = n_out > 0 ? n_out : 1;
     if (g->geo.ndim == 1) k_fused_rows<1><<<nrows, 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
     else k_fused_rows<2><<<nrows, 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);

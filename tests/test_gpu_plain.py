@@ -203,3 +203,54 @@ def test_init_seed_gaussian_rejects_bad_arguments():
         with pytest.raises(PbeError):
             g.init_seed_gaussian(**args)
     g.close()
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_output_times_reused_and_changed(path):
+    """Repeated solves on one grid: the same output times (kept on the device
+    between calls), new times of the same length, a single step in between."""
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(40, 24)
+    ta = np.array(inst.t_out[:7])
+    tb = ta + 30.0
+    tb[0] = 0.0
+    g = P.Grid.from_problem(inst.problem, path=path)
+    runs = []
+    for t_out in (ta, ta, tb, None, ta):
+        g.set_state(inst.n0, inst.C0, 0.0)
+        if t_out is None:
+            g.step(45.0)
+            continue
+        rows, _ = g.solve(t_out)
+        runs.append((t_out, rows))
+    g.close()
+    for t_out, rows in runs:
+        want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, t_out)
+        assert_rows_close(rows, want["rows"])
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][1], runs[3][1])
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_kernel_timing(path):
+    """pbe_set_timing / pbe_kernel_time: the recorded device time of the main
+    launch is positive and below the wall time of the whole call."""
+    import time
+
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(64)
+    g = P.Grid.from_problem(inst.problem, path=path)
+    assert g.kernel_time_ms() == -1.0
+    g.set_state(inst.n0, inst.C0, 0.0)
+    g.solve(inst.t_out)
+    assert g.kernel_time_ms() == -1.0       # timing off
+    g.set_timing(True)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    t0 = time.perf_counter()
+    rows, _ = g.solve(inst.t_out)
+    wall_ms = 1e3 * (time.perf_counter() - t0)
+    ms = g.kernel_time_ms()
+    assert 0.0 < ms < wall_ms
+    g.set_timing(False)
+    g.close()
+    want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out)
+    assert_rows_close(rows, want["rows"])
