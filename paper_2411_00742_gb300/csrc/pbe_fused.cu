@@ -173,18 +173,39 @@ __device__ __forceinline__ void moment_weights(int i, int j, const Geom& g, doub
     }
 }
 
-// Stage a 2-D tile of ti (<= kFTI) rows with its halo and compute every face
-// value, on the `nthr` threads whose rank in the group is `tid`.
-template <class Sync>
+// Stage a 2-D tile of ti (<= kFTI) rows with its halo (HALO_ONLY: only the
+// halo - the tile's own cells are already in shared memory) and compute every
+// face value, on the `nthr` threads whose rank in the group is `tid`.  The
+// faces read the halo rows at the tile's columns and the halo columns at its
+// rows, never the corners.
+template <bool HALO_ONLY, class Sync>
 __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, int ti, const Geom& g,
                                              Tile2DSmem<kFTI, kFTJ>& s, int tid, int nthr, Sync sync)
 {
     constexpr int W = kFTJ + 3;
     const int N1 = g.N1, N2 = g.N2;
-    for (int k = tid; k < (ti + 3) * W; k += nthr) {
-        const int r = k / W, c = k - r * W;
-        const int gi = i0 - 2 + r, gj = j0 - 2 + c;
-        s.tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? __ldcg(in + (size_t)gi * N2 + gj) : 0.0;
+    if (HALO_ONLY) {
+        const int nrow = 3 * kFTJ;   // rows -2, -1, ti at the tile's columns; then columns -2, -1, 32 at its rows
+        for (int k = tid; k < nrow + 3 * ti; k += nthr) {
+            int r, c;
+            if (k < nrow) {
+                const int h = k / kFTJ;
+                r = h < 2 ? h : ti + 2;
+                c = 2 + (k - h * kFTJ);
+            } else {
+                const int kk = k - nrow, h = kk / ti;
+                r = 2 + (kk - h * ti);
+                c = h < 2 ? h : kFTJ + 2;
+            }
+            const int gi = i0 - 2 + r, gj = j0 - 2 + c;
+            s.tile[r * W + c] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? __ldcg(in + (size_t)gi * N2 + gj) : 0.0;
+        }
+    } else {
+        for (int k = tid; k < (ti + 3) * W; k += nthr) {
+            const int r = k / W, c = k - r * W;
+            const int gi = i0 - 2 + r, gj = j0 - 2 + c;
+            s.tile[k] = (gi >= 0 && gi < N1 && gj >= 0 && gj < N2) ? __ldcg(in + (size_t)gi * N2 + gj) : 0.0;
+        }
     }
     sync();
     for (int k = tid; k < (ti + 1) * kFTJ; k += nthr) {
@@ -198,21 +219,39 @@ __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, i
     }
 }
 
-template <int NDIM, class Sync>
+template <int NDIM, bool HALO_ONLY = false, class Sync>
 __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x, int ti, const Geom& g,
                                             FusedSmem<NDIM>& sm, int tid, int nthr, Sync sync)
 {
     int i0, j0;
     tile_origin<NDIM>(t, tiles_x, ti, i0, j0);
-    if constexpr (NDIM == 1) faces1d<true, true, kFT1>(in, i0, g, sm.tile, sm.h, tid, nthr, sync);
-    else faces2d_rows(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
+    if constexpr (NDIM == 1) {
+        if (HALO_ONLY) {   // cells i0-2, i0-1 and i0+T
+            const int N = g.N1;
+            if (tid < 3) {
+                const int k = tid < 2 ? tid : kFT1 + 2, gi = i0 - 2 + k;
+                sm.tile[k] = (gi >= 0 && gi < N) ? __ldcg(in + gi) : 0.0;
+            }
+            sync();
+            for (int f = tid; f <= kFT1; f += nthr) sm.h[f] = face_value<true>(sm.tile[f], sm.tile[f + 1], sm.tile[f + 2]);
+        } else {
+            faces1d<true, true, kFT1>(in, i0, g, sm.tile, sm.h, tid, nthr, sync);
+        }
+    } else {
+        faces2d_rows<HALO_ONLY>(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
+    }
 }
 
-// update of cell local index k of tile (i0, j0) from the faces in shared memory
-template <int STAGE, int NDIM>
+// update of cell local index k of tile (i0, j0) from the faces in shared memory.
+// ONE_TILE (the block keeps its tile for the whole solve): the stage-2 base
+// value n^k comes from the register `keep` (updated here), and the new value
+// also replaces the cell's own entry of the shared tile, the next stage's
+// input - the faces of this stage are already computed and each thread reads
+// only its own cells' entries here.
+template <int STAGE, int NDIM, bool ONE_TILE>
 __device__ __forceinline__ double cell_update(const double* old, double* out, int k, int i0, int j0, int ti, const Geom& g,
-                                              const StageCoef& sc, const FusedSmem<NDIM>& sm, bool& valid, int& i,
-                                              int& j)
+                                              const StageCoef& sc, FusedSmem<NDIM>& sm, double& keep, bool& valid,
+                                              int& i, int& j)
 {
     int r, c;
     cell_of<NDIM>(k, i0, j0, i, j, r, c);
@@ -220,20 +259,27 @@ __device__ __forceinline__ double cell_update(const double* old, double* out, in
     if (!valid) return 0.0;
     double v;
     size_t gidx;
+    double* slot;
     if constexpr (NDIM == 1) {
-        v = sm.tile[r + 2] + sc.c1 * (sm.h[r] - sm.h[r + 1]);
+        slot = sm.tile + r + 2;
+        v = *slot + sc.c1 * (sm.h[r] - sm.h[r + 1]);
         gidx = i;
         if (i == 0) v += sc.src;
     } else {
         constexpr int W = kFTJ + 3;
-        const auto& s = sm.t;
-        v = s.tile[(r + 2) * W + c + 2] + sc.c1 * (s.h1[r * kFTJ + c] - s.h1[(r + 1) * kFTJ + c]) +
+        auto& s = sm.t;
+        slot = s.tile + (r + 2) * W + c + 2;
+        v = *slot + sc.c1 * (s.h1[r * kFTJ + c] - s.h1[(r + 1) * kFTJ + c]) +
             sc.c2 * (s.h2[r * (kFTJ + 1) + c] - s.h2[r * (kFTJ + 1) + c + 1]);
         gidx = (size_t)i * g.N2 + j;
         if (i == 0 && j == 0) v += sc.src;
     }
-    if (STAGE == 2) v = 0.5 * old[gidx] + 0.5 * v;
+    if (STAGE == 2) v = 0.5 * (ONE_TILE ? keep : old[gidx]) + 0.5 * v;
     out[gidx] = v;
+    if (ONE_TILE) {
+        *slot = v;
+        if (STAGE == 2) keep = v;
+    }
     return v;
 }
 
@@ -283,6 +329,8 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
 
     // moment weights of this thread's cells (one tile per block: fixed for the whole solve)
     double wgt[ONE_TILE ? CPT : 1][ONE_TILE ? NM : 1];
+    double keep[ONE_TILE ? CPT : 1];   // n at the start of the step for this thread's cells
+    keep[0] = 0.0;
     if constexpr (ONE_TILE) {
         int i0, j0;
         tile_origin<NDIM>(blockIdx.x, tiles_x, ti, i0, j0);
@@ -291,6 +339,8 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             int i, j, r, c;
             cell_of<NDIM>(threadIdx.x + q * kFNT, i0, j0, i, j, r, c);
             moment_weights<NDIM>(i, j, g, wgt[q]);
+            const bool valid = (NDIM == 1) ? (i < g.N1) : (r < ti && i < g.N1 && j < g.N2);
+            keep[q] = valid && (int)blockIdx.x < ntiles ? n[(size_t)i * g.N2 + j] : 0.0;
         }
     }
 
@@ -316,8 +366,10 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 for (int q = 0; q < CPT; ++q) {
                     bool valid;
                     int i, j;
-                    const double v = stage == 1 ? cell_update<1, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, valid, i, j)
-                                                : cell_update<2, NDIM>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, valid, i, j);
+                    double& kq = keep[ONE_TILE ? q : 0];
+                    const double v = stage == 1
+                        ? cell_update<1, NDIM, ONE_TILE>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j)
+                        : cell_update<2, NDIM, ONE_TILE>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j);
                     if (!valid) continue;
                     double wl[NM];
                     if constexpr (ONE_TILE) {
@@ -365,8 +417,9 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
             } else if (warp <= kFaceWarps) {
                 // faces of the next stage's input for this block's first tile
-                fused_faces<NDIM>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x - 32, 32 * kFaceWarps,
-                                  GroupSync());
+                // (one tile per block: its cells are in shared memory, only the halo is loaded)
+                fused_faces<NDIM, ONE_TILE>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x - 32,
+                                            32 * kFaceWarps, GroupSync());
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one
                 constexpr int NT2 = kFNT - 32 * (kFaceWarps + 1);
@@ -410,16 +463,20 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
 }
 
 // Moments of the rows the fused solve emitted: sums of the per-block partials
-// in block order (one block per row, one thread per moment).
+// (one block per row, one warp per moment: lane-strided partial sums, then a
+// butterfly; a fixed order, so the rows are the same on every run).
 template <int NDIM>
 __global__ void k_fused_rows(const double* rowpart, int G, const Scal* S, double* rows)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     const int r = S->row_first + blockIdx.x;
-    if (r >= S->out_idx || threadIdx.x >= NM) return;
+    const int m = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (r >= S->out_idx || m >= NM) return;
     double acc = 0.0;
-    for (int b = 0; b < G; ++b) acc += rowpart[((size_t)r * G + b) * NM + threadIdx.x];
-    rows[(size_t)r * (NM + 2) + 1 + threadIdx.x] = acc;
+    for (int b = lane; b < G; b += 32) acc += rowpart[((size_t)r * G + b) * NM + m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) rows[(size_t)r * (NM + 2) + 1 + m] = acc;
 }
 
 // Tiles of the fused launch: 1-D 1024 cells; 2-D ti x 32 with the smallest
@@ -481,8 +538,8 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     if (e != cudaSuccess) return e;
     if (g->timing && (e = cudaEventRecord(g->ev_k1, g->stream)) != cudaSuccess) return e;
     const int nrows = n_out > 0 ? n_out : 1;
-    if (g->geo.ndim == 1) k_fused_rows<1><<<nrows, 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
-    else k_fused_rows<2><<<nrows, 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
+    if (g->geo.ndim == 1) k_fused_rows<1><<<nrows, 4 * 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
+    else k_fused_rows<2><<<nrows, 10 * 32, 0, g->stream>>>(g->d_rowpart, G, g->d_S, g->d_rows);
     return cudaGetLastError();
 }
 

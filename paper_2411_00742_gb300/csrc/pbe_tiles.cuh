@@ -17,33 +17,40 @@
 
 namespace pbe {
 
-// Half the van Leer limited slope with a Newton-Raphson quotient:
-// q = b / (a + b) from the hardware reciprocal approximation r ~ 1/s
-// refined by one Newton-Raphson step on the quotient (q1 = q0 + r (b - s q0),
-// error ~ (1 - s r)^2), and the same-sign test on the sign/exponent bits.
-// Faces where |a| or |b| is below 2^-959 are treated as flat (their limited
-// slope is below 1e-288).
-__device__ __forceinline__ double half_psi_fast(double a, double b)
+// The van Leer quotient q = b / (a + b) for a, b of the same strict sign,
+// else 0 (the limited slope is then 2 a q, see Eq. 3), by the Newton-Raphson
+// form: the hardware reciprocal approximation r ~ 1/s refined by one step on
+// the quotient (q1 = q0 + r (b - s q0), error ~ (1 - s r)^2), and the
+// same-sign test on the sign/exponent bits.  Faces where |a| or |b| is below
+// 2^-959 are treated as flat (their limited slope is below 1e-288).
+__device__ __forceinline__ double psi_quot_fast(double a, double b)
 {
     const int ha = __double2hiint(a), hb = __double2hiint(b);
     const bool same = ((ha ^ hb) >= 0) && ((ha & 0x7ff00000) >= 0x04000000) && ((hb & 0x7ff00000) >= 0x04000000);
-    double r = 0.0;
+    double q = 0.0;
     if (same) {
         const double s = a + b;
         double rc;
         asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rc) : "d"(s));
         const double q0 = b * rc;
         const double e = fma(-s, q0, b);
-        const double q = fma(rc, e, q0);
-        r = a * q;
+        q = fma(rc, e, q0);
     }
-    return r;
+    return q;
 }
 
+// Half the van Leer limited slope, a q.
+__device__ __forceinline__ double half_psi_fast(double a, double b) { return a * psi_quot_fast(a, b); }
+
+// Face value n_up + psi/2 (FAST: one FMA on the quotient).
 template <bool FAST>
 __device__ __forceinline__ double face_value(double nm2, double up, double dn)
 {
-    return FAST ? up + half_psi_fast(up - nm2, dn - up) : up + half_psi(up - nm2, dn - up);
+    if (FAST) {
+        const double a = up - nm2;
+        return fma(a, psi_quot_fast(a, dn - up), up);
+    }
+    return up + half_psi(up - nm2, dn - up);
 }
 
 template <bool CG>
