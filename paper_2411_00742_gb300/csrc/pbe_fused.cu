@@ -114,6 +114,13 @@ struct GroupSync {  // named barrier over the face warps 1..kFaceWarps
 struct MomSync {    // named barrier over warps kFaceWarps+1..7
     __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 2, %0;" ::"r"(kFNT - 32 * (kFaceWarps + 1)) : "memory"); }
 };
+// Named barrier 3: warp 0 arrives once the device-wide barrier of the stage
+// is done (non-blocking), the face warps wait on it before they load the halo.
+// The unaligned forms: warp 0 reaches it after thread 0's wait.
+struct HaloGo {
+    static __device__ __forceinline__ void arrive() { asm volatile("barrier.arrive 3, %0;" ::"r"(32 * (kFaceWarps + 1)) : "memory"); }
+    static __device__ __forceinline__ void wait() { asm volatile("barrier.sync 3, %0;" ::"r"(32 * (kFaceWarps + 1)) : "memory"); }
+};
 struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
@@ -173,11 +180,12 @@ __device__ __forceinline__ void moment_weights(int i, int j, const Geom& g, doub
     }
 }
 
-// Stage a 2-D tile of ti (<= kFTI) rows with its halo (HALO_ONLY: only the
-// halo - the tile's own cells are already in shared memory) and compute every
-// face value, on the `nthr` threads whose rank in the group is `tid`.  The
-// faces read the halo rows at the tile's columns and the halo columns at its
-// rows, never the corners.
+// Stage a 2-D tile of ti (<= kFTI) rows with its halo and compute every face
+// value, on the `nthr` threads whose rank in the group is `tid`.  HALO_ONLY:
+// the tile's own cells are already in shared memory and the faces that read
+// only them (faces2d_interior) are done; load the halo and compute the faces
+// that read it.  The faces read the halo rows at the tile's columns and the
+// halo columns at its rows, never the corners.
 template <bool HALO_ONLY, class Sync>
 __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, int ti, const Geom& g,
                                              Tile2DSmem<kFTI, kFTJ>& s, int tid, int nthr, Sync sync)
@@ -208,14 +216,50 @@ __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, i
         }
     }
     sync();
-    for (int k = tid; k < (ti + 1) * kFTJ; k += nthr) {
-        const int f = k / kFTJ, c = k - f * kFTJ;
-        s.h1[k] = face_value<true>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2], s.tile[(f + 2) * W + c + 2]);
+    if (HALO_ONLY) {
+        // L1 faces 0, 1 and ti of every column, then L2 faces 0, 1 and 32 of every row
+        const int nrow = 3 * kFTJ;
+        for (int k = tid; k < nrow + 3 * ti; k += nthr) {
+            if (k < nrow) {
+                const int h = k / kFTJ, c = k - h * kFTJ, f = h < 2 ? h : ti;
+                s.h1[f * kFTJ + c] = face_value<true>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2],
+                                                      s.tile[(f + 2) * W + c + 2]);
+            } else {
+                const int kk = k - nrow, h = kk / ti, r = kk - h * ti, f = h < 2 ? h : kFTJ;
+                const double* row = s.tile + (r + 2) * W;
+                s.h2[r * (kFTJ + 1) + f] = face_value<true>(row[f], row[f + 1], row[f + 2]);
+            }
+        }
+    } else {
+        for (int k = tid; k < (ti + 1) * kFTJ; k += nthr) {
+            const int f = k / kFTJ, c = k - f * kFTJ;
+            s.h1[k] = face_value<true>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2], s.tile[(f + 2) * W + c + 2]);
+        }
+        for (int k = tid; k < ti * (kFTJ + 1); k += nthr) {
+            const int r = k / (kFTJ + 1), f = k - r * (kFTJ + 1);
+            const double* row = s.tile + (r + 2) * W;
+            s.h2[k] = face_value<true>(row[f], row[f + 1], row[f + 2]);
+        }
     }
-    for (int k = tid; k < ti * (kFTJ + 1); k += nthr) {
-        const int r = k / (kFTJ + 1), f = k - r * (kFTJ + 1);
+}
+
+// The faces of a 2-D tile that read only the tile's own cells (tile rows and
+// columns 2 .. ti+1 / 2 .. 33 of the staged array): L1 faces 2 .. ti-1 of
+// every column and L2 faces 2 .. 31 of every row.  No memory traffic beyond
+// shared memory, so they can run while the device-wide barrier is pending.
+__device__ __forceinline__ void faces2d_interior(int ti, Tile2DSmem<kFTI, kFTJ>& s, int tid, int nthr)
+{
+    constexpr int W = kFTJ + 3;
+    for (int k = tid; k < (ti - 2) * kFTJ; k += nthr) {
+        const int f = 2 + k / kFTJ, c = k % kFTJ;
+        s.h1[f * kFTJ + c] = face_value<true>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2],
+                                              s.tile[(f + 2) * W + c + 2]);
+    }
+    constexpr int NF = kFTJ - 2;
+    for (int k = tid; k < ti * NF; k += nthr) {
+        const int r = k / NF, f = 2 + (k - r * NF);
         const double* row = s.tile + (r + 2) * W;
-        s.h2[k] = face_value<true>(row[f], row[f + 1], row[f + 2]);
+        s.h2[r * (kFTJ + 1) + f] = face_value<true>(row[f], row[f + 1], row[f + 2]);
     }
 }
 
@@ -226,19 +270,33 @@ __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x
     int i0, j0;
     tile_origin<NDIM>(t, tiles_x, ti, i0, j0);
     if constexpr (NDIM == 1) {
-        if (HALO_ONLY) {   // cells i0-2, i0-1 and i0+T
+        if (HALO_ONLY) {   // cells i0-2, i0-1 and i0+T, then faces 0, 1 and T
             const int N = g.N1;
             if (tid < 3) {
                 const int k = tid < 2 ? tid : kFT1 + 2, gi = i0 - 2 + k;
                 sm.tile[k] = (gi >= 0 && gi < N) ? __ldcg(in + gi) : 0.0;
             }
             sync();
-            for (int f = tid; f <= kFT1; f += nthr) sm.h[f] = face_value<true>(sm.tile[f], sm.tile[f + 1], sm.tile[f + 2]);
+            if (tid < 3) {
+                const int f = tid < 2 ? tid : kFT1;
+                sm.h[f] = face_value<true>(sm.tile[f], sm.tile[f + 1], sm.tile[f + 2]);
+            }
         } else {
             faces1d<true, true, kFT1>(in, i0, g, sm.tile, sm.h, tid, nthr, sync);
         }
     } else {
         faces2d_rows<HALO_ONLY>(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
+    }
+}
+
+// faces of the block's tile that read only its own cells (one tile per block)
+template <int NDIM>
+__device__ __forceinline__ void fused_faces_interior(int ti, FusedSmem<NDIM>& sm, int tid, int nthr)
+{
+    if constexpr (NDIM == 1) {
+        for (int f = 2 + tid; f < kFT1; f += nthr) sm.h[f] = face_value<true>(sm.tile[f], sm.tile[f + 1], sm.tile[f + 2]);
+    } else {
+        faces2d_interior(ti, sm.t, tid, nthr);
     }
 }
 
@@ -389,37 +447,43 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             }
             const int row_here = s.out_idx;
             // only the volume moment is on the critical path; on output steps
-            // the per-thread moments wait in shared memory and are reduced in
-            // the overlap window, the row completed after the solve
+            // the per-thread moments wait in shared memory and are reduced
+            // while the barrier is pending, the row completed after the solve
             if (sc.moms) {
 #pragma unroll
                 for (int k = 0; k < NM; ++k) red[threadIdx.x * (NM + 1) + k] = m[k];
             }
             const long long qb = block_sum_fixed_t0(m[VIDX], inv_u, reinterpret_cast<long long*>(red2));
-            if (threadIdx.x == 0) {
-                double total = 0.0;
-                const int p = (int)(gen & 1u);
-                unsigned long long base = p ? acc_base1 : acc_base0;
-                const bool ok = barrier_sum(acc + p * kAccStride, base, qb, u, (unsigned int)G, wait_limit, total);
-                if (p) acc_base1 = base;
-                else acc_base0 = base;
-                msum[VIDX] = total;
-                fail = !ok;
-            }
-            gen += 1u;
-            __syncthreads();
-            if (fail) break;
             if (warp == 0) {
-                if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
-                else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
-                // the next stage's coefficients, once per block (the divisions of
-                // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
-                if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
+                if (threadIdx.x == 0) {
+                    double total = 0.0;
+                    const int p = (int)(gen & 1u);
+                    unsigned long long base = p ? acc_base1 : acc_base0;
+                    const bool ok = barrier_sum(acc + p * kAccStride, base, qb, u, (unsigned int)G, wait_limit, total);
+                    if (p) acc_base1 = base;
+                    else acc_base0 = base;
+                    msum[VIDX] = total;
+                    fail = !ok;
+                }
+                __syncwarp();
+                HaloGo::arrive();   // the other blocks' outputs are visible: the face warps may load the halo
+                if (!fail) {
+                    if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
+                    else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
+                    // the next stage's coefficients, once per block (the divisions of
+                    // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
+                    if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
+                }
             } else if (warp <= kFaceWarps) {
-                // faces of the next stage's input for this block's first tile
-                // (one tile per block: its cells are in shared memory, only the halo is loaded)
-                fused_faces<NDIM, ONE_TILE>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x - 32,
-                                            32 * kFaceWarps, GroupSync());
+                // one tile per block: the next stage's input is already in shared
+                // memory except the halo, and its faces that do not read the halo
+                // need nothing from the other blocks - computed while the barrier
+                // is pending; then the halo and the faces that read it
+                if (ONE_TILE) fused_faces_interior<NDIM>(ti, sm, threadIdx.x - 32, 32 * kFaceWarps);
+                HaloGo::wait();
+                if (!fail)
+                    fused_faces<NDIM, ONE_TILE>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x - 32,
+                                                32 * kFaceWarps, GroupSync());
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one
                 constexpr int NT2 = kFNT - 32 * (kFaceWarps + 1);
@@ -447,6 +511,9 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                     rowpart[((size_t)row_here * G + blockIdx.x) * NM + t0] = a[0];
                 }
             }
+            gen += 1u;
+            __syncthreads();
+            if (fail) break;
             __syncthreads();
             if (s.done) break;
         }
