@@ -114,6 +114,10 @@ class Grid:
     def set_path(self, path: str):
         _lib.check(self.lib.pbe_set_path(self.h, _PATHS[path]))
 
+    def set_window(self, mode: int):
+        """Plain-path 2-D stage kernel: -1 auto (default), 0 tile kernel, 1 register-window kernel."""
+        _lib.check(self.lib.pbe_set_window(self.h, int(mode)))
+
     def set_wait_limit(self, seconds: float):
         _lib.check(self.lib.pbe_set_wait_limit(self.h, float(seconds)))
 

@@ -59,6 +59,7 @@ SIGNATURES = {
     "pbe_moments": [_P, _P, _I],
     "pbe_set_max_steps": [_P, _I64],
     "pbe_set_wait_limit": [_P, _D],
+    "pbe_set_window": [_P, _I],
     "pbe_set_timing": [_P, _I],
     "pbe_kernel_time": [_P, _PD],
     "pbe_vjp": [_P, _PD, _I, _P, _I, _I, _PD, _P, _PD, _P, _I, _PD],

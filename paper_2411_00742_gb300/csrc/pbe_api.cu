@@ -218,6 +218,13 @@ pbe_status pbe_create_grid(pbe_grid** out, int ndim, const int64_t* ncells, cons
     g->max_steps = 1000000;
     g->wait_cycles = -1;
     g->kernel_ms = -1.0;
+    if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess || g->sms < 1)
+        g->sms = 1;
+    g->window_mode = -1;
+    if (ndim == 2 && pbe::window_setup() != cudaSuccess) {
+        delete g;
+        return fail(PBE_ECUDA, "cannot configure the 2-D stage kernels");
+    }
     g->max_blocks = pbe::plain_max_blocks(g->geo);
     if (g->max_blocks < 1024) g->max_blocks = 1024;
     bool ok = cudaMalloc(&g->d_n, sizeof(double) * nc) == cudaSuccess &&
@@ -269,6 +276,18 @@ pbe_status pbe_set_path(pbe_grid* g, int path)
     if (!g) return fail(PBE_EINVAL, "null grid");
     if (path != PBE_PATH_PLAIN && path != PBE_PATH_FUSED) return fail(PBE_EINVAL, "unknown path %d", path);
     g->path = path;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_window(pbe_grid* g, int mode)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (mode < -1 || mode > 1) return fail(PBE_EINVAL, "window mode must be -1, 0 or 1 (got %d)", mode);
+    if (mode != g->window_mode && g->plain_exec) {   // the graph holds the previous kernels
+        cudaGraphExecDestroy(g->plain_exec);
+        g->plain_exec = nullptr;
+    }
+    g->window_mode = mode;
     return PBE_OK;
 }
 

@@ -118,8 +118,8 @@ struct MomSync {    // named barrier over warps kFaceWarps+1..7
 // is done (non-blocking), the face warps wait on it before they load the halo.
 // The unaligned forms: warp 0 reaches it after thread 0's wait.
 struct HaloGo {
-    static __device__ __forceinline__ void arrive() { asm volatile("barrier.arrive 3, %0;" ::"r"(32 * (kFaceWarps + 1)) : "memory"); }
-    static __device__ __forceinline__ void wait() { asm volatile("barrier.sync 3, %0;" ::"r"(32 * (kFaceWarps + 1)) : "memory"); }
+    static __device__ __forceinline__ void arrive() { asm volatile("bar.arrive 3, %0;" ::"r"(32 * (kFaceWarps + 1)) : "memory"); }
+    static __device__ __forceinline__ void wait() { asm volatile("bar.sync 3, %0;" ::"r"(32 * (kFaceWarps + 1)) : "memory"); }
 };
 struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }

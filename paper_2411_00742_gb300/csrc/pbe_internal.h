@@ -22,6 +22,8 @@ struct pbe_grid {
     double* d_mom;      // moments read-out (kMaxMom doubles)
     unsigned int* d_bar; // fused path: 512 bytes of barrier accumulators (two 64-bit words, 128 B apart)
     int max_blocks;
+    int sms;            // multiprocessors of the grid's device
+    int window_mode;    // 2-D plain stages in the register-window kernel: -1 auto, 0 never, 1 always
     double* d_tout;     // output times (capacity tout_cap)
     double* d_rows;     // output rows (capacity tout_cap rows of 12)
     double* d_rowpart;  // fused path: per-row, per-block moment partials (tout_cap x max_blocks/2 x 10)
@@ -62,6 +64,13 @@ cudaError_t launch_prologue(pbe_grid* g, int n_out, long long max_steps, double*
 cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHandle h);
 cudaError_t launch_plain_stage(pbe_grid* g, int stage);
 cudaError_t launch_set_scalars(pbe_grid* g, double C, double t);
+
+// Plain path, large 2-D grids (pbe_window.cu): one SSP-RK2 stage per kernel
+// in the register-window layout; by default used when it gives at least one
+// block per SM (pbe_set_window)
+bool use_window2d(const pbe_grid* g);
+cudaError_t window_setup();   // shared-memory limit of the kernels, on the current device
+cudaError_t launch_window_stage2d(pbe_grid* g, int stage, bool use_cond, cudaGraphConditionalHandle h);
 // unscaled Gaussian density at the cell centres into d_n; total_dev[0] = its sum,
 // total_dev[1] = its sum weighted by x^3 (1-D) or x1 x2^2 (2-D)
 cudaError_t launch_seed_pdf(pbe_grid* g, const double* mean, const double* sd, double corr, double* total_dev);

@@ -49,16 +49,6 @@ static inline int pdiv(long long a, long long b) { return (int)((a + b - 1) / b)
 
 int paper_blocks2d(const Geom& g) { return pdiv(g.N2, kPOut) * pdiv(g.N1, kPTI); }
 
-// all ten moments of one cell value into m (order of the output rows)
-__device__ __forceinline__ void add_moments(double (&m)[10], double val, double x1, double x2, double area)
-{
-    const double w = val * area;
-    const double x1w = x1 * w, x2w = x2 * w;
-    m[0] += w; m[1] += x1w; m[2] += x2w;
-    m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
-    m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
-}
-
 __global__ void __launch_bounds__(kPNT) k_lw_step2d(double* na, double* nb, Scal* S, Kin K, Geom g, double* part,
                                                      const double* t_out, double* rows, int use_cond,
                                                      cudaGraphConditionalHandle hcond)

@@ -366,6 +366,8 @@ cudaError_t launch_plain_stage(pbe_grid* g, int stage)
         else
             k_stage1d<2><<<nb, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
                                                     g->d_tout, g->d_rows, 0, 0);
+    } else if (use_window2d(g)) {
+        return launch_window_stage2d(g, stage, false, 0);
     } else {
         dim3 grid(cdiv(geo.N2, kTJ), cdiv(geo.N1, kTI));
         if (stage == 1)
@@ -400,6 +402,10 @@ cudaError_t launch_plain_step(pbe_grid* g, bool use_cond, cudaGraphConditionalHa
                                                 g->d_tout, g->d_rows, uc, h);
         k_stage1d<2><<<nb, kNT, 0, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
                                                 g->d_tout, g->d_rows, uc, h);
+    } else if (use_window2d(g)) {
+        cudaError_t e = launch_window_stage2d(g, 1, use_cond, h);
+        if (e == cudaSuccess) e = launch_window_stage2d(g, 2, use_cond, h);
+        return e;
     } else {
         dim3 grid(cdiv(geo.N2, kTJ), cdiv(geo.N1, kTI));
         k_stage2d<1><<<grid, kNT, 0, g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part,

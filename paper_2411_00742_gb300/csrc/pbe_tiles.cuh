@@ -59,6 +59,17 @@ __device__ __forceinline__ double ld_in(const double* p)
     return CG ? __ldcg(p) : *p;
 }
 
+// The 2-D moments of one cell value into m (order of the output rows) except
+// the volume moment m[8], which the row kernels accumulate per column.
+__device__ __forceinline__ void add_moments(double (&m)[10], double val, double x1, double x2, double area)
+{
+    const double w = val * area;
+    const double x1w = x1 * w, x2w = x2 * w;
+    m[0] += w; m[1] += x1w; m[2] += x2w;
+    m[3] += x1 * x1w; m[4] += x1 * x2w; m[5] += x2 * x2w;
+    m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
+}
+
 // Stage coefficients of one stage, uniform over the grid.
 struct StageCoef {
     double c1, c2;   // G_d dt / dL_d

@@ -254,3 +254,52 @@ def test_kernel_timing(path):
     g.close()
     want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out)
     assert_rows_close(rows, want["rows"])
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 200), (37, 53), (64, 64), (100, 251), (129, 31)])
+def test_2d_window_kernel_ragged_sizes(shape):
+    """The register-window stage kernel (forced on small ragged grids: one block,
+    columns and rows not multiples of its 125 x 32 block)."""
+    inst = pi.config_2d(*shape)
+    want = oracle.solve_instance(inst)
+    import paper_2411_00742_gb300 as P
+    g = P.Grid.from_problem(inst.problem)
+    g.set_window(1)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, steps = g.solve(inst.t_out)
+    n, C, t = g.get_state()
+    g.close()
+    assert steps == want["steps"]
+    assert_rows_close(rows, want["rows"])
+    assert_n_close(n, want["n"])
+
+
+def test_2d_window_kernel_chosen_on_large_grids():
+    """A grid with more window blocks than SMs takes the window kernel by
+    default (the same rows as forcing it); the tile kernel agrees to rounding.
+    Three output times of the 1000 x 777 workload keep the oracle short."""
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(1000, 777)
+    t_out = np.array(inst.t_out[:3])
+    want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, t_out)
+    out = {}
+    for mode in (-1, 1, 0):
+        g = P.Grid.from_problem(inst.problem)
+        g.set_window(mode)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        rows, _ = g.solve(t_out)
+        n, _, _ = g.get_state()
+        g.close()
+        assert_rows_close(rows, want["rows"])
+        assert_n_close(n, want["n"])
+        out[mode] = rows
+    assert np.array_equal(out[-1], out[1])
+
+
+def test_window_mode_rejects_bad_values():
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(16)
+    g = P.Grid.from_problem(inst.problem)
+    with pytest.raises(P.PbeError):
+        g.set_window(2)
+    g.close()
