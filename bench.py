@@ -44,6 +44,9 @@ FLOPS_PER_CELL_STEP_2D = 39
 FLOPS_PER_CELL_STEP_PAPER = 20
 BYTES_PER_CELL_STEP_PAPER = 16
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64 (2 FMA/clk/SM x 152 SMs x ~2.07 GHz)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_fused launch on the
+# 256 x 256 solve, from one ncu capture of the current kernel (the state stays in L2)
+FUSED_DRAM_BYTES_PER_LAUNCH = 613632
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -462,7 +465,8 @@ def run_gpu(args):
                   "plain": {"value": plain_value, "ms_per_solve": 1e3 * t_plain / args.steps,
                             "max_rel_err_vs_oracle": err_plain}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
+                     "traffic": FUSED_DRAM_BYTES_PER_LAUNCH if inst.problem.ncells == (256, 256) else None,
                      "kernel": "k_fused (persistent cooperative kernel, one launch per solve)",
                      "launch_ms": 1e3 * k_fused,
                      "note": f"FP64 algorithmic {FLOPS_PER_CELL_STEP_2D} flop/cell-step (division = 1) x "

@@ -1,0 +1,58 @@
+"""Run a few solves of one seeded workload on one execution path: the small,
+self-contained program to put under a profiler (ncu) or a timer.
+
+    python profile_case.py fused 256
+    python profile_case.py plain 4096 --outputs 2 --window 1
+    python profile_case.py paper 6000 --outputs 2
+
+Workloads: ``fused``/``plain`` run the 2-D size-and-shape problem on an N x N
+(or N1 x N2) grid (``pbe_inputs.config_2d``); ``paper`` runs the paper's base
+case at N x N/2 bins (``pbe_inputs.paper_base_case``).  ``--outputs K`` keeps
+the first K output times (a shorter solve); every solve starts from the same
+seeded state.  Prints one line per solve: path, grid, steps, wall time.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("path", choices=["fused", "plain", "paper"])
+    ap.add_argument("N1", type=int)
+    ap.add_argument("N2", type=int, nargs="?")
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--outputs", type=int, default=0, help="keep the first K output times (0: all)")
+    ap.add_argument("--window", type=int, default=-1, choices=[-1, 0, 1],
+                    help="plain-path 2-D stage kernel: -1 auto, 0 tile, 1 register window")
+    args = ap.parse_args(argv)
+
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import torch
+
+    import pbe_inputs as pi
+    import paper_2411_00742_gb300 as P
+
+    if args.path == "paper":
+        inst = pi.paper_base_case(args.N1)
+        path = "plain"
+    else:
+        inst = pi.config_2d(args.N1, args.N2)
+        path = args.path
+    t_out = inst.t_out[: args.outputs] if args.outputs > 0 else inst.t_out
+    g = P.Grid.from_problem(inst.problem, path=path)
+    g.set_window(args.window)
+    n0 = torch.as_tensor(inst.n0).cuda()
+    for _ in range(args.repeat):
+        g.set_state(n0, inst.C0, 0.0)
+        t0 = time.perf_counter()
+        _, steps = g.solve(t_out)
+        print(f"{args.path} {inst.problem.ncells} steps {steps} {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+    g.close()
+
+
+if __name__ == "__main__":
+    main()
