@@ -569,19 +569,18 @@ static int fused_tiles(const Geom& g, int max_blocks, int* tiles_x, int* ti)
 
 bool fused_supported(const pbe_grid* g) { return g->d_bar != nullptr; }
 
-cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
+// Blocks, tiles and kernel of the fused launch of a grid (depends only on the
+// geometry and the device: computed once per grid).
+static cudaError_t fused_config(pbe_grid* g)
 {
-    int sms = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    if (e != cudaSuccess) return e;
+    if (g->fused_fn) return cudaSuccess;
+    const int sms = g->sms;
     int tiles_x, ti;
     const int ntiles = fused_tiles(g->geo, std::min(sms, g->max_blocks / 2), &tiles_x, &ti);
-    const bool one = g->geo.ndim == 1 ? true : true;
     const void* fn_multi = g->geo.ndim == 1 ? (const void*)k_fused<1, false> : (const void*)k_fused<2, false>;
     const void* fn_one = g->geo.ndim == 1 ? (const void*)k_fused<1, true> : (const void*)k_fused<2, true>;
-    (void)one;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn_one, kFNT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn_one, kFNT, 0);
     if (e != cudaSuccess) return e;
     int G = ntiles;
     if (G > occ * sms) G = occ * sms;
@@ -595,6 +594,21 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
         if (e != cudaSuccess) return e;
         if (G > occ2 * sms) G = occ2 * sms;
     }
+    g->fused_blocks = G;
+    g->fused_ntiles = ntiles;
+    g->fused_tiles_x = tiles_x;
+    g->fused_ti = ti;
+    g->fused_fn = fn;
+    return cudaSuccess;
+}
+
+cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
+{
+    cudaError_t e = fused_config(g);
+    if (e != cudaSuccess) return e;
+    const int G = g->fused_blocks;
+    int ntiles = g->fused_ntiles, tiles_x = g->fused_tiles_x, ti = g->fused_ti;
+    const void* fn = g->fused_fn;
     e = cudaMemsetAsync(g->d_bar, 0, 2 * kAccStride * sizeof(unsigned long long), g->stream);
     if (e != cudaSuccess) return e;
     long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);

@@ -24,6 +24,9 @@ struct pbe_grid {
     int max_blocks;
     int sms;            // multiprocessors of the grid's device
     int window_mode;    // 2-D plain stages in the register-window kernel: -1 auto, 0 never, 1 always
+    // fused path launch configuration, fixed per grid (computed at the first fused solve)
+    const void* fused_fn;
+    int fused_blocks, fused_ntiles, fused_tiles_x, fused_ti;
     double* d_tout;     // output times (capacity tout_cap)
     double* d_rows;     // output rows (capacity tout_cap rows of 12)
     double* d_rowpart;  // fused path: per-row, per-block moment partials (tout_cap x max_blocks/2 x 10)
