@@ -32,7 +32,8 @@ namespace pbe {
 
 constexpr int kFNT = 256;     // threads per block (the reductions assume 256)
 constexpr int kFT1 = 1024;    // 1-D tile
-constexpr int kFTI = 16;      // largest 2-D tile height (the launch picks ti <= kFTI)
+constexpr int kFTI = 16;      // 2-D tile height of the multi-tile launch (and the largest of the small one-tile kernel)
+constexpr int kFTIBig = 64;   // largest 2-D tile height of the one-tile kernel for larger grids (dynamic shared memory)
 constexpr int kFTJ = 32;      // 2-D tile columns
 constexpr long long kBarrierCycles = 2000000000LL;  // default wait limit: ~1 s at 2 GHz
 
@@ -125,28 +126,37 @@ struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
-template <int NDIM>
+template <int NDIM, int TI>
 struct FusedSmem;
-template <>
-struct FusedSmem<1> {
+template <int TI>
+struct FusedSmem<1, TI> {
     double tile[kFT1 + 3];
     double h[kFT1 + 1];
 };
-template <>
-struct FusedSmem<2> {
-    Tile2DSmem<kFTI, kFTJ> t;
+template <int TI>
+struct FusedSmem<2, TI> {
+    Tile2DSmem<TI, kFTJ> t;
 };
 
-template <int NDIM>
-struct TileShape;
-template <>
-struct TileShape<1> {
-    static constexpr int CELLS = kFT1;
+// cells of one tile (2-D: up to TI rows of 32)
+template <int NDIM, int TI>
+struct TileShape {
+    static constexpr int CELLS = NDIM == 1 ? kFT1 : TI * kFTJ;
 };
-template <>
-struct TileShape<2> {
-    static constexpr int CELLS = kFTI * kFTJ;
-};
+
+// the tile's shared memory: static for the kFTI-row tiles, dynamic (set at
+// launch) for the taller ones
+template <int NDIM, int TI>
+__device__ __forceinline__ FusedSmem<NDIM, TI>& fused_smem()
+{
+    if constexpr (TI > kFTI) {
+        extern __shared__ __align__(16) double fused_dyn[];
+        return *reinterpret_cast<FusedSmem<NDIM, TI>*>(fused_dyn);
+    } else {
+        __shared__ FusedSmem<NDIM, TI> sm_static;
+        return sm_static;
+    }
+}
 
 template <int NDIM>
 __device__ __forceinline__ void tile_origin(int t, int tiles_x, int ti, int& i0, int& j0)
@@ -186,9 +196,9 @@ __device__ __forceinline__ void moment_weights(int i, int j, const Geom& g, doub
 // only them (faces2d_interior) are done; load the halo and compute the faces
 // that read it.  The faces read the halo rows at the tile's columns and the
 // halo columns at its rows, never the corners.
-template <bool HALO_ONLY, class Sync>
+template <bool HALO_ONLY, int TI, class Sync>
 __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, int ti, const Geom& g,
-                                             Tile2DSmem<kFTI, kFTJ>& s, int tid, int nthr, Sync sync)
+                                             Tile2DSmem<TI, kFTJ>& s, int tid, int nthr, Sync sync)
 {
     constexpr int W = kFTJ + 3;
     const int N1 = g.N1, N2 = g.N2;
@@ -247,7 +257,8 @@ __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, i
 // columns 2 .. ti+1 / 2 .. 33 of the staged array): L1 faces 2 .. ti-1 of
 // every column and L2 faces 2 .. 31 of every row.  No memory traffic beyond
 // shared memory, so they can run while the device-wide barrier is pending.
-__device__ __forceinline__ void faces2d_interior(int ti, Tile2DSmem<kFTI, kFTJ>& s, int tid, int nthr)
+template <int TI>
+__device__ __forceinline__ void faces2d_interior(int ti, Tile2DSmem<TI, kFTJ>& s, int tid, int nthr)
 {
     constexpr int W = kFTJ + 3;
     for (int k = tid; k < (ti - 2) * kFTJ; k += nthr) {
@@ -263,9 +274,9 @@ __device__ __forceinline__ void faces2d_interior(int ti, Tile2DSmem<kFTI, kFTJ>&
     }
 }
 
-template <int NDIM, bool HALO_ONLY = false, class Sync>
+template <int NDIM, bool HALO_ONLY, int TI, class Sync>
 __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x, int ti, const Geom& g,
-                                            FusedSmem<NDIM>& sm, int tid, int nthr, Sync sync)
+                                            FusedSmem<NDIM, TI>& sm, int tid, int nthr, Sync sync)
 {
     int i0, j0;
     tile_origin<NDIM>(t, tiles_x, ti, i0, j0);
@@ -285,13 +296,13 @@ __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x
             faces1d<true, true, kFT1>(in, i0, g, sm.tile, sm.h, tid, nthr, sync);
         }
     } else {
-        faces2d_rows<HALO_ONLY>(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
+        faces2d_rows<HALO_ONLY, TI>(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
     }
 }
 
 // faces of the block's tile that read only its own cells (one tile per block)
-template <int NDIM>
-__device__ __forceinline__ void fused_faces_interior(int ti, FusedSmem<NDIM>& sm, int tid, int nthr)
+template <int NDIM, int TI>
+__device__ __forceinline__ void fused_faces_interior(int ti, FusedSmem<NDIM, TI>& sm, int tid, int nthr)
 {
     if constexpr (NDIM == 1) {
         for (int f = 2 + tid; f < kFT1; f += nthr) sm.h[f] = face_value<true>(sm.tile[f], sm.tile[f + 1], sm.tile[f + 2]);
@@ -306,9 +317,9 @@ __device__ __forceinline__ void fused_faces_interior(int ti, FusedSmem<NDIM>& sm
 // also replaces the cell's own entry of the shared tile, the next stage's
 // input - the faces of this stage are already computed and each thread reads
 // only its own cells' entries here.
-template <int STAGE, int NDIM, bool ONE_TILE>
+template <int STAGE, int NDIM, bool ONE_TILE, int TI>
 __device__ __forceinline__ double cell_update(const double* old, double* out, int k, int i0, int j0, int ti, const Geom& g,
-                                              const StageCoef& sc, FusedSmem<NDIM>& sm, double& keep, bool& valid,
+                                              const StageCoef& sc, FusedSmem<NDIM, TI>& sm, double& keep, bool& valid,
                                               int& i, int& j)
 {
     int r, c;
@@ -341,21 +352,22 @@ __device__ __forceinline__ double cell_update(const double* old, double* out, in
     return v;
 }
 
-template <int NDIM, bool ONE_TILE>
+template <int NDIM, bool ONE_TILE, int TI>
 __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
                                                    const double* t_out, double* rows, unsigned int* bar, int ntiles,
                                                    int tiles_x, int ti, long long wait_limit, double* rowpart)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
-    constexpr int CPT = TileShape<NDIM>::CELLS / kFNT;   // cells per thread per tile
+    constexpr int CPT = TileShape<NDIM, TI>::CELLS / kFNT;   // cells per thread per tile
+    static_assert(TI == kFTI || (NDIM == 2 && ONE_TILE), "tall tiles only for the 2-D one-tile kernel");
     __shared__ Scal s;
     __shared__ StageCoef scs;   // coefficients of the coming stage (written by thread 0)
     __shared__ double red[kFNT * (NM + 1)];
     __shared__ double red2[256];
     __shared__ double msum[NM];
     __shared__ int fail;
-    __shared__ FusedSmem<NDIM> sm;
+    FusedSmem<NDIM, TI>& sm = fused_smem<NDIM, TI>();
     if (threadIdx.x == 0) {
         s = *S;
         s.row_first = s.out_idx;   // rows before this index came from the prologue
@@ -385,8 +397,15 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     }
     unsigned int gen = 0;
 
-    // moment weights of this thread's cells (one tile per block: fixed for the whole solve)
-    double wgt[ONE_TILE ? CPT : 1][ONE_TILE ? NM : 1];
+    // moment weights of this thread's cells (one tile per block: fixed for the
+    // whole solve).  Small tiles: all ten weights of each cell in registers;
+    // tall tiles (eight cells a thread, all in one column since tiles are 32
+    // wide): x1 and the volume weight of each cell, x2^q dA of the column.
+    constexpr bool WREG = ONE_TILE && TI <= kFTI;
+    constexpr bool WCOL = ONE_TILE && !WREG;
+    double wgt[WREG ? CPT : 1][WREG ? NM : 1];
+    double x1c[WCOL ? CPT : 1], w8c[WCOL ? CPT : 1];
+    double wx2[4] = {0.0, 0.0, 0.0, 0.0};
     double keep[ONE_TILE ? CPT : 1];   // n at the start of the step for this thread's cells
     keep[0] = 0.0;
     if constexpr (ONE_TILE) {
@@ -396,13 +415,20 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
         for (int q = 0; q < CPT; ++q) {
             int i, j, r, c;
             cell_of<NDIM>(threadIdx.x + q * kFNT, i0, j0, i, j, r, c);
-            moment_weights<NDIM>(i, j, g, wgt[q]);
+            if constexpr (WCOL) {
+                const double x2 = (j + 0.5) * g.d2, a = g.d1 * g.d2;
+                wx2[0] = a; wx2[1] = a * x2; wx2[2] = wx2[1] * x2; wx2[3] = wx2[2] * x2;
+                x1c[q] = (i + 0.5) * g.d1;
+                w8c[q] = x1c[q] * wx2[2];
+            } else {
+                moment_weights<NDIM>(i, j, g, wgt[q]);
+            }
             const bool valid = (NDIM == 1) ? (i < g.N1) : (r < ti && i < g.N1 && j < g.N2);
             keep[q] = valid && (int)blockIdx.x < ntiles ? n[(size_t)i * g.N2 + j] : 0.0;
         }
     }
 
-    fused_faces<NDIM>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
+    fused_faces<NDIM, false, TI>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
     __syncthreads();
     for (;;) {
 #pragma unroll 1
@@ -415,7 +441,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             for (int k = 0; k < NM; ++k) m[k] = 0.0;
             for (int t = blockIdx.x; t < ntiles; t += G) {
                 if (t != (int)blockIdx.x) {
-                    fused_faces<NDIM>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
+                    fused_faces<NDIM, false, TI>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
                     __syncthreads();
                 }
                 int i0, j0;
@@ -426,11 +452,23 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                     int i, j;
                     double& kq = keep[ONE_TILE ? q : 0];
                     const double v = stage == 1
-                        ? cell_update<1, NDIM, ONE_TILE>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j)
-                        : cell_update<2, NDIM, ONE_TILE>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j);
+                        ? cell_update<1, NDIM, ONE_TILE, TI>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j)
+                        : cell_update<2, NDIM, ONE_TILE, TI>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j);
                     if (!valid) continue;
+                    if constexpr (WCOL) {
+                        if (sc.moms) {
+                            const double x1 = x1c[q], v1 = x1 * v, v2 = x1 * v1, v3 = x1 * v2;
+                            m[0] = fma(wx2[0], v, m[0]);  m[1] = fma(wx2[0], v1, m[1]); m[2] = fma(wx2[1], v, m[2]);
+                            m[3] = fma(wx2[0], v2, m[3]); m[4] = fma(wx2[1], v1, m[4]); m[5] = fma(wx2[2], v, m[5]);
+                            m[6] = fma(wx2[0], v3, m[6]); m[7] = fma(wx2[1], v2, m[7]); m[8] = fma(wx2[2], v1, m[8]);
+                            m[9] = fma(wx2[3], v, m[9]);
+                        } else {
+                            m[VIDX] = fma(w8c[q], v, m[VIDX]);
+                        }
+                        continue;
+                    }
                     double wl[NM];
-                    if constexpr (ONE_TILE) {
+                    if constexpr (WREG) {
 #pragma unroll
                         for (int k = 0; k < NM; ++k) wl[k] = wgt[q][k];
                     } else {
@@ -479,11 +517,11 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 // memory except the halo, and its faces that do not read the halo
                 // need nothing from the other blocks - computed while the barrier
                 // is pending; then the halo and the faces that read it
-                if (ONE_TILE) fused_faces_interior<NDIM>(ti, sm, threadIdx.x - 32, 32 * kFaceWarps);
+                if (ONE_TILE) fused_faces_interior<NDIM, TI>(ti, sm, threadIdx.x - 32, 32 * kFaceWarps);
                 HaloGo::wait();
                 if (!fail)
-                    fused_faces<NDIM, ONE_TILE>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x - 32,
-                                                32 * kFaceWarps, GroupSync());
+                    fused_faces<NDIM, ONE_TILE, TI>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm,
+                                                    threadIdx.x - 32, 32 * kFaceWarps, GroupSync());
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one
                 constexpr int NT2 = kFNT - 32 * (kFaceWarps + 1);
@@ -547,10 +585,12 @@ __global__ void k_fused_rows(const double* rowpart, int G, const Scal* S, double
 }
 
 // Tiles of the fused launch: 1-D 1024 cells; 2-D ti x 32 with the smallest
-// ti (4 <= ti <= 16) that gives every co-resident block at most one tile
-// (all SMs busy, fewer cells each), else 16 x 32 tiles looped over.
-static int fused_tiles(const Geom& g, int max_blocks, int* tiles_x, int* ti)
+// ti (>= 4) that gives every co-resident block at most one tile (all SMs
+// busy, fewer cells each) - ti <= kFTI in the small-tile kernel, up to
+// kFTIBig in the tall-tile one (*tall) - else kFTI x 32 tiles looped over.
+static int fused_tiles(const Geom& g, int max_blocks, int* tiles_x, int* ti, bool* tall)
 {
+    *tall = false;
     if (g.ndim == 1) {
         *tiles_x = 1;
         *ti = 1;
@@ -562,7 +602,12 @@ static int fused_tiles(const Geom& g, int max_blocks, int* tiles_x, int* ti)
         const int rows_of_tiles = max_blocks / *tiles_x;
         int t = (g.N1 + rows_of_tiles - 1) / rows_of_tiles;
         if (t < 4) t = 4;
-        if (t <= kFTI) *ti = t;
+        if (t <= kFTI) {
+            *ti = t;
+        } else if (t <= kFTIBig) {
+            *ti = t;
+            *tall = true;
+        }
     }
     return *tiles_x * ((g.N1 + *ti - 1) / *ti);
 }
@@ -576,28 +621,45 @@ static cudaError_t fused_config(pbe_grid* g)
     if (g->fused_fn) return cudaSuccess;
     const int sms = g->sms;
     int tiles_x, ti;
-    const int ntiles = fused_tiles(g->geo, std::min(sms, g->max_blocks / 2), &tiles_x, &ti);
-    const void* fn_multi = g->geo.ndim == 1 ? (const void*)k_fused<1, false> : (const void*)k_fused<2, false>;
-    const void* fn_one = g->geo.ndim == 1 ? (const void*)k_fused<1, true> : (const void*)k_fused<2, true>;
+    bool tall;
+    int ntiles = fused_tiles(g->geo, std::min(sms, g->max_blocks / 2), &tiles_x, &ti, &tall);
+    const void* fn_multi = g->geo.ndim == 1 ? (const void*)k_fused<1, false, kFTI> : (const void*)k_fused<2, false, kFTI>;
+    const void* fn_one = g->geo.ndim == 1 ? (const void*)k_fused<1, true, kFTI>
+                                          : (tall ? (const void*)k_fused<2, true, kFTIBig> : (const void*)k_fused<2, true, kFTI>);
+    const size_t dyn = tall ? sizeof(FusedSmem<2, kFTIBig>) : 0;
+    cudaError_t e;
+    if (tall && (e = cudaFuncSetAttribute(fn_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
+        return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn_one, kFNT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn_one, kFNT, dyn);
     if (e != cudaSuccess) return e;
     int G = ntiles;
     if (G > occ * sms) G = occ * sms;
     if (2 * G > g->max_blocks) G = g->max_blocks / 2;
     if (G < 1) G = 1;
     if (G > 1000) G = 1000;   // the arrival count of barrier_sum has 10 bits
-    const void* fn = (G >= ntiles) ? fn_one : fn_multi;
-    if (fn == fn_multi) {
+    const void* fn = fn_one;
+    size_t fn_dyn = dyn;
+    if (G < ntiles) {   // more tiles than co-resident blocks: kFTI x 32 tiles looped over
+        fn = fn_multi;
+        fn_dyn = 0;
+        if (g->geo.ndim == 2) {
+            ti = kFTI;
+            ntiles = tiles_x * ((g->geo.N1 + kFTI - 1) / kFTI);
+        }
         int occ2 = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fn_multi, kFNT, 0);
         if (e != cudaSuccess) return e;
-        if (G > occ2 * sms) G = occ2 * sms;
+        G = std::min(ntiles, occ2 * sms);
+        if (2 * G > g->max_blocks) G = g->max_blocks / 2;
+        if (G < 1) G = 1;
+        if (G > 1000) G = 1000;
     }
     g->fused_blocks = G;
     g->fused_ntiles = ntiles;
     g->fused_tiles_x = tiles_x;
     g->fused_ti = ti;
+    g->fused_dyn = fn_dyn;
     g->fused_fn = fn;
     return cudaSuccess;
 }
@@ -615,7 +677,7 @@ cudaError_t launch_fused_solve(pbe_grid* g, int n_out)
     void* args[] = {&g->d_n, &g->d_n1, &g->d_S, &g->kin, &g->geo, &g->d_part, &g->d_tout, &g->d_rows,
                     &g->d_bar, (void*)&ntiles, &tiles_x, &ti, &wait_limit, &g->d_rowpart};
     if (g->timing && (e = cudaEventRecord(g->ev_k0, g->stream)) != cudaSuccess) return e;
-    e = cudaLaunchCooperativeKernel(fn, G, kFNT, args, 0, g->stream);
+    e = cudaLaunchCooperativeKernel(fn, G, kFNT, args, g->fused_dyn, g->stream);
     if (e != cudaSuccess) return e;
     if (g->timing && (e = cudaEventRecord(g->ev_k1, g->stream)) != cudaSuccess) return e;
     const int nrows = n_out > 0 ? n_out : 1;

@@ -27,6 +27,7 @@ struct pbe_grid {
     // fused path launch configuration, fixed per grid (computed at the first fused solve)
     const void* fused_fn;
     int fused_blocks, fused_ntiles, fused_tiles_x, fused_ti;
+    size_t fused_dyn;   // dynamic shared memory of that kernel
     double* d_tout;     // output times (capacity tout_cap)
     double* d_rows;     // output rows (capacity tout_cap rows of 12)
     double* d_rowpart;  // fused path: per-row, per-block moment partials (tout_cap x max_blocks/2 x 10)

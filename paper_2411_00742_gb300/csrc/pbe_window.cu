@@ -9,8 +9,9 @@
 // rows and writing the 125 columns j0 .. j0+124:
 //   1. L1 faces: every thread walks down its column (16 rows) with a register
 //      window of the input (2 rows above, 1 below), each face value once;
-//      the input and the L1 flux difference c1 (h_up - h_dn) of every cell go
-//      to shared memory;
+//      the input and the partial update w n + w c1 (h_up - h_dn) of every cell
+//      go to shared memory (w = 1 in stage 1, 1/2 in stage 2, where the RK
+//      average then adds n^k / 2);
 //   2. L2 faces along the rows (8 warps x 4 rows, four columns per lane): both
 //      stencil differences of a face come from the lane or the lane below,
 //      face values pass between lanes by shuffles; then the update, the
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
 {
     extern __shared__ __align__(16) double wsm[];
     double (*ins)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm);              // stage input
-    double (*f1s)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm + kWTI * kWX); // c1 (h_up - h_dn)
+    double (*f1s)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm + kWTI * kWX); // w (in + c1 (h_up - h_dn))
     __shared__ double x1s[kWTI];
     __shared__ double sh[kWW * 10];
     __shared__ int flag;
@@ -63,6 +64,9 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
     }
     StageCoef sc = stage_coef_fast<STAGE>(*S, g);
     if (K.kind == PBE_KINETICS_MLP) sc.moms = true;   // the closure reads mu0 at every stage
+    // stage 2 is n^k/2 + (n1 + dt L(n1))/2: the factor 1/2 goes into the coefficients
+    constexpr double kW = STAGE == 2 ? 0.5 : 1.0;
+    const double wc1 = kW * sc.c1, wc2 = kW * sc.c2, wsrc = kW * sc.src;
     const int N1 = g.N1, N2 = g.N2;
     const int i0 = blockIdx.y * kWTI, j0 = blockIdx.x * kWOut;
     if (threadIdx.x < kWTI) x1s[threadIdx.x] = (i0 + threadIdx.x + 0.5) * g.d1;
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
             const double d = v[q + 3] - v[q + 2];
             const double hdn = fma(dprev, psi_quot_fast(dprev, d), v[q + 2]);   // face between rows i and i+1
             ins[ra + q][tx] = v[q + 2];
-            f1s[ra + q][tx] = sc.c1 * (hup - hdn);
+            f1s[ra + q][tx] = STAGE == 2 ? fma(wc1, hup - hdn, kW * v[q + 2]) : fma(wc1, hup - hdn, v[q + 2]);
             hup = hdn;
             dprev = d;
         }
@@ -136,9 +140,9 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
 #pragma unroll
         for (int k = 0; k < kWC; ++k) {
             if (!ok[k]) continue;
-            double val = c[k] + fl[k] + sc.c2 * (h[k] - h[k + 1]);
-            if (i == 0 && jb + k == 0) val += sc.src;   // nucleation inflow, cell (0, 0)
-            if (STAGE == 2) val = 0.5 * old[row + jb + k] + 0.5 * val;
+            double val = fma(wc2, h[k] - h[k + 1], fl[k]);
+            if (i == 0 && jb + k == 0) val += wsrc;   // nucleation inflow, cell (0, 0)
+            if (STAGE == 2) val = fma(0.5, old[row + jb + k], val);
             out[row + jb + k] = val;
             acc[k] = fma(x1, val, acc[k]);
             if (sc.moms) add_moments(m, val, x1, x2[k], area);

@@ -28,9 +28,17 @@ def test_fused_2d_full_size():
     compare_instance(pi.config_2d(256), path="fused")
 
 
+@pytest.mark.parametrize("shape", [(300, 333), (1000, 150), (600, 400)])
+def test_fused_2d_tall_tiles(shape):
+    # one tile per block of 17..64 rows (the tall-tile kernel, dynamic shared
+    # memory), ragged in both directions
+    compare_instance(pi.config_2d(*shape), path="fused")
+
+
 def test_fused_2d_larger_than_one_wave():
-    # more tiles than co-resident blocks: blocks loop over several tiles
-    compare_instance(pi.config_2d(600, 400), path="fused")
+    # tiles taller than 64 rows would be needed for one per block: blocks loop
+    # over several 16 x 32 tiles
+    compare_instance(pi.config_2d(1200, 300), path="fused")
 
 
 def test_fused_state_at_every_output_time():
