@@ -151,21 +151,10 @@ __host__ __device__ inline double pbe_log(double x)
     return pbe_fma(ed, ln2_hi, pbe_fma(two_z, P, ed * ln2_lo));
 }
 
-__host__ __device__ inline double pbe_log_tab(double x)
+// log of the positive normal double with bits b, times 2^eadj
+__host__ __device__ __forceinline__ double pbe_log_tab_bits(int64_t b, int eadj)
 {
-    if (!(x > 0.0) || x == __builtin_huge_val()) {
-        if (x == 0.0) return -__builtin_huge_val();
-        if (x == __builtin_huge_val()) return x;
-        return (x - x) / (x - x);   // NaN for negative or NaN input
-    }
-    int64_t b = pbe_double_to_bits(x);
-    int e = (int)((b >> 52) & 0x7ff);
-    if (e == 0) {                    // subnormal: scale into the normal range
-        x *= 18014398509481984.0;    // 2^54
-        b = pbe_double_to_bits(x);
-        e = (int)((b >> 52) & 0x7ff) - 54;
-    }
-    e -= 1023;
+    const int e = (int)(b >> 52) - 1023 + eadj;
     const int j = (int)((b >> 45) & 127);
     const double m = pbe_bits_to_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);   // [1, 2)
 #ifdef __CUDA_ARCH__
@@ -184,6 +173,19 @@ __host__ __device__ inline double pbe_log_tab(double x)
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
     const double ed = (double)e;
     return pbe_fma(ed, ln2_hi, lnc) + pbe_fma(ed, ln2_lo, l1p);
+}
+
+// The main path runs for every x; the classification of x is applied to the
+// result, so it does not lengthen the dependent chain.
+__host__ __device__ inline double pbe_log_tab(double x)
+{
+    const int64_t b = pbe_double_to_bits(x);
+    const double res = pbe_log_tab_bits(b, 0);
+    if (b >= 0x0010000000000000LL && b < 0x7ff0000000000000LL) return res;   // positive normal
+    if (x == 0.0) return -__builtin_huge_val();
+    if (x == __builtin_huge_val()) return x;
+    if (!(x > 0.0)) return (x - x) / (x - x);   // NaN for negative or NaN input
+    return pbe_log_tab_bits(pbe_double_to_bits(x * 18014398509481984.0), -54);   // subnormal, scaled by 2^54
 }
 
 }  // namespace pbe

@@ -26,10 +26,11 @@ def _setup(inst):
     return p, tgt, cols
 
 
-def _gpu_grad(inst, seeds, K):
+def _gpu_grad(inst, seeds, K, window=-1):
     import torch
     import paper_2411_00742_gb300 as P
     g = P.Grid.from_problem(inst.problem)
+    g.set_window(window)
     g.set_state(np.ascontiguousarray(inst.n0), inst.C0, 0.0)
     dn0 = torch.zeros(inst.problem.ncells, dtype=torch.float64, device="cuda")
     rows = torch.zeros(seeds.shape, dtype=torch.float64, device="cuda")
@@ -59,6 +60,21 @@ def test_vjp_matches_cpu_adjoint(case, K):
     assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
     np.testing.assert_allclose(rows[:, 1:], r[:, 1:], rtol=1e-10)
     assert t_end == pytest.approx(inst.t_out[-1])
+
+
+def test_vjp_with_window_stage_kernel_matches_cpu_adjoint():
+    """Forward passes and segment recomputation in the register-window stage
+    kernel (forced on a small rectangular grid)."""
+    inst = _problem("2d_rect")
+    p, tgt, cols = _setup(inst)
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    want, want_dn0, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
+    dth, dn0, dC0, rows, _ = _gpu_grad(inst, seeds, 16, window=1)
+    for j in range(6):
+        assert dth[j] == pytest.approx(want[j], rel=REL_GRAD, abs=1e-300), (j, dth, want)
+    assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
+    np.testing.assert_allclose(rows[:, 1:], r[:, 1:], rtol=1e-10)
 
 
 def test_vjp_checkpoint_interval_does_not_change_result():

@@ -40,6 +40,22 @@ def test_closure_forward_matches_oracle(ndim):
     assert err <= REL_ROWS_MLP, err
 
 
+def test_closure_forward_window_kernel_matches_oracle():
+    """The learned closure on the plain path's register-window stage kernel
+    (forced on a small grid; it reads every moment at every stage)."""
+    inst = cd.trajectories(1, seed=11, N=48)[0]
+    w = cd.initial_weights(3, 0.2)
+    g = _grid(inst, w)
+    g.set_window(1)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, steps = g.solve(inst.t_out)
+    g.close()
+    want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=cd.stored_weights(w))
+    assert steps == want["steps"]
+    err = np.max(np.abs(rows[:, 1:] - want["rows"][:, 1:]) / np.abs(want["rows"][:, 1:]))
+    assert err <= REL_ROWS_MLP, err
+
+
 def test_closure_gradients_match_oracle():
     inst = cd.trajectories(1, seed=12, N=40)[0]
     w = cd.initial_weights(4, 0.2)
