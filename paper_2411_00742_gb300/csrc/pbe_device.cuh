@@ -263,7 +263,7 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
     }
     const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
     const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp_tab(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
     const double d = C - cs;
     if (!(d > 0.0)) {   // S <= 1: no growth, no nucleation
         G1 = 0.0; G2 = 0.0; B = 0.0;
@@ -274,7 +274,7 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
     const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
     double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
     if (K.growth_form == 1 && lane < 2) q -= (lane == 0 ? K.ea1 : K.ea2) / (T + 273.15);   // Arrhenius factor
-    const double e = pbe_exp(fma(p, L, q));
+    const double e = pbe_exp_tab(fma(p, L, q));
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
     B = __shfl_sync(0xffffffffu, e, 2);
@@ -360,9 +360,9 @@ __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t
         return;
     }
     mlp_forward_warp(K, x, o);
-    G1 = pbe_exp((double)o[0] + kLnG1);
-    G2 = (K.ndim == 2) ? pbe_exp((double)o[1] + kLnG2) : 0.0;
-    B = pbe_exp((double)o[2] + kLnB);
+    G1 = pbe_exp_tab((double)o[0] + kLnG1);
+    G2 = (K.ndim == 2) ? pbe_exp_tab((double)o[1] + kLnG2) : 0.0;
+    B = pbe_exp_tab((double)o[2] + kLnB);
 }
 
 __device__ __forceinline__ int timestep_fast(const Kin& K, const Geom& g, double G1, double G2, double t,

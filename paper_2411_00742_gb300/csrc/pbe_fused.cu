@@ -18,7 +18,7 @@
 // block the moment weights of each thread's cells are computed once and kept
 // in registers, the cross-block sum costs no round trip beyond the barrier's
 // own, the stage coefficients are computed once per block, and the kinetics
-// use short-latency exp and table-driven log.
+// use table-driven exp and log.
 //
 // Every wait is bounded: a barrier that does not complete within about one
 // second sets PBE_ETIMEOUT and the kernel returns.

@@ -1,25 +1,28 @@
 // Short-latency FP64 exp and log for the scalar kinetics chain.
 //
-// On GB300 every dependent FP64 operation costs ~65 cycles, so the latency
-// of the scalar chain between stages is set by the depth of the dependency
-// graph of exp/log.  These are written from the textbook constructions:
+// On GB300 every dependent FP64 operation costs ~65 cycles and every FP64
+// instruction occupies the SM's FP64 pipe ~16 cycles, so the latency of the
+// scalar chain between stages is set by the depth and the length of exp/log.
+// These are written from the textbook constructions:
 //   exp: Cody-Waite reduction x = k ln2 + r (|r| <= ln2/2, ln2 split in a
 //        high part with trailing zero bits and a low part), exp(r) by its
 //        Taylor polynomial of degree 13 evaluated with Estrin's scheme, and
 //        the scale 2^k written into the exponent field;
+//   exp_tab: the table-driven form (Tang's method): x = (64 m + j) ln2/64 + r,
+//        exp x = 2^m 2^(j/64) exp(r), |r| <= ln2/128, exp(r) - 1 to r^5;
 //   log: x = 2^e m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(z),
 //        z = (m-1)/(m+1), by the odd Taylor series of atanh to z^23 (Estrin
 //        in w = z^2), plus e ln2.
 //   log_tab: the table-driven form (Tang's method): x = 2^e m, m in [1, 2),
-//        the top 7 bits of m pick a centre c_j (pbe_log_table.h, written by
-//        gen_log_table.py), log x = e ln2 + ln c_j + log1p(r) with
-//        r = m / c_j - 1 (|r| <= 1/257) and log1p by its Taylor polynomial
-//        to r^7 (Estrin); 7 dependent FP64 operations instead of ~16, at an
-//        absolute (not relative) error of a few 1e-16 near x = 1.
-// Relative error is a few units of 2^-53 on the arguments the kinetics use
-// (checked against the C library on the host by the tests).  Arguments
-// outside the handled ranges (non-positive or non-finite log input, exp of
-// |x| > 700) return the IEEE limits of the function.
+//        the top 8 bits of m pick a centre c_j, log x = e ln2 + ln c_j +
+//        log1p(r) with r = m / c_j - 1 (|r| <= 1/513) and log1p by its Taylor
+//        polynomial to r^5 (Estrin), at an absolute (not relative) error of a
+//        few 1e-16 near x = 1.
+// The tables (pbe_log_table.h) are written by gen_log_table.py with 50-digit
+// arithmetic.  Relative error is a few units of 2^-53 on the arguments the
+// kinetics use (checked against the C library on the host by the tests).
+// Arguments outside the handled ranges (non-positive or non-finite log input,
+// exp of |x| > 700) return the IEEE limits of the function.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,11 +34,13 @@
 namespace pbe {
 
 #ifdef __CUDACC__
-static __constant__ double c_log_inv[128] = PBE_LOG_TAB_INV;
-static __constant__ double c_log_ln[128] = PBE_LOG_TAB_LN;
+static __constant__ double c_log_inv[256] = PBE_LOG_TAB_INV;
+static __constant__ double c_log_ln[256] = PBE_LOG_TAB_LN;
+static __constant__ double c_exp_tab[64] = PBE_EXP_TAB;
 #endif
-static const double h_log_inv[128] = PBE_LOG_TAB_INV;
-static const double h_log_ln[128] = PBE_LOG_TAB_LN;
+static const double h_log_inv[256] = PBE_LOG_TAB_INV;
+static const double h_log_ln[256] = PBE_LOG_TAB_LN;
+static const double h_exp_tab[64] = PBE_EXP_TAB;
 
 __host__ __device__ __forceinline__ double pbe_bits_to_double(int64_t b)
 {
@@ -100,6 +105,35 @@ __host__ __device__ inline double pbe_exp(double x)
     return (p * s1) * s2;
 }
 
+// Table-driven exp (Tang's method): x = (64 m + j) ln2/64 + r with
+// |r| <= ln2/128, exp x = 2^m 2^(j/64) exp(r), exp(r) - 1 by its Taylor
+// polynomial to r^5 (the first omitted term, r^6/720, is below 4e-17);
+// 12 FP64 operations against the 22 of pbe_exp.  Same range handling.
+__host__ __device__ inline double pbe_exp_tab(double x)
+{
+    if (!(x > -700.0)) return x != x ? x : 0.0;   // NaN stays NaN
+    if (x > 700.0) return __builtin_huge_val();
+    const double inv_l = 92.332482616893656;            // 64 / ln2
+    const double shifter = 6755399441055744.0;            // 1.5 * 2^52: rounds to an integer
+    const double t = pbe_fma(x, inv_l, shifter);
+    const double nd = t - shifter;
+    const int n = (int)(pbe_double_to_bits(t) & 0xffffffff) - (int)(pbe_double_to_bits(shifter) & 0xffffffff);
+    double r = pbe_fma(-nd, PBE_EXP_LN2_64_HI, x);
+    r = pbe_fma(-nd, PBE_EXP_LN2_64_LO, r);
+    const int j = n & 63, m = (n - j) / 64;
+#ifdef __CUDA_ARCH__
+    const double tj = c_exp_tab[j];
+#else
+    const double tj = h_exp_tab[j];
+#endif
+    const double a = pbe_fma(r, 1.0 / 6, 0.5), b = pbe_fma(r, 1.0 / 120, 1.0 / 24);
+    const double r2 = r * r;
+    const double r4 = r2 * r2;
+    const double u = pbe_fma(r4, b, pbe_fma(r2, a, r));   // exp(r) - 1
+    const double s = pbe_bits_to_double((int64_t)(m + 1023) << 52);
+    return pbe_fma(tj, u, tj) * s;
+}
+
 __host__ __device__ inline double pbe_log(double x)
 {
     if (!(x > 0.0) || x == __builtin_huge_val()) {
@@ -155,21 +189,21 @@ __host__ __device__ inline double pbe_log(double x)
 __host__ __device__ __forceinline__ double pbe_log_tab_bits(int64_t b, int eadj)
 {
     const int e = (int)(b >> 52) - 1023 + eadj;
-    const int j = (int)((b >> 45) & 127);
+    const int j = (int)((b >> 44) & 255);
     const double m = pbe_bits_to_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);   // [1, 2)
 #ifdef __CUDA_ARCH__
     const double inv = c_log_inv[j], lnc = c_log_ln[j];
 #else
     const double inv = h_log_inv[j], lnc = h_log_ln[j];
 #endif
-    const double r = pbe_fma(m, inv, -1.0);
-    // log1p(r) = r + r^2 (c2 + c3 r + c4 r^2 + c5 r^3 + c6 r^4 + c7 r^5), c_k = (-1)^(k+1) / k
-    const double c2 = -0.5, c3 = 1.0 / 3, c4 = -0.25, c5 = 0.2, c6 = -1.0 / 6, c7 = 1.0 / 7;
+    const double r = pbe_fma(m, inv, -1.0);   // |r| <= 1/513
+    // log1p(r) = r + r^2 (c2 + c3 r) + r^4 (c4 + c5 r), c_k = (-1)^(k+1) / k;
+    // the first omitted term, r^6 / 6, is below 1e-17
+    const double c2 = -0.5, c3 = 1.0 / 3, c4 = -0.25, c5 = 0.2;
     const double r2 = r * r;
-    const double p23 = pbe_fma(c3, r, c2), p45 = pbe_fma(c5, r, c4), p67 = pbe_fma(c7, r, c6);
+    const double p23 = pbe_fma(c3, r, c2), p45 = pbe_fma(c5, r, c4);
     const double r4 = r2 * r2;
-    const double q = pbe_fma(r4, p67, pbe_fma(r2, p45, p23));
-    const double l1p = pbe_fma(r2, q, r);
+    const double l1p = pbe_fma(r4, p45, pbe_fma(r2, p23, r));
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
     const double ed = (double)e;
     return pbe_fma(ed, ln2_hi, lnc) + pbe_fma(ed, ln2_lo, l1p);

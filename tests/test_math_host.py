@@ -1,7 +1,7 @@
 """Accuracy of the library's short-latency exp/log (pbe_math.cuh), compiled
 for the host with nvcc and compared with the C library on the ranges the
 kinetics use (argument of exp in [-60, 25], log of [e^-40, e^40]), including
-the table-driven log (absolute error bound) at every table entry."""
+the table-driven log (absolute error bound) and exp at every table entry."""
 import os
 import shutil
 import subprocess
@@ -20,11 +20,17 @@ int main() {
   double me = 0, ml = 0, ma = 0;
   for (int i = 0; i < 400000; ++i) {
     double x = U(rng); double a = pbe::pbe_exp(x), b = std::exp(x); me = fmax(me, fabs(a - b) / b);
+    me = fmax(me, fabs(pbe::pbe_exp_tab(x) - b) / b);
     double y = std::exp(L(rng)); double c = pbe::pbe_log(y), d = std::log(y);
     ml = fmax(ml, fabs(c - d) / fmax(fabs(d), 1e-300));
   }
   for (int i = 0; i < 200000; ++i) { double y = 1.0 + (i - 100000) * 1e-9; ma = fmax(ma, fabs(pbe::pbe_log(y) - std::log(y))); }
+  for (int j = -64 * 20; j <= 64 * 20; ++j) {   // every table entry, at and between the nodes
+    for (double f : {0.0, 0.49, 0.5, 0.51}) { double x = (j + f) * 0.010830424696249145; me = fmax(me, fabs(pbe::pbe_exp_tab(x) - std::exp(x)) / std::exp(x)); }
+  }
   int special = pbe::pbe_exp(-800.0) == 0.0 && std::isinf(pbe::pbe_exp(800.0)) && std::isinf(pbe::pbe_log(0.0))
+                && pbe::pbe_exp_tab(-800.0) == 0.0 && std::isinf(pbe::pbe_exp_tab(800.0)) && pbe::pbe_exp_tab(0.0) == 1.0
+                && std::isnan(pbe::pbe_exp_tab(std::nan("")))
                 && std::isnan(pbe::pbe_log(-1.0)) && pbe::pbe_log(1.0) == 0.0 && pbe::pbe_exp(0.0) == 1.0
                 && std::fabs(pbe::pbe_log(4.9e-320) - std::log(4.9e-320)) < 1e-12;
   // table-driven log: absolute error on [e^-40, e^40] and near 1, special values
@@ -34,8 +40,8 @@ int main() {
     mtr = fmax(mtr, fabs(c - d) / fmax(fabs(d), 1.0));
   }
   for (int i = 0; i < 200000; ++i) { double y = 1.0 + (i - 100000) * 1e-9; mt = fmax(mt, fabs(pbe::pbe_log_tab(y) - std::log(y))); }
-  for (int k = 0; k < 128; ++k) {   // every table entry at its centre and both ends
-    for (double f : {0.0, 0.5, 0.999999}) { double y = 1.0 + (k + f) / 128.0; mt = fmax(mt, fabs(pbe::pbe_log_tab(y) - std::log(y))); }
+  for (int k = 0; k < 256; ++k) {   // every table entry at its centre and both ends
+    for (double f : {0.0, 0.5, 0.999999}) { double y = 1.0 + (k + f) / 256.0; mt = fmax(mt, fabs(pbe::pbe_log_tab(y) - std::log(y))); }
   }
   int special_t = std::isinf(pbe::pbe_log_tab(0.0)) && std::isnan(pbe::pbe_log_tab(-1.0))
                   && std::fabs(pbe::pbe_log_tab(1.0)) < 2e-16 && std::fabs(pbe::pbe_log_tab(4.9e-320) - std::log(4.9e-320)) < 1e-12;
