@@ -273,9 +273,11 @@ __device__ __forceinline__ StageCoef stage_coef_fast(const Scal& S, const Geom& 
     const double G1 = STAGE == 1 ? S.G1a : S.G1b;
     const double G2 = STAGE == 1 ? S.G2a : S.G2b;
     const double B = STAGE == 1 ? S.Ba : S.Bb;
-    sc.c1 = G1 * S.dt * g.inv_d1;
-    sc.c2 = G2 * S.dt * g.inv_d2;
-    sc.src = g.ndim == 1 ? S.dt * B * g.inv_d1 : S.dt * B * (g.inv_d1 * g.inv_d2);
+    // (G / dL) dt: the rates per cell width are known before dt, so one
+    // multiplication follows the step length
+    sc.c1 = (G1 * g.inv_d1) * S.dt;
+    sc.c2 = (G2 * g.inv_d2) * S.dt;
+    sc.src = g.ndim == 1 ? (B * g.inv_d1) * S.dt : (B * (g.inv_d1 * g.inv_d2)) * S.dt;
     sc.moms = STAGE == 2 && S.clipped;
     return sc;
 }
