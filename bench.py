@@ -46,7 +46,7 @@ BYTES_PER_CELL_STEP_PAPER = 16
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64 (2 FMA/clk/SM x 152 SMs x ~2.07 GHz)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_fused launch on the
 # 256 x 256 solve, from one ncu capture of the current kernel (the state stays in L2)
-FUSED_DRAM_BYTES_PER_LAUNCH = 613888
+FUSED_DRAM_BYTES_PER_LAUNCH = 609792
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -182,9 +182,6 @@ def run_gpu(args):
     nrow, ncol = len(inst.t_out), P.ncols(2)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    import oracle
-    want = oracle.solve_instance(inst)
-
     def measure(path):
         g = P.Grid.from_problem(inst.problem, stream=stream, path=path)
         rows = torch.zeros((nrow, ncol), dtype=torch.float64, device="cuda")
@@ -193,7 +190,7 @@ def run_gpu(args):
                 g.set_state(n0_dev, inst.C0, 0.0)
                 _, steps = g.solve(inst.t_out, out=rows)
         torch.cuda.synchronize()
-        err = float(np.max(np.abs(rows.cpu().numpy()[:, 1:] - want["rows"][:, 1:]) / np.abs(want["rows"][:, 1:])))
+        got = rows.cpu().numpy()
         times, ktimes = [], []
         # the library records CUDA events on its stream around the launch that
         # advances the state (the persistent kernel on the fused path)
@@ -211,7 +208,7 @@ def run_gpu(args):
                 times.append(e0.elapsed_time(e1) * 1e-3)
                 ktimes.append(g.kernel_time_ms() * 1e-3)
         g.close()
-        return sum(times), steps, err, sum(ktimes) / len(ktimes)
+        return sum(times), steps, got, sum(ktimes) / len(ktimes)
 
     def e2e(path):
         g = P.Grid.from_problem(inst.problem, stream=stream, path=path)
@@ -281,19 +278,30 @@ def run_gpu(args):
                 "unit": "cell-steps/s",
                 "plain_per_instance": {"value": g_cells / g_time, "sample": "first 64 instances, one grid each"}}
 
+    def loss_seeds(rows, target, cols):
+        """dL/drows of the relative-error loss sum_k sum_c ((r - t) / t)^2 (Eq. 5 with
+        relative residuals) over the columns `cols`."""
+        sd = np.zeros_like(rows)
+        sd[..., cols] = 2.0 * (rows[..., cols] - target[..., cols]) / target[..., cols] ** 2
+        return sd
+
     def adjoint_leg():
         """Gradients of the relative-error loss (50 loss times, target = kinetics x1.1) with
         respect to the kinetic parameters: (a) 2-D 128x128 grid, (b) 1-D 500-cell instances.
-        One gradient = forward with checkpoints every 64 steps + reverse sweep."""
-        out = {}
+        One gradient = forward with checkpoints every 64 steps + reverse sweep.  Targets
+        and seeds come from GPU solves; the CPU adjoint (timing and agreement) is part of
+        the CPU baseline leg."""
+        out, cases = {}, {}
         for name, inst, cols in (("2d_128x128", pi.adjoint_2d(128), [1, 2, 3, 9, 11]),
                                  ("1d_500", pi.adjoint_batch_1d(16)[0], [1, 2, 3, 4, 5])):
             p = inst.problem
-            tgt = oracle.solve(p.with_theta(p.theta * pi.TARGET_FACTOR), inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+            gt = P.Grid.from_problem(p.with_theta(p.theta * pi.TARGET_FACTOR), stream=stream)
+            gt.set_state(inst.n0, inst.C0, 0.0)
+            tgt, _ = gt.solve(inst.t_out)
+            gt.close()
             g = P.Grid.from_problem(p, stream=stream)
             n0d = torch.as_tensor(inst.n0).cuda()
-            seeds = torch.zeros((len(inst.t_out), P.ncols(p.ndim)), dtype=torch.float64, device="cuda")
-            rows = torch.zeros_like(seeds)
+            rows = torch.zeros((len(inst.t_out), P.ncols(p.ndim)), dtype=torch.float64, device="cuda")
             tgt_t = torch.as_tensor(tgt).cuda()
             times = []
             with torch.cuda.stream(stream):
@@ -313,33 +321,27 @@ def run_gpu(args):
                         times.append(e0.elapsed_time(e1) * 1e-3)
             g.close()
             tg = sum(times) / len(times)
-            r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
-            want, _, _ = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, oracle.relative_loss_seeds(r, tgt, cols))
-            idx = [0, 1, 4, 5] if p.ndim == 1 else list(range(6))
-            err = float(np.max(np.abs(dth[idx] - want[idx]) / np.abs(want[idx])))
-            t0 = time.perf_counter()
-            oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, oracle.relative_loss_seeds(r, tgt, cols))
-            tc = time.perf_counter() - t0
-            out[name] = {"grads_per_s": 1.0 / tg, "ms_per_grad": 1e3 * tg, "max_rel_err_vs_cpu_adjoint": err,
-                         "cpu_adjoint_grads_per_s": 1.0 / tc, "checkpoint_every": 64}
+            out[name] = {"grads_per_s": 1.0 / tg, "ms_per_grad": 1e3 * tg, "max_rel_err_vs_cpu_adjoint": None,
+                         "cpu_adjoint_grads_per_s": None, "checkpoint_every": 64}
+            cases[name] = (inst, tgt, cols, dth, sd.cpu().numpy())
         # (b') the batched form: 256 instances of 500 cells, one launch (one warp per instance)
         insts = pi.adjoint_batch_1d(256)
+        cols = [1, 2, 3, 4, 5]
+        bt = P.Batch([x.problem.with_theta(x.problem.theta * pi.TARGET_FACTOR) for x in insts],
+                     [x.C0 for x in insts], stream=stream)
+        bt.set_state(bt.pack([x.n0 for x in insts]))
+        tgts, _ = bt.solve(pi.loss_times())
+        bt.close()
         b = P.Batch([x.problem for x in insts], [x.C0 for x in insts], stream=stream)
         packed = b.pack([x.n0 for x in insts])
-        seeds = np.zeros((len(insts), 50, 6))
-        cols = [1, 2, 3, 4, 5]
-        tgts = []
-        for i, inst in enumerate(insts):
-            p = inst.problem
-            tgt = oracle.solve(p.with_theta(p.theta * pi.TARGET_FACTOR), inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
-            r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
-            seeds[i] = oracle.relative_loss_seeds(r, tgt, cols)
-            tgts.append(tgt)
+        b.set_state(packed)
+        fwd, _ = b.solve(pi.loss_times())
+        seeds = loss_seeds(fwd, tgts, cols)
         seeds_d = torch.as_tensor(seeds).cuda()
         times = []
         with torch.cuda.stream(stream):
-            b.set_state(packed)
             for it in range(args.warmup + max(3, args.steps // 2)):
+                b.set_state(packed)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -350,16 +352,34 @@ def run_gpu(args):
                     times.append(e0.elapsed_time(e1) * 1e-3)
         b.close()
         tb = sum(times) / len(times)
+        out["batch_1d_256x500"] = {"grads_per_s": 256 / tb, "ms_per_batch": 1e3 * tb,
+                                   "max_rel_err_vs_cpu_adjoint_sampled": None, "checkpoint_every": 64,
+                                   "single_instance_path_grads_per_s": out["1d_500"]["grads_per_s"],
+                                   "cpu_adjoint_grads_per_s": None}
+        cases["batch_1d_256x500"] = (insts, seeds, dth_b)
+        return out, cases
+
+    def adjoint_cpu_baseline(adj, cases):
+        """The CPU adjoint of the oracle on the same seeds: its gradients/s and the
+        agreement of the GPU gradients (part of the CPU baseline leg)."""
+        import oracle
+        for name in ("2d_128x128", "1d_500"):
+            inst, tgt, cols, dth, sd = cases[name]
+            p = inst.problem
+            idx = [0, 1, 4, 5] if p.ndim == 1 else list(range(6))
+            t0 = time.perf_counter()
+            want, _, _ = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, sd)
+            tc = time.perf_counter() - t0
+            adj[name]["max_rel_err_vs_cpu_adjoint"] = float(np.max(np.abs(dth[idx] - want[idx]) / np.abs(want[idx])))
+            adj[name]["cpu_adjoint_grads_per_s"] = 1.0 / tc
+        insts, seeds, dth_b = cases["batch_1d_256x500"]
         errs = []
         for i in range(0, 256, 32):
             inst = insts[i]
             want, _, _ = oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds[i])
             errs.append(float(np.max(np.abs(dth_b[i, [0, 1, 4, 5]] - want[[0, 1, 4, 5]]) / np.abs(want[[0, 1, 4, 5]]))))
-        out["batch_1d_256x500"] = {"grads_per_s": 256 / tb, "ms_per_batch": 1e3 * tb,
-                                   "max_rel_err_vs_cpu_adjoint_sampled": max(errs), "checkpoint_every": 64,
-                                   "single_instance_path_grads_per_s": out["1d_500"]["grads_per_s"],
-                                   "cpu_adjoint_grads_per_s": out["1d_500"]["cpu_adjoint_grads_per_s"]}
-        return out
+        adj["batch_1d_256x500"]["max_rel_err_vs_cpu_adjoint_sampled"] = max(errs)
+        adj["batch_1d_256x500"]["cpu_adjoint_grads_per_s"] = adj["1d_500"]["cpu_adjoint_grads_per_s"]
 
     def paper_leg():
         """The paper's own base case (Table 1, Appendix A) at its finest bins: 6000 x 3000
@@ -401,6 +421,35 @@ def run_gpu(args):
                 "paper_context": "JAX (GPU) on an RTX 4090 in FP64: 'almost 3x as fast' as a 1.2 s MATLAB run "
                                  "(Sec. 3.2): about 0.4 s read as total time, about 2.3 s read per time step"}
 
+    def small_1d_leg():
+        """The small 1-D case (200 cells, the oracle-sized workload): latency-bound,
+        reported as solves/s and microseconds per step on both paths, against the
+        oracle on the same solve."""
+        sinst = pi.config_1d(200)
+        n0s = torch.as_tensor(sinst.n0).cuda()
+        rows1 = torch.zeros((len(sinst.t_out), P.ncols(1)), dtype=torch.float64, device="cuda")
+        out = {"workload": "1-D 200 cells on [0, 1000] um, full 0-3600 s solve, 61 output rows"}
+        for path in ("fused", "plain"):
+            g = P.Grid.from_problem(sinst.problem, stream=stream, path=path)
+            times, nsteps = [], 0
+            with torch.cuda.stream(stream):
+                for it in range(3 + max(5, args.steps)):
+                    g.set_state(n0s, sinst.C0, 0.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    _, nsteps = g.solve(sinst.t_out, out=rows1)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if it >= 3:
+                        times.append(e0.elapsed_time(e1) * 1e-3)
+            g.close()
+            t = sum(times) / len(times)
+            out[path] = {"solves_per_s": 1.0 / t, "us_per_step": 1e6 * t / nsteps, "steps": nsteps,
+                         "value": sinst.problem.ncell * nsteps / t, "unit": "cell-steps/s",
+                         "max_rel_err_vs_oracle": None, "rows": rows1.cpu().numpy()}
+        return out
+
     def scaling_leg():
         """Grid-size sweep of the 2-D workload (the paper's Fig. 3b analogue): full
         solves at 512^2, 1024^2 and 2048^2 on the fused and plain paths."""
@@ -437,14 +486,15 @@ def run_gpu(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    t_fused, steps, err_fused, k_fused = measure("fused")
-    t_plain, steps_p, err_plain, _ = measure("plain")
+    t_fused, steps, rows_fused, k_fused = measure("fused")
+    t_plain, steps_p, rows_plain, _ = measure("plain")
     clk = clocks.stop()
     e2e_rate, h2d, d2h = e2e("fused")
     batch = batch_leg() if not args.no_batch else None
-    adjoint = adjoint_leg() if not args.no_adjoint else None
+    adjoint, adjoint_cases = adjoint_leg() if not args.no_adjoint else (None, None)
     paper = paper_leg() if not args.no_paper else None
     scaling = scaling_leg() if not args.no_scaling else None
+    small_1d = small_1d_leg() if not args.no_scaling else None
 
     if ws > 1:
         import torch.distributed as dist
@@ -461,9 +511,9 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "ssp_rk2_steps_per_solve": steps,
-        "paths": {"fused": {"value": value, "ms_per_solve": ms, "max_rel_err_vs_oracle": err_fused},
+        "paths": {"fused": {"value": value, "ms_per_solve": ms, "max_rel_err_vs_oracle": None},
                   "plain": {"value": plain_value, "ms_per_solve": 1e3 * t_plain / args.steps,
-                            "max_rel_err_vs_oracle": err_plain}},
+                            "max_rel_err_vs_oracle": None}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
                      "traffic": FUSED_DRAM_BYTES_PER_LAUNCH if inst.problem.ncells == (256, 256) else None,
@@ -474,6 +524,7 @@ def run_gpu(args):
                              "launch on its stream, mean over the timed solves); peak = nominal GB300 FP64"},
         "e2e": {"value": ws * e2e_rate, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "batch_1d": batch,
+        "small_1d": small_1d,
         "adjoint": adjoint,
         "paper_scheme": paper,
         "scaling_2d": scaling,
@@ -482,9 +533,27 @@ def run_gpu(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        v, reps, el, _ = _oracle_rate(inst, budget_s=args.cpu_seconds)
+        # the CPU baseline leg: the oracle timed on the host, and its rows give the
+        # stated error of the GPU rows on the same solves
+        v, reps, el, want = _oracle_rate(inst, budget_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} full solves of the same 256x256 workload ({el:.1f} s), single thread"}
+
+        def rel_err(got, ref):
+            return float(np.max(np.abs(got[:, 1:] - ref["rows"][:, 1:]) / np.abs(ref["rows"][:, 1:])))
+
+        line["paths"]["fused"]["max_rel_err_vs_oracle"] = rel_err(rows_fused, want)
+        line["paths"]["plain"]["max_rel_err_vs_oracle"] = rel_err(rows_plain, want)
+        if adjoint is not None:
+            adjoint_cpu_baseline(adjoint, adjoint_cases)
+        if small_1d is not None:
+            import oracle
+            want1 = oracle.solve_instance(pi.config_1d(200))
+            for path in ("fused", "plain"):
+                small_1d[path]["max_rel_err_vs_oracle"] = rel_err(small_1d[path]["rows"], want1)
+    if small_1d is not None:
+        for path in ("fused", "plain"):
+            small_1d[path].pop("rows")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
