@@ -5,7 +5,7 @@
 
 Truth trajectories come from the FP64 solver with hidden power-law kinetics
 (pbe_closure_data.hidden_law); the closure is trained with Adam (lr 1e-3) on
-the relative errors of mu00, mu10, mu01, mu12 and C at 50 times, and judged
+the relative errors of mu00, mu10, mu01, mu12 and C at 50 times, and evaluated
 on held-out trajectories against the same solver with the nominal (wrong)
 power-law kinetics, i.e. the method without the closure.
 """
