@@ -252,7 +252,22 @@ __device__ __forceinline__ void finish_stage2(Scal* S, const Kin& K, const Geom&
 // where C - c* is exact for S near 1.  Every lane of the calling warp must
 // participate with identical arguments; all lanes return identical results.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B)
+// Temperature and solubility at time t (they depend on t only, so a caller
+// that evaluates the kinetics twice at one time can compute them once).
+struct KinT {
+    double T, cs;
+};
+
+__device__ __forceinline__ KinT kin_temperature(const Kin& K, double t)
+{
+    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
+    const double T = K.T0 + (K.T1 - K.T0) * frac;
+    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp_tab(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    return KinT{T, cs};
+}
+
+__device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const KinT& tc, double& G1, double& G2,
+                                                double& B)
 {
     const int lane = threadIdx.x & 31;
     if (K.kind == PBE_KINETICS_FIXED) {
@@ -261,9 +276,7 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
         B = K.kb;
         return;
     }
-    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
-    const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp_tab(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double T = tc.T, cs = tc.cs;
     const double d = C - cs;
     if (!(d > 0.0)) {   // S <= 1: no growth, no nucleation
         G1 = 0.0; G2 = 0.0; B = 0.0;
@@ -278,6 +291,15 @@ __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, 
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
     B = __shfl_sync(0xffffffffu, e, 2);
+}
+
+__device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B)
+{
+    if (K.kind == PBE_KINETICS_FIXED) {
+        kinetics_warp_T(K, C, KinT{0.0, 0.0}, G1, G2, B);
+        return;
+    }
+    kinetics_warp_T(K, C, kin_temperature(K, t), G1, G2, B);
 }
 
 // ---------------------------------------------------------------------------
@@ -346,12 +368,14 @@ constexpr double kLnG1 = -4.605170185988091;   // ln 0.01
 constexpr double kLnG2 = -5.298317366548036;   // ln 0.005
 constexpr double kLnB = 11.512925464970229;    // ln 1e5
 
-// kinetics with the moment ratio V/mu0 of the state (used by the closure)
+// kinetics with the moment ratio V/mu0 of the state (used by the closure);
+// pre: temperature and solubility at t when the caller has them
 __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t, double ratio, double& G1,
-                                                double& G2, double& B)
+                                                double& G2, double& B, const KinT* pre = nullptr)
 {
     if (K.kind != PBE_KINETICS_MLP) {
-        kinetics_warp(K, C, t, G1, G2, B);
+        if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B);
+        else kinetics_warp(K, C, t, G1, G2, B);
         return;
     }
     float x[3], o[3];
@@ -410,13 +434,14 @@ __device__ __forceinline__ int timestep_fast(const Kin& K, const Geom& g, double
 
 // Warp versions of prepare_step / finish_stage1 / finish_stage2: called by all
 // lanes of one warp on the same Scal (shared or global); lane 0 writes.
-__device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const Geom& g, const double* t_out)
+__device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const Geom& g, const double* t_out,
+                                                  const KinT* pre = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const double t_next = t_out[S->out_idx];
     const double C = S->C, t = S->t;
     double G1, G2, B, dt, t_new;
-    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B);
+    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre);
     const int clipped = timestep_fast(K, g, G1, G2, t, t_next, dt, t_new);
     __syncwarp();
     if (lane == 0) {
@@ -430,12 +455,14 @@ __device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const G
     __syncwarp();
 }
 
-__device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double V1, double M1 = 1.0)
+// pre (optional): temperature and solubility at S->t_new
+__device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double V1, double M1 = 1.0,
+                                                   const KinT* pre = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const double C1 = S->C - K.kappa * (V1 - S->V0);
     double G1, G2, B;
-    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B);
+    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre);
     __syncwarp();
     if (lane == 0) {
         S->C1 = C1;
@@ -450,8 +477,11 @@ __device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double
     __syncwarp();
 }
 
+// pre (optional): temperature and solubility at S->t_new (the time the next
+// step starts from)
 __device__ __forceinline__ void finish_stage2_warp(Scal* S, const Kin& K, const Geom& g, const double* t_out,
-                                                   double* rows, const double* mom, int nmom, int vidx)
+                                                   double* rows, const double* mom, int nmom, int vidx,
+                                                   const KinT* pre = nullptr)
 {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -485,7 +515,7 @@ __device__ __forceinline__ void finish_stage2_warp(Scal* S, const Kin& K, const 
         }
     }
     __syncwarp();
-    if (!S->done) prepare_step_warp(S, K, g, t_out);
+    if (!S->done) prepare_step_warp(S, K, g, t_out, pre);
 }
 
 }  // namespace pbe

@@ -432,6 +432,10 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     __syncthreads();
     for (;;) {
 #pragma unroll 1
+        // temperature and solubility at the end of this step: both kinetics of
+        // the step are evaluated there (warp 0, once per step)
+        KinT tpre{0.0, 0.0};
+        if (warp == 0 && K.kind != PBE_KINETICS_FIXED) tpre = kin_temperature(K, s.t_new);
         for (int stage = 1; stage <= 2; ++stage) {
             const StageCoef sc = scs;
             const double* in = stage == 1 ? n : n1;
@@ -506,8 +510,8 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 __syncwarp();
                 HaloGo::arrive();   // the other blocks' outputs are visible: the face warps may load the halo
                 if (!fail) {
-                    if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX]);
-                    else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX);
+                    if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX], 1.0, &tpre);
+                    else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX, &tpre);
                     // the next stage's coefficients, once per block (the divisions of
                     // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
                     if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
