@@ -115,6 +115,105 @@ struct GroupSync {  // named barrier over the face warps 1..kFaceWarps
 struct MomSync {    // named barrier over warps kFaceWarps+1..7
     __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 2, %0;" ::"r"(kFNT - 32 * (kFaceWarps + 1)) : "memory"); }
 };
+// The scalar chain between the stages, for the chain warp of the fused
+// kernel: the same arithmetic as finish_stage1_warp / finish_stage2_warp
+// with prepare_step_warp and stage_coef_fast, arranged for latency: every
+// lane reads the scalars it needs at once and keeps them in registers, the
+// kinetics start at once, lane 0's bookkeeping is stores at the end, and the
+// coefficients of the next stage come from registers.  tc: temperature and
+// solubility at the step's end time.
+__device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const Geom& g, double V1, const KinT& tc)
+{
+    const int lane = threadIdx.x & 31;
+    const double C1 = S->C - K.kappa * (V1 - S->V0);
+    const double dt = S->dt;
+    const int clipped = S->clipped;
+    double G1, G2, B;
+    kinetics_warp_T(K, C1, tc, G1, G2, B);
+    if (lane == 0) {
+        S->C1 = C1;
+        S->V1 = V1;
+        S->M1 = 1.0;
+        S->G1b = G1; S->G2b = G2; S->Bb = B;
+        if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
+            S->status = PBE_ENONFINITE;
+            S->done = 1;
+        }
+    }
+    __syncwarp();
+    StageCoef sc;
+    sc.c1 = (G1 * g.inv_d1) * dt;
+    sc.c2 = (G2 * g.inv_d2) * dt;
+    sc.src = g.ndim == 1 ? (B * g.inv_d1) * dt : (B * (g.inv_d1 * g.inv_d2)) * dt;
+    sc.moms = clipped != 0;
+    return sc;
+}
+
+__device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const Geom& g, const double* t_out,
+                                                   double* rows, const double* mom, int nmom, int vidx,
+                                                   const KinT& tc)
+{
+    const int lane = threadIdx.x & 31;
+    const double V2 = mom[vidx], M2 = mom[0];
+    const double C = S->C - K.kappa * (V2 - S->V0);
+    const double t = S->t_new, dt_done = S->dt;
+    const int clipped = S->clipped, out_idx = S->out_idx, n_out = S->n_out;
+    const long long steps = S->steps + 1, max_steps = S->max_steps;
+    const bool finite = isfinite(V2) && isfinite(C);
+    const int oi = (finite && clipped) ? out_idx + 1 : out_idx;
+    const bool done = !finite || oi >= n_out || steps >= max_steps;
+    __syncwarp();   // every lane has read S before lane 0 writes it
+    double G1 = 0.0, G2 = 0.0, B = 0.0, dt = 0.0, t_new = t;
+    int clip2 = 0;
+    if (!done) {   // the next step: kinetics at (C, t), CFL step to the next output time
+        kinetics_warp_T(K, C, tc, G1, G2, B);
+        clip2 = timestep_fast(K, g, G1, G2, t, t_out[oi], dt, t_new);
+    }
+    if (lane == 0) {
+        S->t = t;
+        S->C = C;
+        S->V0 = V2;
+        S->M0 = M2;
+        S->last_dt = dt_done;
+        S->steps = steps;
+        if (!finite) {
+            S->status = PBE_ENONFINITE;
+            S->done = 1;
+        } else {
+            if (clipped) {
+                if (rows) {
+                    double* row = rows + (size_t)out_idx * (nmom + 2);
+                    row[0] = t;
+                    for (int k = 0; k < nmom; ++k) row[1 + k] = mom[k];
+                    row[nmom + 1] = C;
+                }
+                S->out_idx = oi;
+            }
+            if (oi >= n_out) {
+                S->done = 1;
+            } else if (steps >= max_steps) {
+                S->status = PBE_ETIMEOUT;
+                S->done = 1;
+            }
+        }
+        if (!done) {
+            S->G1a = G1; S->G2a = G2; S->Ba = B;
+            S->dt = dt; S->t_new = t_new; S->clipped = clip2;
+            if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
+                S->status = PBE_ENONFINITE;
+                S->done = 1;
+            }
+        }
+    }
+    __syncwarp();
+    StageCoef sc;
+    sc.c1 = (G1 * g.inv_d1) * dt;
+    sc.c2 = (G2 * g.inv_d2) * dt;
+    sc.src = g.ndim == 1 ? (B * g.inv_d1) * dt : (B * (g.inv_d1 * g.inv_d2)) * dt;
+    sc.moms = false;
+    return sc;
+}
+
 // Named barrier 3: warp 0 arrives once the device-wide barrier of the stage
 // is done (non-blocking), the face warps wait on it before they load the halo.
 // The unaligned forms: warp 0 reaches it after thread 0's wait.
@@ -431,11 +530,11 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     fused_faces<NDIM, false, TI>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
     __syncthreads();
     for (;;) {
-#pragma unroll 1
         // temperature and solubility at the end of this step: both kinetics of
         // the step are evaluated there (warp 0, once per step)
         KinT tpre{0.0, 0.0};
         if (warp == 0 && K.kind != PBE_KINETICS_FIXED) tpre = kin_temperature(K, s.t_new);
+#pragma unroll 1
         for (int stage = 1; stage <= 2; ++stage) {
             const StageCoef sc = scs;
             const double* in = stage == 1 ? n : n1;
@@ -510,11 +609,11 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 __syncwarp();
                 HaloGo::arrive();   // the other blocks' outputs are visible: the face warps may load the halo
                 if (!fail) {
-                    if (stage == 1) finish_stage1_warp(&s, K, msum[VIDX], 1.0, &tpre);
-                    else finish_stage2_warp(&s, K, g, t_out, my_rows, msum, NM, VIDX, &tpre);
                     // the next stage's coefficients, once per block (the divisions of
                     // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
-                    if (threadIdx.x == 0) scs = stage == 1 ? stage_coef_fast<2>(s, g) : stage_coef_fast<1>(s, g);
+                    const StageCoef c = stage == 1 ? fused_finish1(&s, K, g, msum[VIDX], tpre)
+                                                   : fused_finish2(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre);
+                    if (threadIdx.x == 0) scs = c;
                 }
             } else if (warp <= kFaceWarps) {
                 // one tile per block: the next stage's input is already in shared
