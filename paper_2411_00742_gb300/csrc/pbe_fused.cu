@@ -1,24 +1,31 @@
 // Fused path for one grid: a single persistent cooperative launch runs the
 // whole solve.  Each block owns a fixed set of tiles (2-D: tiles of ti x 32
 // cells, ti chosen so that every SM gets at most one tile when the grid
-// allows); the two stages of every step are separated by a device-wide
-// barrier that also sums the volume moment over the blocks (barrier_sum).
-// After each barrier the block splits: warp 0 advances the block's private
-// copy of the scalar chain (solute balance, kinetics, CFL step, the next
-// stage's coefficients - identical in every block), warps 1-6 already load
-// the next stage's input tile and compute its face values, which do not
-// depend on the kinetics, and on output steps warp 7 reduces the block's
-// moments (summed into the rows after the solve).  Face quotients use the
-// Newton-Raphson form (half_psi_fast).
+// allows: up to 16 rows in static shared memory, up to 64 rows in dynamic
+// shared memory; larger grids loop over 16 x 32 tiles); the two stages of
+// every step are separated by a device-wide barrier that also sums the
+// volume moment over the blocks (barrier_sum).
+//
+// One tile per block: the tile stays in shared memory for the whole solve
+// (each stage updates it in place, the stage-2 base values n^k live in
+// registers), so between stages only its halo comes from L2.  While thread 0
+// waits at the barrier, warps 1-6 compute the next stage's faces that read
+// only the tile's own cells and warp 7 reduces the output moments of output
+// steps (summed into the rows after the solve).  After the barrier warp 0
+// advances the block's private copy of the scalar chain (solute balance,
+// kinetics, CFL step, the next stage's coefficients - identical in every
+// block) and hands the halo over to warps 1-6 through a named barrier; they
+// load it and compute the faces that read it.  Face values are one FMA on the
+// Newton-Raphson quotient (psi_quot_fast).
 //
 // GB300 FP64 notes that shape this kernel: a warp-wide FP64 instruction
 // occupies the SM's FP64 pipe for ~16 cycles whatever its active lanes, and
 // a dependent FP64 operation takes ~65 cycles, so the scalar chain between
-// stages (the critical path on small grids) is kept short: with one tile per
-// block the moment weights of each thread's cells are computed once and kept
-// in registers, the cross-block sum costs no round trip beyond the barrier's
-// own, the stage coefficients are computed once per block, and the kinetics
-// use table-driven exp and log.
+// stages (the critical path on small grids) is kept short: the moment
+// weights of each thread's cells are computed once, the cross-block sum
+// costs no round trip beyond the barrier's own (fixed-point warp sums), the
+// stage coefficients are computed once per block from registers, the
+// temperature once per step, and the kinetics use table-driven exp and log.
 //
 // Every wait is bounded: a barrier that does not complete within about one
 // second sets PBE_ETIMEOUT and the kernel returns.
