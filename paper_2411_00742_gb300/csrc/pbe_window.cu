@@ -29,16 +29,32 @@ constexpr int kWNT = 256;             // threads per block
 constexpr int kWX = 128;              // columns held per block
 constexpr int kWOut = kWX - 3;        // columns written per block
 constexpr int kWG = kWNT / kWX;       // row groups of the L1 pass
-constexpr int kWR = 16;               // rows per row group
-constexpr int kWTI = kWG * kWR;       // rows per block
 constexpr int kWW = kWNT / 32;        // warps
-constexpr int kWRW = kWTI / kWW;      // rows per warp in the L2 pass
 constexpr int kWC = kWX / 32;         // columns per lane in the L2 pass
-constexpr size_t kWSmem = sizeof(double) * 2 * kWTI * kWX;   // input and L1 flux difference
+// rows per row group R (a block holds 2R rows, each warp 2R/8 of them in the
+// L2 pass): 12, 16 or 20, chosen per grid so that the blocks spread evenly
+// over the SMs (the kernel is bound by each SM's FP64 pipe)
+constexpr size_t win_smem(int R) { return sizeof(double) * 2 * (kWG * R) * kWX; }   // input and partial update
 
 static inline int wdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-int window_blocks2d(const Geom& g) { return wdiv(g.N2, kWOut) * wdiv(g.N1, kWTI); }
+static int window_blocks_r(const Geom& g, int R) { return wdiv(g.N2, kWOut) * wdiv(g.N1, kWG * R); }
+
+int window_blocks2d(const Geom& g) { return window_blocks_r(g, 16); }
+
+// the R whose block count divides most evenly into the SMs (blocks / (SMs x
+// the most blocks any SM runs)); ties keep 16
+static int window_rows(const Geom& g, int sms)
+{
+    int best = 16;
+    double best_bal = 0.0;
+    for (int R : {16, 12, 20}) {
+        const int nb = window_blocks_r(g, R);
+        const double bal = (double)nb / ((double)wdiv(nb, sms) * sms);
+        if (bal > best_bal + 1e-9) { best_bal = bal; best = R; }
+    }
+    return best;
+}
 
 bool use_window2d(const pbe_grid* g)
 {
@@ -46,11 +62,13 @@ bool use_window2d(const pbe_grid* g)
     return g->window_mode == 1 || window_blocks2d(g->geo) >= g->sms;
 }
 
-template <int STAGE>
+template <int STAGE, int kWR>
 __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__ in, const double* old, double* out,
                                                      Scal* S, Kin K, Geom g, double* part, const double* t_out,
                                                      double* rows, int use_cond, cudaGraphConditionalHandle hcond)
 {
+    constexpr int kWTI = kWG * kWR;       // rows per block
+    constexpr int kWRW = kWTI / kWW;      // rows per warp in the L2 pass
     extern __shared__ __align__(16) double wsm[];
     double (*ins)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm);              // stage input
     double (*f1s)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm + kWTI * kWX); // w (in + c1 (h_up - h_dn))
@@ -169,24 +187,43 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
     }
 }
 
+template <int R>
+static cudaError_t window_setup_r()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_stage2d_win<1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem(R));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage2d_win<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem(R));
+    return e;
+}
+
 cudaError_t window_setup()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_stage2d_win<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage2d_win<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem);
+    cudaError_t e = window_setup_r<12>();
+    if (e == cudaSuccess) e = window_setup_r<16>();
+    if (e == cudaSuccess) e = window_setup_r<20>();
     return e;
+}
+
+template <int R>
+static void launch_window_r(pbe_grid* g, int stage, int uc, cudaGraphConditionalHandle h)
+{
+    const Geom& geo = g->geo;
+    const dim3 grid(wdiv(geo.N2, kWOut), wdiv(geo.N1, kWG * R));
+    if (stage == 1)
+        k_stage2d_win<1, R><<<grid, kWNT, win_smem(R), g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo,
+                                                                   g->d_part, g->d_tout, g->d_rows, uc, h);
+    else
+        k_stage2d_win<2, R><<<grid, kWNT, win_smem(R), g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo,
+                                                                   g->d_part, g->d_tout, g->d_rows, uc, h);
 }
 
 cudaError_t launch_window_stage2d(pbe_grid* g, int stage, bool use_cond, cudaGraphConditionalHandle h)
 {
-    const Geom& geo = g->geo;
-    const dim3 grid(wdiv(geo.N2, kWOut), wdiv(geo.N1, kWTI));
     const int uc = use_cond ? 1 : 0;
-    if (stage == 1)
-        k_stage2d_win<1><<<grid, kWNT, kWSmem, g->stream>>>(g->d_n, g->d_n, g->d_n1, g->d_S, g->kin, geo, g->d_part,
-                                                           g->d_tout, g->d_rows, uc, h);
-    else
-        k_stage2d_win<2><<<grid, kWNT, kWSmem, g->stream>>>(g->d_n1, g->d_n, g->d_n, g->d_S, g->kin, geo, g->d_part,
-                                                           g->d_tout, g->d_rows, uc, h);
+    switch (window_rows(g->geo, g->sms)) {
+        case 12: launch_window_r<12>(g, stage, uc, h); break;
+        case 20: launch_window_r<20>(g, stage, uc, h); break;
+        default: launch_window_r<16>(g, stage, uc, h); break;
+    }
     return cudaGetLastError();
 }
 

@@ -296,6 +296,22 @@ def test_2d_window_kernel_chosen_on_large_grids():
     assert np.array_equal(out[-1], out[1])
 
 
+def test_2d_window_kernel_forty_row_blocks():
+    """768 x 768: the window kernel takes 40-row blocks there (the block count
+    that spreads best over the SMs); three output times against the oracle."""
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(768)
+    t_out = np.array(inst.t_out[:3])
+    want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, t_out)
+    g = P.Grid.from_problem(inst.problem)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, _ = g.solve(t_out)
+    n, _, _ = g.get_state()
+    g.close()
+    assert_rows_close(rows, want["rows"])
+    assert_n_close(n, want["n"])
+
+
 def test_window_mode_rejects_bad_values():
     import paper_2411_00742_gb300 as P
     inst = pi.config_2d(16)
