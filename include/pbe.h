@@ -265,7 +265,9 @@ pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double*
 /* Steps taken by each instance in the last pbe_batch_solve (host, count values). */
 pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps);
 
-/* Instances per block (1, 2, 4 or 8 warps, one instance per warp). */
+/* Instances per block (1, 2, 3, 4, 6 or 8 warps, one instance per warp; the
+ * shared memory of a block holds every warp's instance: PBE_EINVAL when that
+ * setting does not fit). */
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 
 /* Gradients of a loss of every instance's output rows (the batched form of

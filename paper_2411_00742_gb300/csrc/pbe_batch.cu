@@ -246,7 +246,9 @@ const void* batch_kernel(int wpb)
     switch (wpb) {
         case 1: return (const void*)k_batch1d<1>;
         case 2: return (const void*)k_batch1d<2>;
+        case 3: return (const void*)k_batch1d<3>;
         case 4: return (const void*)k_batch1d<4>;
+        case 6: return (const void*)k_batch1d<6>;
         case 8: return (const void*)k_batch1d<8>;
         default: return nullptr;
     }
@@ -529,7 +531,7 @@ pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps)
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block)
 {
     if (!b) return bfail(PBE_EINVAL, "null batch");
-    if (!batch_kernel(warps_per_block)) return bfail(PBE_EINVAL, "warps_per_block must be 1, 2, 4 or 8");
+    if (!batch_kernel(warps_per_block)) return bfail(PBE_EINVAL, "warps_per_block must be 1, 2, 3, 4, 6 or 8");
     if (!wpb_fits(b, warps_per_block))
         return bfail(PBE_EINVAL, "%d instances of up to %d cells do not fit in one block's shared memory",
                      warps_per_block, (b->np_max - 35));
@@ -583,7 +585,7 @@ pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int*
     BTRY(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_w = b->wpb;
-    const int cands[] = {1, 2, 4, 8};
+    const int cands[] = {1, 2, 3, 4, 6, 8};
     for (int w : cands) {
         if (!wpb_fits(b, w)) continue;
         float tsum = 0.0f;
