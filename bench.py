@@ -37,6 +37,9 @@ METRIC = "FVM cell-steps/s and adjoint grads/s, fused vs plain GPU, at stated FP
 # update (2 differences + 2 FMA = 6), volume moment (FMA = 2); stage 2 adds the
 # Runge-Kutta average (3): 18 + 21 = 39.
 FLOPS_PER_CELL_STEP_2D = 39
+# 1-D: per stage one face (5), the update (difference + FMA = 3) and the volume
+# moment (FMA = 2) = 10; two stages and the Runge-Kutta average (3): 23
+FLOPS_PER_CELL_STEP_1D = 23
 # the paper's split scheme (Eq. 3, two sweeps): per direction and cell one
 # difference, one sum, one division, one product, the face value (FMA = 2), the
 # flux difference and the update (FMA = 2) = 9; two directions and the volume
@@ -451,8 +454,9 @@ def run_gpu(args):
         return out
 
     def scaling_leg():
-        """Grid-size sweep of the 2-D workload (the paper's Fig. 3b analogue): full
-        solves at 512^2, 1024^2 and 2048^2 on the fused and plain paths."""
+        """Grid-size sweep (the paper's Fig. 3b analogue) on the fused and plain paths:
+        full 2-D solves at 512^2, 1024^2 and 2048^2, and 1-D solves of 2^18 and 2^20
+        cells over a 10 s horizon."""
         out = []
         for N in (512, 1024, 2048):
             sinst = pi.config_2d(N)
@@ -479,7 +483,35 @@ def run_gpu(args):
                 row[path] = {"ms_per_solve": 1e3 * t, "value": rate, "unit": "cell-steps/s",
                              "roofline_frac": FLOPS_PER_CELL_STEP_2D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
             out.append(row)
-        return out
+        out1 = []
+        # 1-D: 2^18 and 2^20 cells (dL ~ 4e-3 / 1e-3 um), 10 s from a supersaturated
+        # start (S = 1.5): every step CFL-limited
+        for N in (1 << 18, 1 << 20):
+            sinst = pi.config_1d_fine(N)
+            n0s = torch.as_tensor(sinst.n0).cuda()
+            row = {"grid": [N], "cells": N, "horizon_s": float(sinst.t_out[-1])}
+            for path in ("fused", "plain"):
+                g = P.Grid.from_problem(sinst.problem, stream=stream, path=path)
+                times, nsteps = [], 0
+                with torch.cuda.stream(stream):
+                    for it in range(3):
+                        g.set_state(n0s, sinst.C0, 0.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        _, nsteps = g.solve(sinst.t_out)
+                        e1.record(stream)
+                        e1.synchronize()
+                        if it >= 1:
+                            times.append(e0.elapsed_time(e1) * 1e-3)
+                g.close()
+                t = min(times)
+                rate = N * nsteps / t
+                row["steps"] = nsteps
+                row[path] = {"ms_per_solve": 1e3 * t, "value": rate, "unit": "cell-steps/s",
+                             "roofline_frac": FLOPS_PER_CELL_STEP_1D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
+            out1.append(row)
+        return out, out1
 
     clocks = ClockSampler(dev)
     if ws > 1:
@@ -493,7 +525,7 @@ def run_gpu(args):
     batch = batch_leg() if not args.no_batch else None
     adjoint, adjoint_cases = adjoint_leg() if not args.no_adjoint else (None, None)
     paper = paper_leg() if not args.no_paper else None
-    scaling = scaling_leg() if not args.no_scaling else None
+    scaling, scaling_1d = scaling_leg() if not args.no_scaling else (None, None)
     small_1d = small_1d_leg() if not args.no_scaling else None
 
     if ws > 1:
@@ -528,6 +560,7 @@ def run_gpu(args):
         "adjoint": adjoint,
         "paper_scheme": paper,
         "scaling_2d": scaling,
+        "scaling_1d": scaling_1d,
         # per timed fused solve: k_set_scalars, k_prologue, k_fused, k_fused_rows
         "gpu_launches": 4 * args.steps,
         "clocks": clk,

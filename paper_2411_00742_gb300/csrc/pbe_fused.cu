@@ -549,6 +549,11 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             double m[NM];
 #pragma unroll
             for (int k = 0; k < NM; ++k) m[k] = 0.0;
+            // several tiles a block, volume moment only: V / dA (2-D: / (dL1 dL2)) from
+            // per-tile bases - the thread's cells of a tile lie kFNT apart in 1-D and
+            // in one column, 8 rows apart, in 2-D (x2^2 sum_q x1 v per tile)
+            const bool vol_only = !ONE_TILE && !sc.moms;
+            double mv = 0.0;
             for (int t = blockIdx.x; t < ntiles; t += G) {
                 if (t != (int)blockIdx.x) {
                     fused_faces<NDIM, false, TI>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
@@ -556,6 +561,38 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 }
                 int i0, j0;
                 tile_origin<NDIM>(t, tiles_x, ti, i0, j0);
+                if (!ONE_TILE && vol_only) {
+                    static_assert(ONE_TILE || NDIM == 1 || (TI * kFTJ == 2 * kFNT && kFNT % kFTJ == 0),
+                                  "2-D multi-tile cells: two a thread, 8 rows apart in one column");
+                    double acc = 0.0;
+                    const double xb = NDIM == 1 ? (i0 + (int)threadIdx.x + 0.5) * g.d1
+                                                : (i0 + warp + 0.5) * g.d1;
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) {
+                        bool valid;
+                        int i, j;
+                        double& kq = keep[0];
+                        const double v = stage == 1
+                            ? cell_update<1, NDIM, ONE_TILE, TI>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j)
+                            : cell_update<2, NDIM, ONE_TILE, TI>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j);
+                        // invalid cells return 0 and add nothing
+                        if (NDIM == 1) {
+                            const double x = q == 0 ? xb : fma((double)(q * kFNT), g.d1, xb);
+                            acc = fma(x * x * x, v, acc);
+                        } else {
+                            const double x1 = q == 0 ? xb : fma((double)(q * (kFNT / kFTJ)), g.d1, xb);
+                            acc = fma(x1, v, acc);
+                        }
+                    }
+                    if (NDIM == 1) {
+                        mv += acc;
+                    } else {
+                        const double x2 = (j0 + (int)(threadIdx.x & 31) + 0.5) * g.d2;
+                        mv = fma(x2 * x2, acc, mv);
+                    }
+                    __syncthreads();
+                    continue;
+                }
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     bool valid;
@@ -593,6 +630,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 }
                 __syncthreads();
             }
+            if (vol_only) m[VIDX] = mv * (NDIM == 1 ? g.d1 : g.d1 * g.d2);
             const int row_here = s.out_idx;
             // only the volume moment is on the critical path; on output steps
             // the per-thread moments wait in shared memory and are reduced

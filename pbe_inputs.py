@@ -204,3 +204,14 @@ def paper_base_case(N1: int = 1200, N2: int | None = None, t_end: float = 3600.0
     n0 = paper_seed_2d(N1, N2)
     t_out = np.array([t_end]) if every is None else output_times(t_end, every)
     return Instance(p, n0, 8.0, 0.0, t_out)
+
+
+def config_1d_fine(N: int = 1 << 20, horizon: float = 10.0, every: float = 1.0, S0: float = 1.5) -> Instance:
+    """1-D problem of ``config_1d`` on a fine grid (up to 2^20 cells of ~1e-3 um on
+    [0, 1000] um), started supersaturated at S = S0 so that every step is CFL-limited
+    (dt ~ 0.5 dL / G): the grid-size sweep of the 1-D path.  Outputs every ``every``
+    seconds up to ``horizon``."""
+    inst = config_1d(N)
+    n_out = int(round(horizon / every))
+    t_out = np.array([k * every for k in range(n_out + 1)], dtype=np.float64)
+    return Instance(inst.problem, inst.n0, S0 * csat_at(40.0), 0.0, t_out)

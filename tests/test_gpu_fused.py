@@ -109,3 +109,19 @@ def test_fused_wait_limit_runs_out_and_context_survives():
     want = oracle.solve_instance(inst)
     assert steps == want["steps"]
     assert_rows_close(rows, want["rows"])
+
+
+@pytest.fixture(scope="module")
+def fine_1d():
+    # the largest 1-D grid (2^20 cells), supersaturated start: ~40 CFL-limited steps
+    inst = pi.config_1d_fine(1 << 20, horizon=1.0, every=0.5)
+    return inst, oracle.solve_instance(inst)
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_1d_max_cells(fine_1d, path):
+    inst, want = fine_1d
+    got = gpu_solve(inst, path=path)
+    assert got["steps"] == want["steps"] >= 30
+    assert_rows_close(got["rows"], want["rows"])
+    assert_n_close(got["n"], want["n"])
