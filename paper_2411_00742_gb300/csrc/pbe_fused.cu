@@ -302,7 +302,7 @@ __device__ __forceinline__ void moment_weights(int i, int j, const Geom& g, doub
 // only them (faces2d_interior) are done; load the halo and compute the faces
 // that read it.  The faces read the halo rows at the tile's columns and the
 // halo columns at its rows, never the corners.
-template <bool HALO_ONLY, int TI, class Sync>
+template <bool HALO_ONLY, int TI, bool MERGE = false, class Sync>
 __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, int ti, const Geom& g,
                                              Tile2DSmem<TI, kFTJ>& s, int tid, int nthr, Sync sync)
 {
@@ -346,6 +346,20 @@ __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, i
                 s.h2[r * (kFTJ + 1) + f] = face_value<true>(row[f], row[f + 1], row[f + 2]);
             }
         }
+    } else if (MERGE) {
+        // L1 and L2 faces in one index space, so that the ragged last pass falls
+        // on consecutive warps (different SM sub-partitions), not twice on warp 0
+        const int n1f = (ti + 1) * kFTJ;
+        for (int k = tid; k < n1f + ti * (kFTJ + 1); k += nthr) {
+            if (k < n1f) {
+                const int f = k / kFTJ, c = k - f * kFTJ;
+                s.h1[k] = face_value<true>(s.tile[f * W + c + 2], s.tile[(f + 1) * W + c + 2], s.tile[(f + 2) * W + c + 2]);
+            } else {
+                const int kk = k - n1f, r = kk / (kFTJ + 1), f = kk - r * (kFTJ + 1);
+                const double* row = s.tile + (r + 2) * W;
+                s.h2[kk] = face_value<true>(row[f], row[f + 1], row[f + 2]);
+            }
+        }
     } else {
         for (int k = tid; k < (ti + 1) * kFTJ; k += nthr) {
             const int f = k / kFTJ, c = k - f * kFTJ;
@@ -380,7 +394,7 @@ __device__ __forceinline__ void faces2d_interior(int ti, Tile2DSmem<TI, kFTJ>& s
     }
 }
 
-template <int NDIM, bool HALO_ONLY, int TI, class Sync>
+template <int NDIM, bool HALO_ONLY, int TI, bool MERGE = false, class Sync>
 __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x, int ti, const Geom& g,
                                             FusedSmem<NDIM, TI>& sm, int tid, int nthr, Sync sync)
 {
@@ -402,7 +416,7 @@ __device__ __forceinline__ void fused_faces(const double* in, int t, int tiles_x
             faces1d<true, true, kFT1>(in, i0, g, sm.tile, sm.h, tid, nthr, sync);
         }
     } else {
-        faces2d_rows<HALO_ONLY, TI>(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
+        faces2d_rows<HALO_ONLY, TI, MERGE>(in, i0, j0, ti, g, sm.t, tid, nthr, sync);
     }
 }
 
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
         }
     }
 
-    fused_faces<NDIM, false, TI>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
+    fused_faces<NDIM, false, TI, !ONE_TILE>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
     __syncthreads();
     for (;;) {
         // temperature and solubility at the end of this step: both kinetics of
@@ -556,7 +570,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             double mv = 0.0;
             for (int t = blockIdx.x; t < ntiles; t += G) {
                 if (t != (int)blockIdx.x) {
-                    fused_faces<NDIM, false, TI>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
+                    fused_faces<NDIM, false, TI, !ONE_TILE>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
                     __syncthreads();
                 }
                 int i0, j0;
@@ -668,7 +682,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (ONE_TILE) fused_faces_interior<NDIM, TI>(ti, sm, threadIdx.x - 32, 32 * kFaceWarps);
                 HaloGo::wait();
                 if (!fail)
-                    fused_faces<NDIM, ONE_TILE, TI>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm,
+                    fused_faces<NDIM, ONE_TILE, TI, !ONE_TILE>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm,
                                                     threadIdx.x - 32, 32 * kFaceWarps, GroupSync());
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one
