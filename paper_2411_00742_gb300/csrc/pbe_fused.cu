@@ -548,7 +548,14 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
         }
     }
 
-    fused_faces<NDIM, false, TI, !ONE_TILE>(n, blockIdx.x, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
+    // this block's tiles: blockIdx.x (if below ntiles) with ONE_TILE; otherwise
+    // an even contiguous share, so that every SM gets ntiles / SMs tiles to within one
+    // whichever way consecutive blocks are placed on the SMs (round-robin strides
+    // gave the first blocks one tile more, and those share SMs)
+    const int t_first = ONE_TILE ? (int)blockIdx.x : (int)(((long long)blockIdx.x * ntiles) / G);
+    const int t_end = ONE_TILE ? ntiles : (int)(((long long)(blockIdx.x + 1) * ntiles) / G);
+    const int t_step = ONE_TILE ? G : 1;
+    fused_faces<NDIM, false, TI, !ONE_TILE>(n, t_first, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
     __syncthreads();
     for (;;) {
         // temperature and solubility at the end of this step: both kinetics of
@@ -568,8 +575,8 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             // in one column, 8 rows apart, in 2-D (x2^2 sum_q x1 v per tile)
             const bool vol_only = !ONE_TILE && !sc.moms;
             double mv = 0.0;
-            for (int t = blockIdx.x; t < ntiles; t += G) {
-                if (t != (int)blockIdx.x) {
+            for (int t = t_first; t < t_end; t += t_step) {
+                if (t != t_first) {
                     fused_faces<NDIM, false, TI, !ONE_TILE>(in, t, tiles_x, ti, g, sm, threadIdx.x, kFNT, BlockSync());
                     __syncthreads();
                 }
@@ -682,7 +689,7 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (ONE_TILE) fused_faces_interior<NDIM, TI>(ti, sm, threadIdx.x - 32, 32 * kFaceWarps);
                 HaloGo::wait();
                 if (!fail)
-                    fused_faces<NDIM, ONE_TILE, TI, !ONE_TILE>(stage == 1 ? n1 : n, blockIdx.x, tiles_x, ti, g, sm,
+                    fused_faces<NDIM, ONE_TILE, TI, !ONE_TILE>(stage == 1 ? n1 : n, t_first, tiles_x, ti, g, sm,
                                                     threadIdx.x - 32, 32 * kFaceWarps, GroupSync());
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one

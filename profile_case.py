@@ -4,10 +4,12 @@ self-contained program to put under a profiler (ncu) or a timer.
     python profile_case.py fused 256
     python profile_case.py plain 4096 --window 1 --steps 3
     python profile_case.py paper 6000 --steps 3
+    python profile_case.py fused 1048576 --ndim 1
 
 Workloads: ``fused``/``plain`` run the 2-D size-and-shape problem on an N x N
 (or N1 x N2) grid (``pbe_inputs.config_2d``); ``paper`` runs the paper's base
-case at N x N/2 bins (``pbe_inputs.paper_base_case``).  ``--outputs K`` keeps
+case at N x N/2 bins (``pbe_inputs.paper_base_case``); ``--ndim 1`` runs the 1-D
+fine-grid problem of N cells (``pbe_inputs.config_1d_fine``).  ``--outputs K`` keeps
 the first K output times (a shorter solve); every solve starts from the same
 seeded state.  ``--steps K`` runs K single steps (``Grid.step``) instead of
 solves: the plain path then launches its stage kernels one by one, outside
@@ -27,6 +29,7 @@ def main(argv=None):
     ap.add_argument("path", choices=["fused", "plain", "paper"])
     ap.add_argument("N1", type=int)
     ap.add_argument("N2", type=int, nargs="?")
+    ap.add_argument("--ndim", type=int, default=2, choices=[1, 2], help="1: the 1-D fine-grid problem")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--outputs", type=int, default=0, help="keep the first K output times (0: all)")
     ap.add_argument("--steps", type=int, default=0, help="run K single steps instead of solves")
@@ -43,6 +46,9 @@ def main(argv=None):
     if args.path == "paper":
         inst = pi.paper_base_case(args.N1)
         path = "plain"
+    elif args.ndim == 1:
+        inst = pi.config_1d_fine(args.N1)
+        path = args.path
     else:
         inst = pi.config_2d(args.N1, args.N2)
         path = args.path
