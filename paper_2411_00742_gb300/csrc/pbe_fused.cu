@@ -2,7 +2,8 @@
 // whole solve.  Each block owns a fixed set of tiles (2-D: tiles of ti x 32
 // cells, ti chosen so that every SM gets at most one tile when the grid
 // allows: up to 16 rows in static shared memory, up to 64 rows in dynamic
-// shared memory; larger grids loop over 16 x 32 tiles); the two stages of
+// shared memory; larger grids loop over 16 x 32 tiles, 1-D over 1024-cell
+// tiles, each block an even contiguous share of them); the two stages of
 // every step are separated by a device-wide barrier that also sums the
 // volume moment over the blocks (barrier_sum).
 //
@@ -347,8 +348,8 @@ __device__ __forceinline__ void faces2d_rows(const double* in, int i0, int j0, i
             }
         }
     } else if (MERGE) {
-        // L1 and L2 faces in one index space, so that the ragged last pass falls
-        // on consecutive warps (different SM sub-partitions), not twice on warp 0
+        // L1 and L2 faces in one index space, so that the ragged last pass runs on
+        // two warps at once rather than twice in a row on warp 0
         const int n1f = (ti + 1) * kFTJ;
         for (int k = tid; k < n1f + ti * (kFTJ + 1); k += nthr) {
             if (k < n1f) {
