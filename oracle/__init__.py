@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("mlp", ctypes.POINTER(ctypes.c_double)),
                 ("scheme", ctypes.c_int), ("growth_form", ctypes.c_int), ("solubility_form", ctypes.c_int),
-                ("ea1", ctypes.c_double), ("ea2", ctypes.c_double)]
+                ("ea1", ctypes.c_double), ("ea2", ctypes.c_double),
+                ("poly", ctypes.POINTER(ctypes.c_double)), ("npoly", ctypes.c_int)]
 
 
 _lib = None
@@ -92,13 +93,22 @@ def _load():
                                      ctypes.c_double, _D, ctypes.c_int, _D, _D]
         lib.orc_vjp.restype = ctypes.c_long
         lib.orc_vjp.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
-                                _D, _D, _D, _D, _D]
+                                _D, _D, _D, _D, _D, _D]
         _lib = lib
     return _lib
 
 
 MLP_NW = 64 * 3 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # learned closure weight count
 _mlp_keep = {}
+
+
+def _poly(problem) -> np.ndarray:
+    """Polynomial growth coefficients of Eq. 6 (growth_form 2): ndim rows of K,
+    a_m1 .. a_mK of G_m = sum_k a_mk (S - 1)^k."""
+    a = np.ascontiguousarray(getattr(problem, "poly", ()), dtype=np.float64).reshape(-1)
+    if getattr(problem, "growth_form", 0) == 2:
+        assert a.size > 0 and a.size % problem.ndim == 0, "poly holds ndim x K coefficients"
+    return a
 
 
 def params(problem, mlp=None) -> Params:
@@ -121,7 +131,11 @@ def params(problem, mlp=None) -> Params:
                float(p.T0), float(p.T1), float(p.t_cool), float(p.kappa), float(p.cfl), mp,
                int(getattr(p, "scheme", 0)), int(getattr(p, "growth_form", 0)), int(getattr(p, "solubility_form", 0)),
                float(getattr(p, "ea", (0.0, 0.0))[0]), float(getattr(p, "ea", (0.0, 0.0))[1]))
-    P._keep = arr if mlp is not None else None
+    poly = _poly(p)
+    if poly.size:
+        P.poly = poly.ctypes.data_as(_D)
+        P.npoly = poly.size // p.ndim
+    P._keep = (arr if mlp is not None else None, poly)
     return P
 
 
@@ -221,8 +235,8 @@ def solve(problem, n0, C0: float, t0: float, t_out, mlp=None):
 
 def solve_cs(problem, which: int, n0, C0: float, t0: float, t_out, h: float = 1e-30, mlp=None):
     """Complex-step derivative of all output rows w.r.t. kinetic parameter
-    ``which`` (0..5 = kg1, g1, kg2, g2, kb, b; 6 + k = closure weight k).
-    Returns (rows, drows)."""
+    ``which`` (0..5 = kg1, g1, kg2, g2, kb, b; 6 + k = closure weight k, or
+    polynomial growth coefficient k with growth_form 2).  Returns (rows, drows)."""
     t_out = np.ascontiguousarray(t_out, dtype=np.float64)
     P = params(problem, mlp)
     n0 = np.ascontiguousarray(n0, dtype=np.float64)
@@ -239,7 +253,8 @@ def solve_instance(inst):
 
 def vjp(problem, n0, C0: float, t0: float, t_out, drows, mlp=None):
     """Hand-written discrete adjoint: dL/dtheta (kg1, g1, kg2, g2, kb, b), dL/dn0, dL/dC0
-    (and dL/dweights of the learned closure when mlp is given) for seeds
+    (and dL/dweights of the learned closure when mlp is given, or dL/d(polynomial
+    growth coefficients) with growth_form 2, as a fourth result) for seeds
     drows = dL/d(rows) (time column ignored)."""
     t_out = np.ascontiguousarray(t_out, dtype=np.float64)
     drows = np.ascontiguousarray(drows, dtype=np.float64)
@@ -250,10 +265,15 @@ def vjp(problem, n0, C0: float, t0: float, t_out, drows, mlp=None):
     dn0 = np.zeros_like(n0)
     dC0 = np.zeros(1)
     dW = np.zeros(MLP_NW)
-    _load().orc_vjp(ctypes.byref(P), _ptr(n0), float(C0), float(t0), _ptr(t_out), len(t_out),
-                    _ptr(drows), _ptr(dth), _ptr(dn0), _ptr(dC0), _ptr(dW))
+    dA = np.zeros(max(_poly(problem).size, 1))
+    steps = _load().orc_vjp(ctypes.byref(P), _ptr(n0), float(C0), float(t0), _ptr(t_out), len(t_out),
+                            _ptr(drows), _ptr(dth), _ptr(dn0), _ptr(dC0), _ptr(dW), _ptr(dA))
+    if steps < 0:
+        raise ValueError("no adjoint for this scheme / kinetics form")
     if mlp is not None:
         return dth, dn0, dC0[0], dW
+    if getattr(problem, "growth_form", 0) == 2:
+        return dth, dn0, dC0[0], dA
     return dth, dn0, dC0[0]
 
 

@@ -45,6 +45,9 @@ typedef struct {
     int growth_form;      /* 0: G = kg s^g; 1: Arrhenius form of Appendix A, G = kg exp(-ea/(T+273.15)) s^g */
     int solubility_form;  /* 0: c* = cs0 + cs1 T + cs2 T^2; 1: c* = cs0 exp(cs1 T) (Appendix A) */
     double ea1, ea2;      /* activation temperatures (K) of the Arrhenius form */
+    const double* poly;   /* growth_form 2 (Eq. 6): G_m = sum_{k=1..npoly} poly[m npoly + k - 1] (S - 1)^k,
+                             m = 0 (L1) and, in 2-D, 1 (L2) */
+    int npoly;
 } orc_params;
 
 /* Learned kinetics closure (the empirical hybrid model of Sec. 4.2: a network
@@ -100,7 +103,7 @@ static int ncols(const orc_params* p) { return p->ndim == 1 ? 6 : 12; }
 
 static ctx_r make_ctx_r(const orc_params* p)
 {
-    ctx_r c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b, p->mlp};
+    ctx_r c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b, p->mlp, p->poly};
     return c;
 }
 
@@ -180,21 +183,27 @@ long orc_solve(const orc_params* p, double* n, double C, double t,
 }
 
 /* Complex-step derivative of every output row with respect to one kinetic
- * parameter (index 0..5 = kg1, g1, kg2, g2, kb, b): the parameter is given
- * the imaginary part h and d(row)/d(param) = Im(row) / h.  rows_re gets the
- * real part, drows the derivative.  Returns the number of steps. */
+ * parameter (index 0..5 = kg1, g1, kg2, g2, kb, b; from 6 on, the closure
+ * weights or, with growth_form 2, the polynomial coefficients): the parameter
+ * is given the imaginary part h and d(row)/d(param) = Im(row) / h.  rows_re
+ * gets the real part, drows the derivative.  Returns the number of steps. */
 long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, double C0, double t0,
                   const double* t_out, int n_out, double* rows_re, double* drows)
 {
     size_t nc = ncells(p);
     int ncol = ncols(p);
-    ctx_c c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b, NULL};
+    ctx_c c = {p, p->kg1, p->g1, p->kg2, p->g2, p->kb, p->b, NULL, NULL};
     double complex* slot[6] = {&c.kg1, &c.g1, &c.kg2, &c.g2, &c.kb, &c.b};
     double complex* wc = NULL;
     if (p->mlp) {
         wc = (double complex*)malloc(MLP_NW * sizeof(double complex));
         for (int k = 0; k < MLP_NW; ++k) wc[k] = p->mlp[k];
         c.w = wc;
+    } else if (p->growth_form == 2) {
+        int na = p->npoly * p->ndim;
+        wc = (double complex*)malloc((na > 0 ? na : 1) * sizeof(double complex));
+        for (int k = 0; k < na; ++k) wc[k] = p->poly[k];
+        c.a = wc;
     }
     if (which < 6) *slot[which] += I * h;
     else wc[which - 6] += I * h;
@@ -322,9 +331,10 @@ static void add_moment_seeds(const orc_params* p, const double* seed, double* la
     }
 }
 
-/* adjoint of (G1, G2, B) = kinetics(C, t): accumulates into *lC, *lt, lth[6] */
+/* adjoint of (G1, G2, B) = kinetics(C, t): accumulates into *lC, *lt, lth[6]
+ * and, for the polynomial growth law of Eq. 6, lpoly[ndim * npoly] */
 static void kinetics_adjoint(const orc_params* p, double C, double t, double lG1, double lG2, double lB,
-                             double* lC, double* lt, double* lth)
+                             double* lC, double* lt, double* lth, double* lpoly)
 {
     if (p->fixed_kinetics) {
         lth[0] += lG1;
@@ -339,6 +349,27 @@ static void kinetics_adjoint(const orc_params* p, double C, double t, double lG1
     double s = C / cs - 1.0;
     if (!(s > 0.0)) return;
     double ls = log(s);
+    if (p->growth_form == 2) {
+        /* G_m = sum_k a_mk s^k: dG_m/da_mk = s^k, dG_m/ds = sum_k k a_mk s^(k-1) */
+        double sb = pow(s, p->b), B = p->kb * sb;
+        double lsum = lB * p->b * p->kb * pow(s, p->b - 1.0);
+        lth[4] += lB * sb;
+        lth[5] += lB * B * ls;
+        for (int m = 0; m < p->ndim; ++m) {
+            const double lG = m == 0 ? lG1 : lG2;
+            const double* a = p->poly + (size_t)m * p->npoly;
+            double skm1 = 1.0, dG = 0.0;  /* s^(k-1) */
+            for (int k = 1; k <= p->npoly; ++k) {
+                lpoly[(size_t)m * p->npoly + k - 1] += lG * (skm1 * s);
+                dG += k * a[k - 1] * skm1;
+                skm1 *= s;
+            }
+            lsum += lG * dG;
+        }
+        *lC += lsum / cs;
+        *lt += lsum * (-C * dcs / (cs * cs)) * dTdt;
+        return;
+    }
     double s1 = pow(s, p->g1), sb = pow(s, p->b);
     double G1 = p->kg1 * s1, B = p->kb * sb;
     double lsum = lG1 * p->g1 * p->kg1 * pow(s, p->g1 - 1.0) + lB * p->b * p->kb * pow(s, p->b - 1.0);
@@ -440,11 +471,15 @@ static void mlp_kinetics_adjoint(const orc_params* p, double C, double t, double
 
 /* Vector-Jacobian product of a solve.  drows[n_out * ncol]: dL/d(row entries)
  * (the time column is ignored).  Outputs dL/dtheta[6] (kg1, g1, kg2, g2, kb, b),
- * and optionally dL/dn0 (ncell) and dL/dC0.  Returns the number of steps. */
+ * and optionally dL/dn0 (ncell) and dL/dC0; dmlp accumulates dL/d(closure
+ * weights), dpoly dL/d(polynomial growth coefficients, growth_form 2; the
+ * growth entries of dtheta are then 0).  Returns the number of steps. */
 long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const double* t_out, int n_out,
-             const double* drows, double* dtheta, double* dn0, double* dC0, double* dmlp)
+             const double* drows, double* dtheta, double* dn0, double* dC0, double* dmlp, double* dpoly)
 {
-    if (p->scheme != 0 || p->growth_form != 0 || p->solubility_form != 0) return -1;  /* adjoint of the SSP-RK2 power-law form only */
+    /* adjoint of the SSP-RK2 scheme with the power-law or polynomial growth law only */
+    if (p->scheme != 0 || (p->growth_form != 0 && p->growth_form != 2) || p->solubility_form != 0) return -1;
+    if (p->growth_form == 2 && (p->mlp || !dpoly)) return -1;
     size_t nc = ncells(p);
     int ncol = ncols(p), nm = ncol - 2;
     double area = (p->ndim == 1) ? p->lmax1 / p->n1 : (p->lmax1 / p->n1) * (p->lmax2 / p->n2);
@@ -506,7 +541,7 @@ long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const 
             double m0 = mu0_r(p, n1), V1 = volume_r(p, n1);
             for (size_t q = 0; q < nc; ++q) lam1[q] += (lr / m0) * w[q] - (lr * V1 / (m0 * m0)) * area;
         } else {
-            kinetics_adjoint(p, r->C1, r->t_new, lG1, lG2, lB, &lC1, &ltn, lth);
+            kinetics_adjoint(p, r->C1, r->t_new, lG1, lG2, lB, &lC1, &ltn, lth, dpoly);
         }
         /* C1 = C - kappa (V1 - V0) */
         lCp += lC1;
@@ -538,7 +573,7 @@ long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const 
             double m0 = mu0_r(p, nk), V0 = volume_r(p, nk);
             for (size_t q = 0; q < nc; ++q) lamp[q] += (lr / m0) * w[q] - (lr * V0 / (m0 * m0)) * area;
         } else {
-            kinetics_adjoint(p, r->C, r->t, lG1, lG2, lB, &lCp, &ltp, lth);
+            kinetics_adjoint(p, r->C, r->t, lG1, lG2, lB, &lCp, &ltp, lth, dpoly);
         }
         memcpy(lam, lamp, nc * sizeof(double));
         lC = lCp;

@@ -31,6 +31,7 @@ typedef struct {
     const orc_params* p;
     SCALAR kg1, g1, kg2, g2, kb, b; /* kinetic parameters (differentiable) */
     const SCALAR* w;                /* learned closure weights, NULL unless p->mlp */
+    const SCALAR* a;                /* polynomial growth coefficients (growth_form 2, differentiable) */
 } SFX(ctx);
 
 static SCALAR SFX(silu)(SCALAR z) { return z / (1.0 + SEXP(-z)); }
@@ -108,6 +109,20 @@ static void SFX(kinetics)(const SFX(ctx)* c, SCALAR C, SCALAR t, SCALAR ratio,
     SCALAR s = C / csat - 1.0;
     if (!(RE(s) > 0.0)) {
         *G1 = 0.0; *G2 = 0.0; *B = 0.0;
+        return;
+    }
+    if (p->growth_form == 2) {  /* Eq. 6: G_m = a_m1 (S-1) + a_m2 (S-1)^2 + ... + a_mK (S-1)^K */
+        SCALAR G[2] = {0.0, 0.0};
+        for (int m = 0; m < p->ndim; ++m) {
+            SCALAR sk = s;  /* (S-1)^k */
+            for (int k = 1; k <= p->npoly; ++k) {
+                G[m] += c->a[m * p->npoly + k - 1] * sk;
+                sk *= s;
+            }
+        }
+        *G1 = G[0];
+        *G2 = G[1];
+        *B = c->kb * SPOW(s, c->b);
         return;
     }
     SCALAR a1 = 1.0, a2 = 1.0;

@@ -46,9 +46,10 @@ class Problem:
     cfl: float = 0.5
     fixed_kinetics: bool = False
     scheme: int = 0            # 0: SSP-RK2 unsplit; 1: Eq. 3 with Godunov splitting
-    growth_form: int = 0       # 0: kg s^g; 1: Arrhenius kg exp(-ea/(T+273.15)) s^g
+    growth_form: int = 0       # 0: kg s^g; 1: Arrhenius kg exp(-ea/(T+273.15)) s^g; 2: polynomial (Eq. 6)
     solubility_form: int = 0   # 0: polynomial csat; 1: csat[0] exp(csat[1] T)
     ea: tuple = (0.0, 0.0)     # activation temperatures of the Arrhenius form (K)
+    poly: tuple = ()           # growth_form 2: ndim x K coefficients, a_m1 .. a_mK of G_m = sum_k a_mk s^k
 
     @property
     def ncell(self) -> int:
@@ -215,3 +216,16 @@ def config_1d_fine(N: int = 1 << 20, horizon: float = 10.0, every: float = 1.0, 
     n_out = int(round(horizon / every))
     t_out = np.array([k * every for k in range(n_out + 1)], dtype=np.float64)
     return Instance(inst.problem, inst.n0, S0 * csat_at(40.0), 0.0, t_out)
+
+
+def poly_growth(problem: Problem, K: int, seed: int = 2414) -> Problem:
+    """The problem with the polynomial growth law of Eq. 6 (growth_form 2) in place
+    of the power law: K non-negative coefficients per growth direction,
+    a_mk = kg_m u_mk 2^-(k-1) with u_mk ~ U[0.5, 1.5] (seeded), so that the
+    leading term is of the size of the power-law rate and the series decays."""
+    rng = np.random.default_rng(seed)
+    a = []
+    for m in range(problem.ndim):
+        u = rng.uniform(0.5, 1.5, size=K)
+        a.extend(float(problem.kg[m] * u[k] * 0.5 ** k) for k in range(K))
+    return dataclasses.replace(problem, growth_form=2, poly=tuple(a))
