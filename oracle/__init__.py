@@ -242,8 +242,10 @@ def solve_cs(problem, which: int, n0, C0: float, t0: float, t_out, h: float = 1e
     n0 = np.ascontiguousarray(n0, dtype=np.float64)
     rows = np.zeros((len(t_out), ncols(problem)))
     drows = np.zeros_like(rows)
-    _load().orc_solve_cs(ctypes.byref(P), int(which), float(h), _ptr(n0), float(C0), float(t0),
-                         _ptr(t_out), len(t_out), _ptr(rows), _ptr(drows))
+    steps = _load().orc_solve_cs(ctypes.byref(P), int(which), float(h), _ptr(n0), float(C0), float(t0),
+                                 _ptr(t_out), len(t_out), _ptr(rows), _ptr(drows))
+    if steps < 0:
+        raise ValueError(f"no differentiable parameter {which}")
     return rows, drows
 
 

@@ -205,6 +205,11 @@ long orc_solve_cs(const orc_params* p, int which, double h, const double* n0, do
         for (int k = 0; k < na; ++k) wc[k] = p->poly[k];
         c.a = wc;
     }
+    int nw = p->mlp ? MLP_NW : (p->growth_form == 2 ? p->npoly * p->ndim : 0);
+    if (which < 0 || which >= 6 + nw) {
+        free(wc);
+        return -1;
+    }
     if (which < 6) *slot[which] += I * h;
     else wc[which - 6] += I * h;
     double complex* n = (double complex*)malloc(nc * sizeof(double complex));
