@@ -571,9 +571,10 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             double m[NM];
 #pragma unroll
             for (int k = 0; k < NM; ++k) m[k] = 0.0;
-            // several tiles a block, volume moment only: V / dA (2-D: / (dL1 dL2)) from
-            // per-tile bases - the thread's cells of a tile lie kFNT apart in 1-D and
-            // in one column, 8 rows apart, in 2-D (x2^2 sum_q x1 v per tile)
+            // several tiles a block, volume moment only (no output step): mv = V / dL
+            // (1-D: sum x^3 v) or V / (dL1 dL2) (2-D: sum over tiles of x2^2 sum_q x1 v),
+            // from per-tile bases - the thread's cells of a tile lie kFNT apart in 1-D
+            // and in one column, 8 rows apart, in 2-D
             const bool vol_only = !ONE_TILE && !sc.moms;
             double mv = 0.0;
             for (int t = t_first; t < t_end; t += t_step) {
