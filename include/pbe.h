@@ -156,6 +156,7 @@ pbe_status pbe_step(pbe_grid* g, double t_limit, double* dt_taken);
  * mu10, mu01, mu20, mu11, mu02, mu30, mu21, mu12, mu03, C), in `mem`
  * memory.  *steps (may be NULL) receives the number of steps taken.
  * Moments follow the SI definition of mu_pq by the midpoint rule.
+ * Synchronizes the grid's stream (the status and step count are read back).
  * Errors: PBE_EINVAL (times), PBE_ESTATE (no state/kinetics),
  * PBE_ENONFINITE, PBE_ETIMEOUT (more than the step budget), PBE_ECUDA. */
 pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, int mem,
@@ -313,8 +314,9 @@ pbe_status pbe_set_wait_limit(pbe_grid* g, double seconds);
  * graph or its chunked step launches) - the prologue, the output-row kernel
  * and the copies stay outside.  pbe_kernel_time writes that duration of the
  * last solve in milliseconds to the HOST double `ms` (-1 when timing was off
- * or the solve failed).  Enabling creates the two events; it does not
- * synchronize. */
+ * or the solve failed); pbe_solve has returned by then, so it does not wait.
+ * Enabling creates the two events; it does not synchronize.  Errors:
+ * PBE_EINVAL (null grid or `ms`), PBE_ECUDA (event creation). */
 pbe_status pbe_set_timing(pbe_grid* g, int enable);
 pbe_status pbe_kernel_time(pbe_grid* g, double* ms);
 
