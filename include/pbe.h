@@ -212,11 +212,16 @@ pbe_status pbe_set_max_steps(pbe_grid* g, int64_t max_steps);
  *   rows     DEVICE memory, n_out rows of 6 doubles (t, mu0..mu3, C)
  *   steps    optional (host) number of steps taken
  *   stream   cudaStream_t the work is ordered on; the call synchronizes it
+ * The kinetics pass the same checks as in pbe_set_kinetics (PBE_EINVAL for a
+ * non-finite parameter or a negative rate prefactor).  The whole solve runs
+ * in ONE thread block with a fixed budget of 1e6 steps (PBE_ETIMEOUT beyond
+ * it): on the largest grid one call can hold one SM for minutes.
  * The first call on each device looks up the working array's device address
- * (make that first call before any stream capture).  All calls share the
- * working array: calls that overlap on a GPU race and must be serialized by
- * the caller.  It calls no cudaMalloc/cudaFree and no allocating library
- * routine. */
+ * and keeps it for the life of the process (make that first call before any
+ * stream capture; a cudaDeviceReset after it is not supported, because the
+ * kept address would then be stale).  All calls share the working array:
+ * calls that overlap on a GPU race and must be serialized by the caller.  It
+ * calls no cudaMalloc/cudaFree and no allocating library routine. */
 pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells, double lmax, double* n, double C0,
                                 double t0, const double* t_out, int n_out, double* rows, int64_t* steps,
                                 void* stream);

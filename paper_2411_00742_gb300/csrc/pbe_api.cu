@@ -181,6 +181,22 @@ pbe_status run_solve(pbe_grid* g, int n_out)
 }
 }  // namespace
 
+// The value checks every entry point applies to a pbe_kinetics: every
+// parameter finite, rate prefactors not negative (a negative growth rate
+// would reverse the upwind direction the stencil assumes), cfl in (0, 1],
+// t_cool > 0.  Sets the thread's error message on failure.
+pbe_status pbe::check_kinetic_values(const pbe_kinetics* k)
+{
+    const double vals[] = {k->kg[0], k->kg[1], k->g[0], k->g[1], k->kb, k->b, k->csat[0], k->csat[1],
+                           k->csat[2], k->T0, k->T1, k->t_cool, k->kappa, k->cfl, k->ea[0], k->ea[1]};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(PBE_EINVAL, "non-finite kinetic parameter");
+    if (k->kg[0] < 0 || k->kg[1] < 0 || k->kb < 0) return fail(PBE_EINVAL, "negative rate prefactor");
+    if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
+    if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
+    return PBE_OK;
+}
+
 extern "C" {
 
 const char* pbe_last_error(void) { return g_err; }
@@ -325,11 +341,8 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
         return fail(PBE_EINVAL, "unknown growth or solubility form");
     if (k->scheme == PBE_SCHEME_PAPER && k->kind == PBE_KINETICS_MLP)
         return fail(PBE_EINVAL, "the learned closure runs with the SSP-RK2 scheme");
-    const double vals[] = {k->kg[0], k->kg[1], k->g[0], k->g[1], k->kb, k->b, k->csat[0], k->csat[1],
-                           k->csat[2], k->T0, k->T1, k->t_cool, k->kappa, k->cfl};
-    for (double v : vals)
-        if (!std::isfinite(v)) return fail(PBE_EINVAL, "non-finite kinetic parameter");
-    if (k->kg[0] < 0 || k->kg[1] < 0 || k->kb < 0) return fail(PBE_EINVAL, "negative rate prefactor");
+    pbe_status pst = pbe::check_kinetic_values(k);
+    if (pst != PBE_OK) return pst;
     pbe::Kin K;
     K.kind = k->kind;
     K.ndim = g->geo.ndim;

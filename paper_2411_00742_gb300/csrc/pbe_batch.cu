@@ -392,6 +392,10 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
             delete b;
             return bfail(PBE_EINVAL, "instance %d: invalid parameters", i);
         }
+        if (check_kinetic_values(k) != PBE_OK) {
+            delete b;
+            return bfail(PBE_EINVAL, "instance %d: %s", i, pbe_last_error());
+        }
         BatchInst& d = h[i];
         memset(&d, 0, sizeof(d));
         d.K.kind = k->kind; d.K.ndim = 1;

@@ -87,6 +87,10 @@ cudaError_t launch_paper_step2d(pbe_grid* g, bool use_cond, cudaGraphConditional
 cudaError_t launch_paper_finish(pbe_grid* g);
 int paper_blocks2d(const Geom& g);
 
+// Value checks of a pbe_kinetics shared by every entry point that takes one
+// (pbe_api.cu): PBE_OK, or PBE_EINVAL with the error message set.
+pbe_status check_kinetic_values(const pbe_kinetics* k);
+
 // Fused path (pbe_fused.cu)
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out);
 bool fused_supported(const pbe_grid* g);

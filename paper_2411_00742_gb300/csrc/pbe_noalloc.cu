@@ -148,8 +148,7 @@ extern "C" pbe_status pbe_solve_1d_noalloc(const pbe_kinetics* k, int64_t ncells
     if (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED) return fail(PBE_EINVAL, "unknown kinetics kind");
     if (k->scheme != PBE_SCHEME_SSPRK2 || k->growth_form != 0 || k->solubility_form != 0)
         return fail(PBE_EINVAL, "this entry point runs the SSP-RK2 scheme with power-law kinetics");
-    if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
-    if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
+    if (check_kinetic_values(k) != PBE_OK) return PBE_EINVAL;   // message set by the check
     if (!(t_out[0] >= t0) || !std::isfinite(t_out[0])) return fail(PBE_EINVAL, "t_out[0] precedes t0");
     for (int j = 1; j < n_out; ++j)
         if (!(t_out[j] > t_out[j - 1]) || !std::isfinite(t_out[j]))

@@ -69,3 +69,58 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
                                   ctypes.c_void_p(rows.data_ptr()), None, None)
     assert st == _lib.PBE_EINVAL
     assert b"65536" in lib.pbe_last_error()
+
+
+def _call(lib, kin, N, n_dev, t_out, rows, C0=0.252, t0=0.0):
+    return lib.pbe_solve_1d_noalloc(ctypes.byref(kin), N, 1000.0, ctypes.c_void_p(n_dev.data_ptr()), C0, t0,
+                                    t_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t_out),
+                                    ctypes.c_void_p(rows.data_ptr()), None, None)
+
+
+def test_noalloc_rejects_bad_kinetics_and_too_many_outputs():
+    """The same value checks as pbe_set_kinetics (a NaN end temperature, a
+    negative growth prefactor), and the 4096-row limit of the working array."""
+    import torch
+    import paper_2411_00742_gb300 as P
+    from paper_2411_00742_gb300 import _lib
+    lib = _lib.load()
+    inst = pi.config_1d(200)
+    n_dev = torch.as_tensor(inst.n0).cuda()
+    rows = torch.zeros((4097, 6), dtype=torch.float64, device="cuda")
+    t_out = np.ascontiguousarray(inst.t_out)
+    kin = P.kinetics_struct(inst.problem)
+    kin.T1 = float("nan")
+    assert _call(lib, kin, 200, n_dev, t_out, rows) == _lib.PBE_EINVAL
+    kin = P.kinetics_struct(inst.problem)
+    kin.kg[0] = -0.05
+    assert _call(lib, kin, 200, n_dev, t_out, rows) == _lib.PBE_EINVAL
+    assert b"negative" in lib.pbe_last_error()
+    kin = P.kinetics_struct(inst.problem)
+    many = np.linspace(0.0, 3600.0, 4097)
+    assert _call(lib, kin, 200, n_dev, many, rows) == _lib.PBE_EINVAL
+    assert b"4096" in lib.pbe_last_error()
+    # the input distribution is untouched by rejected calls
+    assert np.array_equal(n_dev.cpu().numpy(), inst.n0)
+
+
+def test_noalloc_row_at_start_time_and_nonfinite_state():
+    """A first output time equal to t0 gives the moments of n0 and C0 (no
+    step); a NaN in n0 ends the call with PBE_ENONFINITE."""
+    import torch
+    import oracle
+    import paper_2411_00742_gb300 as P
+    from paper_2411_00742_gb300 import _lib
+    lib = _lib.load()
+    inst = pi.config_1d(200)
+    kin = P.kinetics_struct(inst.problem)
+    t_out = np.ascontiguousarray([0.0, 60.0])
+    n_dev = torch.as_tensor(inst.n0).cuda()
+    rows = torch.zeros((2, 6), dtype=torch.float64, device="cuda")
+    assert _call(lib, kin, 200, n_dev, t_out, rows, C0=inst.C0, t0=0.0) == _lib.PBE_OK
+    r0 = rows.cpu().numpy()[0]
+    assert r0[0] == 0.0 and r0[5] == inst.C0
+    np.testing.assert_allclose(r0[1:5], oracle.moments(inst.problem, inst.n0), rtol=1e-13)
+    bad = inst.n0.copy()
+    bad[37] = float("nan")
+    n_bad = torch.as_tensor(bad).cuda()
+    assert _call(lib, kin, 200, n_bad, t_out, rows, C0=inst.C0, t0=0.0) == _lib.PBE_ENONFINITE
