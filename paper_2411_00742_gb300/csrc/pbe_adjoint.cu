@@ -27,6 +27,7 @@
 #include <cmath>
 #include <vector>
 
+#include "pbe_adjoint.cuh"
 #include "pbe_internal.h"
 #include "pbe_tiles.cuh"
 
@@ -47,52 +48,6 @@ constexpr int kANT = 256;
 constexpr int kAT1 = 512;    // 1-D adjoint tile
 constexpr int kATI = 16;     // 2-D adjoint tile
 constexpr int kATJ = 32;
-
-// moment weight W_k at cell (i, j): x1^p x2^q dA (1-D: x^k dL)
-template <int NDIM>
-__device__ __forceinline__ double poly_weights(const double* pc, double x1, double x2, double dA)
-{
-    if (NDIM == 1) return (pc[0] + x1 * (pc[1] + x1 * (pc[2] + x1 * pc[3]))) * dA;
-    // order mu00, mu10, mu01, mu20, mu11, mu02, mu30, mu21, mu12, mu03
-    const double q0 = pc[0] + x2 * (pc[2] + x2 * (pc[5] + x2 * pc[9]));
-    const double q1 = pc[1] + x2 * (pc[4] + x2 * pc[8]);
-    const double q2 = pc[3] + x2 * pc[7];
-    const double q3 = pc[6];
-    return (q0 + x1 * (q1 + x1 * (q2 + x1 * q3))) * dA;
-}
-
-// derivative data of one face: contributions to the cells f-2, f-1, f and h
-struct FaceAdj {
-    double cm2, cm1, c0, hmu;
-};
-
-__device__ __forceinline__ FaceAdj face_adj(double nm2, double up, double dn, double lamL, double lamR, double invd)
-{
-    const double a = up - nm2, b = dn - up;
-    double pa = 0.0, pb = 0.0, half = 0.0;
-    if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) {
-        if (fabs(a) >= kPsiFlat && fabs(b) >= kPsiFlat) {
-            // one division per face; |a + b| >= 2^-958, so 1 / (a + b) is finite
-            const double rs = 1.0 / (a + b);
-            const double qa = b * rs, qb = a * rs;
-            half = a * qa;
-            pa = 2.0 * qa * qa;
-            pb = 2.0 * qb * qb;
-        } else {
-            // differences below 2^-959 count as flat for the derivative (their
-            // ratio is decided by rounding of underflowing tails); the
-            // reciprocal of their sum may overflow, the quotient does not
-            half = a * (b / (a + b));
-        }
-    }
-    const double mu = (lamR - lamL) * invd;
-    FaceAdj r;
-    r.cm2 = -0.5 * pa * mu;
-    r.cm1 = (1.0 + 0.5 * (pa - pb)) * mu;
-    r.c0 = 0.5 * pb * mu;
-    r.hmu = (up + half) * mu;
-    return r;
-}
 
 // ---------------------------------------------------------------------------
 // adjoint stage kernels
@@ -269,43 +224,6 @@ __global__ void __launch_bounds__(kANT) k_adj2d(const double* __restrict__ nin, 
 }
 
 // ---------------------------------------------------------------------------
-// scalar adjoint chain (one thread)
-// ---------------------------------------------------------------------------
-__device__ void kinetics_adjoint(const Kin& K, double C, double t, double lG1, double lG2, double lB, double* lC,
-                                 double* lt, double* lth)
-{
-    if (K.kind == PBE_KINETICS_FIXED) {
-        lth[0] += lG1;
-        if (K.ndim == 2) lth[2] += lG2;
-        lth[4] += lB;
-        return;
-    }
-    const double frac = (t < K.t_cool) ? t / K.t_cool : 1.0;
-    const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) / K.t_cool : 0.0;
-    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
-    const double dcs = K.cs1 + 2.0 * K.cs2 * T;
-    const double s = C / cs - 1.0;
-    if (!(s > 0.0)) return;
-    const double ls = log(s);
-    const double s1 = exp(K.g1 * ls), sb = exp(K.b * ls);
-    const double G1 = K.kg1 * s1, B = K.kb * sb;
-    double lsum = lG1 * K.g1 * G1 / s + lB * K.b * B / s;
-    lth[0] += lG1 * s1;
-    lth[1] += lG1 * G1 * ls;
-    lth[4] += lB * sb;
-    lth[5] += lB * B * ls;
-    if (K.ndim == 2) {
-        const double s2 = exp(K.g2 * ls), G2 = K.kg2 * s2;
-        lth[2] += lG2 * s2;
-        lth[3] += lG2 * G2 * ls;
-        lsum += lG2 * K.g2 * G2 / s;
-    }
-    *lC += lsum / cs;
-    *lt += lsum * (-C * dcs / (cs * cs)) * dTdt;
-}
-
-// ---------------------------------------------------------------------------
 // Scalar steps of the reverse sweep (one thread each).
 // ---------------------------------------------------------------------------
 // Before the stage-2 adjoint of a step: seeds of the output row the step
@@ -322,86 +240,6 @@ __global__ void k_adj_begin(AdjS* A, const Scal* recA, const double* seeds, int 
     a.lCprev = a.lC;
     a.pc[vidx] += -kappa * a.lC;
     *A = a;
-}
-
-// Backward of the learned closure for one evaluation, on 64 threads (one per
-// hidden unit): recomputes the activations from the inputs x, takes the
-// output adjoints lo = dL/d(o), accumulates dL/dweights into dW (fp64, flat
-// layout W1, b1, W2, b2, W3, b3) and returns dL/dx in lx (thread 0).
-__device__ void mlp_backward_block64(const Kin& K, const float x[3], const double lo[3], double* dW, float* sm,
-                                     float lx[3])
-{
-    const int h = threadIdx.x;
-    const __nv_bfloat16* W1 = K.mW;
-    const __nv_bfloat16* W2 = W1 + kMlpH * 3;
-    const __nv_bfloat16* W3 = W2 + kMlpH * kMlpH;
-    const float* b1 = K.mB;
-    const float* b2 = b1 + kMlpH;
-    double* dW1 = dW;
-    double* db1 = dW1 + kMlpH * 3;
-    double* dW2 = db1 + kMlpH;
-    double* db2 = dW2 + kMlpH * kMlpH;
-    double* dW3 = db2 + kMlpH;
-    double* db3 = dW3 + 3 * kMlpH;
-    float* a1s = sm;
-    float* lz2s = sm + kMlpH;
-    float* rs = sm + 2 * kMlpH;   // 3 * 64
-    float z1 = b1[h];
-    z1 = fmaf(__bfloat162float(W1[h * 3]), x[0], z1);
-    z1 = fmaf(__bfloat162float(W1[h * 3 + 1]), x[1], z1);
-    z1 = fmaf(__bfloat162float(W1[h * 3 + 2]), x[2], z1);
-    const float a1 = silu_f(z1);
-    a1s[h] = a1;
-    __syncthreads();
-    float z2 = b2[h];
-    for (int j = 0; j < kMlpH; ++j) z2 = fmaf(__bfloat162float(W2[h * kMlpH + j]), a1s[j], z2);
-    const float a2 = silu_f(z2);
-    float la2 = 0.0f;
-    for (int m = 0; m < 3; ++m) {
-        la2 = fmaf(__bfloat162float(W3[m * kMlpH + h]), (float)lo[m], la2);
-        dW3[m * kMlpH + h] += lo[m] * (double)a2;
-    }
-    if (h < 3) db3[h] += lo[h];
-    const float sg2 = 1.0f / (1.0f + expf(-z2));
-    const float lz2 = la2 * sg2 * (1.0f + z2 * (1.0f - sg2));
-    lz2s[h] = lz2;
-    __syncthreads();
-    for (int j = 0; j < kMlpH; ++j) dW2[h * kMlpH + j] += (double)lz2 * (double)a1s[j];
-    db2[h] += lz2;
-    float la1 = 0.0f;
-    for (int q = 0; q < kMlpH; ++q) la1 = fmaf(__bfloat162float(W2[q * kMlpH + h]), lz2s[q], la1);
-    const float sg1 = 1.0f / (1.0f + expf(-z1));
-    const float lz1 = la1 * sg1 * (1.0f + z1 * (1.0f - sg1));
-    db1[h] += lz1;
-    for (int k = 0; k < 3; ++k) {
-        dW1[h * 3 + k] += (double)lz1 * (double)x[k];
-        rs[h * 3 + k] = __bfloat162float(W1[h * 3 + k]) * lz1;
-    }
-    __syncthreads();
-    if (h == 0) {
-        for (int k = 0; k < 3; ++k) {
-            float v = 0.0f;
-            for (int q = 0; q < kMlpH; ++q) v += rs[q * 3 + k];
-            lx[k] = v;
-        }
-    }
-    __syncthreads();
-}
-
-// dL/d(C, t, ratio) of the closure inputs from dL/dx (thread 0)
-__device__ void mlp_input_adjoint(const Kin& K, double C, double t, const float lx[3], double* lC, double* lt,
-                                  double* lratio)
-{
-    const double frac = (t < K.t_cool) ? t / K.t_cool : 1.0;
-    const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) / K.t_cool : 0.0;
-    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
-    const double dcs = K.cs1 + 2.0 * K.cs2 * T;
-    const double lS = 4.0 * (double)lx[0];
-    const double lT = (double)lx[1] / 10.0 - lS * C * dcs / (cs * cs);
-    *lC += lS / cs;
-    *lt += lT * dTdt;
-    *lratio += 1e-6 * (double)lx[2];
 }
 
 // After the stage-2 adjoint: step length and stage-2 kinetics (at C1, t'),
@@ -426,7 +264,7 @@ __global__ void k_adj_mid(AdjS* A, const Scal* recA, const Scal* recB, Kin K, Ge
     if (run_mlp) {
         float x[3];
         mlp_inputs(K, recB->C1, recA->t_new, recB->V1 / recB->M1, x);
-        mlp_backward_block64(K, x, lo, dW, sm, lx);
+        mlp_backward_block64(K, x, lo, dW, sm, lx, BlockSync64());
     }
     if (threadIdx.x != 0) return;
     AdjS a = *A;
@@ -484,7 +322,7 @@ __global__ void k_adj_end(AdjS* A, const Scal* recA, Kin K, Geom g, const double
     if (run_mlp) {
         float x[3];
         mlp_inputs(K, recA->C, recA->t, recA->V0 / recA->M0, x);
-        mlp_backward_block64(K, x, lo, dW, sm, lx);
+        mlp_backward_block64(K, x, lo, dW, sm, lx, BlockSync64());
     }
     if (threadIdx.x != 0) return;
     AdjS a = *A;
@@ -586,6 +424,9 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     if (!(t_out[0] >= g->t_host)) return afail(PBE_EINVAL, "t_out[0] precedes the current time");
     for (int j = 1; j < n_out; ++j)
         if (!(t_out[j] > t_out[j - 1]) || !std::isfinite(t_out[j])) return afail(PBE_EINVAL, "t_out must increase");
+    if (g->path == PBE_PATH_FUSED && fused_supported(g))
+        return vjp_persistent(g, t_out, n_out, seeds_in, seeds_mem, checkpoint_every, dL_dtheta, dL_dn0, dL_dC0,
+                              rows, mem, dL_dweights);
     const int ncol = g->geo.ndim == 1 ? 6 : 12, vidx = g->geo.ndim == 1 ? 3 : 8;
     const size_t nc = g->ncell, sz = nc * sizeof(double);
     const int K = checkpoint_every;
@@ -626,19 +467,10 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     ATRY(cudaMemcpyAsync(seeds, seeds_in, sizeof(double) * ncol * n_out,
                          seeds_mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     // ---- forward with checkpoints every K steps ----
-    if (n_out > g->tout_cap) {
-        // grow the grid's output buffers through a regular solve-size request
-        cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart); cudaFreeHost(g->h_tout);
-        g->d_tout = nullptr; g->d_rows = nullptr; g->d_rowpart = nullptr; g->h_tout = nullptr; g->tout_cap = 0;
-        if (g->plain_exec) { cudaGraphExecDestroy(g->plain_exec); g->plain_exec = nullptr; }
-        ATRY(cudaMalloc(&g->d_tout, sizeof(double) * n_out));
-        ATRY(cudaMalloc(&g->d_rows, sizeof(double) * 12 * n_out));
-        ATRY(cudaMalloc(&g->d_rowpart, sizeof(double) * (size_t)n_out * (g->max_blocks / 2 + 1) * 10));
-        ATRY(cudaMallocHost(&g->h_tout, sizeof(double) * n_out));
-        g->tout_cap = n_out;
+    {
+        const pbe_status ps = prepare_tout(g, t_out, n_out);
+        if (ps != PBE_OK) { rc = ps; goto done; }
     }
-    ATRY(cudaMemcpyAsync(g->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, st));
-    g->tout_valid_n = 0;
     ATRY(launch_prologue(g, n_out, g->max_steps, nullptr));
     for (;;) {
         double* cn;

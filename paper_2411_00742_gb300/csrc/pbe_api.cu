@@ -62,6 +62,7 @@ cudaMemcpyKind kind_from_device(int mem) { return mem == PBE_MEM_DEVICE ? cudaMe
 
 void free_grid_buffers(pbe_grid* g)
 {
+    pbe::adjoint_work_free(g);
     if (g->plain_exec) cudaGraphExecDestroy(g->plain_exec);
     cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom); cudaFree(g->d_bar);
     cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
@@ -180,6 +181,19 @@ pbe_status run_solve(pbe_grid* g, int n_out)
     return PBE_OK;
 }
 }  // namespace
+
+pbe_status pbe::prepare_tout(pbe_grid* g, const double* t_out, int n_out)
+{
+    pbe_status st = ensure_tout_capacity(g, n_out);
+    if (st) return st;
+    // the output times go to the device only when they changed since the last solve
+    if (n_out != g->tout_valid_n || memcmp(g->h_tout, t_out, sizeof(double) * n_out) != 0) {
+        memcpy(g->h_tout, t_out, sizeof(double) * n_out);
+        CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_tout, sizeof(double) * n_out, cudaMemcpyHostToDevice, g->stream));
+        g->tout_valid_n = n_out;
+    }
+    return PBE_OK;
+}
 
 // The value checks every entry point applies to a pbe_kinetics: every
 // parameter finite, rate prefactors not negative (a negative growth rate
@@ -491,14 +505,8 @@ pbe_status pbe_solve(pbe_grid* g, const double* t_out, int n_out, double* rows, 
             return fail(PBE_EINVAL, "t_out must be strictly increasing and finite (index %d)", j);
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
-    pbe_status st = ensure_tout_capacity(g, n_out);
+    pbe_status st = pbe::prepare_tout(g, t_out, n_out);
     if (st) return st;
-    // the output times go to the device only when they changed since the last solve
-    if (n_out != g->tout_valid_n || memcmp(g->h_tout, t_out, sizeof(double) * n_out) != 0) {
-        memcpy(g->h_tout, t_out, sizeof(double) * n_out);
-        CUDA_TRY(cudaMemcpyAsync(g->d_tout, g->h_tout, sizeof(double) * n_out, cudaMemcpyHostToDevice, g->stream));
-        g->tout_valid_n = n_out;
-    }
     g->kernel_ms = -1.0;
     st = run_solve(g, n_out);
     if (st) return st;

@@ -52,6 +52,8 @@ struct Scal {
     int clipped, out_idx, n_out, done, status;
     int row_first;              // first row a fused solve emitted (its moments are summed afterwards)
     unsigned int counter;       // arrival counter of the last-block reductions
+    double La, Lb;              // ln s of the stage-1 and stage-2 power-law kinetics (warp chains;
+                                // 0 when S <= 1), kept for the adjoint
 };
 
 // S = C / c*(T), s = max(S - 1, 0); G_d = kg_d s^g_d, B = kb s^b (Sec. 2.1,
@@ -266,10 +268,12 @@ __device__ __forceinline__ KinT kin_temperature(const Kin& K, double t)
     return KinT{T, cs};
 }
 
+// Lout (optional) receives ln s (0 for fixed kinetics or S <= 1).
 __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const KinT& tc, double& G1, double& G2,
-                                                double& B)
+                                                double& B, double* Lout = nullptr)
 {
     const int lane = threadIdx.x & 31;
+    if (Lout) *Lout = 0.0;
     if (K.kind == PBE_KINETICS_FIXED) {
         G1 = K.kg1;
         G2 = (K.ndim == 2) ? K.kg2 : 0.0;
@@ -284,6 +288,7 @@ __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const Ki
     }
     const double lx = pbe_log_tab(lane == 0 ? d : cs);
     const double L = __shfl_sync(0xffffffffu, lx, 0) - __shfl_sync(0xffffffffu, lx, 1);
+    if (Lout) *Lout = L;
     const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
     double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
     if (K.growth_form == 1 && lane < 2) q -= (lane == 0 ? K.ea1 : K.ea2) / (T + 273.15);   // Arrhenius factor
@@ -293,13 +298,14 @@ __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const Ki
     B = __shfl_sync(0xffffffffu, e, 2);
 }
 
-__device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B)
+__device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B,
+                                              double* Lout = nullptr)
 {
     if (K.kind == PBE_KINETICS_FIXED) {
-        kinetics_warp_T(K, C, KinT{0.0, 0.0}, G1, G2, B);
+        kinetics_warp_T(K, C, KinT{0.0, 0.0}, G1, G2, B, Lout);
         return;
     }
-    kinetics_warp_T(K, C, kin_temperature(K, t), G1, G2, B);
+    kinetics_warp_T(K, C, kin_temperature(K, t), G1, G2, B, Lout);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,13 +377,15 @@ constexpr double kLnB = 11.512925464970229;    // ln 1e5
 // kinetics with the moment ratio V/mu0 of the state (used by the closure);
 // pre: temperature and solubility at t when the caller has them
 __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t, double ratio, double& G1,
-                                                double& G2, double& B, const KinT* pre = nullptr)
+                                                double& G2, double& B, const KinT* pre = nullptr,
+                                                double* Lout = nullptr)
 {
     if (K.kind != PBE_KINETICS_MLP) {
-        if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B);
-        else kinetics_warp(K, C, t, G1, G2, B);
+        if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B, Lout);
+        else kinetics_warp(K, C, t, G1, G2, B, Lout);
         return;
     }
+    if (Lout) *Lout = 0.0;
     float x[3], o[3];
     if (!mlp_inputs(K, C, t, ratio, x)) {
         G1 = 0.0; G2 = 0.0; B = 0.0;
@@ -440,12 +448,12 @@ __device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const G
     const int lane = threadIdx.x & 31;
     const double t_next = t_out[S->out_idx];
     const double C = S->C, t = S->t;
-    double G1, G2, B, dt, t_new;
-    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre);
+    double G1, G2, B, dt, t_new, L;
+    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre, &L);
     const int clipped = timestep_fast(K, g, G1, G2, t, t_next, dt, t_new);
     __syncwarp();
     if (lane == 0) {
-        S->G1a = G1; S->G2a = G2; S->Ba = B;
+        S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L;
         S->dt = dt; S->t_new = t_new; S->clipped = clipped;
         if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
             S->status = PBE_ENONFINITE;
@@ -461,14 +469,14 @@ __device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double
 {
     const int lane = threadIdx.x & 31;
     const double C1 = S->C - K.kappa * (V1 - S->V0);
-    double G1, G2, B;
-    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre);
+    double G1, G2, B, L;
+    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre, &L);
     __syncwarp();
     if (lane == 0) {
         S->C1 = C1;
         S->V1 = V1;
         S->M1 = M1;
-        S->G1b = G1; S->G2b = G2; S->Bb = B;
+        S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L;
         if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
             S->status = PBE_ENONFINITE;
             S->done = 1;

@@ -33,7 +33,9 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "pbe_chain.cuh"
 #include "pbe_internal.h"
+#include "pbe_sync.cuh"
 #include "pbe_tiles.cuh"
 
 namespace pbe {
@@ -43,74 +45,6 @@ constexpr int kFT1 = 1024;    // 1-D tile
 constexpr int kFTI = 16;      // 2-D tile height of the multi-tile launch (and the largest of the small one-tile kernel)
 constexpr int kFTIBig = 64;   // largest 2-D tile height of the one-tile kernel for larger grids (dynamic shared memory)
 constexpr int kFTJ = 32;      // 2-D tile columns
-constexpr long long kBarrierCycles = 2000000000LL;  // default wait limit: ~1 s at 2 GHz
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long* p, unsigned long long v)
-{
-    unsigned long long old;
-    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-    return old;
-}
-
-// Device-wide barrier over the co-resident blocks of the cooperative launch
-// that also sums one value over the blocks, exactly and independently of the
-// arrival order (so every block, on every run, gets the same total): each
-// block adds its value, an integer multiple q of the unit u (a power of
-// two), as (q << 10) + 1, to a 64-bit accumulator with a release
-// add (cumulative over the writes the block barrier ordered before it), and
-// waits with acquire loads.  The low 10 bits count the arrivals of the
-// stage, the rest sums q (integer addition is associative; the accumulator
-// wraps modulo 2^64, differences stay exact).  Stages alternate between two
-// accumulators (a block cannot reach stage s+2 before every block has read
-// stage s).  Thread 0 only; returns false when the wait runs past `limit`
-// cycles.
-constexpr int kAccStride = 16;   // the two accumulators lie 128 bytes apart
-__device__ bool barrier_sum(unsigned long long* acc, unsigned long long& base, long long q, double u,
-                            unsigned int nblocks, long long limit, double& total)
-{
-    atom_add_release_u64(acc, ((unsigned long long)q << 10) + 1ull);
-    unsigned long long x = ld_acquire_u64(acc);
-    if (((x - base) & 1023ull) != nblocks) {
-        const long long t0 = clock64();
-        const unsigned int spin = limit > 0 ? 64u : 1u;
-        for (unsigned int polls = 0;;) {
-            x = ld_acquire_u64(acc);
-            if (((x - base) & 1023ull) == nblocks) break;
-            if (++polls > spin) {
-                if (clock64() - t0 > limit) return false;
-                __nanosleep(20);
-            }
-        }
-    }
-    const long long sq = (long long)(x - base - nblocks) >> 10;
-    base = x;
-    total = (double)sq * u;
-    return true;
-}
-
-// Block sum of one value (256 threads) in the fixed-point unit of
-// barrier_sum, for thread 0 only: every thread rounds its value to a
-// multiple q of u, each warp adds its q exactly with two 32-bit reductions
-// (the low 26 bits and the rest of q), and thread 0 adds the eight warp
-// sums.  Integer adds leave the FP64 pipe to the other warps and make the
-// sum independent of the order.  |q| < 2^51 (the unit bounds the volume
-// moment by 2^52 u) keeps the reduced high parts inside 32 bits.
-__device__ __forceinline__ long long block_sum_fixed_t0(double v, double inv_u, long long* wsum)
-{
-    const long long q = llrint(v * inv_u);
-    const int hs = __reduce_add_sync(0xffffffffu, (int)(q >> 26));
-    const unsigned ls = __reduce_add_sync(0xffffffffu, (unsigned)(q & 0x3ffffffLL));
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (long long)hs * (1LL << 26) + (long long)ls;
-    __syncthreads();
-    return ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3])) + ((wsum[4] + wsum[5]) + (wsum[6] + wsum[7]));
-}
 
 // In the window after each barrier warp 0 runs the scalar chain, warps 1-6
 // compute the next stage's faces (enough to keep the FP64 pipe busy while
@@ -123,105 +57,6 @@ struct GroupSync {  // named barrier over the face warps 1..kFaceWarps
 struct MomSync {    // named barrier over warps kFaceWarps+1..7
     __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 2, %0;" ::"r"(kFNT - 32 * (kFaceWarps + 1)) : "memory"); }
 };
-// The scalar chain between the stages, for the chain warp of the fused
-// kernel: the same arithmetic as finish_stage1_warp / finish_stage2_warp
-// with prepare_step_warp and stage_coef_fast, arranged for latency: every
-// lane reads the scalars it needs at once and keeps them in registers, the
-// kinetics start at once, lane 0's bookkeeping is stores at the end, and the
-// coefficients of the next stage come from registers.  tc: temperature and
-// solubility at the step's end time.
-__device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const Geom& g, double V1, const KinT& tc)
-{
-    const int lane = threadIdx.x & 31;
-    const double C1 = S->C - K.kappa * (V1 - S->V0);
-    const double dt = S->dt;
-    const int clipped = S->clipped;
-    double G1, G2, B;
-    kinetics_warp_T(K, C1, tc, G1, G2, B);
-    if (lane == 0) {
-        S->C1 = C1;
-        S->V1 = V1;
-        S->M1 = 1.0;
-        S->G1b = G1; S->G2b = G2; S->Bb = B;
-        if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
-            S->status = PBE_ENONFINITE;
-            S->done = 1;
-        }
-    }
-    __syncwarp();
-    StageCoef sc;
-    sc.c1 = (G1 * g.inv_d1) * dt;
-    sc.c2 = (G2 * g.inv_d2) * dt;
-    sc.src = g.ndim == 1 ? (B * g.inv_d1) * dt : (B * (g.inv_d1 * g.inv_d2)) * dt;
-    sc.moms = clipped != 0;
-    return sc;
-}
-
-__device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const Geom& g, const double* t_out,
-                                                   double* rows, const double* mom, int nmom, int vidx,
-                                                   const KinT& tc)
-{
-    const int lane = threadIdx.x & 31;
-    const double V2 = mom[vidx], M2 = mom[0];
-    const double C = S->C - K.kappa * (V2 - S->V0);
-    const double t = S->t_new, dt_done = S->dt;
-    const int clipped = S->clipped, out_idx = S->out_idx, n_out = S->n_out;
-    const long long steps = S->steps + 1, max_steps = S->max_steps;
-    const bool finite = isfinite(V2) && isfinite(C);
-    const int oi = (finite && clipped) ? out_idx + 1 : out_idx;
-    const bool done = !finite || oi >= n_out || steps >= max_steps;
-    __syncwarp();   // every lane has read S before lane 0 writes it
-    double G1 = 0.0, G2 = 0.0, B = 0.0, dt = 0.0, t_new = t;
-    int clip2 = 0;
-    if (!done) {   // the next step: kinetics at (C, t), CFL step to the next output time
-        kinetics_warp_T(K, C, tc, G1, G2, B);
-        clip2 = timestep_fast(K, g, G1, G2, t, t_out[oi], dt, t_new);
-    }
-    if (lane == 0) {
-        S->t = t;
-        S->C = C;
-        S->V0 = V2;
-        S->M0 = M2;
-        S->last_dt = dt_done;
-        S->steps = steps;
-        if (!finite) {
-            S->status = PBE_ENONFINITE;
-            S->done = 1;
-        } else {
-            if (clipped) {
-                if (rows) {
-                    double* row = rows + (size_t)out_idx * (nmom + 2);
-                    row[0] = t;
-                    for (int k = 0; k < nmom; ++k) row[1 + k] = mom[k];
-                    row[nmom + 1] = C;
-                }
-                S->out_idx = oi;
-            }
-            if (oi >= n_out) {
-                S->done = 1;
-            } else if (steps >= max_steps) {
-                S->status = PBE_ETIMEOUT;
-                S->done = 1;
-            }
-        }
-        if (!done) {
-            S->G1a = G1; S->G2a = G2; S->Ba = B;
-            S->dt = dt; S->t_new = t_new; S->clipped = clip2;
-            if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
-                S->status = PBE_ENONFINITE;
-                S->done = 1;
-            }
-        }
-    }
-    __syncwarp();
-    StageCoef sc;
-    sc.c1 = (G1 * g.inv_d1) * dt;
-    sc.c2 = (G2 * g.inv_d2) * dt;
-    sc.src = g.ndim == 1 ? (B * g.inv_d1) * dt : (B * (g.inv_d1 * g.inv_d2)) * dt;
-    sc.moms = false;
-    return sc;
-}
-
 // Named barrier 3: warp 0 arrives once the device-wide barrier of the stage
 // is done (non-blocking), the face warps wait on it before they load the halo.
 // The unaligned forms: warp 0 reaches it after thread 0's wait.

@@ -6,6 +6,10 @@
 #include "pbe.h"
 #include "pbe_device.cuh"
 
+namespace pbe {
+struct AdjWork;   // buffers of the persistent adjoint (pbe_adjoint_fused.cu)
+}
+
 struct pbe_grid {
     int device;
     pbe::Geom geo;
@@ -47,6 +51,7 @@ struct pbe_grid {
     bool timing;
     cudaEvent_t ev_k0, ev_k1;
     double kernel_ms;       // duration of that launch in the last solve (-1: none)
+    pbe::AdjWork* adjw;     // persistent adjoint: checkpoint store and work buffers, kept between calls
 };
 
 namespace pbe {
@@ -90,6 +95,17 @@ int paper_blocks2d(const Geom& g);
 // Value checks of a pbe_kinetics shared by every entry point that takes one
 // (pbe_api.cu): PBE_OK, or PBE_EINVAL with the error message set.
 pbe_status check_kinetic_values(const pbe_kinetics* k);
+
+// Output times of a solve on the device (d_tout, capacity grown as needed;
+// the copy is skipped when they equal the last ones sent) (pbe_api.cu).
+pbe_status prepare_tout(pbe_grid* g, const double* t_out, int n_out);
+
+// Persistent adjoint (pbe_adjoint_fused.cu): pbe_vjp on the fused path, with
+// the arguments pbe_vjp has checked; adjoint_work_free releases its buffers.
+pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const double* seeds, int seeds_mem, int K,
+                          double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem,
+                          double* dL_dweights);
+void adjoint_work_free(pbe_grid* g);
 
 // Fused path (pbe_fused.cu)
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out);

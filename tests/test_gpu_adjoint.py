@@ -1,6 +1,8 @@
 """GPU discrete adjoint (pbe_vjp) against the FP64 CPU adjoint of the oracle
 and against central finite differences of the GPU forward path (the
-gradient bar: 1e-6 relative)."""
+gradient bar: 1e-6 relative), on both paths: the per-stage kernels (plain)
+and the persistent kernel that runs forward, recomputation and reverse
+sweep in one launch (fused)."""
 import numpy as np
 import pytest
 
@@ -13,9 +15,11 @@ REL_GRAD = 1e-6
 
 
 def _problem(case):
+    # 1d_big: several 512-cell tiles and blocks; 2d_tall: 16-row tiles, several per block
     return {"1d": lambda: pi.config_1d(200), "1d_cfl": lambda: pi.config_1d(800),
             "2d": lambda: pi.config_2d(40), "2d_rect": lambda: pi.config_2d(36, 52),
-            "2d_128": lambda: pi.adjoint_2d(128)}[case]()
+            "2d_128": lambda: pi.adjoint_2d(128), "1d_big": lambda: pi.config_1d(2500),
+            "2d_tall": lambda: pi.config_2d(300, 70)}[case]()
 
 
 def _setup(inst):
@@ -26,10 +30,10 @@ def _setup(inst):
     return p, tgt, cols
 
 
-def _gpu_grad(inst, seeds, K, window=-1):
+def _gpu_grad(inst, seeds, K, window=-1, path="plain"):
     import torch
     import paper_2411_00742_gb300 as P
-    g = P.Grid.from_problem(inst.problem)
+    g = P.Grid.from_problem(inst.problem, path=path)
     g.set_window(window)
     g.set_state(np.ascontiguousarray(inst.n0), inst.C0, 0.0)
     dn0 = torch.zeros(inst.problem.ncells, dtype=torch.float64, device="cuda")
@@ -40,14 +44,16 @@ def _gpu_grad(inst, seeds, K, window=-1):
     return dth, dn0.cpu().numpy(), dC0, rows.cpu().numpy(), t
 
 
-@pytest.mark.parametrize("case,K", [("1d", 64), ("1d_cfl", 7), ("2d", 64), ("2d_rect", 5), ("2d_128", 64)])
-def test_vjp_matches_cpu_adjoint(case, K):
+@pytest.mark.parametrize("path", ["plain", "fused"])
+@pytest.mark.parametrize("case,K", [("1d", 64), ("1d_cfl", 7), ("2d", 64), ("2d_rect", 5), ("2d_128", 64),
+                                    ("1d_big", 16), ("2d_tall", 9)])
+def test_vjp_matches_cpu_adjoint(case, K, path):
     inst = _problem(case)
     p, tgt, cols = _setup(inst)
     r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
     seeds = oracle.relative_loss_seeds(r, tgt, cols)
     want, want_dn0, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
-    dth, dn0, dC0, rows, t_end = _gpu_grad(inst, seeds, K)
+    dth, dn0, dC0, rows, t_end = _gpu_grad(inst, seeds, K, path=path)
     for j in range(6):
         assert dth[j] == pytest.approx(want[j], rel=REL_GRAD, abs=1e-300), (case, j, dth, want)
     # d/dn0 on the seed's support; outside it the derivative runs through the
@@ -77,16 +83,71 @@ def test_vjp_with_window_stage_kernel_matches_cpu_adjoint():
     np.testing.assert_allclose(rows[:, 1:], r[:, 1:], rtol=1e-10)
 
 
-def test_vjp_checkpoint_interval_does_not_change_result():
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_vjp_checkpoint_interval_does_not_change_result(path):
     inst = _problem("2d")
     p, tgt, cols = _setup(inst)
     r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
     seeds = oracle.relative_loss_seeds(r, tgt, cols)
-    a = _gpu_grad(inst, seeds, 1)
-    b = _gpu_grad(inst, seeds, 64)
-    c = _gpu_grad(inst, seeds, 1000)
+    a = _gpu_grad(inst, seeds, 1, path=path)
+    b = _gpu_grad(inst, seeds, 64, path=path)
+    c = _gpu_grad(inst, seeds, 1000, path=path)
     assert np.array_equal(a[0], b[0]) and np.array_equal(b[0], c[0])
     assert np.array_equal(a[1], b[1])
+
+
+def test_fused_vjp_grows_its_checkpoint_store_and_repeats_bitwise():
+    """Two output times, the second reached by CFL-limited steps, and a
+    checkpoint every step: the persistent adjoint's first checkpoint store
+    (sized from the output count) is too small and is grown until the solve
+    fits; repeated calls on the same grid reuse the buffers and give the same
+    gradient bit for bit."""
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_1d(800)
+    p = inst.problem
+    inst.t_out = np.array([720.0, 3600.0])
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)
+    assert r["steps"] > 20
+    seeds = np.zeros((2, 6))
+    seeds[:, 1:] = 1.0 / np.abs(r["rows"][:, 1:])
+    want, _, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
+    g = P.Grid.from_problem(p, path="fused")
+    got = []
+    for K in (1, 1, 3):
+        g.set_state(inst.n0, inst.C0, 0.0)
+        dth, _, dC0 = g.vjp(inst.t_out, seeds, K)
+        got.append((dth, dC0))
+    g.close()
+    for dth, dC0 in got:
+        for j in (0, 1, 4, 5):
+            assert dth[j] == pytest.approx(want[j], rel=REL_GRAD), j
+        assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
+    assert np.array_equal(got[0][0], got[1][0]) and np.array_equal(got[0][0], got[2][0])
+
+
+def test_fused_vjp_wait_limit_ends_in_timeout_and_grid_stays_usable():
+    """A zero wait limit makes the persistent adjoint's first device-wide
+    barrier run out (a multi-block grid): PBE_ETIMEOUT, no hang; the grid
+    then solves and differentiates normally."""
+    import paper_2411_00742_gb300 as P
+    from paper_2411_00742_gb300 import _lib
+    inst = _problem("2d")
+    p, tgt, cols = _setup(inst)
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    g = P.Grid.from_problem(p, path="fused")
+    g.set_state(inst.n0, inst.C0, 0.0)
+    g.set_wait_limit(0.0)
+    with pytest.raises(_lib.PbeError) as ei:
+        g.vjp(inst.t_out, seeds, 64)
+    assert "ETIMEOUT" in str(ei.value)
+    g.set_wait_limit(-1.0)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    dth, _, _ = g.vjp(inst.t_out, seeds, 64)
+    g.close()
+    want, _, _ = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
+    for j in range(6):
+        assert dth[j] == pytest.approx(want[j], rel=REL_GRAD), j
 
 
 def test_vjp_matches_central_differences_of_gpu_forward():
@@ -120,13 +181,14 @@ def test_vjp_matches_central_differences_of_gpu_forward():
         assert dth[j] == pytest.approx((Lp - Lm) / (2 * h), rel=REL_GRAD), j
 
 
-def test_autograd_function():
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_autograd_function(path):
     import torch
     import paper_2411_00742_gb300 as P
     from paper_2411_00742_gb300.autograd import PBESolve
     inst = _problem("2d")
     p, tgt, cols = _setup(inst)
-    g = P.Grid.from_problem(p)
+    g = P.Grid.from_problem(p, path=path)
     theta = torch.tensor(p.theta, dtype=torch.float64, requires_grad=True)
     n0 = torch.as_tensor(inst.n0).cuda().requires_grad_(True)
     rows = PBESolve.apply(theta, n0, g, p, inst.C0, 0.0, inst.t_out, 64)
@@ -194,11 +256,12 @@ def test_vjp_with_subnormal_tails_matches_cpu_adjoint():
     r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
     seeds = oracle.relative_loss_seeds(r, tgt, cols)
     want, want_dn0, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
-    dth, dn0, dC0, rows, _ = _gpu_grad(inst, seeds, 64)
-    assert np.all(np.isfinite(dth)) and np.all(np.isfinite(dn0))
-    for j in (0, 1, 4, 5):
-        assert dth[j] == pytest.approx(want[j], rel=REL_GRAD), j
-    assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
+    for path in ("plain", "fused"):
+        dth, dn0, dC0, rows, _ = _gpu_grad(inst, seeds, 64, path=path)
+        assert np.all(np.isfinite(dth)) and np.all(np.isfinite(dn0)), path
+        for j in (0, 1, 4, 5):
+            assert dth[j] == pytest.approx(want[j], rel=REL_GRAD), (path, j)
+        assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD), path
     # the batched adjoint on the same instance
     b = P.Batch([p], [inst.C0])
     b.set_state(b.pack([inst.n0]))

@@ -18,9 +18,9 @@ REL_ROWS_MLP = 2e-5
 REL_GRAD_MLP = 2e-3
 
 
-def _grid(inst, w):
+def _grid(inst, w, path="plain"):
     import paper_2411_00742_gb300 as P
-    g = P.Grid.from_problem(inst.problem)
+    g = P.Grid.from_problem(inst.problem, path=path)
     g.set_closure(w)
     g.set_kinetics(inst.problem, closure=True)
     return g
@@ -56,7 +56,8 @@ def test_closure_forward_window_kernel_matches_oracle():
     assert err <= REL_ROWS_MLP, err
 
 
-def test_closure_gradients_match_oracle():
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_closure_gradients_match_oracle(path):
     inst = cd.trajectories(1, seed=12, N=40)[0]
     w = cd.initial_weights(4, 0.2)
     ws = cd.stored_weights(w)
@@ -65,7 +66,7 @@ def test_closure_gradients_match_oracle():
     r = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=ws)["rows"]
     seeds = oracle.relative_loss_seeds(r, tgt, cols)
     _, _, _, want = oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds, mlp=ws)
-    g = _grid(inst, w)
+    g = _grid(inst, w, path)
     g.set_state(inst.n0, inst.C0, 0.0)
     dW = np.zeros(cd.CLOSURE_SIZE)
     g.vjp(inst.t_out, seeds, 64, dweights_out=dW)
