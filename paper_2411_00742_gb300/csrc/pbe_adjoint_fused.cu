@@ -46,7 +46,8 @@
 namespace pbe {
 
 constexpr int kPNT = 256;   // threads per block
-constexpr int kPT1 = 512;   // 1-D tile (cells)
+constexpr int kPT1 = 512;   // largest 1-D tile (cells)
+constexpr int kPT1Min = 64; // smallest 1-D tile: small grids spread over several blocks
 constexpr int kPTI = 16;    // largest 2-D tile height
 constexpr int kPTJ = 32;    // 2-D tile width
 constexpr int kStatusGrow = -2;   // the checkpoint store is full: the host grows it and runs again
@@ -95,6 +96,7 @@ struct AdjP {
     size_t nc;
     int Kc, ck_cap, n_out, ncol;
     int ntiles, tiles_x, ti;
+    int t1;             // 1-D tile cells (kPT1Min .. kPT1)
     long long wait_limit;
     double t0;
 };
@@ -137,7 +139,7 @@ __device__ __forceinline__ double* st_ptr(const AdjP& P, int c, int q)
 template <int NDIM>
 __device__ __forceinline__ void tile_org(const AdjP& P, int t, int& i0, int& j0)
 {
-    if (NDIM == 1) { i0 = t * kPT1; j0 = 0; }
+    if (NDIM == 1) { i0 = t * P.t1; j0 = 0; }
     else { i0 = (t / P.tiles_x) * P.ti; j0 = (t % P.tiles_x) * kPTJ; }
 }
 
@@ -146,18 +148,19 @@ __device__ __forceinline__ void tile_org(const AdjP& P, int t, int& i0, int& j0)
 // Face values by the Newton-refined quotient (face_value<true>).  Moments of
 // `out`: the volume moment always, mu0 when m0, all when moms.
 template <int STAGE>
-__device__ __forceinline__ void fwd_tile1d(const double* in, const double* old, double* out, int i0, const Geom& g,
-                                           const StageCoef& sc, bool moms, bool m0, double (&m)[kMaxMom], FwdSm1& s)
+__device__ __forceinline__ void fwd_tile1d(const double* in, const double* old, double* out, int i0, int T,
+                                           const Geom& g, const StageCoef& sc, bool moms, bool m0,
+                                           double (&m)[kMaxMom], FwdSm1& s)
 {
     const int N = g.N1;
-    for (int k = threadIdx.x; k < kPT1 + 3; k += kPNT) {
+    for (int k = threadIdx.x; k < T + 3; k += kPNT) {
         const int gi = i0 - 2 + k;
         s.tile[k] = (gi >= 0 && gi < N) ? __ldcg(in + gi) : 0.0;
     }
     __syncthreads();
-    for (int f = threadIdx.x; f <= kPT1; f += kPNT) s.h[f] = face_value<true>(s.tile[f], s.tile[f + 1], s.tile[f + 2]);
+    for (int f = threadIdx.x; f <= T; f += kPNT) s.h[f] = face_value<true>(s.tile[f], s.tile[f + 1], s.tile[f + 2]);
     __syncthreads();
-    for (int c = threadIdx.x; c < kPT1; c += kPNT) {
+    for (int c = threadIdx.x; c < T; c += kPNT) {
         const int i = i0 + c;
         if (i >= N) break;
         double v = s.tile[c + 2] + sc.c1 * (s.h[c] - s.h[c + 1]);
@@ -263,17 +266,19 @@ __device__ __forceinline__ FaceAdj face_adj_fast(double nm2, double up, double d
 // STAGE 1: lam1 = u + pv W_V + p0 W_0; out += lam1 + dt (G1 dD1^T + G2 dD2^T)
 //          lam1 over the stage-1 input nin.
 // acc += (lam_s . D1(nin), lam_s . D2(nin), lam_s at cell 0) of the tile.
+// own (one-tile blocks, else null): stage 2 keeps lam2 of the tile's cells
+// there, stage 1 reads it instead of `out`.
 template <int STAGE>
 __device__ __forceinline__ void rev_tile1d(const double* nin, const double* lam, double* out, double* u, int i0,
-                                           const Geom& g, double dt, double G, const RevS& R, double (&acc)[3],
-                                           RevSm1& s)
+                                           int T, const Geom& g, double dt, double G, const RevS& R, double (&acc)[3],
+                                           double* own, RevSm1& s)
 {
     const int N = g.N1;
-    for (int k = threadIdx.x; k < kPT1 + 4; k += kPNT) {
+    for (int k = threadIdx.x; k < T + 4; k += kPNT) {
         const int i = i0 - 2 + k;
         s.nt[k] = (i >= 0 && i < N) ? __ldcg(nin + i) : 0.0;
     }
-    for (int k = threadIdx.x; k < kPT1 + 3; k += kPNT) {
+    for (int k = threadIdx.x; k < T + 3; k += kPNT) {
         const int i = i0 - 1 + k;
         double v = 0.0;
         if (i >= 0 && i < N) {
@@ -285,15 +290,15 @@ __device__ __forceinline__ void rev_tile1d(const double* nin, const double* lam,
         s.lt[k] = v;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kPT1 + 2; k += kPNT) {
+    for (int k = threadIdx.x; k < T + 2; k += kPNT) {
         const int f = i0 + k;   // face between cells f-1 and f
         if (f > N) { s.fa[0][k] = s.fa[1][k] = s.fa[2][k] = 0.0; continue; }
         const FaceAdj fa = face_adj_fast(s.nt[k], s.nt[k + 1], s.nt[k + 2], s.lt[k], s.lt[k + 1], g.inv_d1);
         s.fa[0][k] = fa.cm2; s.fa[1][k] = fa.cm1; s.fa[2][k] = fa.c0;
-        if (k < kPT1 || (f == N && i0 + kPT1 >= N)) acc[0] += fa.hmu;   // each face counted by one tile
+        if (k < T || (f == N && i0 + T >= N)) acc[0] += fa.hmu;   // each face counted by one tile
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < kPT1; c += kPNT) {
+    for (int c = threadIdx.x; c < T; c += kPNT) {
         const int m = i0 + c;
         if (m >= N) break;
         // cell m receives c0 of face m, cm1 of face m+1 and cm2 of face m+2
@@ -302,9 +307,10 @@ __device__ __forceinline__ void rev_tile1d(const double* nin, const double* lam,
         if (m == 0) acc[2] += ls;
         if (STAGE == 2) {
             out[m] = ls;
+            if (own) own[c] = ls;
             u[m] = fma(dt * G, jt, ls);
         } else {
-            out[m] = __ldcg(out + m) + ls + (dt * G) * jt;
+            out[m] = (own ? own[c] : __ldcg(out + m)) + ls + (dt * G) * jt;
         }
     }
     __syncthreads();
@@ -313,7 +319,7 @@ __device__ __forceinline__ void rev_tile1d(const double* nin, const double* lam,
 template <int STAGE>
 __device__ __forceinline__ void rev_tile2d(const double* nin, const double* lam, double* out, double* u, int i0,
                                            int j0, int ti, const Geom& g, double dt, double G1, double G2,
-                                           const RevS& R, double (&acc)[3], RevSm2& s)
+                                           const RevS& R, double (&acc)[3], double* own, RevSm2& s)
 {
     constexpr int TJ = kPTJ, WN = TJ + 4, WL = TJ + 3;
     const int N1 = g.N1, N2 = g.N2;
@@ -374,9 +380,10 @@ __device__ __forceinline__ void rev_tile2d(const double* nin, const double* lam,
         const double jt = fma(c1, j1, c2 * j2);
         if (STAGE == 2) {
             out[gi] = ls;
+            if (own) own[k] = ls;
             u[gi] = ls + jt;
         } else {
-            out[gi] = __ldcg(out + gi) + ls + jt;
+            out[gi] = (own ? own[k] : __ldcg(out + gi)) + ls + jt;
         }
     }
     __syncthreads();
@@ -384,16 +391,19 @@ __device__ __forceinline__ void rev_tile2d(const double* nin, const double* lam,
 
 // ---- block state --------------------------------------------------------------
 struct BlockSm {
-    TileSm t;
+    TileSm t;        // also the staging area of block_sum_staged
     Scal s;          // forward scalar chain (identical in every block)
     Scal sfin;       // the scalars at the end of the forward pass
     Scal sA, sB;     // records of the step being reversed
+    Scal nA, nB;     // the next reversed step's records, prefetched during the stage-2 cells
+    double own[kPT1];   // one-tile blocks: lam2 of the own cells from stage 2 to stage 1
     RevS R;
     StageCoef sc;    // coefficients of the coming forward stage
-    double red[kPNT / 32 * kMaxMom];
+    double red[kMaxMom];   // block sums of block_sum_staged
     long long wsum[kPNT / 32];
     double psum[4];  // this block's partials (read directly in one-block launches)
     double ik[3];    // 1/kg1, 1/kg2, 1/kb (0 where the prefactor is 0)
+    double inv_dA, inv_cfl;
     float mlp_sm[5 * kMlpH];
     float mlp_lx[3];
     double mlp_lo[3];
@@ -405,6 +415,32 @@ struct BlockSm {
 struct Bar64 {   // named barrier over threads 0..63 (the closure backward)
     __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 5, 64;" ::: "memory"); }
 };
+
+// Block sum of NV values (deterministic): every thread's values go to shared
+// memory, then warp k sums value k (eight values a lane in block order, then
+// a butterfly) - NV warps x 13 FP64 additions instead of the 8 x 5 NV of a
+// shuffle tree in every warp, which on GB300 would hold the SM's FP64 pipe
+// for ~16 cycles each.  `sh` holds kPNT * NV doubles; the sums land in
+// out[0..NV) (shared), valid after the call.
+template <int NV>
+__device__ __forceinline__ void block_sum_staged(const double (&v)[NV], double* sh, double* out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * kPNT + threadIdx.x] = v[k];
+    __syncthreads();
+    for (int k = warp; k < NV; k += kPNT / 32) {
+        const double* col = sh + k * kPNT + lane;
+        double a = col[0];
+#pragma unroll
+        for (int i = 1; i < kPNT / 32; ++i) a += col[32 * i];
+        a = warp_sum(a);
+        if (lane == 0) out[k] = a;
+    }
+    __syncthreads();
+}
+
+static_assert(sizeof(TileSm) >= sizeof(double) * kPNT * kMaxMom, "staging area of the block sums");
 
 // thread 0's state of the device-wide barriers
 struct Sync0 {
@@ -456,10 +492,46 @@ __device__ __forceinline__ void load_scal(Scal& dst, const Scal* src, int tid, i
     for (int k = tid; k < (int)(sizeof(Scal) / 8); k += nthr) d[k] = __ldcg(a + k);
 }
 
+__device__ __forceinline__ void load_scal_sm(Scal& dst, const Scal& src, int tid, int nthr)
+{
+    const unsigned long long* a = reinterpret_cast<const unsigned long long*>(&src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+    for (int k = tid; k < (int)(sizeof(Scal) / 8); k += nthr) d[k] = a[k];
+}
+
+// ---- out-of-line closure paths -------------------------------------------------
+// The learned closure's code is large and only runs with PBE_KINETICS_MLP; out
+// of line it stays out of the instruction stream of the power-law chains.
+static __device__ __noinline__ void mlp_backward_64(const Kin& K, const float* x, const double* lo, double* dW,
+                                                    float* sm, float* lx)
+{
+    const float xx[3] = {x[0], x[1], x[2]};
+    mlp_backward_block64(K, xx, lo, dW, sm, lx, Bar64());
+}
+
+static __device__ __noinline__ StageCoef close1_mlp(Scal* S, const Kin& K, const Geom& g, double V1, double M1,
+                                                    const KinT* tpre)
+{
+    finish_stage1_warp(S, K, V1, M1, tpre);
+    return stage_coef_fast<2>(*S, g);
+}
+
+static __device__ __noinline__ StageCoef close2_mlp(Scal* S, const Kin& K, const Geom& g, const double* t_out,
+                                                    double* rows, const double* mom, int nmom, int vidx,
+                                                    const KinT* tpre)
+{
+    finish_stage2_warp(S, K, g, t_out, rows, mom, nmom, vidx, tpre);
+    return stage_coef_fast<1>(*S, g);
+}
+
 // ---- adjoint scalar chain ----------------------------------------------------
 // Backward of the rates at (C, t) given lG* = dL/dG* and the forward's rates
 // and L = ln s (power law: dG/dkg = s^g = G/kg, dG/dg = G L, dG/ds = g G/s;
 // no exponential or logarithm unless a prefactor is 0).  Adds to lth, *lC, *lt.
+// s^g when the prefactor is 0 (the rate itself is then 0 and cannot give it);
+// a call of its own so that the exponential is not evaluated speculatively
+static __device__ __noinline__ double pow_from_log(double g, double L) { return pbe_exp_tab(g * L); }
+
 __device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, double C, double t, double G1, double G2,
                                              double B, double L, double lG1, double lG2, double lB, double* lC,
                                              double* lt, double* lth)
@@ -475,16 +547,21 @@ __device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, dou
     if (!(d > 0.0)) return;   // S <= 1: the forward's rates were 0 whatever the parameters
     const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) * K.inv_tcool : 0.0;
     const double dcs = K.cs1 + 2.0 * K.cs2 * tc.T;
-    const double rd = div_newton(1.0, d), rcs = div_newton(1.0, tc.cs);
-    const double s1 = K.kg1 > 0.0 ? G1 * ik[0] : pbe_exp_tab(K.g1 * L);
-    const double sb = K.kb > 0.0 ? B * ik[2] : pbe_exp_tab(K.b * L);
+    const double rd = __drcp_rn(d), rcs = __drcp_rn(tc.cs);
+    double s1, sb;
+    if (K.kg1 > 0.0) s1 = G1 * ik[0];
+    else s1 = pow_from_log(K.g1, L);
+    if (K.kb > 0.0) sb = B * ik[2];
+    else sb = pow_from_log(K.b, L);
     double num = lG1 * K.g1 * G1 + lB * K.b * B;   // s dL/ds
     lth[0] += lG1 * s1;
     lth[1] += lG1 * G1 * L;
     lth[4] += lB * sb;
     lth[5] += lB * B * L;
     if (K.ndim == 2) {
-        const double s2 = K.kg2 > 0.0 ? G2 * ik[1] : pbe_exp_tab(K.g2 * L);
+        double s2;
+        if (K.kg2 > 0.0) s2 = G2 * ik[1];
+        else s2 = pow_from_log(K.g2, L);
         lth[2] += lG2 * s2;
         lth[3] += lG2 * G2 * L;
         num += lG2 * K.g2 * G2;
@@ -497,17 +574,22 @@ __device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, dou
 
 // Before the stage-2 adjoint of a step (thread 0): seeds of the row the step
 // emitted, then the adjoint of C' = C - kappa (V(n') - V(n)) (Eq. 4).
+// The chain functions work on a register copy of the adjoint scalars and
+// store it back at the end (their updates are dependent, and a shared-memory
+// round trip each would lengthen the chain).
 __device__ __forceinline__ void rev_begin(const AdjP& P, BlockSm& B, int vidx)
 {
     RevS& R = B.R;
+    double lC = R.lC;
     if (B.sA.clipped) {
         const double* sd = P.seeds + (size_t)B.sA.out_idx * P.ncol;
         for (int k = 0; k < P.ncol - 2; ++k) R.pc[k] += sd[1 + k];
-        R.lC += sd[P.ncol - 1];
+        lC += sd[P.ncol - 1];
     }
-    R.lV0 = P.K.kappa * R.lC;
-    R.lCprev = R.lC;
-    R.pc[vidx] -= P.K.kappa * R.lC;
+    R.lC = lC;
+    R.lV0 = P.K.kappa * lC;
+    R.lCprev = lC;
+    R.pc[vidx] -= P.K.kappa * lC;
 }
 
 // After the stage-2 adjoint (threads 0..63): the step length's share and the
@@ -518,12 +600,12 @@ __device__ __forceinline__ void rev_mid(const AdjP& P, BlockSm& B)
 {
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
     const Kin& K = P.K;
-    const double dA = NDIM == 1 ? P.g.d1 : P.g.d1 * P.g.d2;
+    const double inv_dA = B.inv_dA;
     const Scal& A = B.sA;
     const Scal& Q = B.sB;
     RevS& R = B.R;
     const double P1 = R.sum[0], P2 = R.sum[1], P0 = R.sum[2], dt = A.dt;
-    const double lB = dt * P0 / dA;
+    const double lB = dt * P0 * inv_dA;
     if (K.kind == PBE_KINETICS_MLP) {
         if (threadIdx.x == 0) {
             B.mlp_lo[0] = dt * P1 * Q.G1b;
@@ -535,28 +617,34 @@ __device__ __forceinline__ void rev_mid(const AdjP& P, BlockSm& B)
         if (B.run_mlp) {
             float x[3];
             mlp_inputs(K, Q.C1, A.t_new, Q.V1 / Q.M1, x);
-            mlp_backward_block64(K, x, B.mlp_lo, blockIdx.x == 0 ? P.dW : nullptr, B.mlp_sm, B.mlp_lx, Bar64());
+            mlp_backward_64(K, x, B.mlp_lo, blockIdx.x == 0 ? P.dW : nullptr, B.mlp_sm, B.mlp_lx);
         }
     }
     if (threadIdx.x != 0) return;
-    R.ldt = Q.G1b * P1 + Q.G2b * P2 + Q.Bb * P0 / dA;
-    double lC1 = 0.0, ltn = R.lt;
-    R.pv = 0.0;
-    R.p0 = 0.0;
+    double lth[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) lth[k] = R.lth[k];
+    const double ldt = Q.G1b * P1 + Q.G2b * P2 + Q.Bb * P0 * inv_dA;
+    double lC1 = 0.0, ltn = R.lt, pv = 0.0, p0 = 0.0;
     if (K.kind == PBE_KINETICS_MLP) {
         if (B.run_mlp) {
             double lr = 0.0;
             mlp_input_adjoint(K, Q.C1, A.t_new, B.mlp_lx, &lC1, &ltn, &lr);
-            R.pv += lr / Q.M1;
-            R.p0 += -lr * Q.V1 / (Q.M1 * Q.M1);
+            pv += lr / Q.M1;
+            p0 += -lr * Q.V1 / (Q.M1 * Q.M1);
         }
     } else {
-        kin_backward(K, B.ik, Q.C1, A.t_new, Q.G1b, Q.G2b, Q.Bb, Q.Lb, dt * P1, dt * P2, lB, &lC1, &ltn, R.lth);
+        kin_backward(K, B.ik, Q.C1, A.t_new, Q.G1b, Q.G2b, Q.Bb, Q.Lb, dt * P1, dt * P2, lB, &lC1, &ltn, lth);
     }
+    const double lCprev = R.lCprev, lV0 = R.lV0;
+    R.ldt = ldt;
     R.ltn = ltn;
-    R.lCprev += lC1;
-    R.lV0 += K.kappa * lC1;
-    R.pv += -K.kappa * lC1;
+    R.lCprev = lCprev + lC1;
+    R.lV0 = lV0 + K.kappa * lC1;
+    R.pv = pv - K.kappa * lC1;
+    R.p0 = p0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) R.lth[k] = lth[k];
     (void)VIDX;
 }
 
@@ -569,16 +657,16 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
     const Kin& K = P.K;
     const Geom& g = P.g;
-    const double dA = NDIM == 1 ? g.d1 : g.d1 * g.d2;
+    const double inv_dA = B.inv_dA;
     const Scal& A = B.sA;
     RevS& R = B.R;
     const double P1 = R.sum[0], P2 = R.sum[1], P0 = R.sum[2], dt = A.dt;
-    double ldt = R.ldt + A.G1a * P1 + A.G2a * P2 + A.Ba * P0 / dA;
+    double ldt = R.ldt + A.G1a * P1 + A.G2a * P2 + A.Ba * P0 * inv_dA;
     double lG1 = dt * P1, lG2 = dt * P2;
-    const double lB = dt * P0 / dA;
+    const double lB = dt * P0 * inv_dA;
     if (!A.clipped) {
         ldt += R.ltn;   // t' = t + dt
-        const double dR = -(dt * dt) / K.cfl * ldt;   // d(cfl / R)/dR = -dt^2 / cfl
+        const double dR = -(dt * dt) * B.inv_cfl * ldt;   // d(cfl / R)/dR = -dt^2 / cfl
         lG1 += dR * g.inv_d1;
         if (NDIM == 2) lG2 += dR * g.inv_d2;
     }
@@ -593,26 +681,34 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
         if (B.run_mlp) {
             float x[3];
             mlp_inputs(K, A.C, A.t, A.V0 / A.M0, x);
-            mlp_backward_block64(K, x, B.mlp_lo, blockIdx.x == 0 ? P.dW : nullptr, B.mlp_sm, B.mlp_lx, Bar64());
+            mlp_backward_64(K, x, B.mlp_lo, blockIdx.x == 0 ? P.dW : nullptr, B.mlp_sm, B.mlp_lx);
         }
     }
     if (threadIdx.x != 0) return;
+    double lth[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) lth[k] = R.lth[k];
     double ltp = A.clipped ? -ldt : R.ltn;   // clipped: dt = t_next - t
-    double lC = R.lCprev;
-    for (int k = 0; k < kMaxMom; ++k) R.pc[k] = 0.0;
+    double lC = R.lCprev, pv = 0.0, p0 = 0.0;
     if (K.kind == PBE_KINETICS_MLP) {
         if (B.run_mlp) {
             double lr = 0.0;
             mlp_input_adjoint(K, A.C, A.t, B.mlp_lx, &lC, &ltp, &lr);
-            R.pc[VIDX] += lr / A.M0;
-            R.pc[0] += -lr * A.V0 / (A.M0 * A.M0);
+            pv += lr / A.M0;
+            p0 += -lr * A.V0 / (A.M0 * A.M0);
         }
     } else {
-        kin_backward(K, B.ik, A.C, A.t, A.G1a, A.G2a, A.Ba, A.La, lG1, lG2, lB, &lC, &ltp, R.lth);
+        kin_backward(K, B.ik, A.C, A.t, A.G1a, A.G2a, A.Ba, A.La, lG1, lG2, lB, &lC, &ltp, lth);
     }
+    const double lV0 = R.lV0;
+#pragma unroll
+    for (int k = 0; k < kMaxMom; ++k) R.pc[k] = 0.0;
+    R.pc[VIDX] = pv + lV0;
+    R.pc[0] += p0;
     R.lC = lC;
     R.lt = ltp;
-    R.pc[VIDX] += R.lV0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) R.lth[k] = lth[k];
 }
 
 // ---- forward step --------------------------------------------------------------
@@ -653,8 +749,8 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
             int i0, j0;
             tile_org<NDIM>(P, t, i0, j0);
             if constexpr (NDIM == 1) {
-                if (stage == 1) fwd_tile1d<1>(in1, nullptr, n1, i0, P.g, sc, false, mlp, m, B.t.f1);
-                else fwd_tile1d<2>(n1, in1, out2, i0, P.g, sc, moms, mlp, m, B.t.f1);
+                if (stage == 1) fwd_tile1d<1>(in1, nullptr, n1, i0, P.t1, P.g, sc, false, mlp, m, B.t.f1);
+                else fwd_tile1d<2>(n1, in1, out2, i0, P.t1, P.g, sc, moms, mlp, m, B.t.f1);
             } else {
                 if (stage == 1) fwd_tile2d<1>(in1, nullptr, n1, i0, j0, P.ti, P.g, sc, false, mlp, m, B.t.f2);
                 else fwd_tile2d<2>(n1, in1, out2, i0, j0, P.ti, P.g, sc, moms, mlp, m, B.t.f2);
@@ -666,13 +762,13 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
             double mm[NM];
 #pragma unroll
             for (int k = 0; k < NM; ++k) mm[k] = m[k];
-            block_sum<kPNT, NM>(mm, B.red);
+            block_sum_staged<NM>(mm, reinterpret_cast<double*>(&B.t), B.red);
             if (threadIdx.x == 0) {
                 if (moms)
-                    for (int k = 0; k < NM; ++k) P.rowpart[((size_t)B.s.out_idx * G + blockIdx.x) * NM + k] = mm[k];
+                    for (int k = 0; k < NM; ++k) P.rowpart[((size_t)B.s.out_idx * G + blockIdx.x) * NM + k] = B.red[k];
                 if (mlp) {
-                    B.psum[0] = mm[0];
-                    P.part[((size_t)parity * G + blockIdx.x) * 4] = mm[0];
+                    B.psum[0] = B.red[0];
+                    P.part[((size_t)parity * G + blockIdx.x) * 4] = B.red[0];
                 }
             }
         }
@@ -694,8 +790,7 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
             StageCoef nx;
             if (stage == 1) {
                 if (mlp) {
-                    finish_stage1_warp(&B.s, P.K, B.vtot, M, &tpre);
-                    nx = stage_coef_fast<2>(B.s, P.g);
+                    nx = close1_mlp(&B.s, P.K, P.g, B.vtot, M, &tpre);
                 } else {
                     nx = fused_finish1(&B.s, P.K, P.g, B.vtot, tpre);
                 }
@@ -708,8 +803,7 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
                 mom[VIDX] = B.vtot;
                 double* rows = emit && blockIdx.x == 0 ? P.rows : nullptr;
                 if (mlp) {
-                    finish_stage2_warp(&B.s, P.K, P.g, P.t_out, rows, mom, NM, VIDX, &tpre);
-                    nx = stage_coef_fast<1>(B.s, P.g);
+                    nx = close2_mlp(&B.s, P.K, P.g, P.t_out, rows, mom, NM, VIDX, &tpre);
                 } else {
                     nx = fused_finish2(&B.s, P.K, P.g, P.t_out, rows, mom, NM, VIDX, tpre);
                 }
@@ -742,6 +836,8 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
         B.ik[0] = P.K.kg1 > 0.0 ? 1.0 / P.K.kg1 : 0.0;
         B.ik[1] = P.K.kg2 > 0.0 ? 1.0 / P.K.kg2 : 0.0;
         B.ik[2] = P.K.kb > 0.0 ? 1.0 / P.K.kb : 0.0;
+        B.inv_dA = NDIM == 1 ? P.g.inv_d1 : P.g.inv_d1 * P.g.inv_d2;
+        B.inv_cfl = 1.0 / P.K.cfl;
         memset(&B.R, 0, sizeof(RevS));
     }
     __syncthreads();
@@ -783,7 +879,7 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
         for (int t = t_first; t < t_end; ++t) {
             int i0, j0;
             tile_org<NDIM>(P, t, i0, j0);
-            const int rows_t = NDIM == 1 ? 1 : P.ti, cols_t = NDIM == 1 ? kPT1 : kPTJ;
+            const int rows_t = NDIM == 1 ? 1 : P.ti, cols_t = NDIM == 1 ? P.t1 : kPTJ;
             for (int k = threadIdx.x; k < rows_t * cols_t; k += kPNT) {
                 const int i = i0 + (NDIM == 1 ? k : k / cols_t), j = j0 + (NDIM == 1 ? 0 : k % cols_t);
                 if (i < P.g.N1 && j < P.g.N2) {
@@ -826,8 +922,13 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
         }
         for (int qq = len - 1; qq >= 0; --qq) {
             if (warp == 0) {
-                load_scal(B.sA, P.recA + qq, lane, 32);
-                load_scal(B.sB, P.recB + qq, lane, 32);
+                if (qq == len - 1) {
+                    load_scal(B.sA, P.recA + qq, lane, 32);
+                    load_scal(B.sB, P.recB + qq, lane, 32);
+                } else {   // prefetched during the previous step
+                    load_scal_sm(B.sA, B.nA, lane, 32);
+                    load_scal_sm(B.sB, B.nB, lane, 32);
+                }
                 __syncwarp();
                 if (lane == 0) rev_begin(P, B, VIDX);
             }
@@ -836,30 +937,44 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
             for (int stage = 2; stage >= 1; --stage) {
                 double acc[3] = {0.0, 0.0, 0.0};
                 const double dt = B.sA.dt;
+                // the next step's records: loads issued now, stored after the cells
+                unsigned long long pre[2] = {0ull, 0ull};
+                const bool prefetch = stage == 2 && qq > 0 && warp == 0 && lane < (int)(sizeof(Scal) / 8);
+                if (prefetch) {
+                    pre[0] = __ldcg(reinterpret_cast<const unsigned long long*>(P.recA + qq - 1) + lane);
+                    pre[1] = __ldcg(reinterpret_cast<const unsigned long long*>(P.recB + qq - 1) + lane);
+                }
+                double* own = (t_end - t_first == 1) ? B.own : nullptr;
                 for (int t = t_first; t < t_end; ++t) {
                     int i0, j0;
                     tile_org<NDIM>(P, t, i0, j0);
                     if constexpr (NDIM == 1) {
                         if (stage == 2)
-                            rev_tile1d<2>(P.seg_n1 + (size_t)qq * P.nc, lam, lamo, P.u, i0, P.g, dt, B.sB.G1b, B.R, acc, B.t.r1);
+                            rev_tile1d<2>(P.seg_n1 + (size_t)qq * P.nc, lam, lamo, P.u, i0, P.t1, P.g, dt, B.sB.G1b, B.R,
+                                          acc, own, B.t.r1);
                         else
-                            rev_tile1d<1>(st_ptr(P, cc, qq), P.u, lamo, nullptr, i0, P.g, dt, B.sA.G1a, B.R, acc, B.t.r1);
+                            rev_tile1d<1>(st_ptr(P, cc, qq), P.u, lamo, nullptr, i0, P.t1, P.g, dt, B.sA.G1a, B.R, acc,
+                                          own, B.t.r1);
                     } else {
                         if (stage == 2)
                             rev_tile2d<2>(P.seg_n1 + (size_t)qq * P.nc, lam, lamo, P.u, i0, j0, P.ti, P.g, dt, B.sB.G1b,
-                                          B.sB.G2b, B.R, acc, B.t.r2);
+                                          B.sB.G2b, B.R, acc, own, B.t.r2);
                         else
                             rev_tile2d<1>(st_ptr(P, cc, qq), P.u, lamo, nullptr, i0, j0, P.ti, P.g, dt, B.sA.G1a,
-                                          B.sA.G2a, B.R, acc, B.t.r2);
+                                          B.sA.G2a, B.R, acc, own, B.t.r2);
                     }
                 }
-                block_sum<kPNT, 3>(acc, B.red);
+                if (prefetch) {
+                    reinterpret_cast<unsigned long long*>(&B.nA)[lane] = pre[0];
+                    reinterpret_cast<unsigned long long*>(&B.nB)[lane] = pre[1];
+                }
+                block_sum_staged<3>(acc, reinterpret_cast<double*>(&B.t), B.red);
                 if (threadIdx.x == 0) {
                     const int parity = (int)(y.gen & 1u);
                     B.par = parity;
-                    for (int k = 0; k < 3; ++k) B.psum[k] = acc[k];
+                    for (int k = 0; k < 3; ++k) B.psum[k] = B.red[k];
                     if (G > 1)
-                        for (int k = 0; k < 3; ++k) P.part[((size_t)parity * G + blockIdx.x) * 4 + k] = acc[k];
+                        for (int k = 0; k < 3; ++k) P.part[((size_t)parity * G + blockIdx.x) * 4 + k] = B.red[k];
                     double dummy;
                     B.fail = !grid_barrier(P, y, 0, u, dummy);
                 }
@@ -901,7 +1016,7 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
     for (int t = t_first; t < t_end; ++t) {
         int i0, j0;
         tile_org<NDIM>(P, t, i0, j0);
-        const int rows_t = NDIM == 1 ? 1 : P.ti, cols_t = NDIM == 1 ? kPT1 : kPTJ;
+        const int rows_t = NDIM == 1 ? 1 : P.ti, cols_t = NDIM == 1 ? P.t1 : kPTJ;
         for (int k = threadIdx.x; k < rows_t * cols_t; k += kPNT) {
             const int i = i0 + (NDIM == 1 ? k : k / cols_t), j = j0 + (NDIM == 1 ? 0 : k % cols_t);
             if (i < P.g.N1 && j < P.g.N2) {
@@ -948,7 +1063,7 @@ namespace pbe {
 
 struct AdjWork {
     int K, ck_cap, seeds_cap;
-    int G, ntiles, tiles_x, ti;
+    int G, ntiles, tiles_x, ti, t1;
     long long last_total;   // steps of the last gradient (sizes the checkpoint store of the next)
     double *seg_n, *seg_n1, *ck, *lamA, *lamB, *u, *part, *seeds, *dW;
     Scal *recA, *recB, *ckS;
@@ -985,7 +1100,8 @@ cudaError_t grow(T** p, size_t count)
 
 // Blocks and tiles of the launch: 2-D tiles of ti x 32 cells with the
 // smallest ti (>= 4) that gives every SM at most one tile, up to 16 rows
-// (larger grids: 16-row tiles, several a block); 1-D tiles of 512 cells.
+// (larger grids: 16-row tiles, several a block); 1-D tiles of 64..512 cells
+// chosen the same way.
 cudaError_t adjoint_config(pbe_grid* g, AdjWork* w)
 {
     if (w->G) return cudaSuccess;
@@ -997,9 +1113,12 @@ cudaError_t adjoint_config(pbe_grid* g, AdjWork* w)
     int cap = std::min(g->sms * occ, g->max_blocks / 2);
     cap = std::min(cap, 1000);   // the arrival count of barrier_sum has 10 bits
     if (g->geo.ndim == 1) {
+        // tiles of a multiple of 32 cells, at least kPT1Min, that give every SM at most one when the grid allows
+        const int per = (g->geo.N1 + g->sms - 1) / g->sms;
+        w->t1 = std::min(kPT1, std::max(kPT1Min, (per + 31) / 32 * 32));
         w->tiles_x = 1;
         w->ti = 1;
-        w->ntiles = (g->geo.N1 + kPT1 - 1) / kPT1;
+        w->ntiles = (g->geo.N1 + w->t1 - 1) / w->t1;
     } else {
         w->tiles_x = (g->geo.N2 + kPTJ - 1) / kPTJ;
         const int per = std::max(1, std::min(g->sms, cap) / w->tiles_x);
@@ -1111,7 +1230,7 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
         P.lamA = w->lamA; P.lamB = w->lamB; P.u = w->u; P.part = w->part; P.seeds = w->seeds; P.dW = w->dW;
         P.out = w->out; P.acc = reinterpret_cast<unsigned long long*>(g->d_bar);
         P.nc = nc; P.Kc = K; P.ck_cap = w->ck_cap; P.n_out = n_out; P.ncol = ncol;
-        P.ntiles = w->ntiles; P.tiles_x = w->tiles_x; P.ti = w->ti; P.wait_limit = wait_limit; P.t0 = t0;
+        P.ntiles = w->ntiles; P.tiles_x = w->tiles_x; P.ti = w->ti; P.t1 = w->t1; P.wait_limit = wait_limit; P.t0 = t0;
         void* args[] = {&P};
         const void* fn = ndim == 1 ? (const void*)k_adjoint_persistent<1> : (const void*)k_adjoint_persistent<2>;
         if (g->timing) PTRY(cudaEventRecord(g->ev_k0, st));

@@ -260,11 +260,18 @@ struct KinT {
     double T, cs;
 };
 
+// The exponential solubility form in a call of its own: written inline, the
+// compiler evaluates the exponential speculatively beside the polynomial
+// form and the chain waits for it whichever form is set.
+static __device__ __noinline__ double solubility_exp(double cs0, double cs1, double T) { return cs0 * pbe_exp_tab(cs1 * T); }
+
 __device__ __forceinline__ KinT kin_temperature(const Kin& K, double t)
 {
     const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
     const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp_tab(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    double cs;
+    if (K.solubility_form == 1) cs = solubility_exp(K.cs0, K.cs1, T);
+    else cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
     return KinT{T, cs};
 }
 
