@@ -41,7 +41,11 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
            "-o", tmp] + cfiles + ["-lm"]
-    subprocess.run(cmd, check=True, cwd=_HERE)
+    # with OpenMP where the compiler has it (threads only for the timed CPU
+    # baseline: the results are the same on any thread count)
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], cwd=_HERE, capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -91,6 +95,9 @@ def _load():
         lib.orc_solve_cs.restype = ctypes.c_long
         lib.orc_solve_cs.argtypes = [P, ctypes.c_int, ctypes.c_double, _D, ctypes.c_double,
                                      ctypes.c_double, _D, ctypes.c_int, _D, _D]
+        lib.orc_set_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads(1)   # one thread unless set_threads says otherwise
         lib.orc_vjp.restype = ctypes.c_long
         lib.orc_vjp.argtypes = [P, _D, ctypes.c_double, ctypes.c_double, _D, ctypes.c_int,
                                 _D, _D, _D, _D, _D, _D]
@@ -100,6 +107,12 @@ def _load():
 
 MLP_NW = 64 * 3 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # learned closure weight count
 _mlp_keep = {}
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's element-wise loops (2-D right-hand side and stage
+    updates); returns the count in effect.  Results are identical on any count."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def _poly(problem) -> np.ndarray:

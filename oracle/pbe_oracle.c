@@ -22,9 +22,17 @@
  *  - the solute balance in the difference form of Eq. 4 after each stage,
  *    with kappa = rho_c k_v times a units factor;
  *  - G = B = 0 whenever S <= 1 (no dissolution).
- * Compile with -ffp-contract=off; IEEE double round-to-nearest.
+ * Compile with -ffp-contract=off; IEEE double round-to-nearest.  The
+ * element-wise loops of the 2-D right-hand side and of the stage updates of
+ * grids of 16384 cells or more may run on several OpenMP threads (for the
+ * timed CPU baseline; one thread unless orc_set_threads asks for more); the
+ * results are the same on any thread count, since every sum (the moments)
+ * runs in one thread in a fixed order.
  */
 #include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -112,6 +120,21 @@ static ctx_r make_ctx_r(const orc_params* p)
 /* ------------------------------------------------------------------ */
 
 double orc_psi(double a, double b) { return psi_r(a, b); }
+
+/* Threads of the element-wise loops (the 2-D right-hand side and the stage
+ * updates; OpenMP when the library was built with it).  Results do not depend
+ * on the count: every sum stays in one thread, in a fixed order.  Returns the
+ * count in effect (1 without OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 double orc_temperature(const orc_params* p, double t) { return temperature_r(p, t); }
 

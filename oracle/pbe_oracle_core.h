@@ -221,6 +221,8 @@ static void SFX(rhs2)(const orc_params* p, const SCALAR* n, SCALAR G1, SCALAR G2
 {
     int N1 = p->n1, N2 = p->n2;
     double d1 = p->lmax1 / N1, d2 = p->lmax2 / N2;
+    /* every L[i][j] is computed on its own: the rows may run on several threads */
+#pragma omp parallel for schedule(static) if ((long)N1 * N2 >= 16384)
     for (int i = 0; i < N1; ++i)
         for (int j = 0; j < N2; ++j) {
             SCALAR dF1 = SFX(face2_1)(n, N1, N2, i + 1, j, G1) - SFX(face2_1)(n, N1, N2, i, j, G1);
@@ -322,6 +324,7 @@ static int SFX(step)(const SFX(ctx)* c, SCALAR* n, SCALAR* work, SCALAR* C, SCAL
 
     /* stage 1: n1 = n + dt L(n); solute balance C1 = C - kappa (V(n1) - V(n)) */
     SFX(rhs)(p, n, G1a, G2a, Ba, L);
+#pragma omp parallel for schedule(static) if (nc >= 16384)
     for (size_t k = 0; k < nc; ++k) n1[k] = n[k] + dt * L[k];
     SCALAR V1 = SFX(volume)(p, n1);
     SCALAR C1 = *C - p->kappa * (V1 - V0);
@@ -330,6 +333,7 @@ static int SFX(step)(const SFX(ctx)* c, SCALAR* n, SCALAR* work, SCALAR* C, SCAL
     /* stage 2 with kinetics at (C1, t + dt); n_new = n/2 + (n1 + dt L(n1))/2 */
     SFX(kinetics)(c, C1, t_new, r1, &G1b, &G2b, &Bb);
     SFX(rhs)(p, n1, G1b, G2b, Bb, L);
+#pragma omp parallel for schedule(static) if (nc >= 16384)
     for (size_t k = 0; k < nc; ++k) n[k] = 0.5 * n[k] + 0.5 * (n1[k] + dt * L[k]);
     SCALAR C_new = *C - p->kappa * (SFX(volume)(p, n) - V0);
 
