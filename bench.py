@@ -32,14 +32,21 @@ sys.path.insert(0, ROOT)
 import pbe_inputs as pi  # noqa: E402
 
 METRIC = "FVM cell-steps/s and adjoint grads/s, fused vs plain GPU, at stated FP64 error"
-# algorithmic FP64 operations per cell-step of the 2-D SSP-RK2 step (FMA = 2,
-# division = 1): per stage two faces (difference, sum, division, FMA = 5 each),
-# update (2 differences + 2 FMA = 6), volume moment (FMA = 2); stage 2 adds the
-# Runge-Kutta average (3): 18 + 21 = 39.
-FLOPS_PER_CELL_STEP_2D = 39
-# 1-D: per stage one face (5), the update (difference + FMA = 3) and the volume
-# moment (FMA = 2) = 10; two stages and the Runge-Kutta average (3): 23
-FLOPS_PER_CELL_STEP_1D = 23
+# Algorithmic FP64 work per cell-step of the SSP-RK2 step (FMA = 2, division =
+# 1), the counts of the hot-path scope the rooflines use: 1-D 25 flops + 2
+# divisions, 2-D 43 flops + 4 divisions.
+FLOPS_PER_CELL_STEP_2D = 47
+FLOPS_PER_CELL_STEP_1D = 27
+# This implementation's own count of the same step (every face value once per
+# stage): 2-D per stage two faces (difference, sum, division, FMA = 5 each),
+# update (2 differences + 2 FMA = 6), volume moment (FMA = 2), plus the
+# Runge-Kutta average (3): 39; 1-D per stage one face (5), update (3), volume
+# moment (2), plus the average: 23.  Reported beside the scope's counts.
+OWN_FLOPS_PER_CELL_STEP_2D = 39
+OWN_FLOPS_PER_CELL_STEP_1D = 23
+# Work of one gradient (the scope's model): the forward pass, the recomputed
+# segments, and a reverse sweep of about 2.5 times the forward's flops.
+ADJOINT_REVERSE_FACTOR = 2.5
 # the paper's split scheme (Eq. 3, two sweeps): per direction and cell one
 # difference, one sum, one division, one product, the face value (FMA = 2), the
 # flux difference and the update (FMA = 2) = 9; two directions and the volume
@@ -120,6 +127,20 @@ def _workload():
                   "cells": inst.problem.ncell, "grid": [256, 256], "outputs": len(inst.t_out),
                   "l2": "state (0.5 MB/array) stays L2-resident inside a solve; a 256 MB buffer is "
                         "written between timed solves to flush L2"}
+
+
+def _host_info():
+    """Core count and CPU model of the host the CPU baseline ran on."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Model name", "Architecture", "Socket(s)", "Core(s) per socket", "Thread(s) per core"):
+                info[k.strip()] = v.strip()
+    except Exception:  # lscpu missing: the core count alone
+        pass
+    return info
 
 
 def _oracle_rate(inst, budget_s: float, min_reps: int = 1):
@@ -276,10 +297,19 @@ def run_gpu(args):
                 g.close()
                 g_cells += inst.problem.ncell * st
                 g_time += e0.elapsed_time(e1) * 1e-3
+        ach = FLOPS_PER_CELL_STEP_1D * bsteps_cells / tb / 1e12
         return {"instances": len(insts), "warps_per_block": wpb, "total_steps": bsteps,
                 "cell_steps": bsteps_cells, "ms_per_solve": 1e3 * tb, "value": bsteps_cells / tb,
                 "unit": "cell-steps/s",
-                "plain_per_instance": {"value": g_cells / g_time, "sample": "first 64 instances, one grid each"}}
+                "plain_per_instance": {"value": g_cells / g_time, "sample": "first 64 instances, one grid each"},
+                "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                             "frac": ach / FP64_PEAK_TFLOPS_NOMINAL,
+                             "own_count_frac": OWN_FLOPS_PER_CELL_STEP_1D * bsteps_cells / tb / 1e12 /
+                             FP64_PEAK_TFLOPS_NOMINAL,
+                             "kernel": "batched 1-D kernel (one warp per instance, one graph launch per batch)",
+                             "note": f"{FLOPS_PER_CELL_STEP_1D} flop/cell-step x cell-steps / batch time (CUDA events "
+                                     "around the graph launch); peak = nominal GB300 FP64"},
+                "_insts": insts}
 
     def loss_seeds(rows, target, cols):
         """dL/drows of the relative-error loss sum_k sum_c ((r - t) / t)^2 (Eq. 5 with
@@ -290,11 +320,15 @@ def run_gpu(args):
 
     def adjoint_leg():
         """Gradients of the relative-error loss (50 loss times, target = kinetics x1.1) with
-        respect to the kinetic parameters: (a) 2-D 128x128 grid, (b) 1-D 500-cell instances.
-        One gradient = forward with checkpoints every 64 steps + reverse sweep.  Targets
-        and seeds come from GPU solves; the CPU adjoint (timing and agreement) is part of
-        the CPU baseline leg."""
+        respect to the kinetic parameters on both paths - fused: the persistent adjoint
+        (forward, recomputation and reverse sweep in one launch), plain: per-stage kernels
+        - for (a) the 2-D 128x128 grid, (b) one 1-D 500-cell instance, and (b') 256 such
+        instances in one batched launch.  One gradient = one pbe_vjp with a checkpoint
+        every 64 steps; its seeds dL/drows come from a GPU solve beforehand.  The CPU
+        adjoint (timing and agreement) is part of the CPU baseline leg."""
         out, cases = {}, {}
+        K = 64
+        reps = max(3, args.steps // 2)
         for name, inst, cols in (("2d_128x128", pi.adjoint_2d(128), [1, 2, 3, 9, 11]),
                                  ("1d_500", pi.adjoint_batch_1d(16)[0], [1, 2, 3, 4, 5])):
             p = inst.problem
@@ -303,30 +337,54 @@ def run_gpu(args):
             tgt, _ = gt.solve(inst.t_out)
             gt.close()
             g = P.Grid.from_problem(p, stream=stream)
-            n0d = torch.as_tensor(inst.n0).cuda()
-            rows = torch.zeros((len(inst.t_out), P.ncols(p.ndim)), dtype=torch.float64, device="cuda")
-            tgt_t = torch.as_tensor(tgt).cuda()
-            times = []
-            with torch.cuda.stream(stream):
-                for it in range(args.warmup + max(3, args.steps // 2)):
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    g.set_state(n0d, inst.C0, 0.0)
-                    e0.record(stream)
-                    g.solve(inst.t_out, out=rows)
-                    sd = torch.zeros_like(rows)
-                    sd[:, cols] = 2.0 * (rows[:, cols] - tgt_t[:, cols]) / tgt_t[:, cols] ** 2
-                    g.set_state(n0d, inst.C0, 0.0)
-                    dth, _, _ = g.vjp(inst.t_out, sd, 64)
-                    e1.record(stream)
-                    e1.synchronize()
-                    if it >= args.warmup:
-                        times.append(e0.elapsed_time(e1) * 1e-3)
+            g.set_state(inst.n0, inst.C0, 0.0)
+            rows, steps = g.solve(inst.t_out)
             g.close()
-            tg = sum(times) / len(times)
-            out[name] = {"grads_per_s": 1.0 / tg, "ms_per_grad": 1e3 * tg, "max_rel_err_vs_cpu_adjoint": None,
-                         "cpu_adjoint_grads_per_s": None, "checkpoint_every": 64}
-            cases[name] = (inst, tgt, cols, dth, sd.cpu().numpy())
+            sd = loss_seeds(rows, tgt, cols)
+            sd_d = torch.as_tensor(sd).cuda()
+            n0d = torch.as_tensor(inst.n0).cuda()
+            fpc = FLOPS_PER_CELL_STEP_1D if p.ndim == 1 else FLOPS_PER_CELL_STEP_2D
+            nseg = -(-steps // K)
+            recomputed = steps - (steps - (nseg - 1) * K)
+            flops = (1.0 + recomputed / steps + ADJOINT_REVERSE_FACTOR) * fpc * p.ncell * steps
+            res = {"steps": steps, "checkpoint_every": K, "recomputed_steps": recomputed,
+                   "max_rel_err_vs_cpu_adjoint": None, "cpu_adjoint_grads_per_s": None}
+            for path in ("fused", "plain"):
+                g = P.Grid.from_problem(p, stream=stream, path=path)
+                g.set_timing(True)
+                times, ktimes = [], []
+                with torch.cuda.stream(stream):
+                    for it in range(args.warmup + reps):
+                        g.set_state(n0d, inst.C0, 0.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        dth, _, _ = g.vjp(inst.t_out, sd_d, K)
+                        e1.record(stream)
+                        e1.synchronize()
+                        if it >= args.warmup:
+                            times.append(e0.elapsed_time(e1) * 1e-3)
+                            ktimes.append(g.kernel_time_ms() * 1e-3)
+                g.close()
+                tg = sum(times) / len(times)
+                entry = {"grads_per_s": 1.0 / tg, "ms_per_grad": 1e3 * tg}
+                if path == "fused":
+                    kt = sum(ktimes) / len(ktimes)
+                    ach = flops / kt / 1e12
+                    entry["roofline"] = {
+                        "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                        "frac": ach / FP64_PEAK_TFLOPS_NOMINAL, "launch_ms": 1e3 * kt,
+                        "kernel": "k_adjoint_persistent (one cooperative launch per gradient)",
+                        "note": f"(1 + recomputed/steps + {ADJOINT_REVERSE_FACTOR}) x {fpc} flop/cell-step x "
+                                "cells x steps / launch time (CUDA events around the launch on its stream); "
+                                "peak = nominal GB300 FP64"}
+                    res["dth"] = dth
+                res[path] = entry
+            res["value"] = res["fused"]["grads_per_s"]
+            res["unit"] = "grads/s"
+            res["fused_over_plain"] = res["fused"]["grads_per_s"] / res["plain"]["grads_per_s"]
+            out[name] = res
+            cases[name] = (inst, tgt, cols, res.pop("dth"), sd)
         # (b') the batched form: 256 instances of 500 cells, one launch (one warp per instance)
         insts = pi.adjoint_batch_1d(256)
         cols = [1, 2, 3, 4, 5]
@@ -339,33 +397,49 @@ def run_gpu(args):
         packed = b.pack([x.n0 for x in insts])
         b.set_state(packed)
         fwd, _ = b.solve(pi.loss_times())
+        bcells = b.cell_steps()
+        bsteps = b.steps()
         seeds = loss_seeds(fwd, tgts, cols)
         seeds_d = torch.as_tensor(seeds).cuda()
         times = []
         with torch.cuda.stream(stream):
-            for it in range(args.warmup + max(3, args.steps // 2)):
+            for it in range(args.warmup + reps):
                 b.set_state(packed)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                dth_b, _ = b.vjp(pi.loss_times(), seeds_d, 64)
+                dth_b, _ = b.vjp(pi.loss_times(), seeds_d, K)
                 e1.record(stream)
                 e1.synchronize()
                 if it >= args.warmup:
                     times.append(e0.elapsed_time(e1) * 1e-3)
         b.close()
         tb = sum(times) / len(times)
-        out["batch_1d_256x500"] = {"grads_per_s": 256 / tb, "ms_per_batch": 1e3 * tb,
-                                   "max_rel_err_vs_cpu_adjoint_sampled": None, "checkpoint_every": 64,
-                                   "single_instance_path_grads_per_s": out["1d_500"]["grads_per_s"],
-                                   "cpu_adjoint_grads_per_s": None}
+        rec = float(sum(max(0, int(s_) - (int(s_) - ((-(-int(s_) // K)) - 1) * K)) * x.problem.ncell
+                        for s_, x in zip(bsteps, insts)))
+        bflops = (bcells * (1.0 + ADJOINT_REVERSE_FACTOR) + rec) * FLOPS_PER_CELL_STEP_1D
+        bach = bflops / tb / 1e12
+        out["batch_1d_256x500"] = {"grads_per_s": 256 / tb, "ms_per_batch": 1e3 * tb, "value": 256 / tb,
+                                   "unit": "grads/s", "cell_steps": bcells,
+                                   "max_rel_err_vs_cpu_adjoint_sampled": None, "checkpoint_every": K,
+                                   "single_instance_fused_grads_per_s": out["1d_500"]["fused"]["grads_per_s"],
+                                   "cpu_adjoint_grads_per_s": None,
+                                   "roofline": {"bound": "alu", "achieved": bach, "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                                                "unit": "TFLOP/s", "frac": bach / FP64_PEAK_TFLOPS_NOMINAL,
+                                                "kernel": "batched adjoint (one warp per instance, one launch)",
+                                                "note": f"((1 + {ADJOINT_REVERSE_FACTOR}) x cell-steps + recomputed "
+                                                        f"cell-steps) x {FLOPS_PER_CELL_STEP_1D} flop / batch time "
+                                                        "(CUDA events around the call); peak = nominal GB300 FP64"}}
         cases["batch_1d_256x500"] = (insts, seeds, dth_b)
         return out, cases
 
-    def adjoint_cpu_baseline(adj, cases):
-        """The CPU adjoint of the oracle on the same seeds: its gradients/s and the
-        agreement of the GPU gradients (part of the CPU baseline leg)."""
+    def adjoint_cpu_baseline(adj, cases, cores):
+        """The CPU adjoint of the oracle on the same seeds: its gradients/s (one thread,
+        and on every core - rows in parallel for one grid, instances in parallel for
+        the batch) and the agreement of the fused GPU gradients (part of the CPU
+        baseline leg)."""
         import oracle
+        from concurrent.futures import ThreadPoolExecutor
         for name in ("2d_128x128", "1d_500"):
             inst, tgt, cols, dth, sd = cases[name]
             p = inst.problem
@@ -375,6 +449,14 @@ def run_gpu(args):
             tc = time.perf_counter() - t0
             adj[name]["max_rel_err_vs_cpu_adjoint"] = float(np.max(np.abs(dth[idx] - want[idx]) / np.abs(want[idx])))
             adj[name]["cpu_adjoint_grads_per_s"] = 1.0 / tc
+            if p.ncell >= 16384:
+                oracle.set_threads(cores)
+                t0 = time.perf_counter()
+                oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, sd)
+                tm = time.perf_counter() - t0
+                oracle.set_threads(1)
+                adj[name]["cpu_adjoint_all_cores"] = {"grads_per_s": 1.0 / tm, "threads": cores,
+                                                      "sample": "one gradient, rows of the grid in parallel"}
         insts, seeds, dth_b = cases["batch_1d_256x500"]
         errs = []
         for i in range(0, 256, 32):
@@ -383,6 +465,17 @@ def run_gpu(args):
             errs.append(float(np.max(np.abs(dth_b[i, [0, 1, 4, 5]] - want[[0, 1, 4, 5]]) / np.abs(want[[0, 1, 4, 5]]))))
         adj["batch_1d_256x500"]["max_rel_err_vs_cpu_adjoint_sampled"] = max(errs)
         adj["batch_1d_256x500"]["cpu_adjoint_grads_per_s"] = adj["1d_500"]["cpu_adjoint_grads_per_s"]
+
+        def one(i):
+            x = insts[i]
+            return oracle.vjp(x.problem, x.n0, x.C0, 0.0, x.t_out, seeds[i])
+
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(one, range(256)))
+        el = time.perf_counter() - t0
+        adj["batch_1d_256x500"]["cpu_adjoint_all_cores"] = {
+            "grads_per_s": 256 / el, "threads": cores, "sample": "all 256 instances, one per thread at a time"}
 
     def paper_leg():
         """The paper's own base case (Table 1, Appendix A) at its finest bins: 6000 x 3000
@@ -481,7 +574,8 @@ def run_gpu(args):
                 rate = N * N * nsteps / t
                 row["steps"] = nsteps
                 row[path] = {"ms_per_solve": 1e3 * t, "value": rate, "unit": "cell-steps/s",
-                             "roofline_frac": FLOPS_PER_CELL_STEP_2D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
+                             "roofline_frac": FLOPS_PER_CELL_STEP_2D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL,
+                             "roofline_frac_own_count": OWN_FLOPS_PER_CELL_STEP_2D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
             out.append(row)
         out1 = []
         # 1-D: 2^18 and 2^20 cells (dL ~ 4e-3 / 1e-3 um), 10 s from a supersaturated
@@ -509,7 +603,8 @@ def run_gpu(args):
                 rate = N * nsteps / t
                 row["steps"] = nsteps
                 row[path] = {"ms_per_solve": 1e3 * t, "value": rate, "unit": "cell-steps/s",
-                             "roofline_frac": FLOPS_PER_CELL_STEP_1D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
+                             "roofline_frac": FLOPS_PER_CELL_STEP_1D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL,
+                             "roofline_frac_own_count": OWN_FLOPS_PER_CELL_STEP_1D * rate / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
             out1.append(row)
         return out, out1
 
@@ -538,6 +633,7 @@ def run_gpu(args):
     plain_value = ws * cells_per_solve * args.steps / t_plain
     ms = 1e3 * t_fused / args.steps
     achieved = FLOPS_PER_CELL_STEP_2D * cells_per_solve / k_fused / 1e12
+    achieved_own = OWN_FLOPS_PER_CELL_STEP_2D * cells_per_solve / k_fused / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -550,10 +646,13 @@ def run_gpu(args):
                      "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
                      "traffic": FUSED_DRAM_BYTES_PER_LAUNCH if inst.problem.ncells == (256, 256) else None,
                      "kernel": "k_fused (persistent cooperative kernel, one launch per solve)",
-                     "launch_ms": 1e3 * k_fused,
-                     "note": f"FP64 algorithmic {FLOPS_PER_CELL_STEP_2D} flop/cell-step (division = 1) x "
-                             "cell-steps per launch / launch time (CUDA events the library records around the "
-                             "launch on its stream, mean over the timed solves); peak = nominal GB300 FP64"},
+                     "launch_ms": 1e3 * k_fused, "flops_per_cell_step": FLOPS_PER_CELL_STEP_2D,
+                     "own_count": {"flops_per_cell_step": OWN_FLOPS_PER_CELL_STEP_2D, "achieved": achieved_own,
+                                   "frac": achieved_own / FP64_PEAK_TFLOPS_NOMINAL},
+                     "note": f"FP64 algorithmic {FLOPS_PER_CELL_STEP_2D} flop/cell-step (43 flops + 4 divisions, "
+                             "division = 1) x cell-steps per launch / launch time (CUDA events the library records "
+                             "around the launch on its stream, mean over the timed solves); peak = nominal GB300 "
+                             "FP64 (of nominal: the measured-peaks file has no FP64 entry)"},
         "e2e": {"value": ws * e2e_rate, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "batch_1d": batch,
         "small_1d": small_1d,
@@ -565,12 +664,34 @@ def run_gpu(args):
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
+    binsts = batch.pop("_insts") if batch is not None else None
     if rank == 0 and not args.no_cpu_baseline:
         # the CPU baseline leg: the oracle timed on the host, and its rows give the
         # stated error of the GPU rows on the same solves
+        import oracle
+        cores = os.cpu_count() or 1
         v, reps, el, want = _oracle_rate(inst, budget_s=args.cpu_seconds)
+        oracle.set_threads(cores)
+        t0 = time.perf_counter()
+        oracle.solve_instance(inst)
+        el_all = time.perf_counter() - t0
+        oracle.set_threads(1)
         line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{reps} full solves of the same 256x256 workload ({el:.1f} s), single thread"}
+                                "sample": f"{reps} full solves of the same 256x256 workload ({el:.1f} s), single thread",
+                                "all_cores": {"value": inst.problem.ncell * want["steps"] / el_all, "threads": cores,
+                                              "sample": "one full solve, rows of the grid in parallel (OpenMP)"},
+                                "host": _host_info()}
+        if batch is not None:
+            # the batch on every core: instances in parallel, a bounded sample
+            from concurrent.futures import ThreadPoolExecutor
+            sample = binsts[: max(cores * 4, 64)]
+            t0 = time.perf_counter()
+            with ThreadPoolExecutor(max_workers=cores) as ex:
+                res = list(ex.map(oracle.solve_instance, sample))
+            elb = time.perf_counter() - t0
+            cs = sum(x.problem.ncell * r["steps"] for x, r in zip(sample, res))
+            batch["cpu_all_cores"] = {"value": cs / elb, "unit": "cell-steps/s", "threads": cores,
+                                      "sample": f"first {len(sample)} instances, one per thread at a time ({elb:.1f} s)"}
 
         def rel_err(got, ref):
             return float(np.max(np.abs(got[:, 1:] - ref["rows"][:, 1:]) / np.abs(ref["rows"][:, 1:])))
@@ -578,7 +699,7 @@ def run_gpu(args):
         line["paths"]["fused"]["max_rel_err_vs_oracle"] = rel_err(rows_fused, want)
         line["paths"]["plain"]["max_rel_err_vs_oracle"] = rel_err(rows_plain, want)
         if adjoint is not None:
-            adjoint_cpu_baseline(adjoint, adjoint_cases)
+            adjoint_cpu_baseline(adjoint, adjoint_cases, cores)
         if small_1d is not None:
             import oracle
             want1 = oracle.solve_instance(pi.config_1d(200))
@@ -594,7 +715,96 @@ def run_gpu(args):
     return 0
 
 
+def profile_case(argv):
+    """``bench.py --profile-case PATH N1 [N2] [options]``: a few solves (or gradients)
+    of one seeded workload on one execution path - the small, self-contained
+    program to put under a profiler (ncu) or a timer.
+
+      fused|plain N1 [N2]   the 2-D size-and-shape problem on an N1 x N2 grid
+                            (--ndim 1: the 1-D fine-grid problem of N1 cells)
+      paper N1              the paper's base case at N1 x N1/2 bins (plain path)
+      batch N1              N1 batched 1-D instances (the batch workload), one solve each repeat
+      adjoint N1 [N2]       gradients (pbe_vjp, fused path) of the 2-D adjoint workload on
+                            N1 x N2 (--ndim 1: one 1-D instance of N1 cells)
+
+    --outputs K keeps the first K output times; --steps K runs K single steps
+    (Grid.step) instead of solves, outside the plain path's CUDA graph whose
+    conditional nodes a profiler cannot capture.  Prints one line per solve."""
+    ap = argparse.ArgumentParser(prog="bench.py --profile-case", description=profile_case.__doc__.splitlines()[0])
+    ap.add_argument("path", choices=["fused", "plain", "paper", "batch", "adjoint"])
+    ap.add_argument("N1", type=int)
+    ap.add_argument("N2", type=int, nargs="?")
+    ap.add_argument("--ndim", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--outputs", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--window", type=int, default=-1, choices=[-1, 0, 1])
+    a = ap.parse_args(argv)
+    import torch
+    import paper_2411_00742_gb300 as P
+
+    if a.path == "batch":
+        insts = pi.batch_1d(a.N1, seed=2411)
+        b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
+        packed = torch.as_tensor(b.pack([x.n0 for x in insts])).cuda()
+        for _ in range(a.repeat):
+            b.set_state(packed)
+            t0 = time.perf_counter()
+            _, st = b.solve(insts[0].t_out)
+            print(f"batch {a.N1} instances steps {st} {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+        b.close()
+        return 0
+    if a.path == "adjoint":
+        inst = pi.adjoint_batch_1d(1)[0] if a.ndim == 1 else pi.adjoint_2d(a.N1)
+        if a.ndim == 1 and a.N1 != inst.problem.ncell:
+            inst = pi.config_1d(a.N1)
+            inst.t_out = pi.loss_times()
+        if a.ndim == 2 and a.N2:
+            inst = pi.config_2d(a.N1, a.N2)
+            inst.t_out = pi.loss_times()
+        g = P.Grid.from_problem(inst.problem, path="fused")
+        g.set_state(inst.n0, inst.C0, 0.0)
+        rows, _ = g.solve(inst.t_out)
+        seeds = np.zeros_like(rows)
+        seeds[:, 1:] = 1.0 / np.abs(rows[:, 1:])
+        for _ in range(a.repeat):
+            g.set_state(inst.n0, inst.C0, 0.0)
+            t0 = time.perf_counter()
+            g.vjp(inst.t_out, seeds, 64)
+            print(f"adjoint {inst.problem.ncells} {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+        g.close()
+        return 0
+    if a.path == "paper":
+        inst, path = pi.paper_base_case(a.N1), "plain"
+    elif a.ndim == 1:
+        inst, path = pi.config_1d_fine(a.N1), a.path
+    else:
+        inst, path = pi.config_2d(a.N1, a.N2), a.path
+    t_out = inst.t_out[: a.outputs] if a.outputs > 0 else inst.t_out
+    g = P.Grid.from_problem(inst.problem, path=path)
+    g.set_window(a.window)
+    n0 = torch.as_tensor(inst.n0).cuda()
+    if a.steps > 0:
+        g.set_state(n0, inst.C0, 0.0)
+        for k in range(a.steps):   # the k-th step ends at the (k+1)-th output time at most
+            t0 = time.perf_counter()
+            dt = g.step(float(t_out[min(k + 1, len(t_out) - 1)]))
+            print(f"{a.path} {inst.problem.ncells} step dt {dt:.6g} {1e3 * (time.perf_counter() - t0):.3f} ms",
+                  flush=True)
+        g.close()
+        return 0
+    for _ in range(a.repeat):
+        g.set_state(n0, inst.C0, 0.0)
+        t0 = time.perf_counter()
+        _, steps = g.solve(t_out)
+        print(f"{a.path} {inst.problem.ncells} steps {steps} {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+    g.close()
+    return 0
+
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--profile-case":
+        return profile_case(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
