@@ -82,7 +82,8 @@ typedef struct {
     double kappa;      /* rho_c k_v u: g/g of solute per um^3/kg of crystal     */
     double cfl;        /* Courant number nu of the CFL step (0 < cfl <= 1)      */
     int scheme;        /* PBE_SCHEME_SSPRK2 or PBE_SCHEME_PAPER                  */
-    int growth_form;   /* 0: G = kg s^g; 1: Arrhenius G = kg exp(-ea/(T+273.15)) s^g (Appendix A) */
+    int growth_form;   /* 0: G = kg s^g; 1: Arrhenius G = kg exp(-ea/(T+273.15)) s^g (Appendix A);
+                          2: polynomial G_m = sum_k a_mk s^k (Eq. 6, pbe_set_growth_poly)   */
     int solubility_form; /* 0: polynomial csat; 1: c* = csat[0] exp(csat[1] T) (Appendix A) */
     double ea[2];      /* activation temperatures of the Arrhenius form (K)      */
 } pbe_kinetics;
@@ -117,6 +118,22 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k);
  * rounded to bf16 (round to nearest even), the biases in fp32; arithmetic is
  * fp32.  Solves with the closure run on the plain path. */
 pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count);
+
+/* Coefficients of the polynomial growth law of Eq. 6 (the model of the
+ * parameter estimation study of Sec. 4.1), used with growth_form 2:
+ * G_m = sum_{k=1..K} a[m K + k - 1] s^k for s = S - 1 > 0 (0 otherwise),
+ * m = 0 .. ndim-1 (one polynomial per growth direction); nucleation keeps
+ * B = kb s^b.  a: HOST array of ndim * K doubles, 1 <= K <= 4096.  Call it
+ * before pbe_set_kinetics selects growth_form 2; later calls replace the
+ * coefficients in place.  Synchronizes the grid's stream.  Errors:
+ * PBE_EINVAL (K, non-finite values), PBE_ENOMEM, PBE_ECUDA. */
+pbe_status pbe_set_growth_poly(pbe_grid* g, const double* a, int K);
+
+/* dL/da of the polynomial growth law from the last pbe_vjp of this grid
+ * (fused path; growth_form 2): `count` = ndim * K HOST doubles in the layout
+ * of pbe_set_growth_poly.  Synchronizes.  Errors: PBE_EINVAL (count),
+ * PBE_ESTATE (no such gradient yet), PBE_ECUDA. */
+pbe_status pbe_growth_poly_grad(pbe_grid* g, double* dL_da, int count);
 
 /* Load the state: distribution n (ncell values, `mem` memory), solute
  * concentration C and time t.  Initial condition of Eqs. (5)-(9). */
@@ -178,15 +195,26 @@ pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
  *   seeds              dL/d(rows): n_out x ncol doubles (`seeds_mem` memory);
  *                      the time column is ignored
  *   dL_dtheta          HOST, 6 doubles: d/d(kg[0], g[0], kg[1], g[1], kb, b)
- *                      (power-law kinetics; with fixed kinetics d/d(kg, kb))
+ *                      (power-law kinetics; with fixed kinetics d/d(kg, kb);
+ *                      with the polynomial growth law only kb and b, the
+ *                      coefficients' gradient then comes from
+ *                      pbe_growth_poly_grad)
  *   dL_dn0             optional, ncell doubles (`mem` memory): d/d(initial n)
  *   dL_dC0             optional HOST double: d/d(initial C)
  *   rows               optional, the forward rows (`mem` memory)
  *   dL_dweights        optional HOST, 4611 doubles: gradient with respect to the
  *                      learned closure's weights (PBE_KINETICS_MLP; the layout
  *                      of pbe_set_closure, taken at the stored bf16 values)
- * On return the grid holds the state at the end of the solve.  Allocates
- * work memory for the checkpoints; synchronizes the stream. */
+ * Paths: on PBE_PATH_FUSED one persistent cooperative launch runs the
+ * forward pass (checkpoints, and the records of the current segment), the
+ * recomputation of the earlier segments and the reverse sweep, with work
+ * buffers kept by the grid between calls (grown when a call needs more); on
+ * PBE_PATH_PLAIN per-stage kernels from the host, with buffers allocated per
+ * call.  The polynomial growth law is differentiated on the fused path only
+ * (PBE_EINVAL on the plain path).  Both agree to rounding.
+ * On return the grid holds the state at the end of the solve; synchronizes
+ * the stream.  With pbe_set_timing on, pbe_kernel_time gives the duration of
+ * the fused path's persistent launch. */
 pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const double* seeds, int seeds_mem,
                    int checkpoint_every, double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem,
                    double* dL_dweights);

@@ -144,7 +144,25 @@ class Grid:
 
     def set_kinetics(self, problem, theta=None, closure: bool = False):
         k = kinetics_struct(problem, theta, closure)
+        if k.growth_form == 2:
+            self.set_growth_poly(problem.poly)
         _lib.check(self.lib.pbe_set_kinetics(self.h, ctypes.byref(k)))
+
+    def set_growth_poly(self, a):
+        """Coefficients a_mk of the polynomial growth law (Eq. 6), ndim x K (flat, direction-major)."""
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if a.size == 0 or a.size % self.ndim:
+            raise ValueError("the growth polynomial holds ndim x K coefficients")
+        _lib.check(self.lib.pbe_set_growth_poly(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                a.size // self.ndim))
+        self._npoly = a.size
+
+    def growth_poly_grad(self):
+        """dL/da of the polynomial growth law from the last vjp (fused path)."""
+        out = np.zeros(getattr(self, "_npoly", 0))
+        _lib.check(self.lib.pbe_growth_poly_grad(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 out.size))
+        return out
 
     def set_state(self, n, C: float, t: float):
         p, mem, keep = _buf(n)

@@ -58,6 +58,8 @@ SIGNATURES = {
     "pbe_solve": [_P, _PD, _I, _P, _I, _PI64],
     "pbe_moments": [_P, _P, _I],
     "pbe_set_max_steps": [_P, _I64],
+    "pbe_set_growth_poly": [_P, _PD, _I],
+    "pbe_growth_poly_grad": [_P, _PD, _I],
     "pbe_set_wait_limit": [_P, _D],
     "pbe_set_window": [_P, _I],
     "pbe_set_timing": [_P, _I],

@@ -419,12 +419,16 @@ extern "C" pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const
     if (n_out < 1) return afail(PBE_EINVAL, "n_out must be >= 1");
     if (checkpoint_every < 1) return afail(PBE_EINVAL, "checkpoint_every must be >= 1");
     if (!g->has_kin || !g->has_state) return afail(PBE_ESTATE, "set kinetics and state before pbe_vjp");
-    if (g->kin.scheme != PBE_SCHEME_SSPRK2 || g->kin.growth_form != 0 || g->kin.solubility_form != 0)
-        return afail(PBE_EINVAL, "the adjoint differentiates the SSP-RK2 scheme with power-law kinetics or the closure");
+    if (g->kin.scheme != PBE_SCHEME_SSPRK2 || g->kin.growth_form == 1 || g->kin.solubility_form != 0)
+        return afail(PBE_EINVAL, "the adjoint differentiates the SSP-RK2 scheme with power-law kinetics, the "
+                                 "polynomial growth law or the closure");
+    const bool persistent = g->path == PBE_PATH_FUSED && fused_supported(g);
+    if (g->kin.growth_form == 2 && !persistent)
+        return afail(PBE_EINVAL, "the polynomial growth law is differentiated on the fused path (pbe_set_path)");
     if (!(t_out[0] >= g->t_host)) return afail(PBE_EINVAL, "t_out[0] precedes the current time");
     for (int j = 1; j < n_out; ++j)
         if (!(t_out[j] > t_out[j - 1]) || !std::isfinite(t_out[j])) return afail(PBE_EINVAL, "t_out must increase");
-    if (g->path == PBE_PATH_FUSED && fused_supported(g))
+    if (persistent)
         return vjp_persistent(g, t_out, n_out, seeds_in, seeds_mem, checkpoint_every, dL_dtheta, dL_dn0, dL_dC0,
                               rows, mem, dL_dweights);
     const int ncol = g->geo.ndim == 1 ? 6 : 12, vidx = g->geo.ndim == 1 ? 3 : 8;

@@ -60,6 +60,7 @@ struct RevS {
     double lth[6];            // dL/d(kg1, g1, kg2, g2, kb, b)
     double lCprev, lV0, ldt, ltn;
     double sum[3];            // the last reverse barrier's sums: lam . D1(n), lam . D2(n), lam at cell 0
+    double plG1, plG2, ps, pL;  // polynomial growth law: dL/dG_m, s and ln s of the stage just reversed
 };
 
 struct AdjOut {
@@ -91,6 +92,7 @@ struct AdjP {
     double* part;       // [2][G][4] block partials of the reverse barriers and the mu0 sums
     const double* seeds;
     double* dW;         // learned closure: dL/dweights (fp64), accumulated by block 0
+    double* dpoly;      // polynomial growth law: dL/da (ndim x npoly), accumulated by block 0
     AdjOut* out;
     unsigned long long* acc;
     size_t nc;
@@ -532,9 +534,12 @@ static __device__ __noinline__ StageCoef close2_mlp(Scal* S, const Kin& K, const
 // a call of its own so that the exponential is not evaluated speculatively
 static __device__ __noinline__ double pow_from_log(double g, double L) { return pbe_exp_tab(g * L); }
 
+// sG1, sG2: s dG_m/ds of the polynomial growth law (Eq. 6), recorded by the
+// forward chain; that law's coefficient gradients are accumulated separately
+// (poly_grad_accumulate), its dL/dkg and dL/dg entries stay 0.
 __device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, double C, double t, double G1, double G2,
-                                             double B, double L, double lG1, double lG2, double lB, double* lC,
-                                             double* lt, double* lth)
+                                             double B, double L, double sG1, double sG2, double lG1, double lG2,
+                                             double lB, double* lC, double* lt, double* lth)
 {
     if (K.kind == PBE_KINETICS_FIXED) {
         lth[0] += lG1;
@@ -548,6 +553,17 @@ __device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, dou
     const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) * K.inv_tcool : 0.0;
     const double dcs = K.cs1 + 2.0 * K.cs2 * tc.T;
     const double rd = __drcp_rn(d), rcs = __drcp_rn(tc.cs);
+    if (K.growth_form == 2) {
+        double sb;
+        if (K.kb > 0.0) sb = B * ik[2];
+        else sb = pow_from_log(K.b, L);
+        lth[4] += lB * sb;
+        lth[5] += lB * B * L;
+        const double q = (lG1 * sG1 + lG2 * sG2 + lB * K.b * B) * rd;
+        *lC += q;
+        *lt -= q * (C * rcs) * dcs * dTdt;
+        return;
+    }
     double s1, sb;
     if (K.kg1 > 0.0) s1 = G1 * ik[0];
     else s1 = pow_from_log(K.g1, L);
@@ -634,7 +650,12 @@ __device__ __forceinline__ void rev_mid(const AdjP& P, BlockSm& B)
             p0 += -lr * Q.V1 / (Q.M1 * Q.M1);
         }
     } else {
-        kin_backward(K, B.ik, Q.C1, A.t_new, Q.G1b, Q.G2b, Q.Bb, Q.Lb, dt * P1, dt * P2, lB, &lC1, &ltn, lth);
+        kin_backward(K, B.ik, Q.C1, A.t_new, Q.G1b, Q.G2b, Q.Bb, Q.Lb, Q.sGb1, Q.sGb2, dt * P1, dt * P2, lB, &lC1,
+                     &ltn, lth);
+        R.plG1 = dt * P1;
+        R.plG2 = dt * P2;
+        R.ps = Q.spb;
+        R.pL = Q.Lb;
     }
     const double lCprev = R.lCprev, lV0 = R.lV0;
     R.ldt = ldt;
@@ -698,7 +719,11 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
             p0 += -lr * A.V0 / (A.M0 * A.M0);
         }
     } else {
-        kin_backward(K, B.ik, A.C, A.t, A.G1a, A.G2a, A.Ba, A.La, lG1, lG2, lB, &lC, &ltp, lth);
+        kin_backward(K, B.ik, A.C, A.t, A.G1a, A.G2a, A.Ba, A.La, A.sGa1, A.sGa2, lG1, lG2, lB, &lC, &ltp, lth);
+        R.plG1 = lG1;
+        R.plG2 = lG2;
+        R.ps = A.spa;
+        R.pL = A.La;
     }
     const double lV0 = R.lV0;
 #pragma unroll
@@ -814,6 +839,25 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
         if (!stage2) break;
     }
     return true;
+}
+
+// dL/da_mk += dL/dG_m s^k for the stage just reversed (warp 0 of block 0; lane
+// l owns the terms k0 .. k0 + c - 1 as in poly_growth_warp, so the sums keep
+// a fixed order).  Nothing when S <= 1 (s = 0: the rates were 0).
+__device__ __forceinline__ void poly_grad_accumulate(const Kin& K, const RevS& R, double* dpoly)
+{
+    const double s = R.ps;
+    if (!(s > 0.0)) return;
+    const int lane = threadIdx.x & 31, n = K.npoly;
+    const int c = (n + 31) >> 5, k0 = lane * c + 1;
+    if (k0 > n) return;
+    const int k1 = min(n, k0 + c - 1);
+    const double lG[2] = {R.plG1, R.plG2};
+    double sk = k0 == 1 ? s : pbe_exp_tab((double)k0 * R.pL);
+    for (int k = k0; k <= k1; ++k) {
+        for (int m = 0; m < K.ndim; ++m) dpoly[(size_t)m * n + k - 1] += lG[m] * sk;
+        sk *= s;
+    }
 }
 
 // ---- the kernel ------------------------------------------------------------------
@@ -991,6 +1035,7 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
                     else rev_end<NDIM>(P, B);
                 }
                 __syncthreads();
+                if (P.K.growth_form == 2 && blockIdx.x == 0 && warp == 0) poly_grad_accumulate(P.K, B.R, P.dpoly);
             }
             if (status != PBE_OK) break;
             double* tmp = lam;
@@ -1066,6 +1111,8 @@ struct AdjWork {
     int G, ntiles, tiles_x, ti, t1;
     long long last_total;   // steps of the last gradient (sizes the checkpoint store of the next)
     double *seg_n, *seg_n1, *ck, *lamA, *lamB, *u, *part, *seeds, *dW;
+    double* dpoly;          // dL/d(growth polynomial coefficients) of the last gradient
+    int dpoly_cap;
     Scal *recA, *recB, *ckS;
     AdjOut* out;
     AdjOut* h_out;          // pinned
@@ -1137,7 +1184,7 @@ void adjoint_work_free(pbe_grid* g)
     AdjWork* w = g->adjw;
     if (!w) return;
     cudaFree(w->seg_n); cudaFree(w->seg_n1); cudaFree(w->ck); cudaFree(w->lamA); cudaFree(w->lamB);
-    cudaFree(w->u); cudaFree(w->part); cudaFree(w->seeds); cudaFree(w->dW);
+    cudaFree(w->u); cudaFree(w->part); cudaFree(w->seeds); cudaFree(w->dW); cudaFree(w->dpoly);
     cudaFree(w->recA); cudaFree(w->recB); cudaFree(w->ckS); cudaFree(w->out);
     cudaFreeHost(w->h_out);
     delete w;
@@ -1212,6 +1259,16 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
         }
         w->ck_cap = want_ck;
     }
+    const int npoly_all = g->kin.growth_form == 2 ? g->kin.npoly * ndim : 0;
+    if (npoly_all > w->dpoly_cap) {
+        PTRY(cudaStreamSynchronize(st));
+        if (grow(&w->dpoly, (size_t)npoly_all) != cudaSuccess) {
+            w->dpoly_cap = 0;
+            cudaGetLastError();
+            return afail(PBE_ENOMEM, "allocating the polynomial-coefficient gradient failed");
+        }
+        w->dpoly_cap = npoly_all;
+    }
     PTRY(cudaMemcpyAsync(w->seeds, seeds_in, sizeof(double) * ncol * n_out,
                          seeds_mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     const long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
@@ -1221,6 +1278,7 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
         PTRY(cudaMemsetAsync(w->lamA, 0, sizeof(double) * nc, st));
         PTRY(cudaMemsetAsync(g->d_bar, 0, 2 * kAccStride * sizeof(unsigned long long), st));
         if (g->kin.kind == PBE_KINETICS_MLP) PTRY(cudaMemsetAsync(w->dW, 0, sizeof(double) * kMlpNW, st));
+        if (npoly_all) PTRY(cudaMemsetAsync(w->dpoly, 0, sizeof(double) * npoly_all, st));
         PTRY(launch_prologue(g, n_out, g->max_steps, nullptr));
         AdjP P;
         memset(&P, 0, sizeof(P));
@@ -1228,6 +1286,7 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
         P.t_out = g->d_tout; P.rows = g->d_rows; P.rowpart = g->d_rowpart;
         P.seg_n = w->seg_n; P.seg_n1 = w->seg_n1; P.ck = w->ck; P.recA = w->recA; P.recB = w->recB; P.ckS = w->ckS;
         P.lamA = w->lamA; P.lamB = w->lamB; P.u = w->u; P.part = w->part; P.seeds = w->seeds; P.dW = w->dW;
+        P.dpoly = w->dpoly;
         P.out = w->out; P.acc = reinterpret_cast<unsigned long long*>(g->d_bar);
         P.nc = nc; P.Kc = K; P.ck_cap = w->ck_cap; P.n_out = n_out; P.ncol = ncol;
         P.ntiles = w->ntiles; P.tiles_x = w->tiles_x; P.ti = w->ti; P.t1 = w->t1; P.wait_limit = wait_limit; P.t0 = t0;
@@ -1280,3 +1339,18 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
 }
 
 }  // namespace pbe
+
+// dL/d(polynomial growth coefficients) of the last pbe_vjp (fused path, growth_form 2).
+extern "C" pbe_status pbe_growth_poly_grad(pbe_grid* g, double* dL_da, int count)
+{
+    using namespace pbe;
+    if (!g || !dL_da) return afail(PBE_EINVAL, "null argument");
+    if (g->kin.growth_form != 2 || !g->adjw || !g->adjw->dpoly)
+        return afail(PBE_ESTATE, "no gradient of the polynomial growth law: run pbe_vjp on the fused path first");
+    const int n = g->kin.npoly * g->geo.ndim;
+    if (count != n) return afail(PBE_EINVAL, "the polynomial growth law has %d coefficients (got %d)", n, count);
+    cudaError_t e = cudaMemcpyAsync(dL_da, g->adjw->dpoly, sizeof(double) * n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return afail(PBE_ECUDA, "reading the coefficient gradient failed: %s", cudaGetErrorString(e));
+    return PBE_OK;
+}

@@ -65,7 +65,7 @@ void free_grid_buffers(pbe_grid* g)
     pbe::adjoint_work_free(g);
     if (g->plain_exec) cudaGraphExecDestroy(g->plain_exec);
     cudaFree(g->d_n); cudaFree(g->d_n1); cudaFree(g->d_S); cudaFree(g->d_part); cudaFree(g->d_mom); cudaFree(g->d_bar);
-    cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart);
+    cudaFree(g->d_tout); cudaFree(g->d_rows); cudaFree(g->d_rowpart); cudaFree(g->d_poly);
     cudaFreeHost(g->h_S); cudaFreeHost(g->h_stage); cudaFreeHost(g->h_tout);
     if (g->ev_k0) cudaEventDestroy(g->ev_k0);
     if (g->ev_k1) cudaEventDestroy(g->ev_k1);
@@ -351,10 +351,14 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     if (!(k->cfl > 0.0 && k->cfl <= 1.0)) return fail(PBE_EINVAL, "cfl must lie in (0, 1]");
     if (!(k->t_cool > 0.0)) return fail(PBE_EINVAL, "t_cool must be positive");
     if (k->scheme != PBE_SCHEME_SSPRK2 && k->scheme != PBE_SCHEME_PAPER) return fail(PBE_EINVAL, "unknown scheme %d", k->scheme);
-    if ((k->growth_form != 0 && k->growth_form != 1) || (k->solubility_form != 0 && k->solubility_form != 1))
+    if ((k->growth_form < 0 || k->growth_form > 2) || (k->solubility_form != 0 && k->solubility_form != 1))
         return fail(PBE_EINVAL, "unknown growth or solubility form");
     if (k->scheme == PBE_SCHEME_PAPER && k->kind == PBE_KINETICS_MLP)
         return fail(PBE_EINVAL, "the learned closure runs with the SSP-RK2 scheme");
+    if (k->growth_form == 2 && k->kind != PBE_KINETICS_POWER_LAW)
+        return fail(PBE_EINVAL, "the polynomial growth law replaces the power law (kind PBE_KINETICS_POWER_LAW)");
+    if (k->growth_form == 2 && !g->d_poly)
+        return fail(PBE_ESTATE, "set the growth polynomial (pbe_set_growth_poly) before selecting growth_form 2");
     pbe_status pst = pbe::check_kinetic_values(k);
     if (pst != PBE_OK) return pst;
     pbe::Kin K;
@@ -372,6 +376,8 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     K.ea2 = k->ea[1];
     K.mW = g->d_mW;
     K.mB = g->d_mB;
+    K.poly = g->d_poly;
+    K.npoly = g->npoly;
     g->kin = K;
     g->has_kin = true;
     if (g->plain_exec) {  // kinetics are baked into the graph's kernel arguments
@@ -413,6 +419,36 @@ pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count)
     CUDA_TRY(cudaMemcpy(g->d_mB, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice));
     g->kin.mW = g->d_mW;
     g->kin.mB = g->d_mB;
+    return PBE_OK;
+}
+
+pbe_status pbe_set_growth_poly(pbe_grid* g, const double* a, int K)
+{
+    if (!g || !a) return fail(PBE_EINVAL, "null argument");
+    if (K < 1 || K > 4096) return fail(PBE_EINVAL, "the growth polynomial has 1..4096 terms a direction (got %d)", K);
+    const int n = K * g->geo.ndim;
+    for (int k = 0; k < n; ++k)
+        if (!std::isfinite(a[k])) return fail(PBE_EINVAL, "non-finite growth coefficient %d", k);
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PBE_ECUDA, "cannot select device %d", g->device);
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (g->npoly != K) {
+        cudaFree(g->d_poly);
+        g->d_poly = nullptr;
+        g->npoly = 0;
+        if (cudaMalloc(&g->d_poly, sizeof(double) * n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PBE_ENOMEM, "allocating %d growth coefficients failed", n);
+        }
+        g->npoly = K;
+    }
+    CUDA_TRY(cudaMemcpy(g->d_poly, a, sizeof(double) * n, cudaMemcpyHostToDevice));
+    g->kin.poly = g->d_poly;
+    g->kin.npoly = g->npoly;
+    if (g->plain_exec) {  // the kinetics are baked into the graph's kernel arguments
+        cudaGraphExecDestroy(g->plain_exec);
+        g->plain_exec = nullptr;
+    }
     return PBE_OK;
 }
 

@@ -20,13 +20,13 @@ __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const 
     const double C1 = S->C - K.kappa * (V1 - S->V0);
     const double dt = S->dt;
     const int clipped = S->clipped;
-    double G1, G2, B, L;
-    kinetics_warp_T(K, C1, tc, G1, G2, B, &L);
+    double G1, G2, B, L, sG[3];
+    kinetics_warp_T(K, C1, tc, G1, G2, B, &L, sG);
     if (lane == 0) {
         S->C1 = C1;
         S->V1 = V1;
         S->M1 = 1.0;
-        S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L;
+        S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L; S->sGb1 = sG[0]; S->sGb2 = sG[1]; S->spb = sG[2];
         if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
             S->status = PBE_ENONFINITE;
             S->done = 1;
@@ -55,10 +55,10 @@ __device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const 
     const int oi = (finite && clipped) ? out_idx + 1 : out_idx;
     const bool done = !finite || oi >= n_out || steps >= max_steps;
     __syncwarp();   // every lane has read S before lane 0 writes it
-    double G1 = 0.0, G2 = 0.0, B = 0.0, dt = 0.0, t_new = t, L = 0.0;
+    double G1 = 0.0, G2 = 0.0, B = 0.0, dt = 0.0, t_new = t, L = 0.0, sG[3] = {0.0, 0.0, 0.0};
     int clip2 = 0;
     if (!done) {   // the next step: kinetics at (C, t), CFL step to the next output time
-        kinetics_warp_T(K, C, tc, G1, G2, B, &L);
+        kinetics_warp_T(K, C, tc, G1, G2, B, &L, sG);
         clip2 = timestep_fast(K, g, G1, G2, t, t_out[oi], dt, t_new);
     }
     if (lane == 0) {
@@ -89,7 +89,7 @@ __device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const 
             }
         }
         if (!done) {
-            S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L;
+            S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L; S->sGa1 = sG[0]; S->sGa2 = sG[1]; S->spa = sG[2];
             S->dt = dt; S->t_new = t_new; S->clipped = clip2;
             if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
                 S->status = PBE_ENONFINITE;

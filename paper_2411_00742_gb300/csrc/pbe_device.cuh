@@ -26,6 +26,8 @@ struct Kin {
     double ea1, ea2;          // Arrhenius activation temperatures (growth_form 1)
     const __nv_bfloat16* mW;  // learned closure: W1[64][3], W2[64][64], W3[3][64] (bf16, device)
     const float* mB;          // and b1[64], b2[64], b3[3] (fp32, device)
+    const double* poly;       // growth_form 2 (Eq. 6): a[m * npoly + k - 1], k = 1..npoly, m < ndim (device)
+    int npoly;
 };
 
 constexpr int kMlpH = 64;
@@ -54,6 +56,8 @@ struct Scal {
     unsigned int counter;       // arrival counter of the last-block reductions
     double La, Lb;              // ln s of the stage-1 and stage-2 power-law kinetics (warp chains;
                                 // 0 when S <= 1), kept for the adjoint
+    double sGa1, sGa2, sGb1, sGb2;  // s dG_m/ds of the polynomial growth law (Eq. 6) at both stages
+    double spa, spb;                // s = S - 1 at both stages (polynomial growth law)
 };
 
 // S = C / c*(T), s = max(S - 1, 0); G_d = kg_d s^g_d, B = kb s^b (Sec. 2.1,
@@ -275,12 +279,54 @@ __device__ __forceinline__ KinT kin_temperature(const Kin& K, double t)
     return KinT{T, cs};
 }
 
-// Lout (optional) receives ln s (0 for fixed kinetics or S <= 1).
+// The polynomial growth law of Eq. 6, G_m = sum_{k=1..K} a_mk s^k, and
+// s dG_m/ds = sum_k k a_mk s^k, for both directions, on one warp: lane l takes
+// the terms k0 .. k0 + c - 1 (c = ceil(K / 32), k0 = l c + 1) by Horner's rule
+// in s, scaled by s^k0 = exp(k0 ln s); a butterfly sums the lanes (the same
+// result in every lane).
+__device__ __forceinline__ void poly_growth_warp(const Kin& K, double s, double L, double& G1, double& G2,
+                                                 double& sG1, double& sG2)
+{
+    const int lane = threadIdx.x & 31, n = K.npoly;
+    const int c = (n + 31) >> 5, k0 = lane * c + 1;
+    double g[2] = {0.0, 0.0}, h[2] = {0.0, 0.0};
+    if (k0 <= n) {
+        const int k1 = min(n, k0 + c - 1);
+        const double sk0 = k0 == 1 ? s : pbe_exp_tab((double)k0 * L);
+        for (int m = 0; m < K.ndim; ++m) {
+            const double* a = K.poly + (size_t)m * n;
+            double pg = 0.0, ph = 0.0;
+            for (int k = k1; k >= k0; --k) {
+                const double ak = __ldg(a + k - 1);
+                pg = fma(pg, s, ak);
+                ph = fma(ph, s, (double)k * ak);
+            }
+            g[m] = pg * sk0;
+            h[m] = ph * sk0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        g[0] += __shfl_xor_sync(0xffffffffu, g[0], o);
+        g[1] += __shfl_xor_sync(0xffffffffu, g[1], o);
+        h[0] += __shfl_xor_sync(0xffffffffu, h[0], o);
+        h[1] += __shfl_xor_sync(0xffffffffu, h[1], o);
+    }
+    G1 = g[0];
+    G2 = K.ndim == 2 ? g[1] : 0.0;
+    sG1 = h[0];
+    sG2 = K.ndim == 2 ? h[1] : 0.0;
+}
+
+// Lout (optional) receives ln s (0 for fixed kinetics or S <= 1); sGout
+// (optional, 3 values) s dG_1/ds, s dG_2/ds and s of the polynomial growth
+// law (0 otherwise).
 __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const KinT& tc, double& G1, double& G2,
-                                                double& B, double* Lout = nullptr)
+                                                double& B, double* Lout = nullptr, double* sGout = nullptr)
 {
     const int lane = threadIdx.x & 31;
     if (Lout) *Lout = 0.0;
+    if (sGout) { sGout[0] = 0.0; sGout[1] = 0.0; sGout[2] = 0.0; }
     if (K.kind == PBE_KINETICS_FIXED) {
         G1 = K.kg1;
         G2 = (K.ndim == 2) ? K.kg2 : 0.0;
@@ -303,16 +349,22 @@ __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const Ki
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
     B = __shfl_sync(0xffffffffu, e, 2);
+    if (K.growth_form == 2) {   // Eq. 6 in place of the power law; nucleation keeps its law
+        double sG1, sG2;
+        const double sp = d * __drcp_rn(cs);
+        poly_growth_warp(K, sp, L, G1, G2, sG1, sG2);
+        if (sGout) { sGout[0] = sG1; sGout[1] = sG2; sGout[2] = sp; }
+    }
 }
 
 __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B,
-                                              double* Lout = nullptr)
+                                              double* Lout = nullptr, double* sGout = nullptr)
 {
     if (K.kind == PBE_KINETICS_FIXED) {
-        kinetics_warp_T(K, C, KinT{0.0, 0.0}, G1, G2, B, Lout);
+        kinetics_warp_T(K, C, KinT{0.0, 0.0}, G1, G2, B, Lout, sGout);
         return;
     }
-    kinetics_warp_T(K, C, kin_temperature(K, t), G1, G2, B, Lout);
+    kinetics_warp_T(K, C, kin_temperature(K, t), G1, G2, B, Lout, sGout);
 }
 
 // ---------------------------------------------------------------------------
@@ -385,14 +437,15 @@ constexpr double kLnB = 11.512925464970229;    // ln 1e5
 // pre: temperature and solubility at t when the caller has them
 __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t, double ratio, double& G1,
                                                 double& G2, double& B, const KinT* pre = nullptr,
-                                                double* Lout = nullptr)
+                                                double* Lout = nullptr, double* sGout = nullptr)
 {
     if (K.kind != PBE_KINETICS_MLP) {
-        if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B, Lout);
-        else kinetics_warp(K, C, t, G1, G2, B, Lout);
+        if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B, Lout, sGout);
+        else kinetics_warp(K, C, t, G1, G2, B, Lout, sGout);
         return;
     }
     if (Lout) *Lout = 0.0;
+    if (sGout) { sGout[0] = 0.0; sGout[1] = 0.0; sGout[2] = 0.0; }
     float x[3], o[3];
     if (!mlp_inputs(K, C, t, ratio, x)) {
         G1 = 0.0; G2 = 0.0; B = 0.0;
@@ -455,12 +508,12 @@ __device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const G
     const int lane = threadIdx.x & 31;
     const double t_next = t_out[S->out_idx];
     const double C = S->C, t = S->t;
-    double G1, G2, B, dt, t_new, L;
-    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre, &L);
+    double G1, G2, B, dt, t_new, L, sG[3];
+    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre, &L, sG);
     const int clipped = timestep_fast(K, g, G1, G2, t, t_next, dt, t_new);
     __syncwarp();
     if (lane == 0) {
-        S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L;
+        S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L; S->sGa1 = sG[0]; S->sGa2 = sG[1]; S->spa = sG[2];
         S->dt = dt; S->t_new = t_new; S->clipped = clipped;
         if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
             S->status = PBE_ENONFINITE;
@@ -476,14 +529,14 @@ __device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double
 {
     const int lane = threadIdx.x & 31;
     const double C1 = S->C - K.kappa * (V1 - S->V0);
-    double G1, G2, B, L;
-    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre, &L);
+    double G1, G2, B, L, sG[3];
+    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre, &L, sG);
     __syncwarp();
     if (lane == 0) {
         S->C1 = C1;
         S->V1 = V1;
         S->M1 = M1;
-        S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L;
+        S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L; S->sGb1 = sG[0]; S->sGb2 = sG[1]; S->spb = sG[2];
         if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
             S->status = PBE_ENONFINITE;
             S->done = 1;

@@ -47,6 +47,8 @@ struct pbe_grid {
     long long wait_cycles;  // device-wide wait limit of the fused path (-1: default ~1 s)
     __nv_bfloat16* d_mW;    // learned closure weights (bf16) and biases (fp32)
     float* d_mB;
+    double* d_poly;         // polynomial growth law (Eq. 6): ndim x npoly coefficients
+    int npoly;
     // optional device timing of the launch that advances the state in pbe_solve
     bool timing;
     cudaEvent_t ev_k0, ev_k1;
