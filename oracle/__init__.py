@@ -63,7 +63,8 @@ class Params(ctypes.Structure):
                 ("mlp", ctypes.POINTER(ctypes.c_double)),
                 ("scheme", ctypes.c_int), ("growth_form", ctypes.c_int), ("solubility_form", ctypes.c_int),
                 ("ea1", ctypes.c_double), ("ea2", ctypes.c_double),
-                ("poly", ctypes.POINTER(ctypes.c_double)), ("npoly", ctypes.c_int)]
+                ("poly", ctypes.POINTER(ctypes.c_double)), ("npoly", ctypes.c_int),
+                ("mlp_box", ctypes.c_int), ("mlp_lo", ctypes.c_double * 3), ("mlp_hi", ctypes.c_double * 3)]
 
 
 _lib = None
@@ -148,6 +149,11 @@ def params(problem, mlp=None) -> Params:
     if poly.size:
         P.poly = poly.ctypes.data_as(_D)
         P.npoly = poly.size // p.ndim
+    box = getattr(p, "mlp_box", ())
+    if box:
+        P.mlp_box = 1
+        for k in range(3):
+            P.mlp_lo[k], P.mlp_hi[k] = float(box[0][k]), float(box[1][k])
     P._keep = (arr if mlp is not None else None, poly)
     return P
 

@@ -56,6 +56,8 @@ typedef struct {
     const double* poly;   /* growth_form 2 (Eq. 6): G_m = sum_{k=1..npoly} poly[m npoly + k - 1] (S - 1)^k,
                              m = 0 (L1) and, in 2-D, 1 (L2) */
     int npoly;
+    int mlp_box;          /* learned closure: 1 if its inputs have a training box */
+    double mlp_lo[3], mlp_hi[3];
 } orc_params;
 
 /* Learned kinetics closure (the empirical hybrid model of Sec. 4.2: a network
@@ -423,15 +425,18 @@ static double silu_grad(double z)
 
 /* adjoint of the learned closure at (C, t, ratio): accumulates lC, lt, the
  * adjoint of the moment ratio, and dL/dweights into dW (layout of the weights) */
-static void mlp_kinetics_adjoint(const orc_params* p, double C, double t, double ratio, double lG1, double lG2,
-                                 double lB, double* lC, double* lt, double* lratio, double* dW)
+/* Returns 1, accumulating nothing, when the forward pass took the closure's
+ * plain-kinetics fallback at this evaluation (the caller then differentiates
+ * the power law); 0 otherwise. */
+static int mlp_kinetics_adjoint(const orc_params* p, double C, double t, double ratio, double lG1, double lG2,
+                                double lB, double* lC, double* lt, double* lratio, double* dW)
 {
     double T = temperature_r(p, t);
     double dTdt = (t < p->t_cool) ? (p->T1 - p->T0) / p->t_cool : 0.0;
     double cs = p->cs0 + p->cs1 * T + p->cs2 * T * T;
     double dcs = p->cs1 + 2.0 * p->cs2 * T;
     double s = C / cs - 1.0;
-    if (!(s > 0.0)) return;
+    if (!(s > 0.0)) return 0;
     const double* w = p->mlp;
     const double* W1 = w;
     const double* b1 = W1 + MLP_H * 3;
@@ -462,8 +467,9 @@ static void mlp_kinetics_adjoint(const orc_params* p, double C, double t, double
         for (int h = 0; h < MLP_H; ++h) z += W3[m * MLP_H + h] * a2[h];
         o[m] = z;
     }
-    double lo[3] = {lG1 * exp(o[0] + log(0.01)), p->ndim == 2 ? lG2 * exp(o[1] + log(0.005)) : 0.0,
-                    lB * exp(o[2] + log(1e5))};
+    const double G[3] = {exp(o[0] + log(0.01)), p->ndim == 2 ? exp(o[1] + log(0.005)) : 0.0, exp(o[2] + log(1e5))};
+    if (mlp_fallback_r(p, x, G[0], G[1], G[2])) return 1;
+    double lo[3] = {lG1 * G[0], lG2 * G[1], lB * G[2]};
     double la2[MLP_H], lz2[MLP_H], la1[MLP_H], lz1[MLP_H], lx[3] = {0, 0, 0};
     for (int h = 0; h < MLP_H; ++h) la2[h] = 0.0;
     for (int m = 0; m < 3; ++m) {
@@ -495,6 +501,7 @@ static void mlp_kinetics_adjoint(const orc_params* p, double C, double t, double
     *lC += lS / cs;
     *lt += lT * dTdt;
     *lratio += 1e-6 * lx[2];
+    return 0;
 }
 
 /* Vector-Jacobian product of a solve.  drows[n_out * ncol]: dL/d(row entries)
@@ -563,12 +570,11 @@ long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const 
         double lG1 = r->dt * P[0], lG2 = r->dt * P[1], lB = r->dt * P[2] / area;
         /* kinetics at (C1, t') */
         double lC1 = 0.0, ltn = lt;
-        if (p->mlp) {
-            double lr = 0.0;
-            mlp_kinetics_adjoint(p, r->C1, r->t_new, r->r1, lG1, lG2, lB, &lC1, &ltn, &lr, dmlp);
+        double lr = 0.0;
+        if (p->mlp && !mlp_kinetics_adjoint(p, r->C1, r->t_new, r->r1, lG1, lG2, lB, &lC1, &ltn, &lr, dmlp)) {
             double m0 = mu0_r(p, n1), V1 = volume_r(p, n1);
             for (size_t q = 0; q < nc; ++q) lam1[q] += (lr / m0) * w[q] - (lr * V1 / (m0 * m0)) * area;
-        } else {
+        } else {   /* the power law (also the closure's fallback) */
             kinetics_adjoint(p, r->C1, r->t_new, lG1, lG2, lB, &lC1, &ltn, lth, dpoly);
         }
         /* C1 = C - kappa (V1 - V0) */
@@ -595,12 +601,11 @@ long orc_vjp(const orc_params* p, const double* n0, double C0, double t0, const 
             ltp = -ldt;
         }
         /* kinetics at (C, t) */
-        if (p->mlp) {
-            double lr = 0.0;
-            mlp_kinetics_adjoint(p, r->C, r->t, r->r0, lG1, lG2, lB, &lCp, &ltp, &lr, dmlp);
+        lr = 0.0;
+        if (p->mlp && !mlp_kinetics_adjoint(p, r->C, r->t, r->r0, lG1, lG2, lB, &lCp, &ltp, &lr, dmlp)) {
             double m0 = mu0_r(p, nk), V0 = volume_r(p, nk);
             for (size_t q = 0; q < nc; ++q) lamp[q] += (lr / m0) * w[q] - (lr * V0 / (m0 * m0)) * area;
-        } else {
+        } else {   /* the power law (also the closure's fallback) */
             kinetics_adjoint(p, r->C, r->t, lG1, lG2, lB, &lCp, &ltp, lth, dpoly);
         }
         memcpy(lam, lamp, nc * sizeof(double));

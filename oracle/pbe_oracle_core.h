@@ -74,6 +74,18 @@ static SCALAR SFX(solubility)(const orc_params* p, SCALAR T)
     return p->cs0 + p->cs1 * T + p->cs2 * T * T;
 }
 
+/* The closure's plain-kinetics fallback (its rates stay those of the power
+ * law of the kinetic parameters, which remain the judge of the closure): taken
+ * when an input leaves the training box (if one is set) or a rate is not
+ * finite.  The box test is on the FP64 inputs, as on the GPU. */
+static int SFX(mlp_fallback)(const orc_params* p, const SCALAR* x, SCALAR G1, SCALAR G2, SCALAR B)
+{
+    if (p->mlp_box)
+        for (int k = 0; k < 3; ++k)
+            if (!(RE(x[k]) >= p->mlp_lo[k] && RE(x[k]) <= p->mlp_hi[k])) return 1;
+    return !(isfinite(RE(G1)) && isfinite(RE(G2)) && isfinite(RE(B)));
+}
+
 /* Kinetics at concentration C and time t.
  * S = c / c*(T) (Sec. 2.1); growth and nucleation only for S > 1
  * (Appendix A: growth "only applies when S exceeds one").
@@ -96,7 +108,8 @@ static void SFX(kinetics)(const SFX(ctx)* c, SCALAR C, SCALAR t, SCALAR ratio,
         *G1 = SEXP(o[0] + log(0.01));
         *G2 = (p->ndim == 2) ? SEXP(o[1] + log(0.005)) : (SCALAR)0.0;
         *B = SEXP(o[2] + log(1e5));
-        return;
+        if (!SFX(mlp_fallback)(p, x, *G1, *G2, *B)) return;
+        /* else: the power law below */
     }
     if (p->fixed_kinetics) {
         *G1 = c->kg1;

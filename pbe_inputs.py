@@ -50,6 +50,8 @@ class Problem:
     solubility_form: int = 0   # 0: polynomial csat; 1: csat[0] exp(csat[1] T)
     ea: tuple = (0.0, 0.0)     # activation temperatures of the Arrhenius form (K)
     poly: tuple = ()           # growth_form 2: ndim x K coefficients, a_m1 .. a_mK of G_m = sum_k a_mk s^k
+    mlp_box: tuple = ()        # learned closure: ((lo0, lo1, lo2), (hi0, hi1, hi2)) training box of its
+                               # inputs; outside it (or for a non-finite rate) the power law above is used
 
     @property
     def ncell(self) -> int:

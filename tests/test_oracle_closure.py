@@ -53,3 +53,74 @@ def test_closure_adjoint_matches_complex_step(ndim):
     for k in (0, 5, H * 3 + 7, H * 3 + H + 100, H * 3 + H + H * H + 3, oracle.MLP_NW - 2, oracle.MLP_NW - 1):
         _, dr = oracle.solve_cs(inst.problem, 6 + k, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)
         assert dW[k] == pytest.approx(float(np.sum(seeds * dr)), rel=1e-10, abs=1e-14 * np.max(np.abs(dW))), k
+
+
+def _x0_along(problem, rows):
+    """Closure input x0 = 4 (S - 1) at the output rows (t, ..., C)."""
+    T = np.array([oracle.temperature(problem, t) for t in rows[:, 0]])
+    cs = problem.csat[0] + problem.csat[1] * T + problem.csat[2] * T * T
+    return 4.0 * (rows[:, -1] / cs - 1.0)
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_closure_fallback_box_limits(ndim):
+    """A training box that no input reaches makes the closure solve the power-law
+    solve bit for bit (every rate from the fallback); a box holding every input
+    leaves the closure solve unchanged bit for bit."""
+    import dataclasses
+    inst = pi.config_1d(120) if ndim == 1 else cd.trajectories(1, seed=5, N=20)[0]
+    w = cd.stored_weights(cd.initial_weights(9, 0.2))
+    p = inst.problem
+    plain = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)
+    closure = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)
+    assert not np.array_equal(plain["rows"], closure["rows"])
+    none = dataclasses.replace(p, mlp_box=((50.0, 50.0, 50.0), (60.0, 60.0, 60.0)))
+    allin = dataclasses.replace(p, mlp_box=((-1e300, -1e300, -1e300), (1e300, 1e300, 1e300)))
+    got = oracle.solve(none, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)
+    np.testing.assert_array_equal(got["rows"], plain["rows"])
+    np.testing.assert_array_equal(got["n"], plain["n"])
+    got = oracle.solve(allin, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)
+    np.testing.assert_array_equal(got["rows"], closure["rows"])
+
+
+def test_closure_nonfinite_rate_falls_back_to_the_power_law():
+    """A network whose nucleation output overflows exp() gives the power-law
+    rates at that state, not an infinite rate."""
+    p = pi.config_2d(16).problem
+    w = np.zeros(oracle.MLP_NW)
+    w[-1] = 800.0     # b3[2]: ln B = 800 + ln 1e5 overflows
+    C, t = 1.3 * 0.168, 4000.0
+    got = oracle.kinetics_mlp(p, w, C, t, 3.7e5)
+    want = oracle.kinetics(p, C, t)
+    assert got == want and all(math.isfinite(v) for v in got)
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_closure_adjoint_with_partial_fallback_matches_complex_step(ndim):
+    """A box that cuts the supersaturation input at its median value: the
+    stages above it take the power law, the rest the network.  The adjoint
+    differentiates whichever the forward pass took: the kinetic parameters'
+    derivatives (from the fallback stages) and the weights' (from the network
+    stages) against complex-step derivatives."""
+    import dataclasses
+    inst = pi.config_1d(120) if ndim == 1 else cd.trajectories(1, seed=5, N=20)[0]
+    inst.t_out = pi.loss_times()[:25]
+    w = cd.stored_weights(cd.initial_weights(9, 0.2))
+    r0 = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)["rows"]
+    x0 = _x0_along(inst.problem, r0)
+    cut = float(np.median(x0[x0 > 0]))
+    p = dataclasses.replace(inst.problem, mlp_box=((-10.0, -10.0, -10.0), (cut, 10.0, 10.0)))
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)["rows"]
+    assert not np.array_equal(r, r0)
+    rng = np.random.default_rng(3)
+    seeds = rng.standard_normal(r.shape) / (np.abs(r) + 1.0)
+    seeds[:, 0] = 0.0
+    dth, _, _, dW = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds, mlp=w)
+    for j in ((0, 1, 4, 5) if ndim == 1 else range(6)):
+        _, dr = oracle.solve_cs(p, j, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)
+        assert dth[j] == pytest.approx(float(np.sum(seeds * dr)), rel=1e-10), j
+    assert np.any(dth != 0.0)
+    H = 64
+    for k in (0, 5, H * 3 + 7, H * 3 + H + 100, oracle.MLP_NW - 1):
+        _, dr = oracle.solve_cs(p, 6 + k, inst.n0, inst.C0, 0.0, inst.t_out, mlp=w)
+        assert dW[k] == pytest.approx(float(np.sum(seeds * dr)), rel=1e-10, abs=1e-14 * np.max(np.abs(dW))), k
