@@ -116,7 +116,8 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k);
  * for S <= 1.  w: HOST float array of 4611 values in the layout W1[64][3],
  * b1[64], W2[64][64], b2[64], W3[3][64], b3[3]; the weight matrices are stored
  * rounded to bf16 (round to nearest even), the biases in fp32; arithmetic is
- * fp32.  Solves with the closure run on the plain path. */
+ * fp32.  Rates that are not finite fall back to the power law
+ * (pbe_set_closure_box).  Solves with the closure run on the plain path. */
 pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count);
 
 /* Coefficients of the polynomial growth law of Eq. 6 (the model of the
@@ -134,6 +135,17 @@ pbe_status pbe_set_growth_poly(pbe_grid* g, const double* a, int K);
  * of pbe_set_growth_poly.  Synchronizes.  Errors: PBE_EINVAL (count),
  * PBE_ESTATE (no such gradient yet), PBE_ECUDA. */
 pbe_status pbe_growth_poly_grad(pbe_grid* g, double* dL_da, int count);
+
+/* Training box of the learned closure's inputs, and with it the plain-kinetics
+ * fallback of the hybrid model (Sec. 4.2): at any kinetics evaluation whose
+ * inputs (x0, x1, x2) of pbe_set_closure, in FP64, are not all inside
+ * [lo[k], hi[k]], and at any evaluation where a network rate is not finite,
+ * the rates are those of the power law of the pbe_kinetics parameters (kg,
+ * g, kb, b) instead.  The non-finite test is always on; the box only after
+ * this call.  pbe_vjp differentiates whichever rates each stage used.  lo,
+ * hi: HOST arrays of 3 doubles, lo[k] <= hi[k]; both NULL removes the box.
+ * Errors: PBE_EINVAL. */
+pbe_status pbe_set_closure_box(pbe_grid* g, const double* lo, const double* hi);
 
 /* Load the state: distribution n (ncell values, `mem` memory), solute
  * concentration C and time t.  Initial condition of Eqs. (5)-(9). */

@@ -142,10 +142,23 @@ class Grid:
             raise ValueError(f"the closure has {CLOSURE_SIZE} weights")
         _lib.check(self.lib.pbe_set_closure(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size))
 
+    def set_closure_box(self, lo=None, hi=None):
+        """Training box of the closure's inputs (None: no box); outside it, and for
+        non-finite network rates, the power law of the kinetic parameters is used."""
+        if lo is None or hi is None:
+            _lib.check(self.lib.pbe_set_closure_box(self.h, None, None))
+            return
+        lo = (ctypes.c_double * 3)(*[float(v) for v in lo])
+        hi = (ctypes.c_double * 3)(*[float(v) for v in hi])
+        _lib.check(self.lib.pbe_set_closure_box(self.h, lo, hi))
+
     def set_kinetics(self, problem, theta=None, closure: bool = False):
         k = kinetics_struct(problem, theta, closure)
         if k.growth_form == 2:
             self.set_growth_poly(problem.poly)
+        box = getattr(problem, "mlp_box", ())
+        if closure and box:
+            self.set_closure_box(box[0], box[1])
         _lib.check(self.lib.pbe_set_kinetics(self.h, ctypes.byref(k)))
 
     def set_growth_poly(self, a):

@@ -59,6 +59,7 @@ SIGNATURES = {
     "pbe_moments": [_P, _P, _I],
     "pbe_set_max_steps": [_P, _I64],
     "pbe_set_growth_poly": [_P, _PD, _I],
+    "pbe_set_closure_box": [_P, _PD, _PD],
     "pbe_growth_poly_grad": [_P, _PD, _I],
     "pbe_set_wait_limit": [_P, _D],
     "pbe_set_window": [_P, _I],

@@ -258,7 +258,7 @@ __global__ void k_adj_mid(AdjS* A, const Scal* recA, const Scal* recB, Kin K, Ge
         lo[0] = dt * P1 * recB->G1b;
         lo[1] = g.ndim == 2 ? dt * P2 * recB->G2b : 0.0;
         lo[2] = dt * P0 / dA * recB->Bb;
-        run_mlp = K.kind == PBE_KINETICS_MLP && (recB->G1b > 0.0 || recB->Bb > 0.0);
+        run_mlp = K.kind == PBE_KINETICS_MLP && !recB->fbb && (recB->G1b > 0.0 || recB->Bb > 0.0);
     }
     __syncthreads();
     if (run_mlp) {
@@ -271,7 +271,7 @@ __global__ void k_adj_mid(AdjS* A, const Scal* recA, const Scal* recB, Kin K, Ge
     a.ldt = recB->G1b * P1 + recB->G2b * P2 + recB->Bb * P0 / dA;
     double lC1 = 0.0, ltn = a.lt;
     for (int k = 0; k < kMaxMom; ++k) a.pu[k] = 0.0;
-    if (K.kind == PBE_KINETICS_MLP) {
+    if (K.kind == PBE_KINETICS_MLP && !recB->fbb) {   // else the power law (or the closure's fallback)
         if (run_mlp) {
             double lr = 0.0;
             mlp_input_adjoint(K, recB->C1, recA->t_new, lx, &lC1, &ltn, &lr);
@@ -316,7 +316,7 @@ __global__ void k_adj_end(AdjS* A, const Scal* recA, Kin K, Geom g, const double
         lo[0] = lG1 * recA->G1a;
         lo[1] = g.ndim == 2 ? lG2 * recA->G2a : 0.0;
         lo[2] = sl[3] * recA->Ba;
-        run_mlp = K.kind == PBE_KINETICS_MLP && (recA->G1a > 0.0 || recA->Ba > 0.0);
+        run_mlp = K.kind == PBE_KINETICS_MLP && !recA->fba && (recA->G1a > 0.0 || recA->Ba > 0.0);
     }
     __syncthreads();
     if (run_mlp) {
@@ -329,7 +329,7 @@ __global__ void k_adj_end(AdjS* A, const Scal* recA, Kin K, Geom g, const double
     double ltp = recA->clipped ? -sl[0] : a.ltn;
     double lC = a.lCprev;
     for (int k = 0; k < kMaxMom; ++k) a.pc[k] = 0.0;
-    if (K.kind == PBE_KINETICS_MLP) {
+    if (K.kind == PBE_KINETICS_MLP && !recA->fba) {   // else the power law (or the closure's fallback)
         if (run_mlp) {
             double lr = 0.0;
             mlp_input_adjoint(K, recA->C, recA->t, lx, &lC, &ltp, &lr);

@@ -622,7 +622,8 @@ __device__ __forceinline__ void rev_mid(const AdjP& P, BlockSm& B)
     RevS& R = B.R;
     const double P1 = R.sum[0], P2 = R.sum[1], P0 = R.sum[2], dt = A.dt;
     const double lB = dt * P0 * inv_dA;
-    if (K.kind == PBE_KINETICS_MLP) {
+    const bool net = K.kind == PBE_KINETICS_MLP && !Q.fbb;   // else the power law (or the closure's fallback)
+    if (net) {
         if (threadIdx.x == 0) {
             B.mlp_lo[0] = dt * P1 * Q.G1b;
             B.mlp_lo[1] = NDIM == 2 ? dt * P2 * Q.G2b : 0.0;
@@ -642,7 +643,7 @@ __device__ __forceinline__ void rev_mid(const AdjP& P, BlockSm& B)
     for (int k = 0; k < 6; ++k) lth[k] = R.lth[k];
     const double ldt = Q.G1b * P1 + Q.G2b * P2 + Q.Bb * P0 * inv_dA;
     double lC1 = 0.0, ltn = R.lt, pv = 0.0, p0 = 0.0;
-    if (K.kind == PBE_KINETICS_MLP) {
+    if (net) {
         if (B.run_mlp) {
             double lr = 0.0;
             mlp_input_adjoint(K, Q.C1, A.t_new, B.mlp_lx, &lC1, &ltn, &lr);
@@ -691,7 +692,8 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
         lG1 += dR * g.inv_d1;
         if (NDIM == 2) lG2 += dR * g.inv_d2;
     }
-    if (K.kind == PBE_KINETICS_MLP) {
+    const bool net = K.kind == PBE_KINETICS_MLP && !A.fba;   // else the power law (or the closure's fallback)
+    if (net) {
         if (threadIdx.x == 0) {
             B.mlp_lo[0] = lG1 * A.G1a;
             B.mlp_lo[1] = NDIM == 2 ? lG2 * A.G2a : 0.0;
@@ -711,7 +713,7 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
     for (int k = 0; k < 6; ++k) lth[k] = R.lth[k];
     double ltp = A.clipped ? -ldt : R.ltn;   // clipped: dt = t_next - t
     double lC = R.lCprev, pv = 0.0, p0 = 0.0;
-    if (K.kind == PBE_KINETICS_MLP) {
+    if (net) {
         if (B.run_mlp) {
             double lr = 0.0;
             mlp_input_adjoint(K, A.C, A.t, B.mlp_lx, &lC, &ltp, &lr);

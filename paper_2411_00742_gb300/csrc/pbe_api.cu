@@ -378,6 +378,8 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     K.mB = g->d_mB;
     K.poly = g->d_poly;
     K.npoly = g->npoly;
+    K.mbox = g->mbox;
+    for (int k = 0; k < 3; ++k) { K.mlo[k] = g->mlo[k]; K.mhi[k] = g->mhi[k]; }
     g->kin = K;
     g->has_kin = true;
     if (g->plain_exec) {  // kinetics are baked into the graph's kernel arguments
@@ -445,6 +447,27 @@ pbe_status pbe_set_growth_poly(pbe_grid* g, const double* a, int K)
     CUDA_TRY(cudaMemcpy(g->d_poly, a, sizeof(double) * n, cudaMemcpyHostToDevice));
     g->kin.poly = g->d_poly;
     g->kin.npoly = g->npoly;
+    if (g->plain_exec) {  // the kinetics are baked into the graph's kernel arguments
+        cudaGraphExecDestroy(g->plain_exec);
+        g->plain_exec = nullptr;
+    }
+    return PBE_OK;
+}
+
+pbe_status pbe_set_closure_box(pbe_grid* g, const double* lo, const double* hi)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (!lo || !hi) {
+        g->mbox = 0;
+    } else {
+        for (int k = 0; k < 3; ++k)
+            if (std::isnan(lo[k]) || std::isnan(hi[k]) || !(lo[k] <= hi[k]))
+                return fail(PBE_EINVAL, "closure box: lo[%d] <= hi[%d] required", k, k);
+        g->mbox = 1;
+        for (int k = 0; k < 3; ++k) { g->mlo[k] = lo[k]; g->mhi[k] = hi[k]; }
+    }
+    g->kin.mbox = g->mbox;
+    for (int k = 0; k < 3; ++k) { g->kin.mlo[k] = g->mlo[k]; g->kin.mhi[k] = g->mhi[k]; }
     if (g->plain_exec) {  // the kinetics are baked into the graph's kernel arguments
         cudaGraphExecDestroy(g->plain_exec);
         g->plain_exec = nullptr;

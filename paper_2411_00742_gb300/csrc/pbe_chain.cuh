@@ -27,6 +27,7 @@ __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const 
         S->V1 = V1;
         S->M1 = 1.0;
         S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L; S->sGb1 = sG[0]; S->sGb2 = sG[1]; S->spb = sG[2];
+        S->fbb = 0;
         if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
             S->status = PBE_ENONFINITE;
             S->done = 1;
@@ -90,6 +91,7 @@ __device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const 
         }
         if (!done) {
             S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L; S->sGa1 = sG[0]; S->sGa2 = sG[1]; S->spa = sG[2];
+            S->fba = 0;
             S->dt = dt; S->t_new = t_new; S->clipped = clip2;
             if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
                 S->status = PBE_ENONFINITE;

@@ -28,6 +28,8 @@ struct Kin {
     const float* mB;          // and b1[64], b2[64], b3[3] (fp32, device)
     const double* poly;       // growth_form 2 (Eq. 6): a[m * npoly + k - 1], k = 1..npoly, m < ndim (device)
     int npoly;
+    int mbox;                 // learned closure: 1 if its inputs have a training box [mlo, mhi]
+    double mlo[3], mhi[3];
 };
 
 constexpr int kMlpH = 64;
@@ -58,6 +60,7 @@ struct Scal {
                                 // 0 when S <= 1), kept for the adjoint
     double sGa1, sGa2, sGb1, sGb2;  // s dG_m/ds of the polynomial growth law (Eq. 6) at both stages
     double spa, spb;                // s = S - 1 at both stages (polynomial growth law)
+    int fba, fbb;                   // learned closure: 1 if the stage took the power-law fallback
 };
 
 // S = C / c*(T), s = max(S - 1, 0); G_d = kg_d s^g_d, B = kb s^b (Sec. 2.1,
@@ -415,6 +418,20 @@ __device__ __forceinline__ void mlp_forward_warp(const Kin& K, const float x[3],
     }
 }
 
+// closure inputs in FP64 at (C, t, ratio); returns false when S <= 1
+__device__ __forceinline__ bool mlp_inputs_d(const Kin& K, double C, double t, double ratio, double x[3])
+{
+    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
+    const double T = K.T0 + (K.T1 - K.T0) * frac;
+    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double s = C / cs - 1.0;
+    if (!(s > 0.0)) return false;
+    x[0] = 4.0 * s;
+    x[1] = (T - 25.0) / 10.0;
+    x[2] = 1e-6 * ratio;
+    return true;
+}
+
 // closure inputs at (C, t, ratio); returns false when S <= 1
 __device__ __forceinline__ bool mlp_inputs(const Kin& K, double C, double t, double ratio, float x[3])
 {
@@ -435,10 +452,16 @@ constexpr double kLnB = 11.512925464970229;    // ln 1e5
 
 // kinetics with the moment ratio V/mu0 of the state (used by the closure);
 // pre: temperature and solubility at t when the caller has them
+// The learned closure's plain-kinetics fallback: the power law of the
+// kinetic parameters replaces the network when an input (FP64) leaves the
+// training box (if one is set) or a rate is not finite; fbout (optional)
+// receives 1 when it did.
 __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t, double ratio, double& G1,
                                                 double& G2, double& B, const KinT* pre = nullptr,
-                                                double* Lout = nullptr, double* sGout = nullptr)
+                                                double* Lout = nullptr, double* sGout = nullptr,
+                                                int* fbout = nullptr)
 {
+    if (fbout) *fbout = 0;
     if (K.kind != PBE_KINETICS_MLP) {
         if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B, Lout, sGout);
         else kinetics_warp(K, C, t, G1, G2, B, Lout, sGout);
@@ -446,15 +469,28 @@ __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t
     }
     if (Lout) *Lout = 0.0;
     if (sGout) { sGout[0] = 0.0; sGout[1] = 0.0; sGout[2] = 0.0; }
-    float x[3], o[3];
-    if (!mlp_inputs(K, C, t, ratio, x)) {
+    double xd[3];
+    if (!mlp_inputs_d(K, C, t, ratio, xd)) {
         G1 = 0.0; G2 = 0.0; B = 0.0;
         return;
     }
-    mlp_forward_warp(K, x, o);
-    G1 = pbe_exp_tab((double)o[0] + kLnG1);
-    G2 = (K.ndim == 2) ? pbe_exp_tab((double)o[1] + kLnG2) : 0.0;
-    B = pbe_exp_tab((double)o[2] + kLnB);
+    bool fb = false;
+    if (K.mbox)
+        for (int k = 0; k < 3; ++k) fb = fb || !(xd[k] >= K.mlo[k] && xd[k] <= K.mhi[k]);
+    if (!fb) {
+        const float x[3] = {(float)xd[0], (float)xd[1], (float)xd[2]};
+        float o[3];
+        mlp_forward_warp(K, x, o);
+        G1 = pbe_exp_tab((double)o[0] + kLnG1);
+        G2 = (K.ndim == 2) ? pbe_exp_tab((double)o[1] + kLnG2) : 0.0;
+        B = pbe_exp_tab((double)o[2] + kLnB);
+        fb = !(isfinite(G1) && isfinite(G2) && isfinite(B));
+    }
+    if (fb) {   // the power law (kind != FIXED, growth_form 0 for the closure)
+        if (pre) kinetics_warp_T(K, C, *pre, G1, G2, B, Lout, sGout);
+        else kinetics_warp(K, C, t, G1, G2, B, Lout, sGout);
+        if (fbout) *fbout = 1;
+    }
 }
 
 // a / b for b > 0 (finite) by Newton-Raphson: the hardware reciprocal
@@ -509,11 +545,13 @@ __device__ __forceinline__ void prepare_step_warp(Scal* S, const Kin& K, const G
     const double t_next = t_out[S->out_idx];
     const double C = S->C, t = S->t;
     double G1, G2, B, dt, t_new, L, sG[3];
-    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre, &L, sG);
+    int fb;
+    kinetics_warp_r(K, C, t, K.kind == PBE_KINETICS_MLP ? S->V0 / S->M0 : 0.0, G1, G2, B, pre, &L, sG, &fb);
     const int clipped = timestep_fast(K, g, G1, G2, t, t_next, dt, t_new);
     __syncwarp();
     if (lane == 0) {
         S->G1a = G1; S->G2a = G2; S->Ba = B; S->La = L; S->sGa1 = sG[0]; S->sGa2 = sG[1]; S->spa = sG[2];
+        S->fba = fb;
         S->dt = dt; S->t_new = t_new; S->clipped = clipped;
         if (!isfinite(G1) || !isfinite(G2) || !isfinite(B) || !isfinite(dt)) {
             S->status = PBE_ENONFINITE;
@@ -530,13 +568,15 @@ __device__ __forceinline__ void finish_stage1_warp(Scal* S, const Kin& K, double
     const int lane = threadIdx.x & 31;
     const double C1 = S->C - K.kappa * (V1 - S->V0);
     double G1, G2, B, L, sG[3];
-    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre, &L, sG);
+    int fb;
+    kinetics_warp_r(K, C1, S->t_new, K.kind == PBE_KINETICS_MLP ? V1 / M1 : 0.0, G1, G2, B, pre, &L, sG, &fb);
     __syncwarp();
     if (lane == 0) {
         S->C1 = C1;
         S->V1 = V1;
         S->M1 = M1;
         S->G1b = G1; S->G2b = G2; S->Bb = B; S->Lb = L; S->sGb1 = sG[0]; S->sGb2 = sG[1]; S->spb = sG[2];
+        S->fbb = fb;
         if (!isfinite(V1) || !isfinite(G1) || !isfinite(G2) || !isfinite(B)) {
             S->status = PBE_ENONFINITE;
             S->done = 1;

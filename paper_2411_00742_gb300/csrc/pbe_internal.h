@@ -49,6 +49,8 @@ struct pbe_grid {
     float* d_mB;
     double* d_poly;         // polynomial growth law (Eq. 6): ndim x npoly coefficients
     int npoly;
+    int mbox;               // learned closure: training box of its inputs (pbe_set_closure_box)
+    double mlo[3], mhi[3];
     // optional device timing of the launch that advances the state in pbe_solve
     bool timing;
     cudaEvent_t ev_k0, ev_k1;

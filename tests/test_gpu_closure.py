@@ -119,3 +119,75 @@ def test_trained_closure_beats_the_plain_kinetics():
                 "--lr", "3e-3", "--workers", "8"])
     assert res["loss_history"][-1] < 0.5 * res["loss_history"][0]
     assert res["gain"] > 1.3, res["heldout_rel_rms_error"]
+
+
+def _partial_box(inst, w):
+    """A training box cutting the supersaturation input x0 = 4 (S - 1) at its
+    median along the oracle's closure solve: the stages above it take the
+    power-law fallback, the others the network."""
+    import dataclasses
+    r0 = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=cd.stored_weights(w))["rows"]
+    p = inst.problem
+    T = np.array([oracle.temperature(p, t) for t in r0[:, 0]])
+    x0 = 4.0 * (r0[:, -1] / (p.csat[0] + p.csat[1] * T + p.csat[2] * T * T) - 1.0)
+    cut = float(np.median(x0[x0 > 0]))
+    inst.problem = dataclasses.replace(p, mlp_box=((-10.0, -10.0, -10.0), (cut, 10.0, 10.0)))
+    return inst
+
+
+def test_closure_fallback_forward_matches_oracle():
+    inst = cd.trajectories(1, seed=11, N=48)[0]
+    w = cd.initial_weights(3, 0.2)
+    inst = _partial_box(inst, w)
+    g = _grid(inst, w)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, steps = g.solve(inst.t_out)
+    g.close()
+    want = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=cd.stored_weights(w))
+    assert steps == want["steps"]
+    err = np.max(np.abs(rows[:, 1:] - want["rows"][:, 1:]) / np.abs(want["rows"][:, 1:]))
+    assert err <= REL_ROWS_MLP, err
+
+
+def test_closure_box_excluding_every_input_gives_the_power_law_solve():
+    import dataclasses
+    import paper_2411_00742_gb300 as P
+    inst = cd.trajectories(1, seed=11, N=48)[0]
+    w = cd.initial_weights(3, 0.2)
+    inst.problem = dataclasses.replace(inst.problem, mlp_box=((50.0, 50.0, 50.0), (60.0, 60.0, 60.0)))
+    g = _grid(inst, w)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    rows, steps = g.solve(inst.t_out)
+    g.close()
+    gp = P.Grid.from_problem(inst.problem)
+    gp.set_state(inst.n0, inst.C0, 0.0)
+    want, wsteps = gp.solve(inst.t_out)
+    gp.close()
+    assert steps == wsteps
+    np.testing.assert_allclose(rows[:, 1:], want[:, 1:], rtol=1e-14)
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_closure_fallback_gradients_match_oracle(path):
+    """With a partly active box the adjoint differentiates the network on some
+    stages and the power law on the others: dL/dweights and dL/d(kinetic
+    parameters) against the oracle's adjoint."""
+    inst = cd.trajectories(1, seed=12, N=40)[0]
+    w = cd.initial_weights(4, 0.2)
+    ws = cd.stored_weights(w)
+    inst = _partial_box(inst, w)
+    tgt = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    cols = [1, 2, 3, 9, 11]
+    r = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=ws)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    want_th, _, _, want = oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds, mlp=ws)
+    g = _grid(inst, w, path)
+    g.set_state(inst.n0, inst.C0, 0.0)
+    dW = np.zeros(cd.CLOSURE_SIZE)
+    dth, _, _ = g.vjp(inst.t_out, seeds, 64, dweights_out=dW)
+    g.close()
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(dW - want)) <= REL_GRAD_MLP * scale, np.max(np.abs(dW - want)) / scale
+    assert np.any(want_th != 0.0)
+    for j in range(6):
+        assert dth[j] == pytest.approx(want_th[j], rel=REL_GRAD_MLP, abs=1e-12 * np.max(np.abs(want_th))), j
