@@ -54,7 +54,7 @@ typedef int pbe_status;
 /* kinetic models */
 #define PBE_KINETICS_POWER_LAW 0 /* G_d = kg[d] s^g[d], B = kb s^b, s = max(C/c*(T) - 1, 0) */
 #define PBE_KINETICS_FIXED 1     /* G_d = kg[d], B = kb, independent of S (tests)           */
-#define PBE_KINETICS_MLP 2       /* learned closure set by pbe_set_closure (plain path)      */
+#define PBE_KINETICS_MLP 2       /* learned closure set by pbe_set_closure                   */
 
 /* time schemes */
 #define PBE_SCHEME_SSPRK2 0 /* semi-discrete limited fluxes, two-stage SSP Runge-Kutta, both
@@ -117,7 +117,8 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k);
  * b1[64], W2[64][64], b2[64], W3[3][64], b3[3]; the weight matrices are stored
  * rounded to bf16 (round to nearest even), the biases in fp32; arithmetic is
  * fp32.  Rates that are not finite fall back to the power law
- * (pbe_set_closure_box).  Solves with the closure run on the plain path. */
+ * (pbe_set_closure_box).  On the fused path, solves with the closure run in
+ * the persistent kernel of pbe_vjp, without its reverse sweep. */
 pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count);
 
 /* Coefficients of the polynomial growth law of Eq. 6 (the model of the

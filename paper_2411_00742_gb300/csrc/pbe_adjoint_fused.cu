@@ -99,6 +99,7 @@ struct AdjP {
     int Kc, ck_cap, n_out, ncol;
     int ntiles, tiles_x, ti;
     int t1;             // 1-D tile cells (kPT1Min .. kPT1)
+    int fwd_only;       // 1: the solve only (state in n and fin, stage-1 output in u, no records)
     long long wait_limit;
     double t0;
 };
@@ -739,18 +740,19 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
 }
 
 // ---- forward step --------------------------------------------------------------
-// One SSP-RK2 step (step q of segment c) with its scalar chains, every block
-// on its own tiles: stage 1 n^k -> seg_n1[q], the device-wide barrier with
-// the volume moment (and mu0 for the closure), the stage-1 close and the
-// stage-2 kinetics; stage 2 -> the next step's state slot, the barrier, the
-// step close and the next step's kinetics and length.  Block 0 records the
-// scalars (recA[q] at the start, recB[q] after the stage-1 close).  emit: the
+// One SSP-RK2 step with its scalar chains, every block on its own tiles:
+// stage 1 in1 -> n1, the device-wide barrier with the volume moment (and mu0
+// for the closure), the stage-1 close and the stage-2 kinetics; stage 2 ->
+// out2, the barrier, the step close and the next step's kinetics and length.
+// With q >= 0 block 0 records the scalars (recA[q] at the start, recB[q]
+// after the stage-1 close).  emit: the
 // forward pass (output rows and their per-block moments); with stage2 false
 // (the last step of a recomputed segment) only stage 1 and its close run.
 // Returns false when a device-wide wait ran out.
 template <int NDIM>
-__device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, int c, int q, bool emit, bool stage2,
-                                         int t_first, int t_end, double u, double inv_u)
+__device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, const double* in1, double* n1,
+                                         double* out2, int q, bool emit, bool stage2, int t_first, int t_end,
+                                         double u, double inv_u)
 {
     constexpr int NM = NDIM == 1 ? 4 : 10;
     constexpr int VIDX = NDIM == 1 ? 3 : 8;
@@ -760,10 +762,7 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
     // temperature and solubility at the step's end, where both kinetics of the step are evaluated
     KinT tpre{0.0, 0.0};
     if (warp == 0 && P.K.kind != PBE_KINETICS_FIXED) tpre = kin_temperature(P.K, B.s.t_new);
-    if (threadIdx.x == 0 && blockIdx.x == 0) P.recA[q] = B.s;
-    const double* in1 = st_ptr(P, c, q);
-    double* n1 = P.seg_n1 + (size_t)q * P.nc;
-    double* out2 = q + 1 < P.Kc ? st_ptr(P, c, q + 1) : st_ptr(P, c + 1, 0);
+    if (q >= 0 && threadIdx.x == 0 && blockIdx.x == 0) P.recA[q] = B.s;
 #pragma unroll 1
     for (int stage = 1; stage <= 2; ++stage) {
         if (stage == 2 && B.s.done) break;   // the stage-1 close failed (non-finite)
@@ -821,7 +820,7 @@ __device__ __forceinline__ bool fwd_step(const AdjP& P, BlockSm& B, Sync0& y, in
                 } else {
                     nx = fused_finish1(&B.s, P.K, P.g, B.vtot, tpre);
                 }
-                if (threadIdx.x == 0 && blockIdx.x == 0) P.recB[q] = B.s;
+                if (q >= 0 && threadIdx.x == 0 && blockIdx.x == 0) P.recB[q] = B.s;
             } else {
                 double mom[kMaxMom];
 #pragma unroll
@@ -898,15 +897,67 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
         u = ldexp(1.0, E - 52);
         inv_u = ldexp(1.0, 52 - E);
     }
-    // ---- forward pass ----
     int status = PBE_OK;
+    if (P.fwd_only) {
+        // ---- a solve only (the fused path's closure solves): the state alternates
+        // between n and fin, the stage-1 output goes to u, nothing is recorded ----
+        double* cur = P.n;
+        double* nxt = P.fin;
+        while (!B.s.done) {
+            if (!fwd_step<NDIM>(P, B, y, cur, P.u, nxt, -1, true, true, t_first, t_end, u, inv_u)) {
+                status = PBE_ETIMEOUT;
+                break;
+            }
+            if (!B.s.done || B.s.status == PBE_OK) {
+                double* tmp = cur;
+                cur = nxt;
+                nxt = tmp;
+            }
+        }
+        if (status == PBE_OK && B.s.status != PBE_OK) status = B.s.status;
+        if (status == PBE_OK && cur != P.n) {   // the final state into n (own cells: no barrier needed)
+            for (int t = t_first; t < t_end; ++t) {
+                int i0, j0;
+                tile_org<NDIM>(P, t, i0, j0);
+                const int rows_t = NDIM == 1 ? 1 : P.ti, cols_t = NDIM == 1 ? P.t1 : kPTJ;
+                for (int k = threadIdx.x; k < rows_t * cols_t; k += kPNT) {
+                    const int i = i0 + (NDIM == 1 ? k : k / cols_t), j = j0 + (NDIM == 1 ? 0 : k % cols_t);
+                    if (i < P.g.N1 && j < P.g.N2) {
+                        const size_t gi = (size_t)i * P.g.N2 + j;
+                        P.n[gi] = __ldcg(cur + gi);
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0 && status == PBE_ETIMEOUT) {   // every block that gave up marks the solve
+            P.S->status = PBE_ETIMEOUT;
+            P.S->done = 1;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (status != PBE_ETIMEOUT) {
+                B.s.counter = 0u;
+                *P.S = B.s;
+            }
+            P.out->status = status;
+            P.out->steps = B.s.steps;
+            P.out->row_first = row_first;
+            P.out->row_end = B.s.out_idx;
+        }
+        return;
+    }
+    // ---- forward pass ----
     int c = 0, q = 0;
     while (!B.s.done) {
         if (q == 0) {
             if (c >= P.ck_cap) { status = kStatusGrow; break; }
             if (threadIdx.x == 0 && blockIdx.x == 0) P.ckS[c] = B.s;
         }
-        if (!fwd_step<NDIM>(P, B, y, c, q, true, true, t_first, t_end, u, inv_u)) { status = PBE_ETIMEOUT; break; }
+        double* out2 = q + 1 < P.Kc ? st_ptr(P, c, q + 1) : st_ptr(P, c + 1, 0);
+        if (!fwd_step<NDIM>(P, B, y, st_ptr(P, c, q), P.seg_n1 + (size_t)q * P.nc, out2, q, true, true, t_first,
+                            t_end, u, inv_u)) {
+            status = PBE_ETIMEOUT;
+            break;
+        }
         if (++q == P.Kc) { q = 0; ++c; }
     }
     if (status == PBE_OK && B.s.status != PBE_OK) status = B.s.status;
@@ -951,7 +1002,9 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
             if (threadIdx.x == 0) B.sc = stage_coef_fast<1>(B.s, P.g);
             __syncthreads();
             for (int qq = 0; qq < len; ++qq)
-                if (!fwd_step<NDIM>(P, B, y, cc, qq, false, qq + 1 < len, t_first, t_end, u, inv_u)) {
+                if (!fwd_step<NDIM>(P, B, y, st_ptr(P, cc, qq), P.seg_n1 + (size_t)qq * P.nc,
+                                    qq + 1 < len ? st_ptr(P, cc, qq + 1) : nullptr, qq, false, qq + 1 < len,
+                                    t_first, t_end, u, inv_u)) {
                     status = PBE_ETIMEOUT;
                     break;
                 }
@@ -1191,6 +1244,52 @@ void adjoint_work_free(pbe_grid* g)
     cudaFreeHost(w->h_out);
     delete w;
     g->adjw = nullptr;
+}
+
+// A solve of the fused path with the learned closure: the persistent kernel's
+// forward pass alone (its per-stage mu0 sums give the closure's moment-ratio
+// input).  The caller has put the output times on the device; like the fused
+// solve it leaves the rows in d_rows and the scalars in d_S and does not
+// synchronize.
+cudaError_t launch_solve_persistent(pbe_grid* g, int n_out)
+{
+    if (!g->adjw) {
+        g->adjw = new AdjWork();
+        memset((void*)g->adjw, 0, sizeof(AdjWork));
+        cudaError_t e = cudaMallocHost(&g->adjw->h_out, sizeof(AdjOut));
+        if (e != cudaSuccess) return e;
+    }
+    AdjWork* w = g->adjw;
+    cudaError_t e = adjoint_config(g, w);
+    if (e != cudaSuccess) return e;
+    const size_t nc = g->ncell;
+    cudaStream_t st = g->stream;
+    if (!w->u || !w->part || !w->out) {
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if ((e = grow(&w->u, nc)) != cudaSuccess || (e = grow(&w->part, (size_t)2 * w->G * 4)) != cudaSuccess ||
+            (e = grow(&w->out, (size_t)1)) != cudaSuccess)
+            return e;
+    }
+    if ((e = cudaMemsetAsync(g->d_bar, 0, 2 * kAccStride * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    AdjP P;
+    memset(&P, 0, sizeof(P));
+    P.n = g->d_n; P.fin = g->d_n1; P.S = g->d_S; P.K = g->kin; P.g = g->geo;
+    P.t_out = g->d_tout; P.rows = g->d_rows; P.rowpart = g->d_rowpart;
+    P.u = w->u; P.part = w->part; P.out = w->out;
+    P.acc = reinterpret_cast<unsigned long long*>(g->d_bar);
+    P.nc = nc; P.Kc = 1; P.n_out = n_out; P.ncol = g->geo.ndim == 1 ? 6 : 12;
+    P.ntiles = w->ntiles; P.tiles_x = w->tiles_x; P.ti = w->ti; P.t1 = w->t1;
+    P.wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
+    P.fwd_only = 1;
+    void* args[] = {&P};
+    const void* fn = g->geo.ndim == 1 ? (const void*)k_adjoint_persistent<1> : (const void*)k_adjoint_persistent<2>;
+    if (g->timing && (e = cudaEventRecord(g->ev_k0, st)) != cudaSuccess) return e;
+    if ((e = cudaLaunchCooperativeKernel(fn, w->G, kPNT, args, 0, st)) != cudaSuccess) return e;
+    if (g->timing && (e = cudaEventRecord(g->ev_k1, st)) != cudaSuccess) return e;
+    const int nm = g->geo.ndim == 1 ? 4 : 10;
+    if (g->geo.ndim == 1) k_adjoint_rows<1><<<n_out, nm * 32, 0, st>>>(g->d_rowpart, w->G, w->out, g->d_rows);
+    else k_adjoint_rows<2><<<n_out, nm * 32, 0, st>>>(g->d_rowpart, w->G, w->out, g->d_rows);
+    return cudaGetLastError();
 }
 
 pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const double* seeds_in, int seeds_mem, int K,

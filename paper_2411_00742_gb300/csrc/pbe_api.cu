@@ -152,9 +152,9 @@ pbe_status finish_call(pbe_grid* g)
 pbe_status run_solve(pbe_grid* g, int n_out)
 {
     CUDA_TRY(pbe::launch_prologue(g, n_out, g->max_steps, nullptr));
-    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g) && g->kin.kind != PBE_KINETICS_MLP &&
-        g->kin.scheme == PBE_SCHEME_SSPRK2) {
-        CUDA_TRY(pbe::launch_fused_solve(g, n_out));
+    if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g) && g->kin.scheme == PBE_SCHEME_SSPRK2) {
+        if (g->kin.kind == PBE_KINETICS_MLP) CUDA_TRY(pbe::launch_solve_persistent(g, n_out));
+        else CUDA_TRY(pbe::launch_fused_solve(g, n_out));
         return PBE_OK;
     }
     build_plain_graph(g);

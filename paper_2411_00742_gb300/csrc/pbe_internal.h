@@ -110,6 +110,9 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
                           double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem,
                           double* dL_dweights);
 void adjoint_work_free(pbe_grid* g);
+// A fused-path solve with the learned closure: the persistent kernel's forward
+// pass (per-stage mu0 sums for the closure's moment-ratio input).
+cudaError_t launch_solve_persistent(pbe_grid* g, int n_out);
 
 // Fused path (pbe_fused.cu)
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out);

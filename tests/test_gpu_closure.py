@@ -26,11 +26,12 @@ def _grid(inst, w, path="plain"):
     return g
 
 
+@pytest.mark.parametrize("path", ["plain", "fused"])
 @pytest.mark.parametrize("ndim", [1, 2])
-def test_closure_forward_matches_oracle(ndim):
+def test_closure_forward_matches_oracle(ndim, path):
     inst = pi.config_1d(200) if ndim == 1 else cd.trajectories(1, seed=11, N=48)[0]
     w = cd.initial_weights(3, 0.2)
-    g = _grid(inst, w)
+    g = _grid(inst, w, path)
     g.set_state(inst.n0, inst.C0, 0.0)
     rows, steps = g.solve(inst.t_out)
     g.close()
@@ -135,11 +136,12 @@ def _partial_box(inst, w):
     return inst
 
 
-def test_closure_fallback_forward_matches_oracle():
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_closure_fallback_forward_matches_oracle(path):
     inst = cd.trajectories(1, seed=11, N=48)[0]
     w = cd.initial_weights(3, 0.2)
     inst = _partial_box(inst, w)
-    g = _grid(inst, w)
+    g = _grid(inst, w, path)
     g.set_state(inst.n0, inst.C0, 0.0)
     rows, steps = g.solve(inst.t_out)
     g.close()
@@ -191,3 +193,30 @@ def test_closure_fallback_gradients_match_oracle(path):
     assert np.any(want_th != 0.0)
     for j in range(6):
         assert dth[j] == pytest.approx(want_th[j], rel=REL_GRAD_MLP, abs=1e-12 * np.max(np.abs(want_th))), j
+
+
+def test_fused_closure_solve_at_the_workload_size_and_its_timeout():
+    """The closure's fused-path solve (the persistent kernel's forward pass) on
+    the 128 x 128 closure workload against the plain path; a zero wait limit
+    ends it with PBE_ETIMEOUT and the grid solves normally afterwards."""
+    from paper_2411_00742_gb300 import _lib
+    inst = cd.trajectories(1, seed=21, N=128)[0]
+    w = cd.initial_weights(3, 0.2)
+    out = {}
+    for path in ("plain", "fused"):
+        g = _grid(inst, w, path)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        out[path] = g.solve(inst.t_out)
+        if path == "fused":
+            g.set_wait_limit(0.0)
+            g.set_state(inst.n0, inst.C0, 0.0)
+            with pytest.raises(_lib.PbeError) as ei:
+                g.solve(inst.t_out)
+            assert "ETIMEOUT" in str(ei.value)
+            g.set_wait_limit(-1.0)
+            g.set_state(inst.n0, inst.C0, 0.0)
+            again, _ = g.solve(inst.t_out)
+            np.testing.assert_array_equal(again, out["fused"][0])
+        g.close()
+    assert out["plain"][1] == out["fused"][1]
+    np.testing.assert_allclose(out["fused"][0][:, 1:], out["plain"][0][:, 1:], rtol=REL_ROWS_MLP)
