@@ -217,7 +217,10 @@ pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
  *   rows               optional, the forward rows (`mem` memory)
  *   dL_dweights        optional HOST, 4611 doubles: gradient with respect to the
  *                      learned closure's weights (PBE_KINETICS_MLP; the layout
- *                      of pbe_set_closure, taken at the stored bf16 values)
+ *                      of pbe_set_closure, taken at the stored bf16 values; on
+ *                      the fused path from the recorded evaluations by the
+ *                      kernel of pbe_closure_grad, on the plain path
+ *                      accumulated per stage in fp64)
  * Paths: on PBE_PATH_FUSED one persistent cooperative launch runs the
  * forward pass (checkpoints, and the records of the current segment), the
  * recomputation of the earlier segments and the reverse sweep, with work
@@ -231,6 +234,19 @@ pbe_status pbe_moments(pbe_grid* g, double* mu, int mem);
 pbe_status pbe_vjp(pbe_grid* g, const double* t_out, int n_out, const double* seeds, int seeds_mem,
                    int checkpoint_every, double* dL_dtheta, double* dL_dn0, double* dL_dC0, double* rows, int mem,
                    double* dL_dweights);
+
+/* The learned closure's weight gradient summed over several trajectories (the
+ * training step of the hybrid model of Sec. 4.2 on a minibatch): the sum of
+ * dL/dweights of the last pbe_vjp of each of the `count` grids, computed by one
+ * launch of the weight-gradient kernel over all their recorded closure
+ * evaluations (the 64-wide layers on the tensor cores, bf16 operands with
+ * fp32 accumulation, activations split into two bf16 parts).  Every grid must
+ * use PBE_KINETICS_MLP with the same weights, be on one device, and have run
+ * pbe_vjp on the fused path since its last closure change.  dL_dweights:
+ * HOST, 4611 doubles (layout of pbe_set_closure).  Synchronizes every grid's
+ * stream.  Errors: PBE_EINVAL (arguments, other weights or devices),
+ * PBE_ESTATE (no gradient rows), PBE_ENOMEM, PBE_ECUDA. */
+pbe_status pbe_closure_grad(pbe_grid* const* grids, int count, double* dL_dweights);
 
 /* Upper bound on steps per pbe_solve call (default 1e6); exceeding it stops
  * the solve with PBE_ETIMEOUT. */

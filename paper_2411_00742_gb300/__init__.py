@@ -19,7 +19,7 @@ from ._lib import (PBE_KINETICS_FIXED, PBE_KINETICS_MLP, PBE_KINETICS_POWER_LAW,
 
 CLOSURE_SIZE = 64 * 3 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # weights of the learned closure
 
-__all__ = ["Grid", "Batch", "PbeError", "kinetics_struct", "ncols"]
+__all__ = ["Grid", "Batch", "PbeError", "kinetics_struct", "ncols", "closure_grad"]
 
 _PATHS = {"plain": PBE_PATH_PLAIN, "fused": PBE_PATH_FUSED}
 
@@ -257,6 +257,17 @@ class Grid:
         p, mem, keep = _buf(out, writable=True)
         _lib.check(self.lib.pbe_moments(self.h, p, mem))
         return out
+
+
+def closure_grad(grids) -> np.ndarray:
+    """Summed dL/dweights of the learned closure over the last (fused-path) vjp of
+    every grid: one launch of the tensor-core weight-gradient kernel."""
+    grids = list(grids)
+    arr = (ctypes.c_void_p * len(grids))(*[g.h.value if hasattr(g.h, "value") else g.h for g in grids])
+    out = np.zeros(CLOSURE_SIZE)
+    lib = _lib.load()
+    _lib.check(lib.pbe_closure_grad(arr, len(grids), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 class Batch:

@@ -60,6 +60,7 @@ SIGNATURES = {
     "pbe_set_max_steps": [_P, _I64],
     "pbe_set_growth_poly": [_P, _PD, _I],
     "pbe_set_closure_box": [_P, _PD, _PD],
+    "pbe_closure_grad": [ctypes.POINTER(_P), _I, _PD],
     "pbe_growth_poly_grad": [_P, _PD, _I],
     "pbe_set_wait_limit": [_P, _D],
     "pbe_set_window": [_P, _I],

@@ -67,6 +67,7 @@ struct AdjOut {
     double lth[6];
     double lC;
     long long steps;
+    long long nrows;    // closure evaluations recorded in mrows
     int status;
     int row_first, row_end;
 };
@@ -93,6 +94,8 @@ struct AdjP {
     const double* seeds;
     double* dW;         // learned closure: dL/dweights (fp64), accumulated by block 0
     double* dpoly;      // polynomial growth law: dL/da (ndim x npoly), accumulated by block 0
+    float* mrows;       // learned closure: block 0 records one row (x0, x1, x2, lo0, lo1, lo2) per
+    long long mrows_cap;    // differentiated evaluation, for the weight-gradient kernel (null: none)
     AdjOut* out;
     unsigned long long* acc;
     size_t nc;
@@ -413,6 +416,7 @@ struct BlockSm {
     double vtot;
     int par;         // parity of the last forward barrier (its block partials)
     int run_mlp, fail;
+    long long nrow;  // closure rows recorded (block 0)
 };
 
 struct Bar64 {   // named barrier over threads 0..63 (the closure backward)
@@ -527,6 +531,19 @@ static __device__ __noinline__ StageCoef close2_mlp(Scal* S, const Kin& K, const
     return stage_coef_fast<1>(*S, g);
 }
 
+// One closure evaluation for the weight-gradient kernel: its inputs and the
+// adjoints of its outputs (thread 0 of block 0, after the input adjoint).
+__device__ __forceinline__ void record_mlp_row(const AdjP& P, BlockSm& B, const float* x)
+{
+    if (!P.mrows || blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (B.nrow < P.mrows_cap) {
+        float* r = P.mrows + (size_t)B.nrow * 6;
+        r[0] = x[0]; r[1] = x[1]; r[2] = x[2];
+        r[3] = (float)B.mlp_lo[0]; r[4] = (float)B.mlp_lo[1]; r[5] = (float)B.mlp_lo[2];
+    }
+    B.nrow += 1;
+}
+
 // ---- adjoint scalar chain ----------------------------------------------------
 // Backward of the rates at (C, t) given lG* = dL/dG* and the forward's rates
 // and L = ln s (power law: dG/dkg = s^g = G/kg, dG/dg = G L, dG/ds = g G/s;
@@ -635,7 +652,8 @@ __device__ __forceinline__ void rev_mid(const AdjP& P, BlockSm& B)
         if (B.run_mlp) {
             float x[3];
             mlp_inputs(K, Q.C1, A.t_new, Q.V1 / Q.M1, x);
-            mlp_backward_64(K, x, B.mlp_lo, blockIdx.x == 0 ? P.dW : nullptr, B.mlp_sm, B.mlp_lx);
+            mlp_backward_64(K, x, B.mlp_lo, blockIdx.x == 0 && !P.mrows ? P.dW : nullptr, B.mlp_sm, B.mlp_lx);
+            record_mlp_row(P, B, x);
         }
     }
     if (threadIdx.x != 0) return;
@@ -705,7 +723,8 @@ __device__ __forceinline__ void rev_end(const AdjP& P, BlockSm& B)
         if (B.run_mlp) {
             float x[3];
             mlp_inputs(K, A.C, A.t, A.V0 / A.M0, x);
-            mlp_backward_64(K, x, B.mlp_lo, blockIdx.x == 0 ? P.dW : nullptr, B.mlp_sm, B.mlp_lx);
+            mlp_backward_64(K, x, B.mlp_lo, blockIdx.x == 0 && !P.mrows ? P.dW : nullptr, B.mlp_sm, B.mlp_lx);
+            record_mlp_row(P, B, x);
         }
     }
     if (threadIdx.x != 0) return;
@@ -882,6 +901,7 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
         B.ik[1] = P.K.kg2 > 0.0 ? 1.0 / P.K.kg2 : 0.0;
         B.ik[2] = P.K.kb > 0.0 ? 1.0 / P.K.kb : 0.0;
         B.inv_dA = NDIM == 1 ? P.g.inv_d1 : P.g.inv_d1 * P.g.inv_d2;
+        B.nrow = 0;
         B.inv_cfl = 1.0 / P.K.cfl;
         memset(&B.R, 0, sizeof(RevS));
     }
@@ -1132,6 +1152,7 @@ __global__ void __launch_bounds__(kPNT, 1) k_adjoint_persistent(AdjP P)
         for (int k = 0; k < 6; ++k) P.out->lth[k] = B.R.lth[k];
         P.out->lC = B.R.lC;
         P.out->steps = total;
+        P.out->nrows = B.nrow;
         P.out->status = PBE_OK;
         P.out->row_first = row_first;
         P.out->row_end = B.sfin.out_idx;
@@ -1168,6 +1189,11 @@ struct AdjWork {
     double *seg_n, *seg_n1, *ck, *lamA, *lamB, *u, *part, *seeds, *dW;
     double* dpoly;          // dL/d(growth polynomial coefficients) of the last gradient
     int dpoly_cap;
+    float* mrows;           // closure rows of the last gradient (6 floats each)
+    long long mrows_cap, last_nrows;   // capacity; rows of the last fused-path gradient (-1: none)
+    float* gpart;           // workspace of the weight-gradient kernel
+    float* catrows;         // rows of several grids side by side (pbe_closure_grad)
+    long long catrows_cap;
     Scal *recA, *recB, *ckS;
     AdjOut* out;
     AdjOut* h_out;          // pinned
@@ -1240,6 +1266,7 @@ void adjoint_work_free(pbe_grid* g)
     if (!w) return;
     cudaFree(w->seg_n); cudaFree(w->seg_n1); cudaFree(w->ck); cudaFree(w->lamA); cudaFree(w->lamB);
     cudaFree(w->u); cudaFree(w->part); cudaFree(w->seeds); cudaFree(w->dW); cudaFree(w->dpoly);
+    cudaFree(w->mrows); cudaFree(w->gpart); cudaFree(w->catrows);
     cudaFree(w->recA); cudaFree(w->recB); cudaFree(w->ckS); cudaFree(w->out);
     cudaFreeHost(w->h_out);
     delete w;
@@ -1370,6 +1397,21 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
         }
         w->dpoly_cap = npoly_all;
     }
+    const bool mlp = g->kin.kind == PBE_KINETICS_MLP;
+    w->last_nrows = -1;
+    if (mlp) {
+        const long long cap = 2LL * w->ck_cap * K + 2;
+        if (w->mrows_cap < cap || !w->gpart) {
+            PTRY(cudaStreamSynchronize(st));
+            if (grow(&w->mrows, (size_t)cap * 6) != cudaSuccess ||
+                (!w->gpart && grow(&w->gpart, (size_t)mlp_grad_part_floats()) != cudaSuccess)) {
+                w->mrows_cap = 0;
+                cudaGetLastError();
+                return afail(PBE_ENOMEM, "allocating the closure's gradient rows failed");
+            }
+            w->mrows_cap = cap;
+        }
+    }
     PTRY(cudaMemcpyAsync(w->seeds, seeds_in, sizeof(double) * ncol * n_out,
                          seeds_mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     const long long wait_limit = g->wait_cycles > 0 ? g->wait_cycles : (g->wait_cycles == 0 ? 0 : kBarrierCycles);
@@ -1388,6 +1430,8 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
         P.seg_n = w->seg_n; P.seg_n1 = w->seg_n1; P.ck = w->ck; P.recA = w->recA; P.recB = w->recB; P.ckS = w->ckS;
         P.lamA = w->lamA; P.lamB = w->lamB; P.u = w->u; P.part = w->part; P.seeds = w->seeds; P.dW = w->dW;
         P.dpoly = w->dpoly;
+        P.mrows = mlp ? w->mrows : nullptr;
+        P.mrows_cap = mlp ? w->mrows_cap : 0;
         P.out = w->out; P.acc = reinterpret_cast<unsigned long long*>(g->d_bar);
         P.nc = nc; P.Kc = K; P.ck_cap = w->ck_cap; P.n_out = n_out; P.ncol = ncol;
         P.ntiles = w->ntiles; P.tiles_x = w->tiles_x; P.ti = w->ti; P.t1 = w->t1; P.wait_limit = wait_limit; P.t0 = t0;
@@ -1411,6 +1455,15 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
             return afail(PBE_ENOMEM, "allocating %d adjoint checkpoints of %zu cells failed", cap, nc);
         }
         w->ck_cap = cap;
+        if (mlp) {   // room for two closure rows a step of the larger store
+            const long long rcap = 2LL * cap * K + 2;
+            if (grow(&w->mrows, (size_t)rcap * 6) != cudaSuccess) {
+                w->mrows_cap = 0;
+                cudaGetLastError();
+                return afail(PBE_ENOMEM, "allocating the closure's gradient rows failed");
+            }
+            w->mrows_cap = rcap;
+        }
     }
     const AdjOut o = *w->h_out;
     if (o.status == PBE_ENONFINITE) return afail(PBE_ENONFINITE, "non-finite value in the forward pass of the gradient");
@@ -1428,7 +1481,16 @@ pbe_status vjp_persistent(pbe_grid* g, const double* t_out, int n_out, const dou
     if (dL_dn0)
         PTRY(cudaMemcpyAsync(dL_dn0, w->lamA, sizeof(double) * nc,
                              mem == PBE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (dL_dweights) PTRY(cudaMemcpyAsync(dL_dweights, w->dW, sizeof(double) * kMlpNW, cudaMemcpyDeviceToHost, st));
+    if (mlp) {
+        if (o.nrows > w->mrows_cap) return afail(PBE_ECUDA, "closure rows beyond their store (%lld)", o.nrows);
+        w->last_nrows = o.nrows;
+        if (dL_dweights) {
+            PTRY(launch_mlp_grad(w->mrows, o.nrows, g->d_mW, g->d_mB, w->gpart, w->dW, st));
+            PTRY(cudaMemcpyAsync(dL_dweights, w->dW, sizeof(double) * kMlpNW, cudaMemcpyDeviceToHost, st));
+        }
+    } else if (dL_dweights) {
+        PTRY(cudaMemcpyAsync(dL_dweights, w->dW, sizeof(double) * kMlpNW, cudaMemcpyDeviceToHost, st));
+    }
     PTRY(cudaStreamSynchronize(st));
     g->C_host = g->h_S->C;
     g->t_host = g->h_S->t;
@@ -1453,5 +1515,54 @@ extern "C" pbe_status pbe_growth_poly_grad(pbe_grid* g, double* dL_da, int count
     cudaError_t e = cudaMemcpyAsync(dL_da, g->adjw->dpoly, sizeof(double) * n, cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return afail(PBE_ECUDA, "reading the coefficient gradient failed: %s", cudaGetErrorString(e));
+    return PBE_OK;
+}
+
+// The summed closure weight gradient of the last fused-path pbe_vjp of every
+// grid: one launch of the weight-gradient kernel over all their rows.
+extern "C" pbe_status pbe_closure_grad(pbe_grid* const* grids, int count, double* dL_dweights)
+{
+    using namespace pbe;
+    if (!grids || count < 1 || !dL_dweights) return afail(PBE_EINVAL, "null argument or count < 1");
+    pbe_grid* g0 = grids[0];
+    long long R = 0;
+    for (int i = 0; i < count; ++i) {
+        pbe_grid* g = grids[i];
+        if (!g) return afail(PBE_EINVAL, "grid %d is null", i);
+        if (g->device != g0->device) return afail(PBE_EINVAL, "grid %d is on another device", i);
+        if (g->kin.kind != PBE_KINETICS_MLP || !g->adjw || g->adjw->last_nrows < 0)
+            return afail(PBE_ESTATE, "grid %d has no closure gradient rows: run pbe_vjp on the fused path first", i);
+        if (g->mhash != g0->mhash) return afail(PBE_EINVAL, "grid %d holds other closure weights than grid 0", i);
+        R += g->adjw->last_nrows;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != g0->device && cudaSetDevice(g0->device) != cudaSuccess) return afail(PBE_ECUDA, "cannot select device");
+    struct Restore {
+        int dev;
+        ~Restore() { if (dev >= 0) cudaSetDevice(dev); }
+    } restore{prev != g0->device ? prev : -1};
+    AdjWork* w = g0->adjw;
+    cudaStream_t st = g0->stream;
+    for (int i = 0; i < count; ++i) PTRY(cudaStreamSynchronize(grids[i]->stream));
+    if (w->catrows_cap < R) {
+        if (grow(&w->catrows, (size_t)std::max(R, 1LL) * 6) != cudaSuccess) {
+            w->catrows_cap = 0;
+            cudaGetLastError();
+            return afail(PBE_ENOMEM, "allocating %lld closure rows failed", R);
+        }
+        w->catrows_cap = R;
+    }
+    long long at = 0;
+    for (int i = 0; i < count; ++i) {
+        const long long n = grids[i]->adjw->last_nrows;
+        if (n > 0)
+            PTRY(cudaMemcpyAsync(w->catrows + at * 6, grids[i]->adjw->mrows, sizeof(float) * 6 * n,
+                                 cudaMemcpyDeviceToDevice, st));
+        at += n;
+    }
+    PTRY(launch_mlp_grad(w->catrows, R, g0->d_mW, g0->d_mB, w->gpart, w->dW, st));
+    PTRY(cudaMemcpyAsync(dL_dweights, w->dW, sizeof(double) * kMlpNW, cudaMemcpyDeviceToHost, st));
+    PTRY(cudaStreamSynchronize(st));
     return PBE_OK;
 }

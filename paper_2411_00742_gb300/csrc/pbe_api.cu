@@ -421,6 +421,15 @@ pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count)
     CUDA_TRY(cudaMemcpy(g->d_mB, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice));
     g->kin.mW = g->d_mW;
     g->kin.mB = g->d_mB;
+    // FNV-1a of the stored values: grids whose gradients are summed must agree
+    unsigned long long hsh = 1469598103934665603ULL;
+    auto mix = [&hsh](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) hsh = (hsh ^ c[i]) * 1099511628211ULL;
+    };
+    mix(hw.data(), sizeof(__nv_bfloat16) * hw.size());
+    mix(hb.data(), sizeof(float) * hb.size());
+    g->mhash = hsh;
     return PBE_OK;
 }
 

@@ -49,6 +49,7 @@ struct pbe_grid {
     float* d_mB;
     double* d_poly;         // polynomial growth law (Eq. 6): ndim x npoly coefficients
     int npoly;
+    unsigned long long mhash;  // learned closure: hash of the stored weights (grids that share them agree)
     int mbox;               // learned closure: training box of its inputs (pbe_set_closure_box)
     double mlo[3], mhi[3];
     // optional device timing of the launch that advances the state in pbe_solve
@@ -113,6 +114,13 @@ void adjoint_work_free(pbe_grid* g);
 // A fused-path solve with the learned closure: the persistent kernel's forward
 // pass (per-stage mu0 sums for the closure's moment-ratio input).
 cudaError_t launch_solve_persistent(pbe_grid* g, int n_out);
+
+// The learned closure's weight gradient over recorded evaluations
+// (pbe_mlp_grad.cu): rows of (x0, x1, x2, lo0, lo1, lo2) floats, tensor-core
+// contractions; `part` is a workspace of mlp_grad_part_floats() floats.
+int mlp_grad_part_floats();
+cudaError_t launch_mlp_grad(const float* rows, long long R, const __nv_bfloat16* mW, const float* mB, float* part,
+                            double* dW, cudaStream_t st);
 
 // Fused path (pbe_fused.cu)
 cudaError_t launch_fused_solve(pbe_grid* g, int n_out);

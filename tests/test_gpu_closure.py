@@ -220,3 +220,61 @@ def test_fused_closure_solve_at_the_workload_size_and_its_timeout():
         g.close()
     assert out["plain"][1] == out["fused"][1]
     np.testing.assert_allclose(out["fused"][0][:, 1:], out["plain"][0][:, 1:], rtol=REL_ROWS_MLP)
+
+
+def _closure_grad_case(seed, N=40, w_seed=4):
+    inst = cd.trajectories(1, seed=seed, N=N)[0]
+    w = cd.initial_weights(w_seed, 0.2)
+    ws = cd.stored_weights(w)
+    tgt = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    r = oracle.solve(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, mlp=ws)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, [1, 2, 3, 9, 11])
+    return inst, w, ws, seeds
+
+
+def _assert_dw_close(got, want, rel):
+    """Element-wise where the entry is not negligible against the largest one."""
+    scale = np.max(np.abs(want))
+    big = np.abs(want) >= 1e-3 * scale
+    err = np.abs(got - want)
+    assert np.all(err[big] <= rel * np.abs(want[big])), np.max(err[big] / np.abs(want[big]))
+    assert np.all(err[~big] <= rel * 1e-3 * scale)
+
+
+def test_tensor_core_weight_gradient_matches_fp64_per_stage_accumulation():
+    """The fused path's weight gradient (rows recorded by the adjoint, tensor-core
+    contractions with split bf16 operands) against the plain path's fp64
+    accumulation of the same per-stage products, element by element, and both
+    against the oracle."""
+    inst, w, ws, seeds = _closure_grad_case(12)
+    dws = {}
+    for path in ("plain", "fused"):
+        g = _grid(inst, w, path)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        dws[path] = np.zeros(cd.CLOSURE_SIZE)
+        g.vjp(inst.t_out, seeds, 64, dweights_out=dws[path])
+        g.close()
+    _assert_dw_close(dws["fused"], dws["plain"], 1e-4)
+    _, _, _, want = oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds, mlp=ws)
+    _assert_dw_close(dws["fused"], want, 2e-3)
+
+
+def test_closure_grad_over_several_trajectories_in_one_launch():
+    """pbe_closure_grad over three grids' recorded rows equals the sum of their
+    single-trajectory gradients and the sum of the oracle's."""
+    import paper_2411_00742_gb300 as P
+    cases = [_closure_grad_case(s) for s in (31, 32, 33)]
+    grids, singles, wants = [], [], []
+    for inst, w, ws, seeds in cases:
+        g = _grid(inst, w, "fused")
+        g.set_state(inst.n0, inst.C0, 0.0)
+        d = np.zeros(cd.CLOSURE_SIZE)
+        g.vjp(inst.t_out, seeds, 64, dweights_out=d)
+        singles.append(d)
+        grids.append(g)
+        wants.append(oracle.vjp(inst.problem, inst.n0, inst.C0, 0.0, inst.t_out, seeds, mlp=ws)[3])
+    tot = P.closure_grad(grids)
+    for g in grids:
+        g.close()
+    _assert_dw_close(tot, sum(singles), 1e-5)
+    _assert_dw_close(tot, sum(wants), 2e-3)
