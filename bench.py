@@ -527,6 +527,21 @@ def run_gpu(args):
                 "paper_context": "jax AD with checkpointing about 40x faster than jax ND per iteration at "
                                  "1000 parameters, ND faster below about 20 (Sec. 4.1, RTX 4090)"}
 
+    def closure_leg():
+        """The learned closure at the workload's size (1024 training and 256 held-out
+        trajectories of the 2-D problem on 128 x 128 grids, Adam at lr 1e-3, minibatches
+        of 32): trained through the solver for a bounded time, then the held-out
+        moment-trajectory error against the solver with the nominal (misspecified)
+        power law; gradients/s of the training (solve + persistent adjoint per
+        trajectory, one weight-gradient launch per minibatch)."""
+        from paper_2411_00742_gb300.train_closure import main as train_main
+        res = train_main(["--train", "1024", "--heldout", "256", "--grid", "128", "--epochs", "24",
+                          "--batch", "32", "--lr", "1e-3", "--workers", "8",
+                          "--max-seconds", str(args.closure_seconds)])
+        res["note"] = ("training stopped after max_seconds of wall time; gain = held-out relative RMS error "
+                       "of the misspecified power law / that of the trained closure")
+        return res
+
     def paper_leg():
         """The paper's own base case (Table 1, Appendix A) at its finest bins: 6000 x 3000
         (0.04 um^2), Eq. 3 with Godunov splitting at Courant number 0.9, one hour."""
@@ -671,6 +686,7 @@ def run_gpu(args):
     adjoint, adjoint_cases = adjoint_leg() if not args.no_adjoint else (None, None)
     paper = paper_leg() if not args.no_paper else None
     poly = poly_leg() if not args.no_adjoint else None
+    closure = closure_leg() if not args.no_closure else None
     scaling, scaling_1d = scaling_leg() if not args.no_scaling else (None, None)
     small_1d = small_1d_leg() if not args.no_scaling else None
 
@@ -710,6 +726,7 @@ def run_gpu(args):
         "adjoint": adjoint,
         "paper_scheme": paper,
         "ad_vs_nd": poly,
+        "closure": closure,
         "scaling_2d": scaling,
         "scaling_1d": scaling_1d,
         # per timed fused solve: k_set_scalars, k_prologue, k_fused, k_fused_rows
@@ -868,6 +885,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-scaling", action="store_true")
+    ap.add_argument("--no-closure", action="store_true")
+    ap.add_argument("--closure-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

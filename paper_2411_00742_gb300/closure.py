@@ -2,11 +2,14 @@
 
 The closure (a 3-64-64-3 perceptron replacing the growth and nucleation
 expressions, the empirical hybrid model of Sec. 4.2) is trained by gradient
-descent through the differentiable solver: every gradient is one forward
-solve plus the hand-written discrete adjoint (pbe_vjp), which backpropagates
-through the closure inside every stage; the optimizer is Adam (pbe_adam_update)
-on device arrays.  Several solves run concurrently, one per CUDA stream and
-host thread.  This module only orchestrates calls into the CUDA library.
+descent through the differentiable solver.  One minibatch: for every
+trajectory a forward solve and the persistent discrete adjoint (pbe_vjp on the
+fused path), which backpropagates through the closure inside every stage and
+records each closure evaluation; then one launch of the weight-gradient kernel
+over the whole minibatch's evaluations (pbe_closure_grad, tensor cores); the
+optimizer is Adam (pbe_adam_update) on device arrays.  The trajectories of a
+minibatch run concurrently, one CUDA stream and grid each.  This module only
+orchestrates calls into the CUDA library.
 """
 from __future__ import annotations
 
@@ -17,7 +20,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 import torch
 
-from . import CLOSURE_SIZE, Grid, _lib
+from . import CLOSURE_SIZE, Grid, _lib, closure_grad
 
 LOSS_COLS_2D = [1, 2, 3, 9, 11]   # mu00, mu10, mu01, mu12, C
 LOSS_COLS_1D = [1, 2, 3, 4, 5]
@@ -35,9 +38,23 @@ def relative_loss_and_seeds(rows, target, cols):
 
 
 class _Worker:
-    def __init__(self, problem):
+    def __init__(self, problem, path="plain"):
         self.stream = torch.cuda.Stream()
-        self.grid = Grid.from_problem(problem, stream=self.stream)
+        self.grid = Grid.from_problem(problem, stream=self.stream, path=path)
+
+    def grad_rows(self, inst, target, weights, cols, checkpoint_every=64):
+        """Loss of one trajectory and its adjoint (fused path): the closure
+        evaluations it differentiates stay recorded in the grid for
+        closure_grad."""
+        g = self.grid
+        g.set_closure(weights)
+        g.set_kinetics(inst.problem, closure=True)
+        g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+        rows, _ = g.solve(inst.t_out)
+        L, seeds = relative_loss_and_seeds(rows, target, cols)
+        g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+        g.vjp(inst.t_out, seeds, checkpoint_every)
+        return L
 
     def grad(self, inst, target, weights, cols, checkpoint_every=64):
         g = self.grid
@@ -77,12 +94,13 @@ class ClosureTrainer:
         self._local = threading.local()
         self._problem = problem_like
         self.workers = []
+        self.slots = []   # one fused-path grid per minibatch trajectory
         self._lock = threading.Lock()
 
     def _worker(self):
         w = getattr(self._local, "w", None)
         if w is None:
-            w = _Worker(self._problem)
+            w = _Worker(self._problem, path="fused")
             self._local.w = w
             with self._lock:
                 self.workers.append(w)
@@ -92,12 +110,17 @@ class ClosureTrainer:
         return self.w.float().cpu().numpy()
 
     def batch_grad(self, insts, targets):
+        """Mean loss and mean weight gradient of a minibatch: the trajectories'
+        solves and adjoints on concurrent streams (one fused-path grid each),
+        then one weight-gradient launch over all their closure evaluations."""
         w32 = self.weights32()
         cols = loss_cols(insts[0].problem.ndim)
-        res = list(self.pool.map(lambda it: self._worker().grad(it[0], it[1], w32, cols), zip(insts, targets)))
-        L = float(np.mean([r[0] for r in res]))
-        g = np.mean([r[1] for r in res], axis=0)
-        return L, g
+        n = len(insts)
+        while len(self.slots) < n:
+            self.slots.append(_Worker(self._problem, path="fused"))
+        Ls = list(self.pool.map(lambda i: self.slots[i].grad_rows(insts[i], targets[i], w32, cols), range(n)))
+        g = closure_grad([sl.grid for sl in self.slots[:n]]) / n
+        return float(np.mean(Ls)), g
 
     def step(self, insts, targets):
         L, g = self.batch_grad(insts, targets)
@@ -118,7 +141,7 @@ class ClosureTrainer:
 
     def close(self):
         self.pool.shutdown()
-        for w in self.workers:
+        for w in self.workers + self.slots:
             w.grid.close()
 
 
