@@ -117,8 +117,9 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k);
  * b1[64], W2[64][64], b2[64], W3[3][64], b3[3]; the weight matrices are stored
  * rounded to bf16 (round to nearest even), the biases in fp32; arithmetic is
  * fp32.  Rates that are not finite fall back to the power law
- * (pbe_set_closure_box).  On the fused path, solves with the closure run in
- * the persistent kernel of pbe_vjp, without its reverse sweep. */
+ * (pbe_set_closure_box).  On the fused path, solves with the closure (and
+ * with the polynomial growth law) run in the persistent kernel of pbe_vjp,
+ * without its reverse sweep. */
 pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count);
 
 /* Coefficients of the polynomial growth law of Eq. 6 (the model of the

@@ -565,12 +565,15 @@ __device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, dou
         lth[4] += lB;
         return;
     }
-    const KinT tc = kin_temperature(K, t);
-    const double d = C - tc.cs;
+    // temperature and the polynomial solubility (the adjoint's only form), as kin_temperature
+    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
+    const double T = K.T0 + (K.T1 - K.T0) * frac;
+    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double d = C - cs;
     if (!(d > 0.0)) return;   // S <= 1: the forward's rates were 0 whatever the parameters
     const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) * K.inv_tcool : 0.0;
-    const double dcs = K.cs1 + 2.0 * K.cs2 * tc.T;
-    const double rd = __drcp_rn(d), rcs = __drcp_rn(tc.cs);
+    const double dcs = K.cs1 + 2.0 * K.cs2 * T;
+    const double rd = __drcp_rn(d), rcs = __drcp_rn(cs);
     if (K.growth_form == 2) {
         double sb;
         if (K.kb > 0.0) sb = B * ik[2];

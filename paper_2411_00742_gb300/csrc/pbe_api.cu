@@ -153,7 +153,8 @@ pbe_status run_solve(pbe_grid* g, int n_out)
 {
     CUDA_TRY(pbe::launch_prologue(g, n_out, g->max_steps, nullptr));
     if (g->path == PBE_PATH_FUSED && pbe::fused_supported(g) && g->kin.scheme == PBE_SCHEME_SSPRK2) {
-        if (g->kin.kind == PBE_KINETICS_MLP) CUDA_TRY(pbe::launch_solve_persistent(g, n_out));
+        // the closure and the polynomial growth law: the persistent kernel's forward pass
+        if (g->kin.kind == PBE_KINETICS_MLP || g->kin.growth_form == 2) CUDA_TRY(pbe::launch_solve_persistent(g, n_out));
         else CUDA_TRY(pbe::launch_fused_solve(g, n_out));
         return PBE_OK;
     }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch1d(const BatchInst* __restric
         }
         if (!s.done) {
             double G1, G2, B, dt, t_new;
-            kinetics_warp(K, s.C, s.t, G1, G2, B);
+            kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
             s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
             s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
             if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch1d(const BatchInst* __restric
             const double C1 = s.C - K.kappa * (V1 - s.V0);
             {
                 double G1, G2, B;
-                kinetics_warp(K, C1, s.t_new, G1, G2, B);
+                kinetics_warp<false>(K, C1, s.t_new, G1, G2, B);
                 s.G1b = G1; s.Bb = B;
                 if (!isfinite(V1) || !isfinite(G1) || !isfinite(B)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
             }
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch1d(const BatchInst* __restric
             if (s.out_idx >= n_out) { s.done = 1; break; }
             if (s.steps >= max_steps) { s.status = PBE_ETIMEOUT; s.done = 1; break; }
             double G1, G2, B, dt, t_new;
-            kinetics_warp(K, s.C, s.t, G1, G2, B);
+            kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
             s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
             s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
             if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_vjp(const BatchInst* __restr
         bool done = out_idx >= n_out;
         auto prepare = [&](StepRec1& r) {
             double G1, G2, B, dt, tn;
-            kinetics_warp(Kn, r.C, r.t, G1, G2, B);
+            kinetics_warp<false>(Kn, r.C, r.t, G1, G2, B);
             r.clipped = timestep_fast(Kn, g, G1, G2, r.t, t_out[out_idx], dt, tn);
             r.G1a = G1; r.Ba = B; r.dt = dt; r.t_new = tn; r.out_idx = out_idx;
         };
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_vjp(const BatchInst* __restr
             __syncwarp();
             r.C1 = r.C - Kn.kappa * (V1 - r.V0);
             double G1, G2, B;
-            kinetics_warp(Kn, r.C1, r.t_new, G1, G2, B);
+            kinetics_warp<false>(Kn, r.C1, r.t_new, G1, G2, B);
             r.G1b = G1; r.Bb = B;
             if (record) {
                 for (int k = lane; k < np; k += 32) my_sn1[q * np_max + k] = n1b[k];

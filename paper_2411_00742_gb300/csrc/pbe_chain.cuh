@@ -14,6 +14,7 @@ namespace pbe {
 // kinetics start at once, lane 0's bookkeeping is stores at the end, and the
 // coefficients of the next stage come from registers.  tc: temperature and
 // solubility at the step's end time.
+template <bool POLY = true>
 __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const Geom& g, double V1, const KinT& tc)
 {
     const int lane = threadIdx.x & 31;
@@ -21,7 +22,7 @@ __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const 
     const double dt = S->dt;
     const int clipped = S->clipped;
     double G1, G2, B, L, sG[3];
-    kinetics_warp_T(K, C1, tc, G1, G2, B, &L, sG);
+    kinetics_warp_T<POLY>(K, C1, tc, G1, G2, B, &L, sG);
     if (lane == 0) {
         S->C1 = C1;
         S->V1 = V1;
@@ -42,6 +43,7 @@ __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const 
     return sc;
 }
 
+template <bool POLY = true>
 __device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const Geom& g, const double* t_out,
                                                    double* rows, const double* mom, int nmom, int vidx,
                                                    const KinT& tc)
@@ -59,7 +61,7 @@ __device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const 
     double G1 = 0.0, G2 = 0.0, B = 0.0, dt = 0.0, t_new = t, L = 0.0, sG[3] = {0.0, 0.0, 0.0};
     int clip2 = 0;
     if (!done) {   // the next step: kinetics at (C, t), CFL step to the next output time
-        kinetics_warp_T(K, C, tc, G1, G2, B, &L, sG);
+        kinetics_warp_T<POLY>(K, C, tc, G1, G2, B, &L, sG);
         clip2 = timestep_fast(K, g, G1, G2, t, t_out[oi], dt, t_new);
     }
     if (lane == 0) {

@@ -267,18 +267,11 @@ struct KinT {
     double T, cs;
 };
 
-// The exponential solubility form in a call of its own: written inline, the
-// compiler evaluates the exponential speculatively beside the polynomial
-// form and the chain waits for it whichever form is set.
-static __device__ __noinline__ double solubility_exp(double cs0, double cs1, double T) { return cs0 * pbe_exp_tab(cs1 * T); }
-
 __device__ __forceinline__ KinT kin_temperature(const Kin& K, double t)
 {
     const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
     const double T = K.T0 + (K.T1 - K.T0) * frac;
-    double cs;
-    if (K.solubility_form == 1) cs = solubility_exp(K.cs0, K.cs1, T);
-    else cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
+    const double cs = K.solubility_form == 1 ? K.cs0 * pbe_exp_tab(K.cs1 * T) : K.cs0 + K.cs1 * T + K.cs2 * T * T;
     return KinT{T, cs};
 }
 
@@ -323,7 +316,9 @@ __device__ __forceinline__ void poly_growth_warp(const Kin& K, double s, double 
 
 // Lout (optional) receives ln s (0 for fixed kinetics or S <= 1); sGout
 // (optional, 3 values) s dG_1/ds, s dG_2/ds and s of the polynomial growth
-// law (0 otherwise).
+// law (0 otherwise).  POLY false: a caller that never sees the polynomial law
+// (the fused solve kernel; its register budget sets its occupancy).
+template <bool POLY = true>
 __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const KinT& tc, double& G1, double& G2,
                                                 double& B, double* Lout = nullptr, double* sGout = nullptr)
 {
@@ -352,7 +347,7 @@ __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const Ki
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
     B = __shfl_sync(0xffffffffu, e, 2);
-    if (K.growth_form == 2) {   // Eq. 6 in place of the power law; nucleation keeps its law
+    if (POLY && K.growth_form == 2) {   // Eq. 6 in place of the power law; nucleation keeps its law
         double sG1, sG2;
         const double sp = d * __drcp_rn(cs);
         poly_growth_warp(K, sp, L, G1, G2, sG1, sG2);
@@ -360,14 +355,15 @@ __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const Ki
     }
 }
 
+template <bool POLY = true>
 __device__ __forceinline__ void kinetics_warp(const Kin& K, double C, double t, double& G1, double& G2, double& B,
                                               double* Lout = nullptr, double* sGout = nullptr)
 {
     if (K.kind == PBE_KINETICS_FIXED) {
-        kinetics_warp_T(K, C, KinT{0.0, 0.0}, G1, G2, B, Lout, sGout);
+        kinetics_warp_T<POLY>(K, C, KinT{0.0, 0.0}, G1, G2, B, Lout, sGout);
         return;
     }
-    kinetics_warp_T(K, C, kin_temperature(K, t), G1, G2, B, Lout, sGout);
+    kinetics_warp_T<POLY>(K, C, kin_temperature(K, t), G1, G2, B, Lout, sGout);
 }
 
 // ---------------------------------------------------------------------------

@@ -514,8 +514,8 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (!fail) {
                     // the next stage's coefficients, once per block (the divisions of
                     // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
-                    const StageCoef c = stage == 1 ? fused_finish1(&s, K, g, msum[VIDX], tpre)
-                                                   : fused_finish2(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre);
+                    const StageCoef c = stage == 1 ? fused_finish1<false>(&s, K, g, msum[VIDX], tpre)
+                                                   : fused_finish2<false>(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre);
                     if (threadIdx.x == 0) scs = c;
                 }
             } else if (warp <= kFaceWarps) {
