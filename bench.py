@@ -277,6 +277,7 @@ def run_gpu(args):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1) * 1e-3)
         bsteps_cells = b.cell_steps()
+        wpb, nteam, wcells = b.schedule()
         b.close()
         tb = sum(times) / len(times)
         # plain single-grid path, instance by instance, on a sample
@@ -298,7 +299,8 @@ def run_gpu(args):
                 g_cells += inst.problem.ncell * st
                 g_time += e0.elapsed_time(e1) * 1e-3
         ach = FLOPS_PER_CELL_STEP_1D * bsteps_cells / tb / 1e12
-        return {"instances": len(insts), "warps_per_block": wpb, "total_steps": bsteps,
+        return {"instances": len(insts), "schedule": {"warps_per_block": wpb, "team_instances": nteam,
+                                                      "warp_cells": wcells}, "total_steps": bsteps,
                 "cell_steps": bsteps_cells, "ms_per_solve": 1e3 * tb, "value": bsteps_cells / tb,
                 "unit": "cell-steps/s",
                 "plain_per_instance": {"value": g_cells / g_time, "sample": "first 64 instances, one grid each"},
@@ -793,6 +795,7 @@ def profile_case(argv):
                             (--ndim 1: the 1-D fine-grid problem of N1 cells)
       paper N1              the paper's base case at N1 x N1/2 bins (plain path)
       batch N1              N1 batched 1-D instances (the batch workload), one solve each repeat
+                            (--autotune or --schedule WPB TEAM CELLS first)
       adjoint N1 [N2]       gradients (pbe_vjp, fused path) of the 2-D adjoint workload on
                             N1 x N2 (--ndim 1: one 1-D instance of N1 cells)
 
@@ -808,6 +811,9 @@ def profile_case(argv):
     ap.add_argument("--outputs", type=int, default=0)
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--window", type=int, default=-1, choices=[-1, 0, 1])
+    ap.add_argument("--autotune", action="store_true", help="batch: autotune the schedule first")
+    ap.add_argument("--schedule", type=int, nargs=3, metavar=("WPB", "TEAM", "CELLS"),
+                    help="batch: set this schedule (warps per block, team instances, warp cells)")
     a = ap.parse_args(argv)
     import torch
     import paper_2411_00742_gb300 as P
@@ -816,6 +822,14 @@ def profile_case(argv):
         insts = pi.batch_1d(a.N1, seed=2411)
         b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
         packed = torch.as_tensor(b.pack([x.n0 for x in insts])).cuda()
+        if a.schedule:
+            b.set_schedule(*a.schedule)
+        elif a.autotune:
+            b.set_state(packed)
+            t0 = time.perf_counter()
+            b.autotune(insts[0].t_out)
+            print(f"batch autotune {time.perf_counter() - t0:.2f} s", flush=True)
+        print(f"batch schedule (warps per block, team instances, warp cells) {b.schedule()}", flush=True)
         for _ in range(a.repeat):
             b.set_state(packed)
             t0 = time.perf_counter()

@@ -329,9 +329,23 @@ pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double*
 /* Steps taken by each instance in the last pbe_batch_solve (host, count values). */
 pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps);
 
-/* Instances per block (1, 2, 3, 4, 6 or 8 warps, one instance per warp; the
- * shared memory of a block holds every warp's instance: PBE_EINVAL when that
- * setting does not fit). */
+/* Schedule of the batched launch: warps_per_block (1, 2, 3, 4, 6 or 8),
+ * team_instances (0..count) and warp_cells (0..6144).  Team instances, each
+ * solved by all warps of a block, are the team_instances instances of
+ * largest estimated cost (cells x CFL steps at the peak supersaturation the
+ * cooling alone gives) and every instance of more than warp_cells cells; the
+ * others are solved by one warp each.  A warp's shared-memory slice holds
+ * the largest warp instance, a block's whole allocation the largest team
+ * instance, so a lower warp_cells leaves smaller slices and more blocks per
+ * SM.  Results are bitwise identical under every schedule (moment sums are
+ * formed over fixed 256-cell segments in a fixed order).  PBE_EINVAL when
+ * the schedule does not fit in one block's shared memory.  pbe_batch_create
+ * picks 4 warps, a cost-based team count and the largest warp_cells that
+ * fits; pbe_batch_autotune times alternatives. */
+pbe_status pbe_batch_set_schedule(pbe_batch* b, int warps_per_block, int team_instances, int warp_cells);
+pbe_status pbe_batch_get_schedule(pbe_batch* b, int* warps_per_block, int* team_instances, int* warp_cells);
+
+/* pbe_batch_set_schedule(b, warps_per_block, 0, 6144): one instance per warp. */
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 
 /* Gradients of a loss of every instance's output rows (the batched form of
@@ -346,9 +360,12 @@ pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out, const double* seeds, int seeds_mem,
                          int checkpoint_every, double* dL_dtheta, double* dL_dC0, double* dL_dn0, int mem);
 
-/* Time each admissible instances-per-block setting on this batch and these
- * output times (the state is saved and restored around every trial), keep
- * the fastest and return it in *chosen (may be NULL). */
+/* Time schedules on this batch and these output times (every warps-per-block
+ * setting with 0, 1/2, 1 and 2 times the cost-based team count; then, at the
+ * fastest, the size cut of every higher occupancy level; then team counts
+ * from 1/4 to 3 times the fastest one; the state is saved and restored
+ * around every trial), keep the fastest and return its warps per block in
+ * *chosen (may be NULL; pbe_batch_get_schedule gives the whole schedule). */
 pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int* chosen);
 
 /* One Adam step (the optimizer of the paper's parameter estimation,

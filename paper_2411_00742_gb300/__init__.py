@@ -359,6 +359,19 @@ class Batch:
     def set_config(self, warps_per_block: int):
         _lib.check(self.lib.pbe_batch_set_config(self.h, int(warps_per_block)))
 
+    def set_schedule(self, warps_per_block: int, team_instances: int, warp_cells: int = 6144):
+        """Warps per block, the number of costliest instances solved by a whole
+        block each, and the largest instance solved by one warp (larger ones
+        are team instances too): pbe_batch_set_schedule."""
+        _lib.check(self.lib.pbe_batch_set_schedule(self.h, int(warps_per_block), int(team_instances),
+                                                   int(warp_cells)))
+
+    def schedule(self) -> tuple[int, int, int]:
+        """(warps per block, team instances, warp cells) of the current schedule."""
+        w, t, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(self.lib.pbe_batch_get_schedule(self.h, ctypes.byref(w), ctypes.byref(t), ctypes.byref(c)))
+        return w.value, t.value, c.value
+
     def autotune(self, t_out) -> int:
         t_out = np.ascontiguousarray(t_out, dtype=np.float64)
         w = ctypes.c_int()

@@ -21,6 +21,11 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# Per-unit flags.  The batched kernel is instantiated once per warps-per-block
+# setting and its results must not depend on that choice: with contraction
+# off, every multiply-add it fuses is an explicit fma in the source, so each
+# instantiation rounds the same way.
+UNIT_FLAGS = {"pbe_batch.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -51,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + UNIT_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,13 +1,20 @@
 // Batched 1-D solves: thousands of independent instances (own grid size,
 // kinetics, cooling profile and CFL-limited step count) in one persistent
-// launch.  One warp owns one instance at a time: its distribution and stage
-// buffer live in the warp's slice of shared memory for the whole solve, the
-// limiter stencil's neighbours come from shared memory and warp shuffles,
-// the moment reductions are warp butterflies and the scalar chain runs on
-// the warp's own lanes, so an instance never synchronizes with anything
-// but its own warp.  Warps pull instance ids from an atomic queue ordered by
-// estimated cost (longest first).  The launch is captured in a CUDA graph
-// and replayed; the warps-per-block setting is chosen by pbe_batch_autotune.
+// launch.  An instance is solved either by one warp or, for the costliest
+// ones, by a team (all warps of a block, each a contiguous share of the
+// rows).  Its distribution and stage buffer stay in shared memory for the
+// whole solve, the limiter stencil's neighbours come from shared memory and
+// warp shuffles, and the scalar chain runs redundantly in every lane, so an
+// instance synchronizes only within its warp or block.  Blocks first pull
+// team instances from one atomic queue, then their warps pull the others
+// from a second one; both are ordered by estimated cost (longest first).
+// The launch is captured in a CUDA graph and replayed; the schedule (warps
+// per block, team instances) is chosen by pbe_batch_autotune.
+//
+// Moment sums are formed per segment of kSegRows rows (lane partials in row
+// order, an xor butterfly over the lanes, several values sharing one) and
+// the segment sums added in segment order, so results are bitwise identical
+// under every schedule.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -15,6 +22,9 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <functional>
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "pbe_internal.h"
@@ -29,166 +39,337 @@ constexpr int kMaxBatchCells = 6144;   // largest instance accepted (shared-memo
 // buffer layout per instance (cell i at index i + 2, two zero ghosts below)
 __host__ __device__ inline int batch_np(int N) { return 32 * ((N + 31) / 32 + 1) + 3; }
 
-template <int STAGE>
-__device__ __forceinline__ void warp_stage(const double* in, const double* old, double* out, int N, int rows,
-                                           double c1, double src, double d1, bool moms, double (&m)[4])
+constexpr int kSegRows = 8;                                   // rows of 32 cells per moment segment
+constexpr int kMaxSeg = (kMaxBatchCells / 32 + kSegRows - 1) / kSegRows;
+
+// Butterfly sums over the warp of several values at once, bitwise equal to
+// one xor butterfly (levels 16, 8, 4, 2, 1) per value: at the first levels each lane
+// keeps the values of its half and sends the others, so every partial sum is
+// the one the single-value butterfly forms in that lane.
+//  allsum4_split: v = the sum of m[lane / 8] (lanes 0-7 m0, ..., 24-31 m3).
+//  allsum2_split: v = the sum of a (lanes 0-15) or of b (lanes 16-31).
+__device__ __forceinline__ double allsum4_split(const double (&m)[4])
 {
     const int lane = threadIdx.x & 31;
-    // face f lies between cells f-1 (upwind) and f: (n_{f-2}, n_{f-1}, n_f) = in[f], in[f+1], in[f+2]
-    double hcur = face_value<true>(in[lane], in[lane + 1], in[lane + 2]);
-    double x = (lane + 0.5) * d1;
-    const double dx32 = 32.0 * d1;
-    for (int r = 0; r < rows; ++r) {
-        const int fn = 32 * (r + 1) + lane;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    const double k0 = h16 ? m[2] : m[0], k1 = h16 ? m[3] : m[1];
+    const double s0 = h16 ? m[0] : m[2], s1 = h16 ? m[1] : m[3];
+    const double a0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+    const double a1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+    double v = (h8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, h8 ? a0 : a1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double allsum2_split(double a, double b)
+{
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16;
+    double v = (h16 ? b : a) + __shfl_xor_sync(0xffffffffu, h16 ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One row of a stage (cell i = 32 r + lane): the face value of the next
+// row's faces (hnext, from shared memory), the update with the flux of the
+// lane to the right (shuffle), and the row's moment weights (without the
+// factor dL, applied to the segment sums) added to m.  src_row: the row may
+// hold cell 0, which receives the nucleation source.
+template <int STAGE>
+__device__ __forceinline__ void stage_row(const double* in, const double* old, double* out, int N, int i, double c1,
+                                          double src, bool src_row, bool moms, double& hcur, double x,
+                                          double (&m)[4])
+{
+    const int lane = threadIdx.x & 31;
+    double v;
+    if (STAGE == 0) {
+        v = in[i + 2];
+    } else {
+        const int fn = i + 32;
         const double hnext = face_value<true>(in[fn], in[fn + 1], in[fn + 2]);
         const double a = __shfl_down_sync(0xffffffffu, hcur, 1);
         const double b = __shfl_sync(0xffffffffu, hnext, 0);
         const double hright = lane == 31 ? b : a;
-        const int i = 32 * r + lane;
-        if (i < N) {
-            double v = in[i + 2] + c1 * (hcur - hright);
-            if (i == 0) v += src;
-            if (STAGE == 2) v = 0.5 * old[i + 2] + 0.5 * v;
-            out[i + 2] = v;
-            const double w = v * d1;
-            if (moms) {
-                const double t1 = x * w, t2 = x * t1;
-                m[0] += w; m[1] += t1; m[2] += t2; m[3] += x * t2;
-            } else {
-                m[3] += x * x * x * w;
-            }
-        }
+        v = fma(c1, hcur - hright, in[i + 2]);
+        if (src_row && i == 0) v += src;
+        if (STAGE == 2) v = fma(0.5, old[i + 2], 0.5 * v);
+        if (i < N) out[i + 2] = v;
         hcur = hnext;
-        x += dx32;
+    }
+    if (i < N) {
+        if (moms) {
+            const double t1 = x * v, t2 = x * t1;
+            m[0] += v;
+            m[1] = fma(x, v, m[1]);
+            m[2] = fma(x, t1, m[2]);
+            m[3] = fma(x, t2, m[3]);
+        } else {
+            m[3] = fma(x * x * x, v, m[3]);
+        }
     }
 }
 
-__device__ __forceinline__ double warp_allsum(double v)
+// The lane partials of one segment of a stage (rows r0 .. r0 + nr - 1).
+template <int STAGE>
+__device__ __forceinline__ void stage_segment(const double* in, const double* old, double* out, int N, int r0, int nr,
+                                              double c1, double src, double d1, bool moms, double& hcur,
+                                              double (&m)[4])
 {
+    const int lane = threadIdx.x & 31;
+    const double dx32 = 32.0 * d1;
+    m[0] = 0.0; m[1] = 0.0; m[2] = 0.0; m[3] = 0.0;
+    double x = (32 * r0 + lane + 0.5) * d1;
+    const int i0 = 32 * r0 + lane;
+    if (nr == kSegRows) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+        for (int j = 0; j < kSegRows; ++j) {
+            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, x, m);
+            x += dx32;
+        }
+    } else {
+        for (int j = 0; j < nr; ++j) {
+            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, x, m);
+            x += dx32;
+        }
+    }
 }
 
+// One stage over the segments [p0, p1) of an instance of R rows (32 cells a
+// row, one a lane): STAGE 1 writes n1 = n + dt L(n), STAGE 2 writes
+// n = n/2 + (n1 + dt L(n1))/2, STAGE 0 only measures `in`.  The face values
+// come from shared memory and the lane to the right (shuffle).  Segment sums
+// of the moment weights (all four with `moms`, else mu3 alone) go to
+// seg[4p + k] (when seg is non-null) or are added to tot in segment order.
+template <int STAGE>
+__device__ __forceinline__ void warp_stage(const double* in, const double* old, double* out, int N, int R, int p0,
+                                           int p1, double c1, double src, double d1, bool moms, double* seg,
+                                           double (&tot)[4])
+{
+    const int lane = threadIdx.x & 31;
+    if (p0 >= p1) return;
+    // face f lies between cells f-1 (upwind) and f: (n_{f-2}, n_{f-1}, n_f) = in[f], in[f+1], in[f+2]
+    const int f0 = 32 * p0 * kSegRows + lane;
+    double hcur = 0.0;
+    if (STAGE != 0) hcur = face_value<true>(in[f0], in[f0 + 1], in[f0 + 2]);
+    double m[4];
+    if (moms) {
+        // lane group k = lane / 8 carries moment k
+        double acc = 0.0;
+        for (int p = p0; p < p1; ++p) {
+            const int r0 = p * kSegRows;
+            stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, true, hcur, m);
+            const double v = allsum4_split(m) * d1;
+            if (seg) {
+                if ((lane & 7) == 0) seg[4 * p + (lane >> 3)] = v;
+            } else {
+                acc += v;
+            }
+        }
+        if (!seg) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tot[k] += __shfl_sync(0xffffffffu, acc, 8 * k);
+        }
+        return;
+    }
+    // mu3 alone: segments in pairs
+    double acc = 0.0;
+    for (int p = p0; p < p1; p += 2) {
+        const int r0 = p * kSegRows;
+        stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, false, hcur, m);
+        const double a = m[3];
+        double b = 0.0;
+        if (p + 1 < p1) {
+            stage_segment<STAGE>(in, old, out, N, r0 + kSegRows, min(kSegRows, R - r0 - kSegRows), c1, src, d1,
+                                 false, hcur, m);
+            b = m[3];
+        }
+        const double v = allsum2_split(a, b);
+        const double sa = __shfl_sync(0xffffffffu, v, 0) * d1, sb = __shfl_sync(0xffffffffu, v, 16) * d1;
+        if (seg) {
+            if (lane == 0) seg[4 * p + 3] = sa;
+            if (lane == 16 && p + 1 < p1) seg[4 * (p + 1) + 3] = sb;
+        } else {
+            acc += sa;
+            if (p + 1 < p1) acc += sb;
+        }
+    }
+    if (!seg) tot[3] += acc;
+}
+
+// Block-shared scratch of a team: segment sums, two buffers used alternately
+// so that one block barrier per stage suffices.
+struct TeamSm {
+    double seg[2][kMaxSeg * 4];
+};
+
+// A stage of one instance by one warp (TEAM false: all segments) or by the
+// block (TEAM true: this warp's segments, then the segment sums of all warps
+// added in order after a block barrier, which also orders this stage's
+// writes before the next stage's reads).  Returns the sums in m.
+template <int STAGE, bool TEAM, int WPB>
+__device__ __forceinline__ void inst_stage(const double* in, const double* old, double* out, int N, int R, double c1,
+                                           double src, double d1, bool moms, TeamSm* ts, int& par, double (&m)[4])
+{
+    for (int k = 0; k < 4; ++k) m[k] = 0.0;
+    const int P = (R + kSegRows - 1) / kSegRows;
+    if (!TEAM) {
+        warp_stage<STAGE>(in, old, out, N, R, 0, P, c1, src, d1, moms, nullptr, m);
+        __syncwarp();
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    double* seg = ts->seg[par];
+    warp_stage<STAGE>(in, old, out, N, R, (warp * P) / WPB, ((warp + 1) * P) / WPB, c1, src, d1, moms, seg, m);
+    __syncthreads();
+    for (int p = 0; p < P; ++p) {
+        if (moms) { m[0] += seg[4 * p]; m[1] += seg[4 * p + 1]; m[2] += seg[4 * p + 2]; }
+        m[3] += seg[4 * p + 3];
+    }
+    par ^= 1;
+}
+
+// One instance, solved by one warp (TEAM false) or by all WPB warps of the
+// block (TEAM true).  nb, n1b: the instance's state and stage buffers in
+// shared memory (cell i at index i + 2, two zero ghosts below).
+template <bool TEAM, int WPB>
+__device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict__ inst, double* state, double* Cst,
+                                             double* tst, const double* t_out, int n_out, double* rows,
+                                             long long* steps_out, int* status_out, long long max_steps, double* nb,
+                                             double* n1b, TeamSm* ts)
+{
+    const int lane = threadIdx.x & 31;
+    const int tid = TEAM ? (int)threadIdx.x : lane, nthr = TEAM ? WPB * 32 : 32;
+    const bool writer = TEAM ? threadIdx.x == 0 : lane == 0;
+    int par = 0;
+    const Kin K = inst[id].K;
+    const Geom g = inst[id].g;
+    const long long off = inst[id].offset;
+    const int N = g.N1, R = inst[id].rows;
+    const int np = batch_np(N);
+    for (int k = tid; k < np; k += nthr) {
+        const int i = k - 2;
+        nb[k] = (i >= 0 && i < N) ? state[off + i] : 0.0;
+        n1b[k] = 0.0;
+    }
+    if (TEAM) __syncthreads();
+    else __syncwarp();
+    // scalar state (identical in every lane of the warp or team)
+    Scal s;
+    s.C = Cst[id];
+    s.t = tst[id];
+    s.steps = 0; s.status = 0; s.done = 0; s.out_idx = 0; s.n_out = n_out; s.max_steps = max_steps;
+    double m[4];
+    inst_stage<0, TEAM, WPB>(nb, nb, nb, N, R, 0.0, 0.0, g.d1, true, ts, par, m);
+    s.V0 = m[3];
+    double* my_rows = rows + (size_t)id * n_out * 6;
+    if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(s.C)) {
+        s.status = PBE_ENONFINITE;
+        s.done = 1;
+    } else {
+        while (s.out_idx < n_out && t_out[s.out_idx] == s.t) {
+            if (writer) {
+                double* row = my_rows + (size_t)s.out_idx * 6;
+                row[0] = s.t; row[1] = m[0]; row[2] = m[1]; row[3] = m[2]; row[4] = m[3]; row[5] = s.C;
+            }
+            s.out_idx += 1;
+        }
+        if (s.out_idx >= n_out) s.done = 1;
+    }
+    if (!s.done) {
+        double G1, G2, B, dt, t_new;
+        kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
+        s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
+        s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
+        if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
+    }
+    while (!s.done) {
+        // stage 1: n1 = n + dt L(n)
+        inst_stage<1, TEAM, WPB>(nb, nb, n1b, N, R, s.G1a * s.dt * g.inv_d1, s.dt * s.Ba * g.inv_d1, g.d1, false, ts,
+                                 par, m);
+        const double V1 = m[3];
+        const double C1 = fma(-K.kappa, V1 - s.V0, s.C);
+        {
+            double G1, G2, B;
+            kinetics_warp<false>(K, C1, s.t_new, G1, G2, B);
+            s.G1b = G1; s.Bb = B;
+            if (!isfinite(V1) || !isfinite(G1) || !isfinite(B)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
+        }
+        // stage 2: n = n/2 + (n1 + dt L(n1))/2
+        const bool moms = s.clipped;
+        inst_stage<2, TEAM, WPB>(n1b, nb, nb, N, R, s.G1b * s.dt * g.inv_d1, s.dt * s.Bb * g.inv_d1, g.d1, moms, ts,
+                                 par, m);
+        const double V2 = m[3];
+        s.C = fma(-K.kappa, V2 - s.V0, s.C);
+        s.t = s.t_new;
+        s.V0 = V2;
+        s.steps += 1;
+        if (!isfinite(V2) || !isfinite(s.C)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
+        if (moms) {
+            if (writer) {
+                double* row = my_rows + (size_t)s.out_idx * 6;
+                row[0] = s.t; row[1] = m[0]; row[2] = m[1]; row[3] = m[2]; row[4] = m[3]; row[5] = s.C;
+            }
+            s.out_idx += 1;
+        }
+        if (s.out_idx >= n_out) { s.done = 1; break; }
+        if (s.steps >= max_steps) { s.status = PBE_ETIMEOUT; s.done = 1; break; }
+        double G1, G2, B, dt, t_new;
+        kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
+        s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
+        s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
+        if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
+    }
+    if (TEAM) __syncthreads();
+    else __syncwarp();
+    for (int i = tid; i < N; i += nthr) state[off + i] = nb[i + 2];
+    if (writer) {
+        Cst[id] = s.C;
+        tst[id] = s.t;
+        steps_out[id] = s.steps;
+        status_out[id] = s.status;
+    }
+    if (TEAM) __syncthreads();
+    else __syncwarp();
+}
+
+// The batch kernel.  order[0..nteam) are the team instances (each solved by
+// a whole block, pulled from queue[0]); order[nteam..count) the others (one
+// per warp, from queue[1]).  np_slot: doubles per buffer of a warp's slice
+// (two buffers a warp); a team uses the block's whole allocation, nb at the
+// start and n1b half way.
 template <int WPB>
-__global__ void __launch_bounds__(WPB * 32) k_batch1d(const BatchInst* __restrict__ inst, const int* __restrict__ order,
-                                                      int count, double* state, double* Cst, double* tst,
+__global__ void __maxnreg__(168) k_batch1d(const BatchInst* __restrict__ inst, const int* __restrict__ order,
+                                                      int count, int nteam, double* state, double* Cst, double* tst,
                                                       const double* t_out, int n_out, double* rows,
                                                       long long* steps_out, int* status_out, unsigned int* queue,
-                                                      int np_max, long long max_steps)
+                                                      int np_slot, long long max_steps)
 {
     extern __shared__ double smem[];
+    __shared__ TeamSm ts;
+    __shared__ int s_idx;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* nb = smem + (size_t)warp * 2 * np_max;
-    double* n1b = nb + np_max;
+    if (nteam > 0) {
+        for (;;) {
+            if (threadIdx.x == 0) s_idx = (int)atomicAdd(queue, 1u);
+            __syncthreads();
+            const int idx = s_idx;
+            __syncthreads();
+            if (idx >= nteam) break;
+            run_instance<true, WPB>(order[idx], inst, state, Cst, tst, t_out, n_out, rows, steps_out, status_out,
+                                    max_steps, smem, smem + (size_t)WPB * np_slot, &ts);
+        }
+    }
+    double* nb = smem + (size_t)warp * 2 * np_slot;
+    double* n1b = nb + np_slot;
     for (;;) {
         int idx = 0;
-        if (lane == 0) idx = (int)atomicAdd(queue, 1u);
+        if (lane == 0) idx = nteam + (int)atomicAdd(queue + 1, 1u);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= count) break;
-        const int id = order[idx];
-        const Kin K = inst[id].K;
-        const Geom g = inst[id].g;
-        const long long off = inst[id].offset;
-        const int N = g.N1, R = inst[id].rows;
-        const int np = batch_np(N);
-        for (int k = lane; k < np; k += 32) {
-            const int i = k - 2;
-            nb[k] = (i >= 0 && i < N) ? state[off + i] : 0.0;
-            n1b[k] = 0.0;
-        }
-        __syncwarp();
-        // scalar state (identical in every lane)
-        Scal s;
-        s.C = Cst[id];
-        s.t = tst[id];
-        s.steps = 0; s.status = 0; s.done = 0; s.out_idx = 0; s.n_out = n_out; s.max_steps = max_steps;
-        double m[4] = {0.0, 0.0, 0.0, 0.0};
-        {
-            double x = (lane + 0.5) * g.d1;
-            for (int i = lane; i < N; i += 32, x += 32.0 * g.d1) {
-                const double w = nb[i + 2] * g.d1, t1 = x * w, t2 = x * t1;
-                m[0] += w; m[1] += t1; m[2] += t2; m[3] += x * t2;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) m[k] = warp_allsum(m[k]);
-        s.V0 = m[3];
-        double* my_rows = rows + (size_t)id * n_out * 6;
-        if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(s.C)) {
-            s.status = PBE_ENONFINITE;
-            s.done = 1;
-        } else {
-            while (s.out_idx < n_out && t_out[s.out_idx] == s.t) {
-                if (lane == 0) {
-                    double* row = my_rows + (size_t)s.out_idx * 6;
-                    row[0] = s.t; row[1] = m[0]; row[2] = m[1]; row[3] = m[2]; row[4] = m[3]; row[5] = s.C;
-                }
-                s.out_idx += 1;
-            }
-            if (s.out_idx >= n_out) s.done = 1;
-        }
-        if (!s.done) {
-            double G1, G2, B, dt, t_new;
-            kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
-            s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
-            s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
-            if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
-        }
-        while (!s.done) {
-            // stage 1: n1 = n + dt L(n)
-            for (int k = 0; k < 4; ++k) m[k] = 0.0;
-            warp_stage<1>(nb, nb, n1b, N, R, s.G1a * s.dt * g.inv_d1, s.dt * s.Ba * g.inv_d1, g.d1, false, m);
-            const double V1 = warp_allsum(m[3]);
-            __syncwarp();
-            const double C1 = s.C - K.kappa * (V1 - s.V0);
-            {
-                double G1, G2, B;
-                kinetics_warp<false>(K, C1, s.t_new, G1, G2, B);
-                s.G1b = G1; s.Bb = B;
-                if (!isfinite(V1) || !isfinite(G1) || !isfinite(B)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
-            }
-            // stage 2: n = n/2 + (n1 + dt L(n1))/2
-            const bool moms = s.clipped;
-            for (int k = 0; k < 4; ++k) m[k] = 0.0;
-            warp_stage<2>(n1b, nb, nb, N, R, s.G1b * s.dt * g.inv_d1, s.dt * s.Bb * g.inv_d1, g.d1, moms, m);
-            if (moms) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) m[k] = warp_allsum(m[k]);
-            } else {
-                m[3] = warp_allsum(m[3]);
-            }
-            __syncwarp();
-            const double V2 = m[3];
-            s.C = s.C - K.kappa * (V2 - s.V0);
-            s.t = s.t_new;
-            s.V0 = V2;
-            s.steps += 1;
-            if (!isfinite(V2) || !isfinite(s.C)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
-            if (moms) {
-                if (lane == 0) {
-                    double* row = my_rows + (size_t)s.out_idx * 6;
-                    row[0] = s.t; row[1] = m[0]; row[2] = m[1]; row[3] = m[2]; row[4] = m[3]; row[5] = s.C;
-                }
-                s.out_idx += 1;
-            }
-            if (s.out_idx >= n_out) { s.done = 1; break; }
-            if (s.steps >= max_steps) { s.status = PBE_ETIMEOUT; s.done = 1; break; }
-            double G1, G2, B, dt, t_new;
-            kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
-            s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
-            s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
-            if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
-        }
-        __syncwarp();
-        for (int i = lane; i < N; i += 32) state[off + i] = nb[i + 2];
-        if (lane == 0) {
-            Cst[id] = s.C;
-            tst[id] = s.t;
-            steps_out[id] = s.steps;
-            status_out[id] = s.status;
-        }
-        __syncwarp();
+        run_instance<false, WPB>(order[idx], inst, state, Cst, tst, t_out, n_out, rows, steps_out, status_out,
+                                 max_steps, nb, n1b, &ts);
     }
 }
 
@@ -204,7 +385,17 @@ struct pbe_batch {
     std::vector<double> C0, t0;
     long long total_cells;
     int np_max;
-    int wpb;                          // warps (instances) per block
+    int wpb;                          // warps per block
+    int nteam;                        // the nteam costliest instances are team instances ...
+    int wcells;                       // ... and so is every instance of more than wcells cells
+    int nteam_default;                // the cost heuristic's team count (autotune's starting point)
+    int nmax;                         // cells of the largest instance
+    std::vector<double> cost;         // estimated cost of each instance (cells x CFL steps)
+    std::vector<int> ncells;
+    std::vector<int> by_cost;         // instance ids by estimated cost, longest first
+    std::vector<int> sizes_desc;      // the distinct instance sizes, largest first
+    std::vector<int> order_h;         // the queue order uploaded to d_order ...
+    int order_nteam, order_wcells;    // ... for this team selection (-1: none yet)
     long long max_steps;
     BatchInst* d_inst;
     int* d_order;
@@ -217,7 +408,7 @@ struct pbe_batch {
     double* d_rows;
     int tout_cap;
     cudaGraphExec_t exec;
-    int exec_wpb, exec_nout;
+    int exec_wpb, exec_nteam, exec_wcells, exec_nout;
     long long* h_steps;
     int* h_status;
 };
@@ -254,12 +445,68 @@ const void* batch_kernel(int wpb)
     }
 }
 
-size_t batch_smem(const pbe_batch* b, int wpb) { return (size_t)wpb * 2 * b->np_max * sizeof(double); }
+// The team instances of a selection (the nteam costliest, and every one of
+// more than wcells cells): how many, and the largest team and warp instance.
+struct TeamSplit {
+    int teams, team_nmax, warp_nmax;
+};
 
-cudaError_t launch_batch(pbe_batch* b, int wpb, int n_out, cudaStream_t st)
+TeamSplit team_split(const pbe_batch* b, int nteam, int wcells)
+{
+    TeamSplit t{0, 0, 0};
+    for (int j = 0; j < b->count; ++j) {
+        const int N = b->ncells[b->by_cost[j]];
+        if (j < nteam || N > wcells) {
+            ++t.teams;
+            t.team_nmax = std::max(t.team_nmax, N);
+        } else {
+            t.warp_nmax = std::max(t.warp_nmax, N);
+        }
+    }
+    return t;
+}
+
+// Doubles per buffer of a warp's shared-memory slice under a schedule: large
+// enough for every warp instance, and (the block's 2 * wpb buffers split in
+// two halves) for every team instance.
+int batch_np_slot(const pbe_batch* b, int wpb, int nteam, int wcells)
+{
+    const TeamSplit t = team_split(b, nteam, wcells);
+    int np = t.warp_nmax > 0 ? batch_np(t.warp_nmax) : 0;
+    if (t.teams > 0) np = std::max(np, (batch_np(t.team_nmax) + wpb - 1) / wpb);
+    return np;
+}
+
+size_t batch_smem(const pbe_batch* b, int wpb, int nteam, int wcells)
+{
+    return (size_t)wpb * 2 * batch_np_slot(b, wpb, nteam, wcells) * sizeof(double);
+}
+
+// The queue order of a team selection: the team instances, then the others,
+// each part by estimated cost, longest first.
+cudaError_t upload_order(pbe_batch* b, int nteam, int wcells)
+{
+    if (b->order_nteam == nteam && b->order_wcells == wcells) return cudaSuccess;
+    std::vector<int>& o = b->order_h;
+    o.clear();
+    for (int j = 0; j < b->count; ++j)
+        if (j < nteam || b->ncells[b->by_cost[j]] > wcells) o.push_back(b->by_cost[j]);
+    for (int j = 0; j < b->count; ++j)
+        if (!(j < nteam || b->ncells[b->by_cost[j]] > wcells)) o.push_back(b->by_cost[j]);
+    cudaError_t e = cudaStreamSynchronize(b->stream);   // no launch in flight reads the old order
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_order, o.data(), sizeof(int) * b->count, cudaMemcpyHostToDevice);
+    b->order_nteam = e == cudaSuccess ? nteam : -1;
+    b->order_wcells = wcells;
+    return e;
+}
+
+// Launch of one batch solve under a schedule (the order must be uploaded).
+cudaError_t launch_batch(pbe_batch* b, int wpb, int nteam, int wcells, int n_out, cudaStream_t st)
 {
     const void* fn = batch_kernel(wpb);
-    size_t smem = batch_smem(b, wpb);
+    size_t smem = batch_smem(b, wpb, nteam, wcells);
+    int np_slot = batch_np_slot(b, wpb, nteam, wcells);
+    int teams = team_split(b, nteam, wcells).teams;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0, sms = 0;
@@ -269,20 +516,46 @@ cudaError_t launch_batch(pbe_batch* b, int wpb, int n_out, cudaStream_t st)
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) return e;
     int blocks = occ * sms;
-    const int need = (b->count + wpb - 1) / wpb;
+    const int need = teams + (b->count - teams + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
-    e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), st);
+    e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    void* args[] = {&b->d_inst, &b->d_order, &b->count, &b->d_state, &b->d_C, &b->d_t, &b->d_tout, &n_out,
-                    &b->d_rows, &b->d_steps, &b->d_status, &b->d_queue, &b->np_max, &b->max_steps};
+    void* args[] = {&b->d_inst, &b->d_order, &b->count, &teams, &b->d_state, &b->d_C, &b->d_t, &b->d_tout, &n_out,
+                    &b->d_rows, &b->d_steps, &b->d_status, &b->d_queue, &np_slot, &b->max_steps};
     return cudaLaunchKernel(fn, blocks, wpb * 32, args, smem, st);
 }
 
-bool wpb_fits(const pbe_batch* b, int wpb)
+int max_block_smem(const pbe_batch* b)
 {
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
-    return batch_smem(b, wpb) <= (size_t)maxsm;
+    return maxsm - (int)sizeof(TeamSm) - 64;
+}
+
+bool schedule_fits(const pbe_batch* b, int wpb, int nteam, int wcells)
+{
+    return batch_smem(b, wpb, nteam, wcells) <= (size_t)max_block_smem(b);
+}
+
+// Blocks per SM that a schedule's shared memory (and the registers) allow.
+int blocks_per_sm(const pbe_batch* b, int wpb, int nteam, int wcells)
+{
+    const void* fn = batch_kernel(wpb);
+    int occ = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_block_smem(b)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, wpb * 32, batch_smem(b, wpb, nteam, wcells)) !=
+            cudaSuccess)
+        occ = 0;
+    return occ;
+}
+
+// The largest size cut at or below wcells (a distinct instance size, or 0)
+// with which the schedule fits; -1 when none does.
+int fitting_wcells(const pbe_batch* b, int wpb, int nteam, int wcells)
+{
+    for (int N : b->sizes_desc)
+        if (N <= wcells && schedule_fits(b, wpb, nteam, N)) return N;
+    return schedule_fits(b, wpb, nteam, 0) ? 0 : -1;
 }
 
 pbe_status ensure_tout(pbe_batch* b, int n_out)
@@ -316,7 +589,8 @@ pbe_status check_times(const pbe_batch* b, const double* t_out, int n_out)
 // configuration or the number of output times changes.
 pbe_status run_batch(pbe_batch* b, int n_out)
 {
-    if (!b->exec || b->exec_wpb != b->wpb || b->exec_nout != n_out) {
+    if (!b->exec || b->exec_wpb != b->wpb || b->exec_nteam != b->nteam || b->exec_wcells != b->wcells ||
+        b->exec_nout != n_out) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         cudaStream_t cap;
         BTRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -324,7 +598,7 @@ pbe_status run_batch(pbe_batch* b, int n_out)
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
         cudaError_t le = cudaSuccess;
         if (e == cudaSuccess) {
-            le = launch_batch(b, b->wpb, n_out, cap);
+            le = launch_batch(b, b->wpb, b->nteam, b->wcells, n_out, cap);
             e = cudaStreamEndCapture(cap, &graph);
         }
         if (e == cudaSuccess) e = le;
@@ -336,6 +610,8 @@ pbe_status run_batch(pbe_batch* b, int n_out)
             return bfail(PBE_ECUDA, "building the batch graph failed: %s", cudaGetErrorString(e));
         }
         b->exec_wpb = b->wpb;
+        b->exec_nteam = b->nteam;
+        b->exec_wcells = b->wcells;
         b->exec_nout = n_out;
     }
     BTRY(cudaGraphLaunch(b->exec, b->stream));
@@ -425,14 +701,39 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
     }
     b->total_cells = b->offsets[count];
     b->np_max = batch_np(nmax);
-    b->wpb = 4;
     b->max_steps = 1000000;
-    std::vector<int> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    b->cost = cost;
+    b->nmax = nmax;
+    b->ncells.resize(count);
+    for (int i = 0; i < count; ++i) b->ncells[i] = h[i].g.N1;
+    b->by_cost.resize(count);
+    std::iota(b->by_cost.begin(), b->by_cost.end(), 0);
+    std::stable_sort(b->by_cost.begin(), b->by_cost.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    b->sizes_desc = b->ncells;
+    std::sort(b->sizes_desc.begin(), b->sizes_desc.end(), std::greater<int>());
+    b->sizes_desc.erase(std::unique(b->sizes_desc.begin(), b->sizes_desc.end()), b->sizes_desc.end());
+    b->order_nteam = -1;
+    b->order_wcells = -1;
     if (cudaGetDevice(&b->device) != cudaSuccess) {
         delete b;
         return bfail(PBE_ECUDA, "no CUDA device available");
+    }
+    // default schedule: 3 warps a block; team instances: every instance whose
+    // estimated cost is above the mean load of a warp (the warps the launch
+    // keeps resident), i.e. that one warp alone would make the launch's tail
+    {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        const int wpb = 3;
+        const int warps = std::max(blocks_per_sm(b, wpb, 0, kMaxBatchCells), 1) * wpb * std::max(sms, 1);
+        double total = 0.0;
+        for (int i = 0; i < count; ++i) total += cost[i];
+        int nt = 0;
+        for (int i = 0; i < count; ++i) nt += cost[i] > total / warps;
+        b->wpb = wpb;
+        b->nteam = nt;
+        b->nteam_default = nt;
+        b->wcells = fitting_wcells(b, wpb, nt, kMaxBatchCells);   // fits at wcells = 0 at the latest
     }
     bool ok = cudaMalloc(&b->d_inst, sizeof(BatchInst) * count) == cudaSuccess &&
               cudaMalloc(&b->d_order, sizeof(int) * count) == cudaSuccess &&
@@ -441,7 +742,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
               cudaMalloc(&b->d_t, sizeof(double) * count) == cudaSuccess &&
               cudaMalloc(&b->d_steps, sizeof(long long) * count) == cudaSuccess &&
               cudaMalloc(&b->d_status, sizeof(int) * count) == cudaSuccess &&
-              cudaMalloc(&b->d_queue, sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&b->d_queue, 2 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMallocHost(&b->h_steps, sizeof(long long) * count) == cudaSuccess &&
               cudaMallocHost(&b->h_status, sizeof(int) * count) == cudaSuccess;
     if (!ok) {
@@ -450,7 +751,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         return bfail(PBE_ENOMEM, "allocating the batch failed");
     }
     if (cudaMemcpy(b->d_inst, h.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        upload_order(b, b->nteam, b->wcells) != cudaSuccess ||
         cudaMemset(b->d_state, 0, sizeof(double) * b->total_cells) != cudaSuccess ||
         cudaMemcpy(b->d_C, b->C0.data(), sizeof(double) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_t, b->t0.data(), sizeof(double) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -532,15 +833,39 @@ pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps)
     return PBE_OK;
 }
 
-pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block)
+pbe_status pbe_batch_set_schedule(pbe_batch* b, int warps_per_block, int team_instances, int warp_cells)
 {
     if (!b) return bfail(PBE_EINVAL, "null batch");
     if (!batch_kernel(warps_per_block)) return bfail(PBE_EINVAL, "warps_per_block must be 1, 2, 3, 4, 6 or 8");
-    if (!wpb_fits(b, warps_per_block))
-        return bfail(PBE_EINVAL, "%d instances of up to %d cells do not fit in one block's shared memory",
-                     warps_per_block, (b->np_max - 35));
+    if (team_instances < 0 || team_instances > b->count)
+        return bfail(PBE_EINVAL, "team_instances = %d outside [0, %d]", team_instances, b->count);
+    if (warp_cells < 0 || warp_cells > kMaxBatchCells)
+        return bfail(PBE_EINVAL, "warp_cells = %d outside [0, %d]", warp_cells, kMaxBatchCells);
+    if (!schedule_fits(b, warps_per_block, team_instances, warp_cells))
+        return bfail(PBE_EINVAL,
+                     "%d warps a block with %d team instances and warp instances of up to %d cells do not fit in "
+                     "one block's shared memory",
+                     warps_per_block, team_instances, warp_cells);
+    BTRY(upload_order(b, team_instances, warp_cells));
     b->wpb = warps_per_block;
+    b->nteam = team_instances;
+    b->wcells = warp_cells;
     return PBE_OK;
+}
+
+pbe_status pbe_batch_get_schedule(pbe_batch* b, int* warps_per_block, int* team_instances, int* warp_cells)
+{
+    if (!b) return bfail(PBE_EINVAL, "null batch");
+    if (warps_per_block) *warps_per_block = b->wpb;
+    if (team_instances) *team_instances = b->nteam;
+    if (warp_cells) *warp_cells = b->wcells;
+    return PBE_OK;
+}
+
+pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block)
+{
+    if (!b) return bfail(PBE_EINVAL, "null batch");
+    return pbe_batch_set_schedule(b, warps_per_block, 0, kMaxBatchCells);
 }
 
 pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double* rows, int mem, int64_t* total_steps)
@@ -550,11 +875,6 @@ pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double*
     if (st) return st;
     for (int i = 0; i < b->count; ++i)
         if (t_out[0] < b->t0[i]) return bfail(PBE_EINVAL, "t_out[0] precedes instance %d's start time", i);
-    if (!wpb_fits(b, b->wpb)) {
-        int w = b->wpb;
-        while (w > 1 && !wpb_fits(b, w)) w /= 2;
-        b->wpb = w;
-    }
     st = ensure_tout(b, n_out);
     if (st) return st;
     BTRY(cudaMemcpyAsync(b->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, b->stream));
@@ -580,41 +900,93 @@ pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int*
         cudaFree(save); cudaFree(saveC); cudaFree(savet);
         return bfail(PBE_ENOMEM, "autotune scratch allocation failed");
     }
-    BTRY(cudaMemcpyAsync(save, b->d_state, sizeof(double) * b->total_cells, cudaMemcpyDeviceToDevice, b->stream));
-    BTRY(cudaMemcpyAsync(saveC, b->d_C, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
-    BTRY(cudaMemcpyAsync(savet, b->d_t, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
-    BTRY(cudaMemcpyAsync(b->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, b->stream));
-    cudaEvent_t e0, e1;
-    BTRY(cudaEventCreate(&e0));
-    BTRY(cudaEventCreate(&e1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     float best = 1e30f;
-    int best_w = b->wpb;
-    const int cands[] = {1, 2, 3, 4, 6, 8};
-    for (int w : cands) {
-        if (!wpb_fits(b, w)) continue;
-        float tsum = 0.0f;
-        for (int rep = 0; rep < 2; ++rep) {
-            BTRY(cudaMemcpyAsync(b->d_state, save, sizeof(double) * b->total_cells, cudaMemcpyDeviceToDevice, b->stream));
-            BTRY(cudaMemcpyAsync(b->d_C, saveC, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
-            BTRY(cudaMemcpyAsync(b->d_t, savet, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
-            BTRY(cudaEventRecord(e0, b->stream));
-            BTRY(launch_batch(b, w, n_out, b->stream));
-            BTRY(cudaEventRecord(e1, b->stream));
-            BTRY(cudaEventSynchronize(e1));
+    int best_w = b->wpb, best_t = b->nteam, best_c = b->wcells;
+    // the trials; every exit path below frees the scratch and events
+    auto run = [&]() -> pbe_status {
+        BTRY(cudaMemcpyAsync(save, b->d_state, sizeof(double) * b->total_cells, cudaMemcpyDeviceToDevice, b->stream));
+        BTRY(cudaMemcpyAsync(saveC, b->d_C, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
+        BTRY(cudaMemcpyAsync(savet, b->d_t, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
+        BTRY(cudaMemcpyAsync(b->d_tout, t_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, b->stream));
+        BTRY(cudaEventCreate(&e0));
+        BTRY(cudaEventCreate(&e1));
+        // time one schedule (the first of two runs warms up); <0 when it does not fit
+        auto trial = [&](int w, int nt, int wc, float* ms_out) -> cudaError_t {
+            *ms_out = -1.0f;
+            if (!schedule_fits(b, w, nt, wc)) return cudaSuccess;
+            cudaError_t e = upload_order(b, nt, wc);
+            if (e != cudaSuccess) return e;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                if ((e = cudaMemcpyAsync(b->d_state, save, sizeof(double) * b->total_cells, cudaMemcpyDeviceToDevice,
+                                         b->stream)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(b->d_C, saveC, sizeof(double) * b->count, cudaMemcpyDeviceToDevice,
+                                         b->stream)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(b->d_t, savet, sizeof(double) * b->count, cudaMemcpyDeviceToDevice,
+                                         b->stream)) != cudaSuccess ||
+                    (e = cudaEventRecord(e0, b->stream)) != cudaSuccess ||
+                    (e = launch_batch(b, w, nt, wc, n_out, b->stream)) != cudaSuccess ||
+                    (e = cudaEventRecord(e1, b->stream)) != cudaSuccess ||
+                    (e = cudaEventSynchronize(e1)) != cudaSuccess || (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+                    return e;
+            }
+            *ms_out = ms;
+            return cudaSuccess;
+        };
+        std::set<std::tuple<int, int, int>> tried;
+        auto consider = [&](int w, int nt, int wc) -> cudaError_t {
+            if (nt < 0 || nt > b->count || wc < 0 || !tried.insert({w, nt, wc}).second) return cudaSuccess;
             float ms;
-            BTRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) tsum += ms;   // first run warms up
+            cudaError_t e = trial(w, nt, wc, &ms);
+            if (e == cudaSuccess && ms >= 0.0f && ms < best) { best = ms; best_w = w; best_t = nt; best_c = wc; }
+            return e;
+        };
+        // (1) every warps-per-block setting with 0, d/2, d and 2d of the
+        // costliest instances as teams (d: the cost heuristic's count), with
+        // the largest size cut that fits ...
+        const int d = b->nteam_default;
+        const int cands[] = {1, 2, 3, 4, 6, 8};
+        for (int w : cands)
+            for (int nt : {0, d / 2, d, 2 * d}) BTRY(consider(w, nt, fitting_wcells(b, w, nt, kMaxBatchCells)));
+        // (2) ... then, at the fastest, the largest size cut of every higher
+        // occupancy level (the warp slices shrink as the size cut falls) ...
+        {
+            const int w = best_w, nt = best_t;
+            int level = blocks_per_sm(b, w, nt, best_c);
+            std::vector<int> cuts(b->sizes_desc);
+            cuts.push_back(0);
+            for (int N : cuts) {
+                if (N >= best_c || !schedule_fits(b, w, nt, N)) continue;
+                const int k = blocks_per_sm(b, w, nt, N);
+                if (k > level) {
+                    level = k;
+                    BTRY(consider(w, nt, N));
+                }
+            }
         }
-        if (tsum < best) { best = tsum; best_w = w; }
-    }
-    BTRY(cudaMemcpyAsync(b->d_state, save, sizeof(double) * b->total_cells, cudaMemcpyDeviceToDevice, b->stream));
-    BTRY(cudaMemcpyAsync(b->d_C, saveC, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
-    BTRY(cudaMemcpyAsync(b->d_t, savet, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
-    BTRY(cudaStreamSynchronize(b->stream));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+        // (3) ... and team counts around the fastest
+        {
+            const int w = best_w, t = best_t, c = best_c;
+            for (int nt : {t / 4, t / 2, (3 * t) / 4, (5 * t) / 4, (3 * t) / 2, 2 * t, 3 * t})
+                BTRY(consider(w, nt, fitting_wcells(b, w, std::min(nt, b->count), c)));
+        }
+        BTRY(upload_order(b, best_t, best_c));
+        BTRY(cudaMemcpyAsync(b->d_state, save, sizeof(double) * b->total_cells, cudaMemcpyDeviceToDevice, b->stream));
+        BTRY(cudaMemcpyAsync(b->d_C, saveC, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
+        BTRY(cudaMemcpyAsync(b->d_t, savet, sizeof(double) * b->count, cudaMemcpyDeviceToDevice, b->stream));
+        BTRY(cudaStreamSynchronize(b->stream));
+        return PBE_OK;
+    };
+    st = run();
+    cudaStreamSynchronize(b->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaFree(save); cudaFree(saveC); cudaFree(savet);
+    if (st) return st;
     b->wpb = best_w;
+    b->nteam = best_t;
+    b->wcells = best_c;
     if (chosen) *chosen = best_w;
     return PBE_OK;
 }

@@ -74,12 +74,59 @@ def test_batch_config_independent_bitwise(wpb):
     assert all(np.array_equal(a, b) for a, b in zip(ref[2], got[2]))
 
 
+def _run_schedule(insts, wpb, nteam, wcells=6144):
+    import paper_2411_00742_gb300 as P
+    b = P.Batch([x.problem for x in insts], [x.C0 for x in insts], [x.t0 for x in insts])
+    b.set_state(b.pack([x.n0 for x in insts]))
+    b.set_schedule(wpb, nteam, wcells)
+    assert b.schedule() == (wpb, nteam, wcells)
+    rows, steps = b.solve(insts[0].t_out)
+    n, C, t = b.get_state()
+    b.close()
+    return rows, steps, n, C, t
+
+
+@pytest.mark.parametrize("wpb,nteam,wcells", [(1, 3, 6144), (2, 7, 6144), (3, 40, 6144), (4, 13, 6144),
+                                              (6, 1, 6144), (8, -1, 6144), (4, 0, 300), (2, 5, 0), (3, 2, 257)])
+def test_batch_team_schedules_bitwise(wpb, nteam, wcells):
+    """Instances solved by a whole block (team) give the same bits as the
+    same instances solved by one warp: the moment sums are formed per fixed
+    segment whichever warp forms them.  Teams chosen by cost and by a size
+    cut; sizes from 1 cell to 2 segments per warp of the widest block, ragged
+    tails included."""
+    insts = [x for x in pi.batch_1d(60, seed=31) if x.problem.ncells[0] <= 1500][:40]
+    for N in (1, 31, 255, 256, 257, 1500):
+        insts.append(pi.config_1d(N))
+    ref = _run_schedule(insts, 4, 0)
+    got = _run_schedule(insts, wpb, len(insts) if nteam < 0 else nteam, wcells)
+    assert np.array_equal(ref[0], got[0]) and ref[1] == got[1]
+    assert all(np.array_equal(a, b) for a, b in zip(ref[2], got[2]))
+    assert np.array_equal(ref[3], got[3]) and np.array_equal(ref[4], got[4])
+
+
+def test_batch_team_instances_match_oracle():
+    """Every instance a team instance, including the largest admissible grid
+    (6144 cells: 24 segments over 8 warps)."""
+    insts = pi.batch_1d(10, seed=8)
+    for N in (6144, 3000, 520):
+        insts.append(pi.config_1d(N))
+    import paper_2411_00742_gb300 as P
+    b = P.Batch([x.problem for x in insts], [x.C0 for x in insts], [x.t0 for x in insts])
+    b.set_state(b.pack([x.n0 for x in insts]))
+    b.set_schedule(8, len(insts))
+    rows, steps = b.solve(insts[0].t_out)
+    n, C, t = b.get_state()
+    b.close()
+    _check_against_oracle(insts, rows, steps, n, C)
+
+
 def test_batch_autotune_keeps_results():
     insts = pi.batch_1d(200, seed=5)
     ref = _run_batch(insts, wpb=4)
     got = _run_batch(insts, autotune=True)
     assert got[5] in (1, 2, 3, 4, 6, 8)
     assert np.array_equal(ref[0], got[0])
+    assert all(np.array_equal(a, b) for a, b in zip(ref[2], got[2]))
 
 
 def test_batch_continues_from_state():
@@ -116,6 +163,15 @@ def test_batch_rejects_config_that_does_not_fit():
     b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
     with pytest.raises(P.PbeError):
         b.set_config(8)
+    with pytest.raises(P.PbeError):
+        b.set_schedule(4, 5)            # more team instances than instances
+    with pytest.raises(P.PbeError):
+        b.set_schedule(3, 0)            # 3 warp instances of 6000 cells: 3 x 97 KB, ...
+    b.set_schedule(4, 4)                # ... all four as team instances: 97 KB a block
+    assert b.schedule() == (4, 4, 6144)
+    b.set_schedule(4, 0, 5999)          # the same four by the size cut
+    with pytest.raises(P.PbeError):
+        b.set_schedule(4, 0, 6145)
     b.close()
 
 
