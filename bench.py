@@ -308,7 +308,8 @@ def run_gpu(args):
                              "frac": ach / FP64_PEAK_TFLOPS_NOMINAL,
                              "own_count_frac": OWN_FLOPS_PER_CELL_STEP_1D * bsteps_cells / tb / 1e12 /
                              FP64_PEAK_TFLOPS_NOMINAL,
-                             "kernel": "batched 1-D kernel (one warp per instance, one graph launch per batch)",
+                             "kernel": "batched 1-D kernel (a warp per instance, a block per costly instance; one graph launch "
+                                       "per batch)",
                              "note": f"{FLOPS_PER_CELL_STEP_1D} flop/cell-step x cell-steps / batch time (CUDA events "
                                      "around the graph launch); peak = nominal GB300 FP64"},
                 "_insts": insts}
@@ -387,7 +388,7 @@ def run_gpu(args):
             res["fused_over_plain"] = res["fused"]["grads_per_s"] / res["plain"]["grads_per_s"]
             out[name] = res
             cases[name] = (inst, tgt, cols, res.pop("dth"), sd)
-        # (b') the batched form: 256 instances of 500 cells, one launch (one warp per instance)
+        # (b') the batched form: 256 instances of 500 cells, one launch (a team of warps per instance)
         insts = pi.adjoint_batch_1d(256)
         cols = [1, 2, 3, 4, 5]
         bt = P.Batch([x.problem.with_theta(x.problem.theta * pi.TARGET_FACTOR) for x in insts],
@@ -428,7 +429,7 @@ def run_gpu(args):
                                    "cpu_adjoint_grads_per_s": None,
                                    "roofline": {"bound": "alu", "achieved": bach, "peak": FP64_PEAK_TFLOPS_NOMINAL,
                                                 "unit": "TFLOP/s", "frac": bach / FP64_PEAK_TFLOPS_NOMINAL,
-                                                "kernel": "batched adjoint (one warp per instance, one launch)",
+                                                "kernel": "batched adjoint (a team of warps per instance, one launch)",
                                                 "note": f"((1 + {ADJOINT_REVERSE_FACTOR}) x cell-steps + recomputed "
                                                         f"cell-steps) x {FLOPS_PER_CELL_STEP_1D} flop / batch time "
                                                         "(CUDA events around the call); peak = nominal GB300 FP64"}}
@@ -796,6 +797,8 @@ def profile_case(argv):
       paper N1              the paper's base case at N1 x N1/2 bins (plain path)
       batch N1              N1 batched 1-D instances (the batch workload), one solve each repeat
                             (--autotune or --schedule WPB TEAM CELLS first)
+      batch-adjoint N1      batched gradients (pbe_batch_vjp) of N1 instances of 500 cells
+                            (the gradient batch workload; --vjp-warps W per instance)
       adjoint N1 [N2]       gradients (pbe_vjp, fused path) of the 2-D adjoint workload on
                             N1 x N2 (--ndim 1: one 1-D instance of N1 cells)
 
@@ -803,7 +806,7 @@ def profile_case(argv):
     (Grid.step) instead of solves, outside the plain path's CUDA graph whose
     conditional nodes a profiler cannot capture.  Prints one line per solve."""
     ap = argparse.ArgumentParser(prog="bench.py --profile-case", description=profile_case.__doc__.splitlines()[0])
-    ap.add_argument("path", choices=["fused", "plain", "paper", "batch", "adjoint"])
+    ap.add_argument("path", choices=["fused", "plain", "paper", "batch", "batch-adjoint", "adjoint"])
     ap.add_argument("N1", type=int)
     ap.add_argument("N2", type=int, nargs="?")
     ap.add_argument("--ndim", type=int, default=2, choices=[1, 2])
@@ -812,6 +815,8 @@ def profile_case(argv):
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--window", type=int, default=-1, choices=[-1, 0, 1])
     ap.add_argument("--autotune", action="store_true", help="batch: autotune the schedule first")
+    ap.add_argument("--vjp-warps", type=int, default=0, help="batch-adjoint: warps per instance (0: automatic)")
+    ap.add_argument("--vjp-blocks", type=int, default=0, help="batch-adjoint: teams per SM (0: automatic)")
     ap.add_argument("--schedule", type=int, nargs=3, metavar=("WPB", "TEAM", "CELLS"),
                     help="batch: set this schedule (warps per block, team instances, warp cells)")
     a = ap.parse_args(argv)
@@ -835,6 +840,30 @@ def profile_case(argv):
             t0 = time.perf_counter()
             _, st = b.solve(insts[0].t_out)
             print(f"batch {a.N1} instances steps {st} {1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
+        b.close()
+        return 0
+    if a.path == "batch-adjoint":
+        insts = pi.adjoint_batch_1d(a.N1)
+        bt = P.Batch([x.problem.with_theta(x.problem.theta * pi.TARGET_FACTOR) for x in insts],
+                     [x.C0 for x in insts])
+        bt.set_state(bt.pack([x.n0 for x in insts]))
+        tgts, _ = bt.solve(pi.loss_times())
+        bt.close()
+        b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
+        packed = b.pack([x.n0 for x in insts])
+        b.set_state(packed)
+        fwd, _ = b.solve(pi.loss_times())
+        cols = [1, 2, 3, 4, 5]
+        sd = np.zeros_like(fwd)
+        sd[..., cols] = 2.0 * (fwd[..., cols] - tgts[..., cols]) / tgts[..., cols] ** 2   # relative-error loss
+        seeds = torch.as_tensor(sd).cuda()
+        b.set_vjp_schedule(a.vjp_warps, a.vjp_blocks)
+        for _ in range(a.repeat):
+            b.set_state(packed)
+            t0 = time.perf_counter()
+            b.vjp(pi.loss_times(), seeds, 64)
+            print(f"batch-adjoint {a.N1} x 500 cells, warps {a.vjp_warps} blocks/SM {a.vjp_blocks} "
+                  f"{1e3 * (time.perf_counter() - t0):.3f} ms", flush=True)
         b.close()
         return 0
     if a.path == "adjoint":

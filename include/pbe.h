@@ -349,9 +349,10 @@ pbe_status pbe_batch_get_schedule(pbe_batch* b, int* warps_per_block, int* team_
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 
 /* Gradients of a loss of every instance's output rows (the batched form of
- * pbe_vjp: the same hand-written discrete adjoint, one warp per instance, the
- * forward with checkpoints every `checkpoint_every` steps and the reverse
- * sweep with recomputation, up to 4096 steps per instance).  Starts from the
+ * pbe_vjp: the same hand-written discrete adjoint by a team of warps (one
+ * block, pbe_batch_set_vjp_schedule) per instance, the forward with
+ * checkpoints every `checkpoint_every` steps and the reverse sweep with
+ * recomputation, up to 4096 steps per instance).  Starts from the
  * batch's current state; seeds: count * n_out rows of 6 doubles (dL/drows,
  * instance-major, `seeds_mem` memory); dL_dtheta HOST count x 6
  * (kg1, g1, kg2, g2, kb, b per instance); dL_dC0 optional HOST count;
@@ -359,6 +360,14 @@ pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
  * batch state is left unchanged.  Synchronizes. */
 pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out, const double* seeds, int seeds_mem,
                          int checkpoint_every, double* dL_dtheta, double* dL_dC0, double* dL_dn0, int mem);
+
+/* Launch shape of pbe_batch_vjp: warps per instance (1, 2, 4 or 8; 0, the
+ * default: 4 while there are at most 4 instances per SM, else 2) and
+ * resident teams per SM (1..32, capped by what fits; 0, the default: 1
+ * while there are at most 2 instances per SM, else 8 / warps).  Results
+ * depend on the warps per instance (the order of the sums), not on
+ * blocks_per_sm. */
+pbe_status pbe_batch_set_vjp_schedule(pbe_batch* b, int warps, int blocks_per_sm);
 
 /* Time schedules on this batch and these output times (every warps-per-block
  * setting with 0, 1/2, 1 and 2 times the cost-based team count; then, at the

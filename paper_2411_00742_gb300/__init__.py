@@ -366,6 +366,11 @@ class Batch:
         _lib.check(self.lib.pbe_batch_set_schedule(self.h, int(warps_per_block), int(team_instances),
                                                    int(warp_cells)))
 
+    def set_vjp_schedule(self, warps: int = 0, blocks_per_sm: int = 0):
+        """Warps per instance of vjp (1, 2, 4, 8) and resident teams per SM;
+        0 = chosen from the batch size (pbe_batch_set_vjp_schedule)."""
+        _lib.check(self.lib.pbe_batch_set_vjp_schedule(self.h, int(warps), int(blocks_per_sm)))
+
     def schedule(self) -> tuple[int, int, int]:
         """(warps per block, team instances, warp cells) of the current schedule."""
         w, t, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -232,39 +232,6 @@ __device__ __forceinline__ void fwd_tile2d(const double* in, const double* old, 
 }
 
 // ---- reverse stage of one tile ---------------------------------------------
-// Derivative data of the face with upwind-upwind, upwind and downwind cells
-// (nm2, up, dn) for the fast forward: h = up + a q, a = up - nm2,
-// b = dn - up, q = b/(a+b) (reciprocal approximation refined twice) when a
-// and b have the same strict sign and both magnitudes reach 2^-959 (the
-// forward's flat threshold), else h = up.  Returns mu times dh/d(nm2, up, dn)
-// and h mu, mu = (lamR - lamL) / dL.
-__device__ __forceinline__ FaceAdj face_adj_fast(double nm2, double up, double dn, double lamL, double lamR,
-                                                 double invd)
-{
-    const double a = up - nm2, b = dn - up;
-    const int ha = __double2hiint(a), hb = __double2hiint(b);
-    const bool same = ((ha ^ hb) >= 0) && ((ha & 0x7ff00000) >= 0x04000000) && ((hb & 0x7ff00000) >= 0x04000000);
-    const double mu = (lamR - lamL) * invd;
-    FaceAdj r;
-    if (same) {
-        const double s = a + b;
-        double rc;
-        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rc) : "d"(s));
-        rc = fma(rc, fma(-s, rc, 1.0), rc);
-        rc = fma(rc, fma(-s, rc, 1.0), rc);
-        const double q = b * rc, qm = q * mu, p = 1.0 - q;
-        r.cm2 = -q * qm;
-        r.cm1 = 2.0 * qm;
-        r.c0 = (p * mu) * p;
-        r.hmu = fma(a, q, up) * mu;
-    } else {
-        r.cm2 = 0.0;
-        r.cm1 = mu;
-        r.c0 = 0.0;
-        r.hmu = up * mu;
-    }
-    return r;
-}
 
 // STAGE 2: lam2 = (lam + sum_k pc[k] W_k)/2; out = lam2 (the Runge-Kutta
 //          average's share of lam_n); u = lam2 + dt (G1 dD1^T + G2 dD2^T) lam2
@@ -545,69 +512,6 @@ __device__ __forceinline__ void record_mlp_row(const AdjP& P, BlockSm& B, const 
 }
 
 // ---- adjoint scalar chain ----------------------------------------------------
-// Backward of the rates at (C, t) given lG* = dL/dG* and the forward's rates
-// and L = ln s (power law: dG/dkg = s^g = G/kg, dG/dg = G L, dG/ds = g G/s;
-// no exponential or logarithm unless a prefactor is 0).  Adds to lth, *lC, *lt.
-// s^g when the prefactor is 0 (the rate itself is then 0 and cannot give it);
-// a call of its own so that the exponential is not evaluated speculatively
-static __device__ __noinline__ double pow_from_log(double g, double L) { return pbe_exp_tab(g * L); }
-
-// sG1, sG2: s dG_m/ds of the polynomial growth law (Eq. 6), recorded by the
-// forward chain; that law's coefficient gradients are accumulated separately
-// (poly_grad_accumulate), its dL/dkg and dL/dg entries stay 0.
-__device__ __forceinline__ void kin_backward(const Kin& K, const double* ik, double C, double t, double G1, double G2,
-                                             double B, double L, double sG1, double sG2, double lG1, double lG2,
-                                             double lB, double* lC, double* lt, double* lth)
-{
-    if (K.kind == PBE_KINETICS_FIXED) {
-        lth[0] += lG1;
-        if (K.ndim == 2) lth[2] += lG2;
-        lth[4] += lB;
-        return;
-    }
-    // temperature and the polynomial solubility (the adjoint's only form), as kin_temperature
-    const double frac = (t < K.t_cool) ? t * K.inv_tcool : 1.0;
-    const double T = K.T0 + (K.T1 - K.T0) * frac;
-    const double cs = K.cs0 + K.cs1 * T + K.cs2 * T * T;
-    const double d = C - cs;
-    if (!(d > 0.0)) return;   // S <= 1: the forward's rates were 0 whatever the parameters
-    const double dTdt = (t < K.t_cool) ? (K.T1 - K.T0) * K.inv_tcool : 0.0;
-    const double dcs = K.cs1 + 2.0 * K.cs2 * T;
-    const double rd = __drcp_rn(d), rcs = __drcp_rn(cs);
-    if (K.growth_form == 2) {
-        double sb;
-        if (K.kb > 0.0) sb = B * ik[2];
-        else sb = pow_from_log(K.b, L);
-        lth[4] += lB * sb;
-        lth[5] += lB * B * L;
-        const double q = (lG1 * sG1 + lG2 * sG2 + lB * K.b * B) * rd;
-        *lC += q;
-        *lt -= q * (C * rcs) * dcs * dTdt;
-        return;
-    }
-    double s1, sb;
-    if (K.kg1 > 0.0) s1 = G1 * ik[0];
-    else s1 = pow_from_log(K.g1, L);
-    if (K.kb > 0.0) sb = B * ik[2];
-    else sb = pow_from_log(K.b, L);
-    double num = lG1 * K.g1 * G1 + lB * K.b * B;   // s dL/ds
-    lth[0] += lG1 * s1;
-    lth[1] += lG1 * G1 * L;
-    lth[4] += lB * sb;
-    lth[5] += lB * B * L;
-    if (K.ndim == 2) {
-        double s2;
-        if (K.kg2 > 0.0) s2 = G2 * ik[1];
-        else s2 = pow_from_log(K.g2, L);
-        lth[2] += lG2 * s2;
-        lth[3] += lG2 * G2 * L;
-        num += lG2 * K.g2 * G2;
-    }
-    // s = (C - c*)/c*: dL/dC = (dL/ds) / c* = num / (C - c*); dL/dt through c*(T(t))
-    const double q = num * rd;
-    *lC += q;
-    *lt -= q * (C * rcs) * dcs * dTdt;
-}
 
 // Before the stage-2 adjoint of a step (thread 0): seeds of the row the step
 // emitted, then the adjoint of C' = C - kappa (V(n') - V(n)) (Eq. 4).

@@ -31,6 +31,7 @@
 #include "pbe_tiles.cuh"
 
 void pbe_set_error_message(int code, const char* msg);  // pbe_api.cu
+extern "C" void pbe_batch_internal_free_vjp_work(void* w);   // pbe_batch_adjoint.cu
 
 namespace pbe {
 
@@ -396,6 +397,10 @@ struct pbe_batch {
     std::vector<int> sizes_desc;      // the distinct instance sizes, largest first
     std::vector<int> order_h;         // the queue order uploaded to d_order ...
     int order_nteam, order_wcells;    // ... for this team selection (-1: none yet)
+    int vjp_warps;                    // warps per instance of pbe_batch_vjp (0: chosen from the batch size)
+    int vjp_blocks;                   // resident teams per SM of pbe_batch_vjp (0: as many as fit)
+    int power_law;                    // every instance has power-law kinetics and the polynomial solubility
+    void* vjp_work;                   // pbe_batch_vjp's device scratch (pbe_batch_adjoint.cu)
     long long max_steps;
     BatchInst* d_inst;
     int* d_order;
@@ -652,6 +657,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
     b->t0.resize(count);
     b->offsets[0] = 0;
     int nmax = 1;
+    bool power_law = true;
     for (int i = 0; i < count; ++i) {
         const pbe_instance& p = inst[i];
         const pbe_kinetics* k = &p.kin;
@@ -681,6 +687,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         d.K.lkg1 = std::log(k->kg[0]); d.K.lkg2 = -INFINITY; d.K.lkb = std::log(k->kb);
         d.K.inv_tcool = 1.0 / k->t_cool;
         d.K.growth_form = k->growth_form;
+        power_law = power_law && k->growth_form == 0 && k->solubility_form == 0;
         d.K.solubility_form = k->solubility_form;
         d.K.ea1 = k->ea[0];
         d.g.ndim = 1; d.g.N1 = (int)p.ncells; d.g.N2 = 1; d.g.d1 = p.lmax / (double)p.ncells; d.g.d2 = 1.0;
@@ -700,6 +707,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         cost[i] = (double)p.ncells * (1.0 + G * k->t_cool / (k->cfl * d.g.d1));
     }
     b->total_cells = b->offsets[count];
+    b->power_law = power_law ? 1 : 0;
     b->np_max = batch_np(nmax);
     b->max_steps = 1000000;
     b->cost = cost;
@@ -767,6 +775,7 @@ pbe_status pbe_batch_destroy(pbe_batch* b)
     if (!b) return PBE_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    pbe_batch_internal_free_vjp_work(b->vjp_work);
     cudaFree(b->d_inst); cudaFree(b->d_order); cudaFree(b->d_state); cudaFree(b->d_C); cudaFree(b->d_t);
     cudaFree(b->d_steps); cudaFree(b->d_status); cudaFree(b->d_queue); cudaFree(b->d_tout); cudaFree(b->d_rows);
     cudaFreeHost(b->h_steps); cudaFreeHost(b->h_status);
@@ -823,6 +832,24 @@ pbe_status pbe_batch_internal_view(pbe_batch* b, const void** inst, const int** 
     *np_max = b->np_max;
     *device = b->device;
     *stream = (void*)b->stream;
+    return PBE_OK;
+}
+
+// accessors for the batched adjoint; not part of the public header
+int pbe_batch_internal_vjp_warps(const pbe_batch* b) { return b->vjp_warps; }
+int pbe_batch_internal_vjp_blocks(const pbe_batch* b) { return b->vjp_blocks; }
+int pbe_batch_internal_power_law(const pbe_batch* b) { return b->power_law; }
+void** pbe_batch_internal_vjp_work(pbe_batch* b) { return &b->vjp_work; }
+
+pbe_status pbe_batch_set_vjp_schedule(pbe_batch* b, int warps, int blocks_per_sm)
+{
+    if (!b) return bfail(PBE_EINVAL, "null batch");
+    if (warps != 0 && warps != 1 && warps != 2 && warps != 4 && warps != 8)
+        return bfail(PBE_EINVAL, "warps per instance must be 0 (automatic), 1, 2, 4 or 8");
+    if (blocks_per_sm < 0 || blocks_per_sm > 32)
+        return bfail(PBE_EINVAL, "blocks_per_sm must be 0 (as many as fit) .. 32");
+    b->vjp_warps = warps;
+    b->vjp_blocks = blocks_per_sm;
     return PBE_OK;
 }
 

@@ -203,11 +203,13 @@ def test_autograd_function(path):
     g.close()
 
 
-@pytest.mark.parametrize("K", [64, 9])
-def test_batched_vjp_matches_cpu_adjoint(K):
-    """The batched adjoint (one warp per instance) against the CPU adjoint,
+@pytest.mark.parametrize("K,warps", [(64, 0), (9, 0), (64, 1), (9, 2), (64, 8)])
+def test_batched_vjp_matches_cpu_adjoint(K, warps):
+    """The batched adjoint (a team of warps per instance; warps 0 = chosen
+    from the batch size, 4 for these 29 instances) against the CPU adjoint,
     instance by instance: 1-D instances with 500 cells and sampled kinetics
-    (the gradient batch workload), plus mixed sizes."""
+    (the gradient batch workload), plus mixed sizes down to 33 cells (two
+    rows: teams of 8 warps leave warps without rows)."""
     import torch
     import paper_2411_00742_gb300 as P
     insts = pi.adjoint_batch_1d(20) + [x for x in pi.batch_1d(8, seed=77, t_out=pi.loss_times())]
@@ -215,6 +217,7 @@ def test_batched_vjp_matches_cpu_adjoint(K):
     insts[-1].t_out = pi.loss_times()
     b = P.Batch([x.problem for x in insts], [x.C0 for x in insts])
     b.set_state(b.pack([x.n0 for x in insts]))
+    b.set_vjp_schedule(warps)
     cols = [1, 2, 3, 4, 5]
     seeds = np.zeros((len(insts), 50, 6))
     wants = []
