@@ -384,11 +384,13 @@ pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int*
 pbe_status pbe_adam_update(double* w, const double* grad, double* m, double* v, int n, double lr, double beta1,
                            double beta2, double eps, int step, void* stream);
 
-/* Kernel of the plain path's 2-D SSP-RK2 stages: -1 (default) the
+/* Kernel of the 2-D SSP-RK2 stages.  Plain path: -1 (default) the
  * register-window kernel when the grid gives it at least one block per SM,
- * else the tile kernel; 0 always the tile kernel; 1 always the window kernel.
- * Both compute the same stage; results agree to rounding.  PBE_EINVAL for
- * another mode. */
+ * else the tile kernel; 0 always the tile kernel; 1 always the window
+ * kernel.  Fused path, grids too large for one tile per co-resident block:
+ * -1 and 1 the persistent window kernel, 0 a loop over 16 x 32 tiles.  All
+ * compute the same stage; results agree to rounding.  PBE_EINVAL for another
+ * mode. */
 pbe_status pbe_set_window(pbe_grid* g, int mode);
 
 /* Limit of every device-wide wait of the fused path (seconds; < 0 restores

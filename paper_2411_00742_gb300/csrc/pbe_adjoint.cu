@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kANT) k_adj1d(const double* __restrict__ nin, 
         const int f = i0 + k;  // face between cells f-1 and f
         if (f > N) { fa[0][k] = fa[1][k] = fa[2][k] = 0.0; continue; }
         // nt index of cell c is c - i0 + 2; lt index of cell c is c - i0 + 1
-        const FaceAdj fa_ = face_adj(nt[k], nt[k + 1], nt[k + 2], lt[k], lt[k + 1], g.inv_d1);
+        const FaceAdj fa_ = face_adj_fast(nt[k], nt[k + 1], nt[k + 2], lt[k], lt[k + 1], g.inv_d1);
         fa[0][k] = fa_.cm2; fa[1][k] = fa_.cm1; fa[2][k] = fa_.c0;
         if (k < kAT1 || (f == N && i0 + kAT1 >= N)) dot += fa_.hmu;   // each face counted by one tile
     }

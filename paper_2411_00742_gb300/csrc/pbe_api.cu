@@ -318,6 +318,7 @@ pbe_status pbe_set_window(pbe_grid* g, int mode)
         cudaGraphExecDestroy(g->plain_exec);
         g->plain_exec = nullptr;
     }
+    if (mode != g->window_mode) g->fused_fn = nullptr;   // the fused launch shape is chosen again
     g->window_mode = mode;
     return PBE_OK;
 }

@@ -646,6 +646,20 @@ static cudaError_t fused_config(pbe_grid* g)
     if (G > 1000) G = 1000;   // the arrival count of barrier_sum has 10 bits
     const void* fn = fn_one;
     size_t fn_dyn = dyn;
+    if (G < ntiles && g->geo.ndim == 2 && g->window_mode != 0) {
+        // more tiles than co-resident blocks on a large 2-D grid: the persistent
+        // window kernel (no halo faces recomputed per 16 x 32 tile)
+        FusedWinCfg c;
+        e = fused_window_config(g->geo, sms, g->max_blocks / 2, &c);
+        if (e != cudaSuccess) return e;
+        g->fused_blocks = c.G;
+        g->fused_ntiles = c.ntiles;
+        g->fused_tiles_x = c.tiles_x;
+        g->fused_ti = c.ti;
+        g->fused_dyn = c.dyn;
+        g->fused_fn = c.fn;
+        return cudaSuccess;
+    }
     if (G < ntiles) {   // more tiles than co-resident blocks: kFTI x 32 tiles looped over
         fn = fn_multi;
         fn_dyn = 0;

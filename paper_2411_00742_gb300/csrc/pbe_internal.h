@@ -85,6 +85,14 @@ cudaError_t launch_set_scalars(pbe_grid* g, double C, double t);
 bool use_window2d(const pbe_grid* g);
 cudaError_t window_setup();   // shared-memory limit of the kernels, on the current device
 cudaError_t launch_window_stage2d(pbe_grid* g, int stage, bool use_cond, cudaGraphConditionalHandle h);
+// Fused path, the same grids (pbe_window.cu): the persistent window kernel
+// (k_fused's parameters) and its launch shape
+struct FusedWinCfg {
+    const void* fn;
+    size_t dyn;
+    int G, ntiles, tiles_x, ti;
+};
+cudaError_t fused_window_config(const Geom& g, int sms, int max_blocks, FusedWinCfg* c);
 // unscaled Gaussian density at the cell centres into d_n; total_dev[0] = its sum,
 // total_dev[1] = its sum weighted by x^3 (1-D) or x1 x2^2 (2-D)
 cudaError_t launch_seed_pdf(pbe_grid* g, const double* mean, const double* sd, double corr, double* total_dev);

@@ -89,14 +89,14 @@ __global__ void __launch_bounds__(kNT) k_solve1d_noalloc(double* n, double* scra
     while (!s.done) {
         StageCoef sc = stage_coef<1>(s, g);
         for (int k = 0; k < 4; ++k) m[k] = 0.0;
-        for (int t = 0; t < ntiles; ++t) tile1d<1, false, false, kTile, kNT>(n, n, n1, t * kTile, g, sc, m, tile, h);
+        for (int t = 0; t < ntiles; ++t) tile1d<1, true, false, kTile, kNT>(n, n, n1, t * kTile, g, sc, m, tile, h);
         block_sum<kNT, 4>(m, sh);
         if (threadIdx.x == 0) finish_stage1(&s, K, m[3]);
         __syncthreads();
         if (s.done) break;
         sc = stage_coef<2>(s, g);
         for (int k = 0; k < 4; ++k) m[k] = 0.0;
-        for (int t = 0; t < ntiles; ++t) tile1d<2, false, false, kTile, kNT>(n1, n, n, t * kTile, g, sc, m, tile, h);
+        for (int t = 0; t < ntiles; ++t) tile1d<2, true, false, kTile, kNT>(n1, n, n, t * kTile, g, sc, m, tile, h);
         block_sum<kNT, 4>(m, sh);
         if (threadIdx.x == 0) finish_stage2(&s, K, g, t_out, rows, m, 4, 3);
         __syncthreads();

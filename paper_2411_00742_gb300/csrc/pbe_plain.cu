@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kNT) k_stage1d(const double* __restrict__ in, 
     StageCoef sc = stage_coef<STAGE>(*S, g);
     if (K.kind == PBE_KINETICS_MLP) sc.moms = true;   // the closure reads mu0 at every stage
     double m[4] = {0.0, 0.0, 0.0, 0.0};
-    tile1d<STAGE, false, false, kT1, kNT>(in, old, out, blockIdx.x * kT1, g, sc, m, tile, h);
+    tile1d<STAGE, true, false, kT1, kNT>(in, old, out, blockIdx.x * kT1, g, sc, m, tile, h);
     block_sum<kNT, 4>(m, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < 4; ++k) part[(size_t)blockIdx.x * kMaxMom + k] = m[k];

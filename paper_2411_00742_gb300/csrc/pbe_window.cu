@@ -1,41 +1,26 @@
-// Plain path, large 2-D grids: one SSP-RK2 stage per kernel with the
-// register-window layout of the split scheme's step kernel (pbe_paper.cu),
-// for the unsplit stage of Eq. 3 in flux form
-//   out = in + c1 (h1_{i-1/2} - h1_{i+1/2}) + c2 (h2_{j-1/2} - h2_{j+1/2})
-//   (+ the nucleation inflow in cell (0, 0); stage 2 averages with n),
-// both directions' faces from the same stage input.
+// Plain path, large 2-D grids: one SSP-RK2 stage per kernel in the
+// register-window layout (the tile body is window_tile, pbe_window.cuh), then
+// the moments and the last-block close of the stage (solute balance, kinetics
+// and step of the next stage) as in the tile kernels.  With 64 KB of shared
+// memory and 4000 cells a block, the kernel is used when the grid gives at
+// least one block per SM; smaller grids keep the tile kernels.
 //
-// Block = 256 threads holding 128 consecutive columns j0-2 .. j0+125 of 32
-// rows and writing the 125 columns j0 .. j0+124:
-//   1. L1 faces: every thread walks down its column (16 rows) with a register
-//      window of the input (2 rows above, 1 below), each face value once;
-//      the input and the partial update w n + w c1 (h_up - h_dn) of every cell
-//      go to shared memory (w = 1 in stage 1, 1/2 in stage 2, where the RK
-//      average then adds n^k / 2);
-//   2. L2 faces along the rows (8 warps x 4 rows, four columns per lane): both
-//      stencil differences of a face come from the lane or the lane below,
-//      face values pass between lanes by shuffles; then the update, the
-//      moments, and the last-block close of the stage (solute balance,
-//      kinetics and step of the next stage) as in the tile kernels.
-// Face quotients by the Newton-Raphson form (psi_quot_fast).  With 64 KB of
-// shared memory and 4000 cells a block, the kernel is used when the grid
-// gives at least one block per SM; smaller grids keep the tile kernels.
+// Fused path, the same grids: one persistent cooperative launch per solve
+// (k_fused_win) whose blocks loop over window tiles, the stages separated by
+// the device-wide barrier that sums the volume moment (barrier_sum), every
+// block advancing its own copy of the scalar chain (fused_finish*).
+#include "pbe_chain.cuh"
 #include "pbe_internal.h"
-#include "pbe_tiles.cuh"
+#include "pbe_sync.cuh"
+#include "pbe_window.cuh"
+
+#include <algorithm>
 
 namespace pbe {
 
-constexpr int kWNT = 256;             // threads per block
-constexpr int kWX = 128;              // columns held per block
-constexpr int kWOut = kWX - 3;        // columns written per block
-constexpr int kWG = kWNT / kWX;       // row groups of the L1 pass
-constexpr int kWW = kWNT / 32;        // warps
-constexpr int kWC = kWX / 32;         // columns per lane in the L2 pass
 // rows per row group R (a block holds 2R rows, each warp 2R/8 of them in the
 // L2 pass): 12, 16 or 20, chosen per grid so that the blocks spread evenly
 // over the SMs (the kernel is bound by each SM's FP64 pipe)
-constexpr size_t win_smem(int R) { return sizeof(double) * 2 * (kWG * R) * kWX; }   // input and partial update
-
 static inline int wdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 static int window_blocks_r(const Geom& g, int R) { return wdiv(g.N2, kWOut) * wdiv(g.N1, kWG * R); }
@@ -67,12 +52,8 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
                                                      Scal* S, Kin K, Geom g, double* part, const double* t_out,
                                                      double* rows, int use_cond, cudaGraphConditionalHandle hcond)
 {
-    constexpr int kWTI = kWG * kWR;       // rows per block
-    constexpr int kWRW = kWTI / kWW;      // rows per warp in the L2 pass
     extern __shared__ __align__(16) double wsm[];
-    double (*ins)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm);              // stage input
-    double (*f1s)[kWX] = reinterpret_cast<double (*)[kWX]>(wsm + kWTI * kWX); // w (in + c1 (h_up - h_dn))
-    __shared__ double x1s[kWTI];
+    __shared__ double x1s[kWG * kWR];
     __shared__ double sh[kWW * 10];
     __shared__ int flag;
     if (S->done) {
@@ -82,92 +63,10 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
     }
     StageCoef sc = stage_coef_fast<STAGE>(*S, g);
     if (K.kind == PBE_KINETICS_MLP) sc.moms = true;   // the closure reads mu0 at every stage
-    // stage 2 is n^k/2 + (n1 + dt L(n1))/2: the factor 1/2 goes into the coefficients
-    constexpr double kW = STAGE == 2 ? 0.5 : 1.0;
-    const double wc1 = kW * sc.c1, wc2 = kW * sc.c2, wsrc = kW * sc.src;
-    const int N1 = g.N1, N2 = g.N2;
-    const int i0 = blockIdx.y * kWTI, j0 = blockIdx.x * kWOut;
-    if (threadIdx.x < kWTI) x1s[threadIdx.x] = (i0 + threadIdx.x + 0.5) * g.d1;
-
-    // 1. L1 faces down this thread's column: input rows i0+ra-2 .. i0+ra+kWR
-    {
-        const int tx = threadIdx.x % kWX, ra = (threadIdx.x / kWX) * kWR;
-        const int j = j0 - 2 + tx;
-        const bool jin = j >= 0 && j < N2;
-        double v[kWR + 3];
-#pragma unroll
-        for (int q = 0; q < kWR + 3; ++q) {
-            const int i = i0 + ra - 2 + q;
-            v[q] = (jin && i >= 0 && i < N1) ? __ldg(in + (size_t)i * N2 + j) : 0.0;
-        }
-        const double a0 = v[1] - v[0];
-        double dprev = v[2] - v[1];
-        double hup = fma(a0, psi_quot_fast(a0, dprev), v[1]);   // face between rows i-1 and i
-#pragma unroll
-        for (int q = 0; q < kWR; ++q) {
-            const double d = v[q + 3] - v[q + 2];
-            const double hdn = fma(dprev, psi_quot_fast(dprev, d), v[q + 2]);   // face between rows i and i+1
-            ins[ra + q][tx] = v[q + 2];
-            f1s[ra + q][tx] = STAGE == 2 ? fma(wc1, hup - hdn, kW * v[q + 2]) : fma(wc1, hup - hdn, v[q + 2]);
-            hup = hdn;
-            dprev = d;
-        }
-    }
-    __syncthreads();
-
-    // 2. L2 faces, update and moments.  Local face c lies between columns c-1
-    // and c; column c is updated from faces c and c+1.  Written columns:
-    // local 2 .. kWX-2 (0, 1 and kWX-1 are halo).
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c0 = kWC * lane, jb = j0 - 2 + c0;
-    const double area = g.d1 * g.d2;
-    double x2[kWC], acc[kWC];
-    bool ok[kWC];
-#pragma unroll
-    for (int k = 0; k < kWC; ++k) {
-        x2[k] = (jb + k + 0.5) * g.d2;
-        acc[k] = 0.0;
-        ok[k] = c0 + k >= 2 && c0 + k <= kWX - 2 && jb + k < N2;
-    }
     double m[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) m[k] = 0.0;
-#pragma unroll
-    for (int q = 0; q < kWRW; ++q) {
-        const int r = warp * kWRW + q, i = i0 + r;
-        const double2 p0 = *reinterpret_cast<const double2*>(&ins[r][c0]);
-        const double2 p1 = *reinterpret_cast<const double2*>(&ins[r][c0 + 2]);
-        const double c[kWC] = {p0.x, p0.y, p1.x, p1.y};
-        const double cl = __shfl_up_sync(0xffffffffu, c[kWC - 1], 1);   // column c0-1
-        double d[kWC];
-        d[0] = c[0] - cl;
-#pragma unroll
-        for (int k = 1; k < kWC; ++k) d[k] = c[k] - c[k - 1];
-        const double a0 = __shfl_up_sync(0xffffffffu, d[kWC - 1], 1);  // across face c0-1
-        double h[kWC + 1];
-        h[0] = fma(a0, psi_quot_fast(a0, d[0]), cl);
-#pragma unroll
-        for (int k = 1; k < kWC; ++k) h[k] = fma(d[k - 1], psi_quot_fast(d[k - 1], d[k]), c[k - 1]);
-        h[kWC] = __shfl_down_sync(0xffffffffu, h[0], 1);                // face c0+kWC
-        if (i >= N1) continue;
-        const double2 f0 = *reinterpret_cast<const double2*>(&f1s[r][c0]);
-        const double2 f1 = *reinterpret_cast<const double2*>(&f1s[r][c0 + 2]);
-        const double fl[kWC] = {f0.x, f0.y, f1.x, f1.y};
-        const size_t row = (size_t)i * N2;
-        const double x1 = x1s[r];
-#pragma unroll
-        for (int k = 0; k < kWC; ++k) {
-            if (!ok[k]) continue;
-            double val = fma(wc2, h[k] - h[k + 1], fl[k]);
-            if (i == 0 && jb + k == 0) val += wsrc;   // nucleation inflow, cell (0, 0)
-            if (STAGE == 2) val = fma(0.5, old[row + jb + k], val);
-            out[row + jb + k] = val;
-            acc[k] = fma(x1, val, acc[k]);
-            if (sc.moms) add_moments(m, val, x1, x2[k], area);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kWC; ++k) m[8] = fma(acc[k], x2[k] * x2[k] * area, m[8]);
+    window_tile<STAGE, kWR, false>(in, old, out, g, sc, blockIdx.y * kWG * kWR, blockIdx.x * kWOut, wsm, x1s, m);
 
     const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
     block_sum<kWNT, 10>(m, sh);
@@ -185,6 +84,165 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
         finish_stage2_warp(S, K, g, t_out, rows, m, 10, 8);
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(hcond, S->done ? 0u : 1u);
     }
+}
+
+// Fused path, large 2-D grids: the whole solve in one cooperative launch.
+// Each block owns an even contiguous share of the window tiles (tile t:
+// rows (t / tiles_x) 2R.., columns (t % tiles_x) 125..) and runs them every
+// stage, so a cell's stage-2 base value is read back by the thread that wrote
+// it; halo rows and columns written by other blocks are read through L2
+// (window_tile<.., CG = true>) after the device-wide barrier of the stage,
+// which also sums the volume moment in fixed point (barrier_sum).  Warp 0 of
+// every block then advances the block's copy of the scalar chain
+// (fused_finish1/2, identical in every block).  Output steps: every block's
+// ten moments go to rowpart, summed per row after the solve (k_fused_rows).
+// Same parameters as k_fused; ti = rows per tile.
+template <int kWR>
+__global__ void __launch_bounds__(kWNT, 2) k_fused_win(double* n, double* n1, Scal* S, Kin K, Geom g, double* part,
+                                                      const double* t_out, double* rows, unsigned int* bar,
+                                                      int ntiles, int tiles_x, int ti, long long wait_limit,
+                                                      double* rowpart)
+{
+    constexpr int NM = 10, VIDX = 8;
+    constexpr int kWTI = kWG * kWR;
+    extern __shared__ __align__(16) double wsm[];
+    __shared__ double x1s[kWTI];
+    __shared__ Scal s;
+    __shared__ StageCoef scs;
+    __shared__ double red[kWW * NM];
+    __shared__ long long wsum[kWW];
+    __shared__ double msum[NM];
+    __shared__ int fail;
+    (void)part;
+    (void)ti;
+    if (threadIdx.x == 0) {
+        s = *S;
+        s.row_first = s.out_idx;   // rows before this index came from the prologue
+        scs = stage_coef_fast<1>(s, g);
+        fail = 0;
+    }
+    if (threadIdx.x < NM) msum[threadIdx.x] = 0.0;
+    __syncthreads();
+    if (s.done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) S->row_first = s.row_first;
+        return;
+    }
+    const int G = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* my_rows = blockIdx.x == 0 ? rows : nullptr;
+    // fixed-point unit of the volume-moment sum, as in k_fused
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(bar);
+    unsigned long long acc_base0 = 0ull, acc_base1 = 0ull;
+    double u, inv_u;
+    {
+        double vmax = 2.0 * (s.V0 + (K.kappa > 0.0 ? s.C / K.kappa : 0.0));
+        if (!(vmax > 0.0) || !isfinite(vmax)) vmax = 1.0;
+        const int E = ilogb(vmax) + 1;
+        u = ldexp(1.0, E - 52);
+        inv_u = ldexp(1.0, 52 - E);
+    }
+    unsigned int gen = 0;
+    const int t_first = (int)(((long long)blockIdx.x * ntiles) / G);
+    const int t_end = (int)(((long long)(blockIdx.x + 1) * ntiles) / G);
+    for (;;) {
+        KinT tpre{0.0, 0.0};
+        if (warp == 0 && K.kind != PBE_KINETICS_FIXED) tpre = kin_temperature(K, s.t_new);
+#pragma unroll 1
+        for (int stage = 1; stage <= 2; ++stage) {
+            const StageCoef sc = scs;
+            double m[NM];
+#pragma unroll
+            for (int k = 0; k < NM; ++k) m[k] = 0.0;
+            for (int t = t_first; t < t_end; ++t) {
+                const int i0 = (t / tiles_x) * kWTI, j0 = (t % tiles_x) * kWOut;
+                if (stage == 1) window_tile<1, kWR, true>(n, n, n1, g, sc, i0, j0, wsm, x1s, m);
+                else window_tile<2, kWR, true>(n1, n, n, g, sc, i0, j0, wsm, x1s, m);
+                __syncthreads();
+            }
+            const int row_here = s.out_idx;
+            if (sc.moms) {
+#pragma unroll
+                for (int k = 0; k < NM; ++k) {
+                    double v = m[k];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) red[warp * NM + k] = v;
+                }
+            }
+            const long long qb = block_sum_fixed_t0(m[VIDX], inv_u, wsum);   // its barrier orders red
+            if (sc.moms && threadIdx.x < NM) {
+                double v = 0.0;
+#pragma unroll
+                for (int w = 0; w < kWW; ++w) v += red[w * NM + threadIdx.x];
+                rowpart[((size_t)row_here * G + blockIdx.x) * NM + threadIdx.x] = v;
+            }
+            if (warp == 0) {
+                if (threadIdx.x == 0) {
+                    double total = 0.0;
+                    const int p = (int)(gen & 1u);
+                    unsigned long long base = p ? acc_base1 : acc_base0;
+                    const bool ok = barrier_sum(acc + p * kAccStride, base, qb, u, (unsigned int)G, wait_limit, total);
+                    if (p) acc_base1 = base;
+                    else acc_base0 = base;
+                    msum[VIDX] = total;
+                    fail = !ok;
+                }
+                __syncwarp();
+                if (!fail) {
+                    const StageCoef c = stage == 1 ? fused_finish1<false>(&s, K, g, msum[VIDX], tpre)
+                                                   : fused_finish2<false>(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre);
+                    if (threadIdx.x == 0) scs = c;
+                }
+            }
+            gen += 1u;
+            __syncthreads();
+            if (fail || s.done) break;
+        }
+        if (s.done || fail) break;
+    }
+    if (threadIdx.x == 0 && fail) {
+        S->status = PBE_ETIMEOUT;
+        S->done = 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !fail) {
+        s.counter = 0u;
+        *S = s;
+    }
+}
+
+// Configuration of the fused window launch of a 2-D grid: the R (rows per
+// group) with the least work on the busiest SM, estimated as the tiles per SM
+// times the rows a tile loads (2R + 3, halo included); blocks = the
+// co-resident ones, at most one per tile and max_blocks.
+cudaError_t fused_window_config(const Geom& g, int sms, int max_blocks, FusedWinCfg* c)
+{
+    double best = 1e300;
+    for (int R : {16, 12, 20}) {
+        const void* fn = R == 12 ? (const void*)k_fused_win<12> : R == 20 ? (const void*)k_fused_win<20>
+                                                                         : (const void*)k_fused_win<16>;
+        const size_t dyn = win_smem(R);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kWNT, dyn);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) continue;
+        const int tiles_x = wdiv(g.N2, kWOut), ntiles = tiles_x * wdiv(g.N1, kWG * R);
+        int G = std::min(ntiles, occ * sms);
+        G = std::min(G, max_blocks);
+        G = std::min(G, 1000);   // the arrival count of barrier_sum has 10 bits
+        const double cost = (double)wdiv(ntiles, sms) * (2 * R + 3);
+        if (cost < best - 1e-9) {
+            best = cost;
+            c->fn = fn;
+            c->dyn = dyn;
+            c->G = G < 1 ? 1 : G;
+            c->ntiles = ntiles;
+            c->tiles_x = tiles_x;
+            c->ti = kWG * R;
+        }
+    }
+    return best < 1e300 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
 template <int R>

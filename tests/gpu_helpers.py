@@ -9,10 +9,11 @@ REL_ROWS = 1e-10      # moments mu and concentration C, relative, every output t
 REL_N = 1e-9          # distribution: L-inf error <= REL_N * max(n)
 
 
-def gpu_solve(inst, path="plain", device_buffers=True):
+def gpu_solve(inst, path="plain", device_buffers=True, window=-1):
     import torch
     import paper_2411_00742_gb300 as P
     g = P.Grid.from_problem(inst.problem, path=path)
+    g.set_window(window)
     if device_buffers:
         g.set_state(torch.as_tensor(np.ascontiguousarray(inst.n0)).cuda(), inst.C0, inst.t0)
         rows_t = torch.zeros((len(inst.t_out), P.ncols(inst.problem.ndim)), dtype=torch.float64, device="cuda")
@@ -45,9 +46,9 @@ def assert_n_close(got, want, rel=REL_N):
     assert err <= rel * scale, f"L-inf error {err:.3e} > {rel:.0e} * max(n) = {rel * scale:.3e}"
 
 
-def compare_instance(inst, path="plain", device_buffers=True):
+def compare_instance(inst, path="plain", device_buffers=True, window=-1):
     want = oracle.solve_instance(inst)
-    got = gpu_solve(inst, path=path, device_buffers=device_buffers)
+    got = gpu_solve(inst, path=path, device_buffers=device_buffers, window=window)
     assert got["steps"] == want["steps"], (got["steps"], want["steps"])
     assert_rows_close(got["rows"], want["rows"])
     assert_n_close(got["n"], want["n"])

@@ -37,8 +37,26 @@ def test_fused_2d_tall_tiles(shape):
 
 def test_fused_2d_larger_than_one_wave():
     # tiles taller than 64 rows would be needed for one per block: blocks loop
-    # over several 16 x 32 tiles
-    compare_instance(pi.config_2d(1200, 300), path="fused")
+    # over several 16 x 32 tiles (window kernel off)
+    compare_instance(pi.config_2d(1200, 300), path="fused", window=0)
+
+
+@pytest.mark.parametrize("shape", [(1200, 300), (700, 530), (333, 1000)])
+def test_fused_2d_window_kernel(shape):
+    # grids too large for one tile per block, on the persistent window kernel
+    # (the default there): blocks loop over 2R x 125 window tiles, halo rows
+    # and columns from the other blocks through L2, ragged in both directions
+    compare_instance(pi.config_2d(*shape), path="fused", window=1)
+
+
+def test_fused_window_kernel_matches_tile_loop_closely():
+    inst = pi.config_2d(1200, 300)
+    a = gpu_solve(inst, path="fused", window=0)
+    b = gpu_solve(inst, path="fused", window=1)
+    assert a["steps"] == b["steps"]
+    np.testing.assert_allclose(b["rows"], a["rows"], rtol=1e-12)
+    c = gpu_solve(inst, path="fused", window=1)
+    assert np.array_equal(b["rows"], c["rows"]) and np.array_equal(b["n"], c["n"])
 
 
 def test_fused_state_at_every_output_time():
