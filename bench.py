@@ -540,7 +540,7 @@ def run_gpu(args):
         from paper_2411_00742_gb300.train_closure import main as train_main
         res = train_main(["--train", "1024", "--heldout", "256", "--grid", "128", "--epochs", "24",
                           "--batch", "32", "--lr", "1e-3", "--workers", "8",
-                          "--max-seconds", str(args.closure_seconds)])
+                          "--max-seconds", str(args.closure_seconds)], emit=False)
         res["note"] = ("training stopped after max_seconds of wall time; gain = held-out relative RMS error "
                        "of the misspecified power law / that of the trained closure")
         return res

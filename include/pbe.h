@@ -362,7 +362,7 @@ pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out, const dou
                          int checkpoint_every, double* dL_dtheta, double* dL_dC0, double* dL_dn0, int mem);
 
 /* Launch shape of pbe_batch_vjp: warps per instance (1, 2, 4 or 8; 0, the
- * default: 4 while there are at most 4 instances per SM, else 2) and
+ * default: 4 while there are at most 8 instances per SM, else 2) and
  * resident teams per SM (1..32, capped by what fits; 0, the default: 1
  * while there are at most 2 instances per SM, else 8 / warps).  Results
  * depend on the warps per instance (the order of the sums), not on

@@ -40,10 +40,19 @@ __device__ __forceinline__ double wsum(double v)
     return v;
 }
 
+// Pairwise sum of n values (a fixed tree: the same on every run).
+template <int N>
+__device__ __forceinline__ double tree_sum(const double* p)
+{
+    if constexpr (N == 1) return p[0];
+    else return tree_sum<N / 2>(p) + tree_sum<N - N / 2>(p + N / 2);
+}
+
 // Block-level sums of a team of W warps: warp butterflies, then the warp
-// sums added in warp order (two buffers used alternately so that one barrier
-// per sum suffices; the barrier also orders the shared-memory writes before
-// the sum against the reads after it).  W = 1: the butterfly alone.
+// sums added pairwise in a fixed tree (two buffers used alternately so that
+// one barrier per sum suffices; the barrier also orders the shared-memory
+// writes before the sum against the reads after it).  W = 1: the butterfly
+// alone.
 template <int W>
 struct Team {
     double* red;   // [2][W] in shared memory
@@ -62,9 +71,7 @@ struct Team {
         }
         if ((threadIdx.x & 31) == 0) red[par * W + (threadIdx.x >> 5)] = v;
         __syncthreads();
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) t += red[par * W + w];
+        const double t = tree_sum<W>(red + par * W);
         par ^= 1;
         return t;
     }
@@ -141,7 +148,9 @@ __device__ __forceinline__ void adj_stage(const double* nt, const double* lam, c
 }
 
 // One instance at a time per block of W warps (the team); slot = the
-// block's scratch in the checkpoint and segment stores.
+// block's scratch in the checkpoint and segment stores.  The forward pass
+// also records the steps of the segment it is in (the last segment is then
+// not recomputed).
 template <int W>
 __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restrict__ inst, const int* __restrict__ order,
                                                       int count, const double* __restrict__ state0,
@@ -156,6 +165,7 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
     extern __shared__ double smem[];
     __shared__ double red[2 * W];
     __shared__ double chs[6];   // chain values handed from warp 0 to the team
+    __shared__ double pcs[4], pus[4];   // pending moment-weight coefficients of the stage adjoints
     __shared__ int s_idx;
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long slot = blockIdx.x;
@@ -248,14 +258,16 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
             if (record) {
                 for (int k = tid; k < np; k += NT) my_sn[q * np_max + k] = nb[k];
             }
-            const double V1 = tm.sum(fwd_stage<1>(nb, nb, n1b, N, r0, r1, r.G1a * r.dt * g.inv_d1, r.dt * r.Ba * g.inv_d1, d1));
+            const double V1 =
+                tm.sum(fwd_stage<1>(nb, nb, n1b, N, r0, r1, r.G1a * r.dt * g.inv_d1, r.dt * r.Ba * g.inv_d1, d1));
             r.C1 = r.C - Kn.kappa * (V1 - r.V0);
             stage2_rates(r);
             if (record) {
                 for (int k = tid; k < np; k += NT) my_sn1[q * np_max + k] = n1b[k];
                 if (tid == 0) my_sr[q] = r;
             }
-            const double V2 = tm.sum(fwd_stage<2>(n1b, nb, nb, N, r0, r1, r.G1b * r.dt * g.inv_d1, r.dt * r.Bb * g.inv_d1, d1));
+            const double V2 =
+                tm.sum(fwd_stage<2>(n1b, nb, nb, N, r0, r1, r.G1b * r.dt * g.inv_d1, r.dt * r.Bb * g.inv_d1, d1));
             StepRec1 nx = r;
             nx.C = r.C - Kn.kappa * (V2 - r.V0);
             nx.t = r.t_new;
@@ -271,7 +283,7 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
                 for (int k = tid; k < np; k += NT) my_ck[c * np_max + k] = nb[k];
                 if (tid == 0) my_ckr[c] = s;
             }
-            step(s, false, 0);
+            step(s, true, total % K);
             ++total;
             if (!isfinite(s.C) || !isfinite(s.V0)) { status = PBE_ENONFINITE; break; }
             if (out_idx >= n_out) done = true;
@@ -279,6 +291,11 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
         }
         tm.sync();
         // ---------------- reverse sweep ----------------
+        // The scalar adjoint chain (seed rows, solute balance, rate adjoints,
+        // step length) runs in warp 0 alone; the team needs only the pending
+        // moment-weight coefficients of each stage adjoint, handed over in
+        // pcs / pus (shared memory) before the barrier that precedes the stage.
+        const bool chain = W == 1 || warp == 0;
         double lC = 0.0, lt = 0.0, lth[6] = {0, 0, 0, 0, 0, 0};
         double pc[4] = {0.0, 0.0, 0.0, 0.0};
         for (int k = tid; k < np; k += NT) lam[k] = 0.0;
@@ -286,86 +303,108 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
         const long long nck = status ? 0 : (total + K - 1) / K;
         for (long long c = nck - 1; c >= 0; --c) {
             const long long s0 = c * K, s1 = (s0 + K < total) ? s0 + K : total;
-            for (int k = tid; k < np; k += NT) {
-                nb[k] = my_ck[c * np_max + k];
-                n1b[k] = 0.0;
-            }
-            tm.sync();
-            StepRec1 r = my_ckr[c];
-            out_idx = r.out_idx;
-            for (long long q = 0; q < s1 - s0; ++q) {
-                if (q > 0) prepare(r);
-                step(r, true, q);
+            if (c < nck - 1) {   // the last segment's records come from the forward pass
+                for (int k = tid; k < np; k += NT) {
+                    nb[k] = my_ck[c * np_max + k];
+                    n1b[k] = 0.0;
+                }
+                tm.sync();
+                StepRec1 r = my_ckr[c];
+                out_idx = r.out_idx;
+                for (long long q = 0; q < s1 - s0; ++q) {
+                    if (q > 0) prepare(r);
+                    step(r, true, q);
+                }
             }
             tm.sync();
             for (long long q = s1 - s0 - 1; q >= 0; --q) {
                 const StepRec1 rr = my_sr[q];
-                if (rr.clipped) {
-                    const double* row = sd + (size_t)rr.out_idx * 6;
-                    for (int k = 0; k < 4; ++k) pc[k] += row[1 + k];
-                    lC += row[5];
+                double lV0 = 0.0, lCprev = 0.0;
+                if (chain) {
+                    if (rr.clipped) {
+                        const double* row = sd + (size_t)rr.out_idx * 6;
+                        for (int k = 0; k < 4; ++k) pc[k] += row[1 + k];
+                        lC += row[5];
+                    }
+                    lV0 = Kn.kappa * lC;
+                    lCprev = lC;
+                    pc[3] += -Kn.kappa * lC;
+                    if (tid == 0)
+                        for (int k = 0; k < 4; ++k) pcs[k] = pc[k];
                 }
-                double lV0 = Kn.kappa * lC, lCprev = lC;
-                pc[3] += -Kn.kappa * lC;
                 // stage-2 adjoint: input n1 (recorded), lam_eff = (lam + pc.W)/2
                 for (int k = tid; k < np; k += NT) nb[k] = my_sn1[q * np_max + k];
                 tm.sync();
                 double P1, P0;
-                adj_stage<W>(nb, lam, pc, 0.5, leff, fc, N, R, d1, tm, P1, P0);
+                adj_stage<W>(nb, lam, pcs, 0.5, leff, fc, N, R, d1, tm, P1, P0);
                 for (int i = tid; i < N; i += NT) {
                     const double jt = fc[3 * (i + 2)] + fc[3 * (i + 1) + 1] + fc[3 * i + 2];
                     const double l2 = leff[i + 2];
                     lamo[i + 2] = l2;
                     u[i + 2] = l2 + rr.dt * rr.G1b * jt;
                 }
-                double ldt = rr.G1b * P1 + rr.Bb * P0 * g.inv_d1;
-                double lC1 = 0.0, ltn = lt;
-                kin_backward(Kn, ik, rr.C1, rr.t_new, rr.G1b, 0.0, rr.Bb, rr.Lb, 0.0, 0.0, rr.dt * P1, 0.0,
-                             rr.dt * P0 * g.inv_d1, &lC1, &ltn, lth);
-                lCprev += lC1;
-                lV0 += Kn.kappa * lC1;
-                double pu[4] = {0.0, 0.0, 0.0, -Kn.kappa * lC1};
+                double ldt = 0.0, ltn = 0.0;
+                if (chain) {
+                    ldt = rr.G1b * P1 + rr.Bb * P0 * g.inv_d1;
+                    double lC1 = 0.0;
+                    ltn = lt;
+                    kin_backward(Kn, ik, rr.C1, rr.t_new, rr.G1b, 0.0, rr.Bb, rr.Lb, 0.0, 0.0, rr.dt * P1, 0.0,
+                                 rr.dt * P0 * g.inv_d1, &lC1, &ltn, lth);
+                    lCprev += lC1;
+                    lV0 += Kn.kappa * lC1;
+                    if (tid == 0) {
+                        pus[0] = 0.0; pus[1] = 0.0; pus[2] = 0.0;
+                        pus[3] = -Kn.kappa * lC1;
+                    }
+                }
                 // stage-1 adjoint: input n (recorded), lam_eff = u + pu.W
-                tm.sync();   // nb, leff and fc are rewritten below
+                tm.sync();   // nb, leff and fc are rewritten below; pus is complete
                 for (int k = tid; k < np; k += NT) nb[k] = my_sn[q * np_max + k];
                 tm.sync();
-                adj_stage<W>(nb, u, pu, 1.0, leff, fc, N, R, d1, tm, P1, P0);
+                adj_stage<W>(nb, u, pus, 1.0, leff, fc, N, R, d1, tm, P1, P0);
                 for (int i = tid; i < N; i += NT) {
                     const double jt = fc[3 * (i + 2)] + fc[3 * (i + 1) + 1] + fc[3 * i + 2];
                     lamo[i + 2] += leff[i + 2] + rr.dt * rr.G1a * jt;
                 }
                 tm.sync();   // lamo complete before it becomes lam; fc, leff free again
-                ldt += rr.G1a * P1 + rr.Ba * P0 * g.inv_d1;
-                double lG1 = rr.dt * P1;
-                const double lB = rr.dt * P0 * g.inv_d1;
-                double ltp;
-                if (!rr.clipped) {
-                    ltp = ltn;
-                    ldt += ltn;
-                    // dt = cfl / (G1 / dL): d dt / d G1 = -cfl dL / G1^2 = -dt^2 / (cfl dL)
-                    lG1 += -(rr.dt * rr.dt * inv_cfl) * ldt * g.inv_d1;
-                } else {
-                    ltp = -ldt;
+                if (chain) {
+                    ldt += rr.G1a * P1 + rr.Ba * P0 * g.inv_d1;
+                    double lG1 = rr.dt * P1;
+                    const double lB = rr.dt * P0 * g.inv_d1;
+                    double ltp;
+                    if (!rr.clipped) {
+                        ltp = ltn;
+                        ldt += ltn;
+                        // dt = cfl / (G1 / dL): d dt / d G1 = -cfl dL / G1^2 = -dt^2 / (cfl dL)
+                        lG1 += -(rr.dt * rr.dt * inv_cfl) * ldt * g.inv_d1;
+                    } else {
+                        ltp = -ldt;
+                    }
+                    kin_backward(Kn, ik, rr.C, rr.t, rr.G1a, 0.0, rr.Ba, rr.La, 0.0, 0.0, lG1, 0.0, lB, &lCprev,
+                                 &ltp, lth);
+                    lC = lCprev;
+                    lt = ltp;
+                    pc[0] = pc[1] = pc[2] = 0.0;
+                    pc[3] = lV0;
                 }
-                kin_backward(Kn, ik, rr.C, rr.t, rr.G1a, 0.0, rr.Ba, rr.La, 0.0, 0.0, lG1, 0.0, lB, &lCprev, &ltp,
-                             lth);
-                lC = lCprev;
-                lt = ltp;
-                pc[0] = pc[1] = pc[2] = 0.0;
-                pc[3] = lV0;
                 double* tmp = lam;
                 lam = lamo;
                 lamo = tmp;
             }
         }
-        if (row0) {
-            for (int k = 0; k < 4; ++k) pc[k] += sd[1 + k];
-            lC += sd[5];
+        if (chain) {
+            if (row0) {
+                for (int k = 0; k < 4; ++k) pc[k] += sd[1 + k];
+                lC += sd[5];
+            }
+            if (tid == 0)
+                for (int k = 0; k < 4; ++k) pcs[k] = pc[k];
         }
+        tm.sync();
         if (dn0_out) {
             for (int i = tid; i < N; i += NT) {
                 const double x = (i + 0.5) * d1;
-                dn0_out[off + i] = lam[i + 2] + (pc[0] + x * (pc[1] + x * (pc[2] + x * pc[3]))) * d1;
+                dn0_out[off + i] = lam[i + 2] + (pcs[0] + x * (pcs[1] + x * (pcs[2] + x * pcs[3]))) * d1;
             }
         }
         if (tid == 0) {
@@ -478,8 +517,8 @@ extern "C" pbe_status pbe_batch_vjp(pbe_batch* b, const double* t_out, int n_out
     BATRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     if (count < 1) goto out;
     // warps per instance (measured on the 500-cell gradient workload: teams of
-    // 4 while there are at most 4 instances per SM, else of 2)
-    if (W == 0) W = (long long)count <= 4LL * sms ? 4 : 2;
+    // 4 while there are at most 8 instances per SM, else of 2)
+    if (W == 0) W = (long long)count <= 8LL * sms ? 4 : 2;
     smem = (size_t)10 * npa * sizeof(double);
     if (smem + 2 * 8 * sizeof(double) + 64 > (size_t)maxsm) {
         rc = bafail(PBE_EINVAL, "instances too large for the batched adjoint");

@@ -20,7 +20,9 @@ import time
 import numpy as np
 
 
-def main(argv=None):
+def main(argv=None, emit=True):
+    """Train and report; progress lines go to stderr, the result (a dict) is
+    returned and, with emit, printed to stdout as one JSON line."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=1024)
     ap.add_argument("--heldout", type=int, default=256)
@@ -67,7 +69,7 @@ def main(argv=None):
                 break
         history.append(float(np.mean(losses)))
         print(f"epoch {ep}: mean loss {history[-1]:.4e} ({steps} Adam steps, {time.perf_counter() - t_train:.1f} s)",
-              flush=True)
+              file=sys.stderr, flush=True)
         if time.perf_counter() - t_train > args.max_seconds:
             break
     t_train = time.perf_counter() - t_train
@@ -86,7 +88,8 @@ def main(argv=None):
                                      "plain_misspecified_median": float(np.median(e_plain))},
            "gain": float(e_plain.mean() / e_closure.mean()), "total_seconds": time.perf_counter() - t0}
     tr.close()
-    print(json.dumps(res), flush=True)
+    if emit:
+        print(json.dumps(res), flush=True)
     if args.out:
         with open(args.out, "w") as f:
             json.dump(res, f, indent=1)
