@@ -77,10 +77,13 @@ __device__ __forceinline__ double allsum2_split(double a, double b)
 // row's faces (hnext, from shared memory), the update with the flux of the
 // lane to the right (shuffle), and the row's moment weights (without the
 // factor dL, applied to the segment sums) added to m.  src_row: the row may
-// hold cell 0, which receives the nucleation source.
+// hold cell 0, which receives the nucleation source.  A face's upwind
+// difference n_{f-1} - n_{f-2} is the downwind difference of the face one
+// lane to the left (lane 0: of lane 31 one row up, carried in b31), so each
+// face computes one difference (the same value face_value forms).
 template <int STAGE>
 __device__ __forceinline__ void stage_row(const double* in, const double* old, double* out, int N, int i, double c1,
-                                          double src, bool src_row, bool moms, double& hcur, double x,
+                                          double src, bool src_row, bool moms, double& hcur, double& b31, double x,
                                           double (&m)[4])
 {
     const int lane = threadIdx.x & 31;
@@ -89,7 +92,11 @@ __device__ __forceinline__ void stage_row(const double* in, const double* old, d
         v = in[i + 2];
     } else {
         const int fn = i + 32;
-        const double hnext = face_value<true>(in[fn], in[fn + 1], in[fn + 2]);
+        const double up = in[fn + 1], bq = in[fn + 2] - up;
+        const double au = __shfl_up_sync(0xffffffffu, bq, 1);
+        const double aq = lane == 0 ? b31 : au;
+        b31 = __shfl_sync(0xffffffffu, bq, 31);
+        const double hnext = fma(aq, psi_quot_fast(aq, bq), up);
         const double a = __shfl_down_sync(0xffffffffu, hcur, 1);
         const double b = __shfl_sync(0xffffffffu, hnext, 0);
         const double hright = lane == 31 ? b : a;
@@ -116,7 +123,7 @@ __device__ __forceinline__ void stage_row(const double* in, const double* old, d
 template <int STAGE>
 __device__ __forceinline__ void stage_segment(const double* in, const double* old, double* out, int N, int r0, int nr,
                                               double c1, double src, double d1, bool moms, double& hcur,
-                                              double (&m)[4])
+                                              double& b31, double (&m)[4])
 {
     const int lane = threadIdx.x & 31;
     const double dx32 = 32.0 * d1;
@@ -126,12 +133,12 @@ __device__ __forceinline__ void stage_segment(const double* in, const double* ol
     if (nr == kSegRows) {
 #pragma unroll
         for (int j = 0; j < kSegRows; ++j) {
-            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, x, m);
+            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, b31, x, m);
             x += dx32;
         }
     } else {
         for (int j = 0; j < nr; ++j) {
-            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, x, m);
+            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, b31, x, m);
             x += dx32;
         }
     }
@@ -152,15 +159,18 @@ __device__ __forceinline__ void warp_stage(const double* in, const double* old, 
     if (p0 >= p1) return;
     // face f lies between cells f-1 (upwind) and f: (n_{f-2}, n_{f-1}, n_f) = in[f], in[f+1], in[f+2]
     const int f0 = 32 * p0 * kSegRows + lane;
-    double hcur = 0.0;
-    if (STAGE != 0) hcur = face_value<true>(in[f0], in[f0 + 1], in[f0 + 2]);
+    double hcur = 0.0, b31 = 0.0;
+    if (STAGE != 0) {
+        hcur = face_value<true>(in[f0], in[f0 + 1], in[f0 + 2]);
+        b31 = __shfl_sync(0xffffffffu, in[f0 + 2] - in[f0 + 1], 31);
+    }
     double m[4];
     if (moms) {
         // lane group k = lane / 8 carries moment k
         double acc = 0.0;
         for (int p = p0; p < p1; ++p) {
             const int r0 = p * kSegRows;
-            stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, true, hcur, m);
+            stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, true, hcur, b31, m);
             const double v = allsum4_split(m) * d1;
             if (seg) {
                 if ((lane & 7) == 0) seg[4 * p + (lane >> 3)] = v;
@@ -178,12 +188,12 @@ __device__ __forceinline__ void warp_stage(const double* in, const double* old, 
     double acc = 0.0;
     for (int p = p0; p < p1; p += 2) {
         const int r0 = p * kSegRows;
-        stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, false, hcur, m);
+        stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, false, hcur, b31, m);
         const double a = m[3];
         double b = 0.0;
         if (p + 1 < p1) {
             stage_segment<STAGE>(in, old, out, N, r0 + kSegRows, min(kSegRows, R - r0 - kSegRows), c1, src, d1,
-                                 false, hcur, m);
+                                 false, hcur, b31, m);
             b = m[3];
         }
         const double v = allsum2_split(a, b);
