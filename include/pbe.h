@@ -399,6 +399,15 @@ pbe_status pbe_set_window(pbe_grid* g, int mode);
  * wait that does not complete at once run out (used to exercise that path). */
 pbe_status pbe_set_wait_limit(pbe_grid* g, double seconds);
 
+/* Most thread blocks the fused path's persistent launches of this grid may
+ * use (the solve and the gradient; 0, the default: one per SM).  Grids
+ * solved side by side on several streams (a minibatch of trajectories) can
+ * then run at the same time: a cooperative launch starts only when all its
+ * blocks fit.  The tiles are chosen again (several a block where needed);
+ * results agree to rounding.  Synchronizes the grid's stream when the
+ * limit changes.  PBE_EINVAL for a negative count. */
+pbe_status pbe_set_block_limit(pbe_grid* g, int blocks);
+
 /* Device timing of pbe_solve.  With `enable` != 0 every later pbe_solve
  * records two CUDA events on the grid's stream around the launch that
  * advances the state (the fused path's persistent kernel; the plain path's

@@ -121,6 +121,10 @@ class Grid:
     def set_wait_limit(self, seconds: float):
         _lib.check(self.lib.pbe_set_wait_limit(self.h, float(seconds)))
 
+    def set_block_limit(self, blocks: int):
+        """Most blocks of the fused path's persistent launches (0: one per SM)."""
+        _lib.check(self.lib.pbe_set_block_limit(self.h, int(blocks)))
+
     def set_max_steps(self, n: int):
         _lib.check(self.lib.pbe_set_max_steps(self.h, int(n)))
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "pbe_closure_grad": [ctypes.POINTER(_P), _I, _PD],
     "pbe_growth_poly_grad": [_P, _PD, _I],
     "pbe_set_wait_limit": [_P, _D],
+    "pbe_set_block_limit": [_P, _I],
     "pbe_set_window": [_P, _I],
     "pbe_set_timing": [_P, _I],
     "pbe_kernel_time": [_P, _PD],

@@ -38,9 +38,11 @@ def relative_loss_and_seeds(rows, target, cols):
 
 
 class _Worker:
-    def __init__(self, problem, path="plain"):
+    def __init__(self, problem, path="plain", block_limit=0):
         self.stream = torch.cuda.Stream()
         self.grid = Grid.from_problem(problem, stream=self.stream, path=path)
+        if block_limit:
+            self.grid.set_block_limit(block_limit)
 
     def grad_rows(self, inst, target, weights, cols, checkpoint_every=64):
         """Loss of one trajectory and its adjoint (fused path): the closure
@@ -83,8 +85,14 @@ class _Worker:
 class ClosureTrainer:
     """Adam on the closure weights through the solver's adjoint."""
 
-    def __init__(self, w0, problem_like, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, workers=8):
+    def __init__(self, w0, problem_like, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, workers=8, grid_blocks=None):
+        """grid_blocks: the block limit of each trajectory's grid (default: the
+        SMs shared by the `workers` concurrent trajectories, so that their
+        cooperative launches run side by side; 0 = one block per SM)."""
         self.lib = _lib.load()
+        if grid_blocks is None:
+            grid_blocks = max(8, torch.cuda.get_device_properties(0).multi_processor_count // workers)
+        self.grid_blocks = grid_blocks
         self.w = torch.as_tensor(np.asarray(w0, dtype=np.float64)).cuda()
         self.m = torch.zeros_like(self.w)
         self.v = torch.zeros_like(self.w)
@@ -100,7 +108,7 @@ class ClosureTrainer:
     def _worker(self):
         w = getattr(self._local, "w", None)
         if w is None:
-            w = _Worker(self._problem, path="fused")
+            w = _Worker(self._problem, path="fused", block_limit=self.grid_blocks)
             self._local.w = w
             with self._lock:
                 self.workers.append(w)
@@ -117,7 +125,7 @@ class ClosureTrainer:
         cols = loss_cols(insts[0].problem.ndim)
         n = len(insts)
         while len(self.slots) < n:
-            self.slots.append(_Worker(self._problem, path="fused"))
+            self.slots.append(_Worker(self._problem, path="fused", block_limit=self.grid_blocks))
         Ls = list(self.pool.map(lambda i: self.slots[i].grad_rows(insts[i], targets[i], w32, cols), range(n)))
         g = closure_grad([sl.grid for sl in self.slots[:n]]) / n
         return float(np.mean(Ls)), g

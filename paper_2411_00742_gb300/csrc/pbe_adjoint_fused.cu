@@ -1147,9 +1147,11 @@ cudaError_t adjoint_config(pbe_grid* g, AdjWork* w)
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int cap = std::min(g->sms * occ, g->max_blocks / 2);
     cap = std::min(cap, 1000);   // the arrival count of barrier_sum has 10 bits
+    if (g->block_limit > 0) cap = std::min(cap, g->block_limit);
     if (g->geo.ndim == 1) {
-        // tiles of a multiple of 32 cells, at least kPT1Min, that give every SM at most one when the grid allows
-        const int per = (g->geo.N1 + g->sms - 1) / g->sms;
+        // tiles of a multiple of 32 cells, at least kPT1Min, that give every block at most one when the grid allows
+        const int nb = std::min(g->sms, cap);
+        const int per = (g->geo.N1 + nb - 1) / nb;
         w->t1 = std::min(kPT1, std::max(kPT1Min, (per + 31) / 32 * 32));
         w->tiles_x = 1;
         w->ti = 1;

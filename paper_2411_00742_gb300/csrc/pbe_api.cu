@@ -323,6 +323,20 @@ pbe_status pbe_set_window(pbe_grid* g, int mode)
     return PBE_OK;
 }
 
+pbe_status pbe_set_block_limit(pbe_grid* g, int blocks)
+{
+    if (!g) return fail(PBE_EINVAL, "null grid");
+    if (blocks < 0) return fail(PBE_EINVAL, "block limit must be >= 0 (got %d)", blocks);
+    if (blocks != g->block_limit) {
+        // the launch shapes are chosen again (the adjoint's buffers with them)
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        g->fused_fn = nullptr;
+        pbe::adjoint_work_free(g);
+        g->block_limit = blocks;
+    }
+    return PBE_OK;
+}
+
 pbe_status pbe_set_wait_limit(pbe_grid* g, double seconds)
 {
     if (!g) return fail(PBE_EINVAL, "null grid");

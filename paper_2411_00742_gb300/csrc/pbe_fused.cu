@@ -626,9 +626,13 @@ static cudaError_t fused_config(pbe_grid* g)
 {
     if (g->fused_fn) return cudaSuccess;
     const int sms = g->sms;
+    // blocks the launch may use: one per SM, at most max_blocks / 2 (the row
+    // partials' store) and the grid's block limit
+    int lim = std::min(sms, g->max_blocks / 2);
+    if (g->block_limit > 0) lim = std::min(lim, g->block_limit);
     int tiles_x, ti;
     bool tall;
-    int ntiles = fused_tiles(g->geo, std::min(sms, g->max_blocks / 2), &tiles_x, &ti, &tall);
+    int ntiles = fused_tiles(g->geo, lim, &tiles_x, &ti, &tall);
     const void* fn_multi = g->geo.ndim == 1 ? (const void*)k_fused<1, false, kFTI> : (const void*)k_fused<2, false, kFTI>;
     const void* fn_one = g->geo.ndim == 1 ? (const void*)k_fused<1, true, kFTI>
                                           : (tall ? (const void*)k_fused<2, true, kFTIBig> : (const void*)k_fused<2, true, kFTI>);
@@ -642,6 +646,7 @@ static cudaError_t fused_config(pbe_grid* g)
     int G = ntiles;
     if (G > occ * sms) G = occ * sms;
     if (2 * G > g->max_blocks) G = g->max_blocks / 2;
+    if (g->block_limit > 0 && G > g->block_limit) G = g->block_limit;
     if (G < 1) G = 1;
     if (G > 1000) G = 1000;   // the arrival count of barrier_sum has 10 bits
     const void* fn = fn_one;
@@ -650,7 +655,8 @@ static cudaError_t fused_config(pbe_grid* g)
         // more tiles than co-resident blocks on a large 2-D grid: the persistent
         // window kernel (no halo faces recomputed per 16 x 32 tile)
         FusedWinCfg c;
-        e = fused_window_config(g->geo, sms, g->max_blocks / 2, &c);
+        e = fused_window_config(g->geo, sms, g->block_limit > 0 ? std::min(g->max_blocks / 2, g->block_limit)
+                                                                : g->max_blocks / 2, &c);
         if (e != cudaSuccess) return e;
         g->fused_blocks = c.G;
         g->fused_ntiles = c.ntiles;
@@ -672,6 +678,7 @@ static cudaError_t fused_config(pbe_grid* g)
         if (e != cudaSuccess) return e;
         G = std::min(ntiles, occ2 * sms);
         if (2 * G > g->max_blocks) G = g->max_blocks / 2;
+        if (g->block_limit > 0 && G > g->block_limit) G = g->block_limit;
         if (G < 1) G = 1;
         if (G > 1000) G = 1000;
     }

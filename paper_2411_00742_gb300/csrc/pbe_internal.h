@@ -28,6 +28,7 @@ struct pbe_grid {
     int max_blocks;
     int sms;            // multiprocessors of the grid's device
     int window_mode;    // 2-D plain stages in the register-window kernel: -1 auto, 0 never, 1 always
+    int block_limit;    // most blocks of the fused path's persistent launches (0: no limit)
     // fused path launch configuration, fixed per grid (computed at the first fused solve)
     const void* fused_fn;
     int fused_blocks, fused_ntiles, fused_tiles_x, fused_ti;

@@ -31,6 +31,8 @@ def main(argv=None, emit=True):
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--grid-blocks", type=int, default=None,
+                    help="block limit of each trajectory's grid (default: SMs / workers; 0: one block per SM)")
     ap.add_argument("--max-seconds", type=float, default=1e9)
     ap.add_argument("--out", default=None)
     ap.add_argument("--weights-out", default=None)
@@ -46,7 +48,8 @@ def main(argv=None, emit=True):
     t0 = time.perf_counter()
     train = cd.trajectories(args.train, seed=24130, N=args.grid)
     held = cd.trajectories(args.heldout, seed=24131, N=args.grid)
-    tr = ClosureTrainer(cd.initial_weights(), train[0].problem, lr=args.lr, workers=args.workers)
+    tr = ClosureTrainer(cd.initial_weights(), train[0].problem, lr=args.lr, workers=args.workers,
+                        grid_blocks=args.grid_blocks)
     # truth: the FP64 solver with the hidden law
     t_truth = time.perf_counter()
     y_train = tr.rows(train)

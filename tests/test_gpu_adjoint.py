@@ -96,6 +96,30 @@ def test_vjp_checkpoint_interval_does_not_change_result(path):
     assert np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("case,blocks", [("2d_128", 19), ("1d", 2)])
+def test_fused_vjp_with_block_limit_matches_cpu_adjoint(case, blocks):
+    """The persistent adjoint on a limited number of blocks (several tiles a
+    block), as the closure trainer runs its concurrent trajectories."""
+    import torch
+    import paper_2411_00742_gb300 as P
+    inst = _problem(case)
+    p, tgt, cols = _setup(inst)
+    r = oracle.solve(p, inst.n0, inst.C0, 0.0, inst.t_out)["rows"]
+    seeds = oracle.relative_loss_seeds(r, tgt, cols)
+    want, want_dn0, want_dC0 = oracle.vjp(p, inst.n0, inst.C0, 0.0, inst.t_out, seeds)
+    g = P.Grid.from_problem(p, path="fused")
+    g.set_block_limit(blocks)
+    g.set_state(np.ascontiguousarray(inst.n0), inst.C0, 0.0)
+    dn0 = torch.zeros(p.ncells, dtype=torch.float64, device="cuda")
+    dth, _, dC0 = g.vjp(inst.t_out, seeds, 64, dn0_out=dn0)
+    g.close()
+    for j in range(6):
+        assert dth[j] == pytest.approx(want[j], rel=REL_GRAD, abs=1e-300), (j, dth, want)
+    assert dC0 == pytest.approx(want_dC0, rel=REL_GRAD)
+    supp = inst.n0 > 1e-3 * inst.n0.max()
+    assert np.max(np.abs(dn0.cpu().numpy() - want_dn0)[supp]) <= REL_GRAD * np.max(np.abs(want_dn0))
+
+
 def test_fused_vjp_grows_its_checkpoint_store_and_repeats_bitwise():
     """Two output times, the second reached by CFL-limited steps, and a
     checkpoint every step: the persistent adjoint's first checkpoint store

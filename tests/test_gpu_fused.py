@@ -59,6 +59,27 @@ def test_fused_window_kernel_matches_tile_loop_closely():
     assert np.array_equal(b["rows"], c["rows"]) and np.array_equal(b["n"], c["n"])
 
 
+@pytest.mark.parametrize("blocks", [8, 19])
+def test_fused_block_limit(blocks):
+    """A block limit (grids solved side by side): the one-tile launch takes
+    taller tiles, or blocks loop over several; parity with the oracle and
+    with the unlimited launch."""
+    import paper_2411_00742_gb300 as P
+    inst = pi.config_2d(128)
+    ref = gpu_solve(inst, path="fused")
+    g = P.Grid.from_problem(inst.problem, path="fused")
+    g.set_block_limit(blocks)
+    g.set_state(np.ascontiguousarray(inst.n0), inst.C0, inst.t0)
+    rows, steps = g.solve(inst.t_out)
+    n, C, _ = g.get_state()
+    g.close()
+    assert steps == ref["steps"]
+    np.testing.assert_allclose(rows, ref["rows"], rtol=1e-12)
+    want = oracle.solve_instance(inst)
+    assert_rows_close(rows, want["rows"])
+    assert_n_close(n, want["n"])
+
+
 def test_fused_state_at_every_output_time():
     import paper_2411_00742_gb300 as P
     inst = pi.config_2d(48, 40)
