@@ -817,6 +817,7 @@ def profile_case(argv):
     ap.add_argument("--autotune", action="store_true", help="batch: autotune the schedule first")
     ap.add_argument("--vjp-warps", type=int, default=0, help="batch-adjoint: warps per instance (0: automatic)")
     ap.add_argument("--vjp-blocks", type=int, default=0, help="batch-adjoint: teams per SM (0: automatic)")
+    ap.add_argument("--block-limit", type=int, default=0, help="fused/adjoint: most blocks of the launch (0: none)")
     ap.add_argument("--schedule", type=int, nargs=3, metavar=("WPB", "TEAM", "CELLS"),
                     help="batch: set this schedule (warps per block, team instances, warp cells)")
     a = ap.parse_args(argv)
@@ -875,6 +876,7 @@ def profile_case(argv):
             inst = pi.config_2d(a.N1, a.N2)
             inst.t_out = pi.loss_times()
         g = P.Grid.from_problem(inst.problem, path="fused")
+        g.set_block_limit(a.block_limit)
         g.set_state(inst.n0, inst.C0, 0.0)
         rows, _ = g.solve(inst.t_out)
         seeds = np.zeros_like(rows)
@@ -895,6 +897,7 @@ def profile_case(argv):
     t_out = inst.t_out[: a.outputs] if a.outputs > 0 else inst.t_out
     g = P.Grid.from_problem(inst.problem, path=path)
     g.set_window(a.window)
+    g.set_block_limit(a.block_limit)
     n0 = torch.as_tensor(inst.n0).cuda()
     if a.steps > 0:
         g.set_state(n0, inst.C0, 0.0)
