@@ -345,6 +345,17 @@ pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps);
 pbe_status pbe_batch_set_schedule(pbe_batch* b, int warps_per_block, int team_instances, int warp_cells);
 pbe_status pbe_batch_get_schedule(pbe_batch* b, int* warps_per_block, int* team_instances, int* warp_cells);
 
+/* The learned closure of the batch's PBE_KINETICS_MLP instances (the
+ * weights and box as pbe_set_closure / pbe_set_closure_box; one copy on the
+ * device for the whole batch; such instances need growth_form 0, whose power
+ * law is the closure's fallback).  The batch kernel then sums mu0 at every
+ * stage for the closure's input ratio V / mu0.  pbe_batch_solve and
+ * pbe_batch_autotune fail with PBE_ESTATE while a batch with closure
+ * instances has no weights; the batched adjoint differentiates the power law
+ * only (PBE_EINVAL for closure instances).  Synchronizes. */
+pbe_status pbe_batch_set_closure(pbe_batch* b, const float* weights, int count);
+pbe_status pbe_batch_set_closure_box(pbe_batch* b, const double* lo, const double* hi);
+
 /* pbe_batch_set_schedule(b, warps_per_block, 0, 6144): one instance per warp. */
 pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block);
 

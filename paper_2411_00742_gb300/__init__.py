@@ -278,7 +278,10 @@ class Batch:
     """Many independent 1-D instances solved by one persistent launch
     (thin wrapper over pbe_batch)."""
 
-    def __init__(self, problems, C0, t0=None, stream=None):
+    def __init__(self, problems, C0, t0=None, stream=None, closure=False):
+        """closure: the instances' rates come from the learned closure (set its
+        weights with set_closure before solving; the power law of each problem
+        is the fallback)."""
         self.lib = _lib.load()
         n = len(problems)
         arr = (_lib.Instance * n)()
@@ -287,7 +290,7 @@ class Batch:
                 raise ValueError("batched solves are 1-D")
             arr[i].ncells = int(p.ncells[0])
             arr[i].lmax = float(p.lmax[0])
-            arr[i].kin = kinetics_struct(p)
+            arr[i].kin = kinetics_struct(p, closure=closure)
             arr[i].C0 = float(C0[i])
             arr[i].t0 = 0.0 if t0 is None else float(t0[i])
         h = ctypes.c_void_p()
@@ -362,6 +365,23 @@ class Batch:
 
     def set_config(self, warps_per_block: int):
         _lib.check(self.lib.pbe_batch_set_config(self.h, int(warps_per_block)))
+
+    def set_closure(self, weights):
+        """Weights of the learned closure for the batch's closure instances
+        (flat float32, the layout of Grid.set_closure)."""
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        if w.size != CLOSURE_SIZE:
+            raise ValueError(f"the closure has {CLOSURE_SIZE} weights")
+        _lib.check(self.lib.pbe_batch_set_closure(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size))
+
+    def set_closure_box(self, lo=None, hi=None):
+        """Training box of the closure's inputs (None: no box), as Grid.set_closure_box."""
+        if lo is None or hi is None:
+            _lib.check(self.lib.pbe_batch_set_closure_box(self.h, None, None))
+            return
+        lo = (ctypes.c_double * 3)(*[float(v) for v in lo])
+        hi = (ctypes.c_double * 3)(*[float(v) for v in hi])
+        _lib.check(self.lib.pbe_batch_set_closure_box(self.h, lo, hi))
 
     def set_schedule(self, warps_per_block: int, team_instances: int, warp_cells: int = 6144):
         """Warps per block, the number of costliest instances solved by a whole

@@ -79,6 +79,8 @@ SIGNATURES = {
     "pbe_batch_solve": [_P, _PD, _I, _P, _I, _PI64],
     "pbe_batch_set_config": [_P, _I],
     "pbe_batch_set_schedule": [_P, _I, _I, _I],
+    "pbe_batch_set_closure": [_P, ctypes.POINTER(ctypes.c_float), _I],
+    "pbe_batch_set_closure_box": [_P, _P, _P],
     "pbe_batch_set_vjp_schedule": [_P, _I, _I],
     "pbe_batch_get_schedule": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "pbe_batch_vjp": [_P, _PD, _I, _P, _I, _I, _PD, _PD, _P, _I],

@@ -212,6 +212,28 @@ pbe_status pbe::check_kinetic_values(const pbe_kinetics* k)
     return PBE_OK;
 }
 
+namespace pbe {
+// The flat closure layout W1, b1, W2, b2, W3, b3 split into the bf16
+// matrices and fp32 biases the kernels read.
+void pack_closure(const float* w, std::vector<__nv_bfloat16>& hw, std::vector<float>& hb)
+{
+    const int H = kMlpH;
+    hw.assign(H * 3 + H * H + 3 * H, __float2bfloat16_rn(0.0f));
+    hb.assign(H + H + 3, 0.0f);
+    const float* W1 = w;
+    const float* b1 = W1 + H * 3;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + 3 * H;
+    for (int k = 0; k < H * 3; ++k) hw[k] = __float2bfloat16_rn(W1[k]);
+    for (int k = 0; k < H * H; ++k) hw[H * 3 + k] = __float2bfloat16_rn(W2[k]);
+    for (int k = 0; k < 3 * H; ++k) hw[H * 3 + H * H + k] = __float2bfloat16_rn(W3[k]);
+    for (int k = 0; k < H; ++k) { hb[k] = b1[k]; hb[H + k] = b2[k]; }
+    for (int k = 0; k < 3; ++k) hb[2 * H + k] = b3[k];
+}
+}  // namespace pbe
+
 extern "C" {
 
 const char* pbe_last_error(void) { return g_err; }
@@ -405,6 +427,7 @@ pbe_status pbe_set_kinetics(pbe_grid* g, const pbe_kinetics* k)
     return PBE_OK;
 }
 
+
 pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count)
 {
     if (!g || !w) return fail(PBE_EINVAL, "null argument");
@@ -412,21 +435,9 @@ pbe_status pbe_set_closure(pbe_grid* g, const float* w, int count)
     for (int k = 0; k < count; ++k)
         if (!std::isfinite(w[k])) return fail(PBE_EINVAL, "non-finite closure weight %d", k);
     DeviceGuard dg(g->device);
-    const int H = pbe::kMlpH;
-    // split the flat layout W1, b1, W2, b2, W3, b3 into bf16 matrices and fp32 biases
-    std::vector<__nv_bfloat16> hw(H * 3 + H * H + 3 * H);
-    std::vector<float> hb(H + H + 3);
-    const float* W1 = w;
-    const float* b1 = W1 + H * 3;
-    const float* W2 = b1 + H;
-    const float* b2 = W2 + H * H;
-    const float* W3 = b2 + H;
-    const float* b3 = W3 + 3 * H;
-    for (int k = 0; k < H * 3; ++k) hw[k] = __float2bfloat16_rn(W1[k]);
-    for (int k = 0; k < H * H; ++k) hw[H * 3 + k] = __float2bfloat16_rn(W2[k]);
-    for (int k = 0; k < 3 * H; ++k) hw[H * 3 + H * H + k] = __float2bfloat16_rn(W3[k]);
-    for (int k = 0; k < H; ++k) { hb[k] = b1[k]; hb[H + k] = b2[k]; }
-    for (int k = 0; k < 3; ++k) hb[2 * H + k] = b3[k];
+    std::vector<__nv_bfloat16> hw;
+    std::vector<float> hb;
+    pbe::pack_closure(w, hw, hb);
     if (!g->d_mW) {
         if (cudaMalloc(&g->d_mW, sizeof(__nv_bfloat16) * hw.size()) != cudaSuccess ||
             cudaMalloc(&g->d_mB, sizeof(float) * hb.size()) != cudaSuccess)

@@ -241,10 +241,21 @@ __device__ __forceinline__ void inst_stage(const double* in, const double* old, 
     par ^= 1;
 }
 
+// The rates of one instance at (C, t): the power law (or fixed rates), or,
+// in batches with the learned closure (MLP), the closure with its moment-
+// ratio input V / mu0 and its fallback to the power law.
+template <bool MLP>
+__device__ __forceinline__ void batch_rates(const Kin& K, double C, double t, double ratio, double& G1, double& B)
+{
+    double G2;
+    if constexpr (MLP) kinetics_warp_r(K, C, t, ratio, G1, G2, B);
+    else kinetics_warp<false>(K, C, t, G1, G2, B);
+}
+
 // One instance, solved by one warp (TEAM false) or by all WPB warps of the
 // block (TEAM true).  nb, n1b: the instance's state and stage buffers in
 // shared memory (cell i at index i + 2, two zero ghosts below).
-template <bool TEAM, int WPB>
+template <bool TEAM, int WPB, bool MLP>
 __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict__ inst, double* state, double* Cst,
                                              double* tst, const double* t_out, int n_out, double* rows,
                                              long long* steps_out, int* status_out, long long max_steps, double* nb,
@@ -274,6 +285,7 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
     double m[4];
     inst_stage<0, TEAM, WPB>(nb, nb, nb, N, R, 0.0, 0.0, g.d1, true, ts, par, m);
     s.V0 = m[3];
+    double M0 = m[0];   // mu0 of the current state (the closure's input ratio V / mu0)
     double* my_rows = rows + (size_t)id * n_out * 6;
     if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(s.C)) {
         s.status = PBE_ENONFINITE;
@@ -289,29 +301,30 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
         if (s.out_idx >= n_out) s.done = 1;
     }
     if (!s.done) {
-        double G1, G2, B, dt, t_new;
-        kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
-        s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
+        double G1, B, dt, t_new;
+        batch_rates<MLP>(K, s.C, s.t, MLP ? s.V0 / M0 : 0.0, G1, B);
+        s.clipped = timestep_fast(K, g, G1, 0.0, s.t, t_out[s.out_idx], dt, t_new);
         s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
         if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
     }
     while (!s.done) {
         // stage 1: n1 = n + dt L(n)
-        inst_stage<1, TEAM, WPB>(nb, nb, n1b, N, R, s.G1a * s.dt * g.inv_d1, s.dt * s.Ba * g.inv_d1, g.d1, false, ts,
+        inst_stage<1, TEAM, WPB>(nb, nb, n1b, N, R, s.G1a * s.dt * g.inv_d1, s.dt * s.Ba * g.inv_d1, g.d1, MLP, ts,
                                  par, m);
         const double V1 = m[3];
         const double C1 = fma(-K.kappa, V1 - s.V0, s.C);
         {
-            double G1, G2, B;
-            kinetics_warp<false>(K, C1, s.t_new, G1, G2, B);
+            double G1, B;
+            batch_rates<MLP>(K, C1, s.t_new, MLP ? V1 / m[0] : 0.0, G1, B);
             s.G1b = G1; s.Bb = B;
             if (!isfinite(V1) || !isfinite(G1) || !isfinite(B)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
         }
         // stage 2: n = n/2 + (n1 + dt L(n1))/2
         const bool moms = s.clipped;
-        inst_stage<2, TEAM, WPB>(n1b, nb, nb, N, R, s.G1b * s.dt * g.inv_d1, s.dt * s.Bb * g.inv_d1, g.d1, moms, ts,
-                                 par, m);
+        inst_stage<2, TEAM, WPB>(n1b, nb, nb, N, R, s.G1b * s.dt * g.inv_d1, s.dt * s.Bb * g.inv_d1, g.d1,
+                                 moms || MLP, ts, par, m);
         const double V2 = m[3];
+        if (MLP) M0 = m[0];
         s.C = fma(-K.kappa, V2 - s.V0, s.C);
         s.t = s.t_new;
         s.V0 = V2;
@@ -326,9 +339,9 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
         }
         if (s.out_idx >= n_out) { s.done = 1; break; }
         if (s.steps >= max_steps) { s.status = PBE_ETIMEOUT; s.done = 1; break; }
-        double G1, G2, B, dt, t_new;
-        kinetics_warp<false>(K, s.C, s.t, G1, G2, B);
-        s.clipped = timestep_fast(K, g, G1, G2, s.t, t_out[s.out_idx], dt, t_new);
+        double G1, B, dt, t_new;
+        batch_rates<MLP>(K, s.C, s.t, MLP ? s.V0 / M0 : 0.0, G1, B);
+        s.clipped = timestep_fast(K, g, G1, 0.0, s.t, t_out[s.out_idx], dt, t_new);
         s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
         if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }
     }
@@ -350,7 +363,7 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
 // per warp, from queue[1]).  np_slot: doubles per buffer of a warp's slice
 // (two buffers a warp); a team uses the block's whole allocation, nb at the
 // start and n1b half way.
-template <int WPB>
+template <int WPB, bool MLP>
 __global__ void __maxnreg__(168) k_batch1d(const BatchInst* __restrict__ inst, const int* __restrict__ order,
                                                       int count, int nteam, double* state, double* Cst, double* tst,
                                                       const double* t_out, int n_out, double* rows,
@@ -368,7 +381,7 @@ __global__ void __maxnreg__(168) k_batch1d(const BatchInst* __restrict__ inst, c
             const int idx = s_idx;
             __syncthreads();
             if (idx >= nteam) break;
-            run_instance<true, WPB>(order[idx], inst, state, Cst, tst, t_out, n_out, rows, steps_out, status_out,
+            run_instance<true, WPB, MLP>(order[idx], inst, state, Cst, tst, t_out, n_out, rows, steps_out, status_out,
                                     max_steps, smem, smem + (size_t)WPB * np_slot, &ts);
         }
     }
@@ -379,7 +392,7 @@ __global__ void __maxnreg__(168) k_batch1d(const BatchInst* __restrict__ inst, c
         if (lane == 0) idx = nteam + (int)atomicAdd(queue + 1, 1u);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= count) break;
-        run_instance<false, WPB>(order[idx], inst, state, Cst, tst, t_out, n_out, rows, steps_out, status_out,
+        run_instance<false, WPB, MLP>(order[idx], inst, state, Cst, tst, t_out, n_out, rows, steps_out, status_out,
                                  max_steps, nb, n1b, &ts);
     }
 }
@@ -410,6 +423,11 @@ struct pbe_batch {
     int vjp_warps;                    // warps per instance of pbe_batch_vjp (0: chosen from the batch size)
     int vjp_blocks;                   // resident teams per SM of pbe_batch_vjp (0: as many as fit)
     int power_law;                    // every instance has power-law kinetics and the polynomial solubility
+    int mlp;                          // some instance has the learned closure (the MLP kernel variant)
+    int closure_set;                  // its weights are on the device (pbe_batch_set_closure)
+    std::vector<BatchInst> h_inst;    // host copy of the instance descriptors
+    __nv_bfloat16* d_mW;              // the batch's closure weights (bf16 matrices, fp32 biases)
+    float* d_mB;
     void* vjp_work;                   // pbe_batch_vjp's device scratch (pbe_batch_adjoint.cu)
     long long max_steps;
     BatchInst* d_inst;
@@ -447,15 +465,15 @@ pbe_status bfail(pbe_status code, const char* fmt, ...)
         if (e_ != cudaSuccess) return bfail(PBE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-const void* batch_kernel(int wpb)
+const void* batch_kernel(int wpb, bool mlp = false)
 {
     switch (wpb) {
-        case 1: return (const void*)k_batch1d<1>;
-        case 2: return (const void*)k_batch1d<2>;
-        case 3: return (const void*)k_batch1d<3>;
-        case 4: return (const void*)k_batch1d<4>;
-        case 6: return (const void*)k_batch1d<6>;
-        case 8: return (const void*)k_batch1d<8>;
+        case 1: return mlp ? (const void*)k_batch1d<1, true> : (const void*)k_batch1d<1, false>;
+        case 2: return mlp ? (const void*)k_batch1d<2, true> : (const void*)k_batch1d<2, false>;
+        case 3: return mlp ? (const void*)k_batch1d<3, true> : (const void*)k_batch1d<3, false>;
+        case 4: return mlp ? (const void*)k_batch1d<4, true> : (const void*)k_batch1d<4, false>;
+        case 6: return mlp ? (const void*)k_batch1d<6, true> : (const void*)k_batch1d<6, false>;
+        case 8: return mlp ? (const void*)k_batch1d<8, true> : (const void*)k_batch1d<8, false>;
         default: return nullptr;
     }
 }
@@ -518,7 +536,7 @@ cudaError_t upload_order(pbe_batch* b, int nteam, int wcells)
 // Launch of one batch solve under a schedule (the order must be uploaded).
 cudaError_t launch_batch(pbe_batch* b, int wpb, int nteam, int wcells, int n_out, cudaStream_t st)
 {
-    const void* fn = batch_kernel(wpb);
+    const void* fn = batch_kernel(wpb, b->mlp != 0);
     size_t smem = batch_smem(b, wpb, nteam, wcells);
     int np_slot = batch_np_slot(b, wpb, nteam, wcells);
     int teams = team_split(b, nteam, wcells).teams;
@@ -555,7 +573,7 @@ bool schedule_fits(const pbe_batch* b, int wpb, int nteam, int wcells)
 // Blocks per SM that a schedule's shared memory (and the registers) allow.
 int blocks_per_sm(const pbe_batch* b, int wpb, int nteam, int wcells)
 {
-    const void* fn = batch_kernel(wpb);
+    const void* fn = batch_kernel(wpb, b->mlp != 0);
     int occ = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_block_smem(b)) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, wpb * 32, batch_smem(b, wpb, nteam, wcells)) !=
@@ -677,10 +695,11 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         }
         if (!(p.lmax > 0.0) || !std::isfinite(p.lmax) || !std::isfinite(p.C0) || !std::isfinite(p.t0) ||
             !(k->cfl > 0.0 && k->cfl <= 1.0) || !(k->t_cool > 0.0) ||
-            (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED) || k->kg[0] < 0 || k->kb < 0 ||
-            k->scheme != PBE_SCHEME_SSPRK2 || (k->growth_form != 0 && k->growth_form != 1) ||
-            (k->solubility_form != 0 && k->solubility_form != 1)) {
-            // (the learned closure runs on the single-grid plain path only)
+            (k->kind != PBE_KINETICS_POWER_LAW && k->kind != PBE_KINETICS_FIXED && k->kind != PBE_KINETICS_MLP) ||
+            k->kg[0] < 0 || k->kb < 0 || k->scheme != PBE_SCHEME_SSPRK2 ||
+            (k->growth_form != 0 && k->growth_form != 1) || (k->solubility_form != 0 && k->solubility_form != 1) ||
+            (k->kind == PBE_KINETICS_MLP && k->growth_form != 0)) {
+            // (the learned closure falls back to the power law: growth_form 0)
             delete b;
             return bfail(PBE_EINVAL, "instance %d: invalid parameters", i);
         }
@@ -697,7 +716,8 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
         d.K.lkg1 = std::log(k->kg[0]); d.K.lkg2 = -INFINITY; d.K.lkb = std::log(k->kb);
         d.K.inv_tcool = 1.0 / k->t_cool;
         d.K.growth_form = k->growth_form;
-        power_law = power_law && k->growth_form == 0 && k->solubility_form == 0;
+        power_law = power_law && k->growth_form == 0 && k->solubility_form == 0 && k->kind != PBE_KINETICS_MLP;
+        if (k->kind == PBE_KINETICS_MLP) b->mlp = 1;
         d.K.solubility_form = k->solubility_form;
         d.K.ea1 = k->ea[0];
         d.g.ndim = 1; d.g.N1 = (int)p.ncells; d.g.N2 = 1; d.g.d1 = p.lmax / (double)p.ncells; d.g.d2 = 1.0;
@@ -722,6 +742,7 @@ pbe_status pbe_batch_create(pbe_batch** out, const pbe_instance* inst, int count
     b->max_steps = 1000000;
     b->cost = cost;
     b->nmax = nmax;
+    b->h_inst = h;
     b->ncells.resize(count);
     for (int i = 0; i < count; ++i) b->ncells[i] = h[i].g.N1;
     b->by_cost.resize(count);
@@ -786,6 +807,7 @@ pbe_status pbe_batch_destroy(pbe_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     pbe_batch_internal_free_vjp_work(b->vjp_work);
+    cudaFree(b->d_mW); cudaFree(b->d_mB);
     cudaFree(b->d_inst); cudaFree(b->d_order); cudaFree(b->d_state); cudaFree(b->d_C); cudaFree(b->d_t);
     cudaFree(b->d_steps); cudaFree(b->d_status); cudaFree(b->d_queue); cudaFree(b->d_tout); cudaFree(b->d_rows);
     cudaFreeHost(b->h_steps); cudaFreeHost(b->h_status);
@@ -870,6 +892,61 @@ pbe_status pbe_batch_steps(pbe_batch* b, int64_t* steps)
     return PBE_OK;
 }
 
+// The descriptors of the closure instances point at the batch's weights and box.
+static pbe_status upload_inst(pbe_batch* b)
+{
+    BTRY(cudaStreamSynchronize(b->stream));
+    BTRY(cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice));
+    return PBE_OK;
+}
+
+pbe_status pbe_batch_set_closure(pbe_batch* b, const float* w, int count)
+{
+    if (!b || !w) return bfail(PBE_EINVAL, "null argument");
+    if (count != kMlpNW) return bfail(PBE_EINVAL, "the closure has %d weights (got %d)", kMlpNW, count);
+    for (int k = 0; k < count; ++k)
+        if (!std::isfinite(w[k])) return bfail(PBE_EINVAL, "non-finite closure weight %d", k);
+    std::vector<__nv_bfloat16> hw;
+    std::vector<float> hb;
+    pack_closure(w, hw, hb);
+    BTRY(cudaStreamSynchronize(b->stream));
+    if (!b->d_mW) {
+        if (cudaMalloc(&b->d_mW, sizeof(__nv_bfloat16) * hw.size()) != cudaSuccess ||
+            cudaMalloc(&b->d_mB, sizeof(float) * hb.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(PBE_ENOMEM, "allocating the closure weights failed");
+        }
+    }
+    BTRY(cudaMemcpy(b->d_mW, hw.data(), sizeof(__nv_bfloat16) * hw.size(), cudaMemcpyHostToDevice));
+    BTRY(cudaMemcpy(b->d_mB, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice));
+    for (BatchInst& d : b->h_inst) {
+        d.K.mW = b->d_mW;
+        d.K.mB = b->d_mB;
+    }
+    pbe_status st = upload_inst(b);
+    if (st) return st;
+    b->closure_set = 1;
+    return PBE_OK;
+}
+
+pbe_status pbe_batch_set_closure_box(pbe_batch* b, const double* lo, const double* hi)
+{
+    if (!b) return bfail(PBE_EINVAL, "null batch");
+    const bool box = lo && hi;   // either bound NULL: no box (as pbe_set_closure_box)
+    if (box)
+        for (int k = 0; k < 3; ++k)
+            if (std::isnan(lo[k]) || std::isnan(hi[k]) || !(lo[k] <= hi[k]))
+                return bfail(PBE_EINVAL, "closure box: lo[%d] <= hi[%d] required", k, k);
+    for (BatchInst& d : b->h_inst) {
+        d.K.mbox = box ? 1 : 0;
+        for (int k = 0; k < 3; ++k) {
+            d.K.mlo[k] = box ? lo[k] : 0.0;
+            d.K.mhi[k] = box ? hi[k] : 0.0;
+        }
+    }
+    return upload_inst(b);
+}
+
 pbe_status pbe_batch_set_schedule(pbe_batch* b, int warps_per_block, int team_instances, int warp_cells)
 {
     if (!b) return bfail(PBE_EINVAL, "null batch");
@@ -908,6 +985,8 @@ pbe_status pbe_batch_set_config(pbe_batch* b, int warps_per_block)
 pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double* rows, int mem, int64_t* total_steps)
 {
     if (!b || !rows) return bfail(PBE_EINVAL, "null argument");
+    if (b->mlp && !b->closure_set)
+        return bfail(PBE_ESTATE, "instances with the learned closure: set its weights first (pbe_batch_set_closure)");
     pbe_status st = check_times(b, t_out, n_out);
     if (st) return st;
     for (int i = 0; i < b->count; ++i)
@@ -925,6 +1004,8 @@ pbe_status pbe_batch_solve(pbe_batch* b, const double* t_out, int n_out, double*
 pbe_status pbe_batch_autotune(pbe_batch* b, const double* t_out, int n_out, int* chosen)
 {
     if (!b) return bfail(PBE_EINVAL, "null batch");
+    if (b->mlp && !b->closure_set)
+        return bfail(PBE_ESTATE, "instances with the learned closure: set its weights first (pbe_batch_set_closure)");
     pbe_status st = check_times(b, t_out, n_out);
     if (st) return st;
     st = ensure_tout(b, n_out);

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "pbe.h"
 #include "pbe_device.cuh"
 
@@ -109,6 +111,10 @@ int paper_blocks2d(const Geom& g);
 // Value checks of a pbe_kinetics shared by every entry point that takes one
 // (pbe_api.cu): PBE_OK, or PBE_EINVAL with the error message set.
 pbe_status check_kinetic_values(const pbe_kinetics* k);
+
+// The learned closure's flat weights (W1, b1, W2, b2, W3, b3; kMlpNW floats)
+// as the kernels store them: bf16 matrices and fp32 biases (pbe_api.cu).
+void pack_closure(const float* w, std::vector<__nv_bfloat16>& hw, std::vector<float>& hb);
 
 // Output times of a solve on the device (d_tout, capacity grown as needed;
 // the copy is skipped when they equal the last ones sent) (pbe_api.cu).
