@@ -489,19 +489,20 @@ __device__ __forceinline__ void kinetics_warp_r(const Kin& K, double C, double t
     }
 }
 
-// a / b for b > 0 (finite) by Newton-Raphson: the hardware reciprocal
-// approximation (relative error 2^-20) refined twice (error ~2^-80, below
-// the rounding), then one residual correction of the quotient
-// (q + r (a - b q)), which leaves it within an ulp of the rounded quotient;
-// 7 FP64 operations against the longer IEEE division sequence.
+// a / b for b > 0 (finite) by Newton-Raphson: from the hardware reciprocal
+// approximation y0 (relative error e = 1 - b y0 below 2^-20), the first-order
+// refinements of the reciprocal, y1 = y0 + y0 e, and of the quotient,
+// q1 = a y0 + (a y0) e, side by side (relative error ~e^2), then one residual
+// correction q1 + y1 (a - b q1) (error ~e^4, below the rounding), which leaves
+// the result within an ulp of the rounded quotient: four dependent FP64
+// operations after the approximation.
 __device__ __forceinline__ double div_newton(double a, double b)
 {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
-    r = fma(r, fma(-b, r, 1.0), r);
-    r = fma(r, fma(-b, r, 1.0), r);
-    const double q = a * r;
-    return fma(r, fma(-b, q, a), q);
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(b));
+    const double e = fma(-b, y0, 1.0), q0 = a * y0;
+    const double y1 = fma(y0, e, y0), q1 = fma(q0, e, q0);
+    return fma(y1, fma(-b, q1, a), q1);
 }
 
 __device__ __forceinline__ int timestep_fast(const Kin& K, const Geom& g, double G1, double G2, double t,

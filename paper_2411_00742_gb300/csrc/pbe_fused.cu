@@ -354,14 +354,25 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
     unsigned int gen = 0;
 
     // moment weights of this thread's cells (one tile per block: fixed for the
-    // whole solve).  Small tiles: all ten weights of each cell in registers;
-    // tall tiles (eight cells a thread, all in one column since tiles are 32
-    // wide): x1 and the volume weight of each cell, x2^q dA of the column.
-    constexpr bool WREG = ONE_TILE && TI <= kFTI;
-    constexpr bool WCOL = ONE_TILE && !WREG;
+    // whole solve).  1-D: the four weights of each cell in registers.  2-D
+    // tiles of up to kFTI rows (two cells a thread): the moments are
+    // separable, mu_pq = sum_j x2_j^q dA sum_i x1_i^p n_ij, and a thread's
+    // cells lie in one column (tiles are 32 wide), so each thread keeps x1,
+    // x1^2, x1^3 of its cells and x2^q dA of its column and sums
+    // S_p = sum x1^p v over its cells (four FMAs a cell instead of ten), and
+    // the moment warp combines the columns (about 50 FP64 instructions
+    // against 90 for the per-thread moments: it was the last warp of the
+    // stage on output steps).  Tall tiles (eight cells a thread, measured
+    // faster this way): x1 and the volume weight of each cell, x2^q dA of the
+    // column, all ten moments a thread.
+    constexpr bool WREG = ONE_TILE && NDIM == 1;
+    constexpr bool SEP = ONE_TILE && NDIM == 2 && TI <= kFTI;
+    constexpr bool WCOL = ONE_TILE && NDIM == 2 && !SEP;
+    static_assert(!SEP || kFNT - 32 * (kFaceWarps + 1) == 32, "one moment warp");
     double wgt[WREG ? CPT : 1][WREG ? NM : 1];
+    double x1p[SEP ? CPT : 1][3];
     double x1c[WCOL ? CPT : 1], w8c[WCOL ? CPT : 1];
-    double wx2[4] = {0.0, 0.0, 0.0, 0.0};
+    double wx2[4] = {0.0, 0.0, 0.0, 0.0};   // x2^q dA of this thread's column
     double keep[ONE_TILE ? CPT : 1];   // n at the start of the step for this thread's cells
     keep[0] = 0.0;
     if constexpr (ONE_TILE) {
@@ -371,11 +382,16 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
         for (int q = 0; q < CPT; ++q) {
             int i, j, r, c;
             cell_of<NDIM>(threadIdx.x + q * kFNT, i0, j0, i, j, r, c);
-            if constexpr (WCOL) {
+            if constexpr (SEP || WCOL) {
                 const double x2 = (j + 0.5) * g.d2, a = g.d1 * g.d2;
                 wx2[0] = a; wx2[1] = a * x2; wx2[2] = wx2[1] * x2; wx2[3] = wx2[2] * x2;
-                x1c[q] = (i + 0.5) * g.d1;
-                w8c[q] = x1c[q] * wx2[2];
+                const double x1 = (i + 0.5) * g.d1;
+                if constexpr (SEP) {
+                    x1p[q][0] = x1; x1p[q][1] = x1 * x1; x1p[q][2] = x1p[q][1] * x1;
+                } else {
+                    x1c[q] = x1;
+                    w8c[q] = x1 * wx2[2];
+                }
             } else {
                 moment_weights<NDIM>(i, j, g, wgt[q]);
             }
@@ -460,6 +476,17 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                         ? cell_update<1, NDIM, ONE_TILE, TI>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j)
                         : cell_update<2, NDIM, ONE_TILE, TI>(n, out, threadIdx.x + q * kFNT, i0, j0, ti, g, sc, sm, kq, valid, i, j);
                     if (!valid) continue;
+                    if constexpr (SEP) {   // m[p] = S_p of the thread's column
+                        if (sc.moms) {
+                            m[0] += v;
+                            m[1] = fma(x1p[q][0], v, m[1]);
+                            m[2] = fma(x1p[q][1], v, m[2]);
+                            m[3] = fma(x1p[q][2], v, m[3]);
+                        } else {
+                            m[1] = fma(x1p[q][0], v, m[1]);
+                        }
+                        continue;
+                    }
                     if constexpr (WCOL) {
                         if (sc.moms) {
                             const double x1 = x1c[q], v1 = x1 * v, v2 = x1 * v1, v3 = x1 * v2;
@@ -493,7 +520,13 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
             // only the volume moment is on the critical path; on output steps
             // the per-thread moments wait in shared memory and are reduced
             // while the barrier is pending, the row completed after the solve
-            if (sc.moms) {
+            if constexpr (SEP) {
+                if (sc.moms) {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) red[p * kFNT + threadIdx.x] = m[p];
+                }
+                m[VIDX] = wx2[2] * m[1];   // mu_12 = x2^2 dA sum x1 v
+            } else if (sc.moms) {
 #pragma unroll
                 for (int k = 0; k < NM; ++k) red[threadIdx.x * (NM + 1) + k] = m[k];
             }
@@ -528,6 +561,22 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (!fail)
                     fused_faces<NDIM, ONE_TILE, TI, !ONE_TILE>(stage == 1 ? n1 : n, t_first, tiles_x, ti, g, sm,
                                                     threadIdx.x - 32, 32 * kFaceWarps, GroupSync());
+            } else if (SEP && sc.moms) {
+                // the block's ten moments from the column sums S_p: lane c sums its
+                // column over the eight warps, weights it with x2_c^q dA (its own
+                // column's weights), and a transposed butterfly sums the columns
+                const int lane = threadIdx.x & 31;
+                double T[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const double* rp = red + p * kFNT + lane;
+                    T[p] = ((rp[0] + rp[32]) + (rp[64] + rp[96])) + ((rp[128] + rp[160]) + (rp[192] + rp[224]));
+                }
+                const double mu[10] = {wx2[0] * T[0], wx2[0] * T[1], wx2[1] * T[0], wx2[0] * T[2], wx2[1] * T[1],
+                                       wx2[2] * T[0], wx2[0] * T[3], wx2[1] * T[2], wx2[2] * T[1], wx2[3] * T[0]};
+                int idx;
+                const double tot = transposed_sum10(mu, lane, idx);
+                if ((lane & 1) == 0 && idx < NM) rowpart[((size_t)row_here * G + blockIdx.x) * NM + idx] = tot;
             } else if (sc.moms) {
                 // two-level sum of the block's moments: 16 threads per moment, then one
                 constexpr int NT2 = kFNT - 32 * (kFaceWarps + 1);

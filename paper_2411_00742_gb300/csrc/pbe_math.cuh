@@ -9,7 +9,8 @@
 //        Taylor polynomial of degree 13 evaluated with Estrin's scheme, and
 //        the scale 2^k written into the exponent field;
 //   exp_tab: the table-driven form (Tang's method): x = (64 m + j) ln2/64 + r,
-//        exp x = 2^m 2^(j/64) exp(r), |r| <= ln2/128, exp(r) - 1 to r^5;
+//        exp x = 2^m 2^(j/64) exp(r), |r| <= ln2/128, exp(r) - 1 to r^5,
+//        seven dependent FP64 operations;
 //   log: x = 2^e m with m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(z),
 //        z = (m-1)/(m+1), by the odd Taylor series of atanh to z^23 (Estrin
 //        in w = z^2), plus e ln2.
@@ -107,31 +108,40 @@ __host__ __device__ inline double pbe_exp(double x)
 
 // Table-driven exp (Tang's method): x = (64 m + j) ln2/64 + r with
 // |r| <= ln2/128, exp x = 2^m 2^(j/64) exp(r), exp(r) - 1 by its Taylor
-// polynomial to r^5 (the first omitted term, r^6/720, is below 4e-17);
-// 12 FP64 operations against the 22 of pbe_exp.  Same range handling.
+// polynomial to r^5 (the first omitted term, r^6/720, is below 4e-17).  The
+// low part c = n (ln2/64)_lo of the reduction (|c| < 3e-14) enters only the
+// linear term (r - c; the neglected c r is below 1.2e-16 even at |x| = 700,
+// below 4e-18 for |x| < 20), so the polynomial starts one dependent operation
+// earlier, and 2^m is added to the exponent field of the table value (exact:
+// the result of an in-range argument is normal) instead of a multiplication:
+// seven dependent FP64 operations.  The range test is an integer compare on
+// the bits of x, applied to the result.
 __host__ __device__ inline double pbe_exp_tab(double x)
 {
-    if (!(x > -700.0)) return x != x ? x : 0.0;   // NaN stays NaN
-    if (x > 700.0) return __builtin_huge_val();
     const double inv_l = 92.332482616893656;            // 64 / ln2
     const double shifter = 6755399441055744.0;            // 1.5 * 2^52: rounds to an integer
     const double t = pbe_fma(x, inv_l, shifter);
     const double nd = t - shifter;
     const int n = (int)(pbe_double_to_bits(t) & 0xffffffff) - (int)(pbe_double_to_bits(shifter) & 0xffffffff);
-    double r = pbe_fma(-nd, PBE_EXP_LN2_64_HI, x);
-    r = pbe_fma(-nd, PBE_EXP_LN2_64_LO, r);
+    const double r = pbe_fma(-nd, PBE_EXP_LN2_64_HI, x);
+    const double c = nd * PBE_EXP_LN2_64_LO;
     const int j = n & 63, m = (n - j) / 64;
 #ifdef __CUDA_ARCH__
     const double tj = c_exp_tab[j];
 #else
     const double tj = h_exp_tab[j];
 #endif
+    const double tjs =
+        pbe_bits_to_double((int64_t)((uint64_t)pbe_double_to_bits(tj) + ((uint64_t)(int64_t)m << 52)));   // tj 2^m
     const double a = pbe_fma(r, 1.0 / 6, 0.5), b = pbe_fma(r, 1.0 / 120, 1.0 / 24);
-    const double r2 = r * r;
+    const double r2 = r * r, rc = r - c;
     const double r4 = r2 * r2;
-    const double u = pbe_fma(r4, b, pbe_fma(r2, a, r));   // exp(r) - 1
-    const double s = pbe_bits_to_double((int64_t)(m + 1023) << 52);
-    return pbe_fma(tj, u, tj) * s;
+    const double u = pbe_fma(r4, b, pbe_fma(r2, a, rc));   // exp(r - c) - 1
+    const double res = pbe_fma(tjs, u, tjs);
+    const uint64_t ax = (uint64_t)pbe_double_to_bits(x) & 0x7fffffffffffffffULL;
+    if (ax <= 0x4085E00000000000ULL) return res;   // |x| <= 700 (NaN has larger bits)
+    if (x != x) return x;                          // NaN stays NaN
+    return x > 0.0 ? __builtin_huge_val() : 0.0;
 }
 
 __host__ __device__ inline double pbe_log(double x)
@@ -196,17 +206,20 @@ __host__ __device__ __forceinline__ double pbe_log_tab_bits(int64_t b, int eadj)
 #else
     const double inv = h_log_inv[j], lnc = h_log_ln[j];
 #endif
-    const double r = pbe_fma(m, inv, -1.0);   // |r| <= 1/513
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double ed = (double)e;
+    const double H = pbe_fma(ed, ln2_hi, lnc);   // off the dependent chain
+    const double r = pbe_fma(m, inv, -1.0);       // |r| <= 1/513
     // log1p(r) = r + r^2 (c2 + c3 r) + r^4 (c4 + c5 r), c_k = (-1)^(k+1) / k;
-    // the first omitted term, r^6 / 6, is below 1e-17
+    // the first omitted term, r^6 / 6, is below 1e-17.  The small part
+    // e ln2_lo joins r first, the large part H last: five dependent operations
     const double c2 = -0.5, c3 = 1.0 / 3, c4 = -0.25, c5 = 0.2;
     const double r2 = r * r;
     const double p23 = pbe_fma(c3, r, c2), p45 = pbe_fma(c5, r, c4);
+    const double s1 = pbe_fma(ed, ln2_lo, r);
     const double r4 = r2 * r2;
-    const double l1p = pbe_fma(r4, p45, pbe_fma(r2, p23, r));
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double ed = (double)e;
-    return pbe_fma(ed, ln2_hi, lnc) + pbe_fma(ed, ln2_lo, l1p);
+    const double s2 = pbe_fma(r2, p23, s1);
+    return H + pbe_fma(r4, p45, s2);
 }
 
 // The main path runs for every x; the classification of x is applied to the

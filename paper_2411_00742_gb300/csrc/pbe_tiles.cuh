@@ -70,6 +70,46 @@ __device__ __forceinline__ void add_moments(double (&m)[10], double val, double 
     m[6] += x1 * x1 * x1w; m[7] += x1 * x1 * x2w; m[9] += x2 * x2 * x2w;
 }
 
+// The sums over the 32 lanes of ten values, in the lanes (transposed
+// butterfly: at offsets 16, 8, 4, 2 each lane keeps the lower or the upper
+// part of its list, ceil(n/2) entries, and adds its partner's copy of it,
+// then the pair at offset 1 adds).  Returns the total of value idx (lanes 2k
+// and 2k+1 hold value k; idx >= 10 in the lanes that hold padding).  Twelve
+// additions a lane against 310 in a lane-by-lane sum, in a fixed order.
+__device__ __forceinline__ double transposed_sum10(const double (&v)[10], int lane, int& idx)
+{
+    const unsigned full = 0xffffffffu;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    double w[5], x[3], y[2];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const double keep = b4 ? v[5 + i] : v[i], send = b4 ? v[i] : v[5 + i];
+        w[i] = keep + __shfl_xor_sync(full, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double hi = i + 3 < 5 ? w[i + 3] : 0.0;
+        const double keep = b3 ? hi : w[i], send = b3 ? w[i] : hi;
+        x[i] = keep + __shfl_xor_sync(full, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double hi = i + 2 < 3 ? x[i + 2] : 0.0;
+        const double keep = b2 ? hi : x[i], send = b2 ? x[i] : hi;
+        y[i] = keep + __shfl_xor_sync(full, send, 4);
+    }
+    const double z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(full, b1 ? y[0] : y[1], 2);
+    // the kept entry's index, and whether it is a value or padding (real
+    // entries of the kept list: 5 | 5, then 3 | 2 of five, 2 | 1 of three,
+    // 1 | 1 of two; an upper part with fewer real entries is padded)
+    int r = 5;
+    r = b3 ? r - 3 : (r < 3 ? r : 3);
+    r = b2 ? (r > 2 ? r - 2 : 0) : (r < 2 ? r : 2);
+    r = b1 ? (r > 1 ? r - 1 : 0) : (r < 1 ? r : 1);
+    idx = r > 0 ? (b4 ? 5 : 0) + (b3 ? 3 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0) : 16;
+    return z + __shfl_xor_sync(full, z, 1);
+}
+
 // Stage coefficients of one stage, uniform over the grid.
 struct StageCoef {
     double c1, c2;   // G_d dt / dL_d

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
                                                      double* rows, int use_cond, cudaGraphConditionalHandle hcond)
 {
     extern __shared__ __align__(16) double wsm[];
-    __shared__ double x1s[kWG * kWR];
+    __shared__ double x1s[3 * kWG * kWR];
     __shared__ double sh[kWW * 10];
     __shared__ int flag;
     if (S->done) {
@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(kWNT) k_stage2d_win(const double* __restrict__
     double m[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) m[k] = 0.0;
-    window_tile<STAGE, kWR, false>(in, old, out, g, sc, blockIdx.y * kWG * kWR, blockIdx.x * kWOut, wsm, x1s, m);
+    if (sc.moms) window_tile<STAGE, kWR, false, true>(in, old, out, g, sc, blockIdx.y * kWG * kWR, blockIdx.x * kWOut, wsm, x1s, m);
+    else window_tile<STAGE, kWR, false, false>(in, old, out, g, sc, blockIdx.y * kWG * kWR, blockIdx.x * kWOut, wsm, x1s, m);
 
     const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
     block_sum<kWNT, 10>(m, sh);
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kWNT, 2) k_fused_win(double* n, double* n1, Sc
     constexpr int NM = 10, VIDX = 8;
     constexpr int kWTI = kWG * kWR;
     extern __shared__ __align__(16) double wsm[];
-    __shared__ double x1s[kWTI];
+    __shared__ double x1s[3 * kWTI];
     __shared__ Scal s;
     __shared__ StageCoef scs;
     __shared__ double red[kWW * NM];
@@ -155,19 +156,20 @@ __global__ void __launch_bounds__(kWNT, 2) k_fused_win(double* n, double* n1, Sc
             for (int k = 0; k < NM; ++k) m[k] = 0.0;
             for (int t = t_first; t < t_end; ++t) {
                 const int i0 = (t / tiles_x) * kWTI, j0 = (t % tiles_x) * kWOut;
-                if (stage == 1) window_tile<1, kWR, true>(n, n, n1, g, sc, i0, j0, wsm, x1s, m);
-                else window_tile<2, kWR, true>(n1, n, n, g, sc, i0, j0, wsm, x1s, m);
+                if (stage == 1) {
+                    if (sc.moms) window_tile<1, kWR, true, true>(n, n, n1, g, sc, i0, j0, wsm, x1s, m);
+                    else window_tile<1, kWR, true, false>(n, n, n1, g, sc, i0, j0, wsm, x1s, m);
+                } else {
+                    if (sc.moms) window_tile<2, kWR, true, true>(n1, n, n, g, sc, i0, j0, wsm, x1s, m);
+                    else window_tile<2, kWR, true, false>(n1, n, n, g, sc, i0, j0, wsm, x1s, m);
+                }
                 __syncthreads();
             }
             const int row_here = s.out_idx;
-            if (sc.moms) {
-#pragma unroll
-                for (int k = 0; k < NM; ++k) {
-                    double v = m[k];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) red[warp * NM + k] = v;
-                }
+            if (sc.moms) {   // the warp's ten moments (transposed butterfly), then over the warps
+                int idx;
+                const double tot = transposed_sum10(m, lane, idx);
+                if ((lane & 1) == 0 && idx < NM) red[warp * NM + idx] = tot;
             }
             const long long qb = block_sum_fixed_t0(m[VIDX], inv_u, wsum);   // its barrier orders red
             if (sc.moms && threadIdx.x < NM) {

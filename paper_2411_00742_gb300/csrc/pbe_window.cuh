@@ -45,10 +45,16 @@ __device__ __forceinline__ double win_ld(const double* p)
 
 // The tile with origin (i0, j0) of stage STAGE.  Adds the tile's moments
 // (all ten on output steps, sc.moms; else only the volume moment m[8]) to m.
-// wsm: win_smem(kWR) bytes of dynamic shared memory; x1s: kWG * kWR doubles.
+// The moments are separable, mu_pq = sum_j x2_j^q dA sum_i x1_i^p n_ij: each
+// lane sums S_p = sum_i x1_i^p n_ij down each of its four columns (three FMAs
+// a cell beyond the volume moment's, instead of the ten moments a cell) and
+// weights them with x2_j^q dA at the end of the tile.
+// wsm: win_smem(kWR) bytes of dynamic shared memory; x1s: 3 kWG kWR doubles
+// (x1, x1^2, x1^3 of the tile's rows).  MOMS: the caller's sc.moms, as a
+// template argument so that the volume-only form carries no column sums.
 // Starts and ends with the block's threads in step (one barrier between the
 // passes); the caller separates consecutive tiles with a block barrier.
-template <int STAGE, int kWR, bool CG>
+template <int STAGE, int kWR, bool CG, bool MOMS>
 __device__ __forceinline__ void window_tile(const double* __restrict__ in, const double* old, double* out,
                                             const Geom& g, const StageCoef& sc, int i0, int j0, double* wsm,
                                             double* x1s, double (&m)[10])
@@ -61,7 +67,14 @@ __device__ __forceinline__ void window_tile(const double* __restrict__ in, const
     constexpr double kW = STAGE == 2 ? 0.5 : 1.0;
     const double wc1 = kW * sc.c1, wc2 = kW * sc.c2, wsrc = kW * sc.src;
     const int N1 = g.N1, N2 = g.N2;
-    if (threadIdx.x < kWTI) x1s[threadIdx.x] = (i0 + threadIdx.x + 0.5) * g.d1;
+    if (threadIdx.x < kWTI) {
+        const double x1 = (i0 + threadIdx.x + 0.5) * g.d1;
+        x1s[threadIdx.x] = x1;
+        if (MOMS) {
+            x1s[kWTI + threadIdx.x] = x1 * x1;
+            x1s[2 * kWTI + threadIdx.x] = x1 * x1 * x1;
+        }
+    }
 
     // 1. L1 faces down this thread's column: input rows i0+ra-2 .. i0+ra+kWR
     {
@@ -95,12 +108,11 @@ __device__ __forceinline__ void window_tile(const double* __restrict__ in, const
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = kWC * lane, jb = j0 - 2 + c0;
     const double area = g.d1 * g.d2;
-    double x2[kWC], acc[kWC];
+    double acc[kWC], s0[kWC], s2[kWC], s3[kWC];   // S_1 (acc), S_0, S_2, S_3 of the lane's columns
     bool ok[kWC];
 #pragma unroll
     for (int k = 0; k < kWC; ++k) {
-        x2[k] = (jb + k + 0.5) * g.d2;
-        acc[k] = 0.0;
+        acc[k] = 0.0; s0[k] = 0.0; s2[k] = 0.0; s3[k] = 0.0;
         ok[k] = c0 + k >= 2 && c0 + k <= kWX - 2 && jb + k < N2;
     }
 #pragma unroll
@@ -134,11 +146,23 @@ __device__ __forceinline__ void window_tile(const double* __restrict__ in, const
             if (STAGE == 2) val = fma(0.5, CG ? __ldcg(old + row + jb + k) : old[row + jb + k], val);
             out[row + jb + k] = val;
             acc[k] = fma(x1, val, acc[k]);
-            if (sc.moms) add_moments(m, val, x1, x2[k], area);
+            if (MOMS) {
+                s0[k] += val;
+                s2[k] = fma(x1s[kWTI + r], val, s2[k]);
+                s3[k] = fma(x1s[2 * kWTI + r], val, s3[k]);
+            }
         }
     }
 #pragma unroll
-    for (int k = 0; k < kWC; ++k) m[8] = fma(acc[k], x2[k] * x2[k] * area, m[8]);
+    for (int k = 0; k < kWC; ++k) {
+        const double x2 = (jb + k + 0.5) * g.d2, a1 = x2 * area, a2 = x2 * a1;
+        m[8] = fma(acc[k], a2, m[8]);
+        if (MOMS) {   // mu_pq in row order; mu_12 (m[8]) above
+            m[0] = fma(area, s0[k], m[0]); m[1] = fma(area, acc[k], m[1]); m[2] = fma(a1, s0[k], m[2]);
+            m[3] = fma(area, s2[k], m[3]); m[4] = fma(a1, acc[k], m[4]); m[5] = fma(a2, s0[k], m[5]);
+            m[6] = fma(area, s3[k], m[6]); m[7] = fma(a1, s2[k], m[7]); m[9] = fma(x2 * a2, s0[k], m[9]);
+        }
+    }
 }
 
 }  // namespace pbe
