@@ -66,6 +66,10 @@ typedef int pbe_status;
 /* execution paths of pbe_solve */
 #define PBE_PATH_PLAIN 0 /* two stage kernels per step, device-resident scalars, CUDA graph loop */
 #define PBE_PATH_FUSED 1 /* one persistent kernel for the whole solve                              */
+#define PBE_PATH_AUTO 2  /* the faster path for the configuration: the fused path (faster than the
+                            plain one at every measured size of the SSP-RK2 scheme, 1-D 200 to 2^20
+                            cells, 2-D 128^2 to 2048^2), the plain path where the fused one does not
+                            apply (the paper scheme of Eq. 3)                                      */
 
 typedef struct pbe_grid pbe_grid;
 
@@ -99,8 +103,10 @@ pbe_status pbe_destroy_grid(pbe_grid* g);
 /* Order all later work of this grid on `cuda_stream` (a cudaStream_t). */
 pbe_status pbe_set_stream(pbe_grid* g, void* cuda_stream);
 
-/* Select the execution path of pbe_solve (PBE_PATH_PLAIN or PBE_PATH_FUSED).
- * Both compute the same step; results agree to rounding. */
+/* Select the execution path of pbe_solve and pbe_vjp (PBE_PATH_PLAIN,
+ * PBE_PATH_FUSED or PBE_PATH_AUTO; AUTO behaves as FUSED, whose solves fall
+ * back to the plain path for the paper scheme).  Both compute the same step;
+ * results agree to rounding.  Errors: PBE_EINVAL for another value. */
 pbe_status pbe_set_path(pbe_grid* g, int path);
 
 /* Set the kinetic model (Sec. 2.1 S = c/c*; Appendix A growth law only for

@@ -15,13 +15,13 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PBE_KINETICS_FIXED, PBE_KINETICS_MLP, PBE_KINETICS_POWER_LAW, PBE_MEM_DEVICE, PBE_MEM_HOST,
-                   PBE_PATH_FUSED, PBE_PATH_PLAIN, PbeError, Kinetics)
+                   PBE_PATH_AUTO, PBE_PATH_FUSED, PBE_PATH_PLAIN, PbeError, Kinetics)
 
 CLOSURE_SIZE = 64 * 3 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # weights of the learned closure
 
 __all__ = ["Grid", "Batch", "PbeError", "kinetics_struct", "ncols", "closure_grad"]
 
-_PATHS = {"plain": PBE_PATH_PLAIN, "fused": PBE_PATH_FUSED}
+_PATHS = {"plain": PBE_PATH_PLAIN, "fused": PBE_PATH_FUSED, "auto": PBE_PATH_AUTO}
 
 
 def ncols(ndim: int) -> int:
@@ -112,6 +112,8 @@ class Grid:
         _lib.check(self.lib.pbe_set_stream(self.h, ctypes.c_void_p(int(handle))))
 
     def set_path(self, path: str):
+        """"plain", "fused" or "auto" (the faster path for the configuration: fused,
+        which falls back to plain for the paper scheme)."""
         _lib.check(self.lib.pbe_set_path(self.h, _PATHS[path]))
 
     def set_window(self, mode: int):

@@ -10,7 +10,7 @@ from . import build as _build
 PBE_OK, PBE_EINVAL, PBE_ENOMEM, PBE_ECUDA, PBE_ENONFINITE, PBE_ETIMEOUT, PBE_ESTATE = range(7)
 PBE_MEM_HOST, PBE_MEM_DEVICE = 0, 1
 PBE_KINETICS_POWER_LAW, PBE_KINETICS_FIXED, PBE_KINETICS_MLP = 0, 1, 2
-PBE_PATH_PLAIN, PBE_PATH_FUSED = 0, 1
+PBE_PATH_PLAIN, PBE_PATH_FUSED, PBE_PATH_AUTO = 0, 1, 2
 
 STATUS_NAMES = {0: "PBE_OK", 1: "PBE_EINVAL", 2: "PBE_ENOMEM", 3: "PBE_ECUDA", 4: "PBE_ENONFINITE",
                 5: "PBE_ETIMEOUT", 6: "PBE_ESTATE"}

@@ -327,8 +327,9 @@ pbe_status pbe_set_stream(pbe_grid* g, void* stream)
 pbe_status pbe_set_path(pbe_grid* g, int path)
 {
     if (!g) return fail(PBE_EINVAL, "null grid");
-    if (path != PBE_PATH_PLAIN && path != PBE_PATH_FUSED) return fail(PBE_EINVAL, "unknown path %d", path);
-    g->path = path;
+    if (path != PBE_PATH_PLAIN && path != PBE_PATH_FUSED && path != PBE_PATH_AUTO)
+        return fail(PBE_EINVAL, "unknown path %d", path);
+    g->path = path == PBE_PATH_AUTO ? PBE_PATH_FUSED : path;   // fused falls back to plain where it does not apply
     return PBE_OK;
 }
 

@@ -110,6 +110,31 @@ def test_fused_deterministic_bitwise():
     assert np.array_equal(a["rows"], b["rows"]) and np.array_equal(a["n"], b["n"])
 
 
+def test_auto_path_is_the_fused_path_with_the_plain_fallback():
+    # SSP-RK2: "auto" runs the fused kernels (the same bits); the paper scheme
+    # (plain path only) still solves under "auto", as on the plain path; other
+    # values are rejected
+    import dataclasses
+    import paper_2411_00742_gb300 as P
+    a = gpu_solve(pi.config_2d(96, 80), path="auto")
+    b = gpu_solve(pi.config_2d(96, 80), path="fused")
+    assert a["steps"] == b["steps"]
+    assert np.array_equal(a["rows"], b["rows"]) and np.array_equal(a["n"], b["n"])
+    inst = pi.config_1d(300)
+    paper = dataclasses.replace(inst.problem, scheme=1)
+    rows = {}
+    for path in ("auto", "plain"):
+        g = P.Grid.from_problem(paper, path=path)
+        g.set_state(inst.n0, inst.C0, 0.0)
+        rows[path], _ = g.solve(inst.t_out)
+        g.close()
+    assert np.array_equal(rows["auto"], rows["plain"])
+    g = P.Grid.from_problem(inst.problem)
+    with pytest.raises(P.PbeError):
+        P._lib.check(g.lib.pbe_set_path(g.h, 3))
+    g.close()
+
+
 def test_fused_step_budget_and_nonfinite():
     import paper_2411_00742_gb300 as P
     inst = pi.config_2d(64)
