@@ -73,17 +73,31 @@ __device__ __forceinline__ double allsum2_split(double a, double b)
     return v;
 }
 
+// The integer w as a double, exactly, for 0 <= w < 2^52: w in the low
+// mantissa bits of 2^52, minus 2^52 (one FP64 addition).
+__device__ __forceinline__ double exact_int_double(long long w)
+{
+    return __longlong_as_double(0x4330000000000000LL | w) - 4503599627370496.0;
+}
+
+// The moment weights are x_i^k = (2i + 1)^k (dL/2)^k: the integer powers are
+// formed in integer arithmetic (exact: (2 kMaxBatchCells)^3 < 2^52) and
+// converted by one addition each, the factor (dL/2)^k dL applied to the
+// segment sums; the volume moment alone costs two FP64 operations a cell.
+static_assert((2.0 * kMaxBatchCells) * (2.0 * kMaxBatchCells) * (2.0 * kMaxBatchCells) < 4503599627370496.0,
+              "exact moment weights");
+
 // One row of a stage (cell i = 32 r + lane): the face value of the next
 // row's faces (hnext, from shared memory), the update with the flux of the
-// lane to the right (shuffle), and the row's moment weights (without the
-// factor dL, applied to the segment sums) added to m.  src_row: the row may
+// lane to the right (shuffle), and the row's moment weights (2i + 1)^k
+// (the factors (dL/2)^k dL are applied to the segment sums) added to m.  src_row: the row may
 // hold cell 0, which receives the nucleation source.  A face's upwind
 // difference n_{f-1} - n_{f-2} is the downwind difference of the face one
 // lane to the left (lane 0: of lane 31 one row up, carried in b31), so each
 // face computes one difference (the same value face_value forms).
 template <int STAGE>
 __device__ __forceinline__ void stage_row(const double* in, const double* old, double* out, int N, int i, double c1,
-                                          double src, bool src_row, bool moms, double& hcur, double& b31, double x,
+                                          double src, bool src_row, bool moms, double& hcur, double& b31,
                                           double (&m)[4])
 {
     const int lane = threadIdx.x & 31;
@@ -107,15 +121,13 @@ __device__ __forceinline__ void stage_row(const double* in, const double* old, d
         hcur = hnext;
     }
     if (i < N) {
+        const long long w1 = 2LL * i + 1, w3 = w1 * w1 * w1;
         if (moms) {
-            const double t1 = x * v, t2 = x * t1;
             m[0] += v;
-            m[1] = fma(x, v, m[1]);
-            m[2] = fma(x, t1, m[2]);
-            m[3] = fma(x, t2, m[3]);
-        } else {
-            m[3] = fma(x * x * x, v, m[3]);
+            m[1] = fma(exact_int_double(w1), v, m[1]);
+            m[2] = fma(exact_int_double(w1 * w1), v, m[2]);
         }
+        m[3] = fma(exact_int_double(w3), v, m[3]);
     }
 }
 
@@ -126,21 +138,15 @@ __device__ __forceinline__ void stage_segment(const double* in, const double* ol
                                               double& b31, double (&m)[4])
 {
     const int lane = threadIdx.x & 31;
-    const double dx32 = 32.0 * d1;
     m[0] = 0.0; m[1] = 0.0; m[2] = 0.0; m[3] = 0.0;
-    double x = (32 * r0 + lane + 0.5) * d1;
     const int i0 = 32 * r0 + lane;
     if (nr == kSegRows) {
 #pragma unroll
-        for (int j = 0; j < kSegRows; ++j) {
-            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, b31, x, m);
-            x += dx32;
-        }
+        for (int j = 0; j < kSegRows; ++j)
+            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, b31, m);
     } else {
-        for (int j = 0; j < nr; ++j) {
-            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, b31, x, m);
-            x += dx32;
-        }
+        for (int j = 0; j < nr; ++j)
+            stage_row<STAGE>(in, old, out, N, i0 + 32 * j, c1, src, j == 0 && r0 == 0, moms, hcur, b31, m);
     }
 }
 
@@ -165,13 +171,17 @@ __device__ __forceinline__ void warp_stage(const double* in, const double* old, 
         b31 = __shfl_sync(0xffffffffu, in[f0 + 2] - in[f0 + 1], 31);
     }
     double m[4];
+    // the weights' factors (dL/2)^k dL
+    const double hd = 0.5 * d1, f1 = d1 * hd, f2 = f1 * hd, f3 = f2 * hd;
     if (moms) {
         // lane group k = lane / 8 carries moment k
+        const int k8 = lane >> 3;
+        const double fk = k8 == 0 ? d1 : (k8 == 1 ? f1 : (k8 == 2 ? f2 : f3));
         double acc = 0.0;
         for (int p = p0; p < p1; ++p) {
             const int r0 = p * kSegRows;
             stage_segment<STAGE>(in, old, out, N, r0, min(kSegRows, R - r0), c1, src, d1, true, hcur, b31, m);
-            const double v = allsum4_split(m) * d1;
+            const double v = allsum4_split(m) * fk;
             if (seg) {
                 if ((lane & 7) == 0) seg[4 * p + (lane >> 3)] = v;
             } else {
@@ -197,7 +207,7 @@ __device__ __forceinline__ void warp_stage(const double* in, const double* old, 
             b = m[3];
         }
         const double v = allsum2_split(a, b);
-        const double sa = __shfl_sync(0xffffffffu, v, 0) * d1, sb = __shfl_sync(0xffffffffu, v, 16) * d1;
+        const double sa = __shfl_sync(0xffffffffu, v, 0) * f3, sb = __shfl_sync(0xffffffffu, v, 16) * f3;
         if (seg) {
             if (lane == 0) seg[4 * p + 3] = sa;
             if (lane == 16 && p + 1 < p1) seg[4 * (p + 1) + 3] = sb;
