@@ -77,15 +77,23 @@ struct Team {
     }
 };
 
+// The integer w as a double, exactly, for 0 <= w < 2^52 (one FP64 addition).
+__device__ __forceinline__ double exact_int_double(long long w)
+{
+    return __longlong_as_double(0x4330000000000000LL | w) - 4503599627370496.0;
+}
+
 // forward stage over the rows [r0, r1) of this warp (fused-path quotient),
-// as in pbe_batch.cu; returns this lane's partial of the volume moment
+// as in pbe_batch.cu; returns this lane's partial of the volume moment.  The
+// weights x_i^3 dL = (2i+1)^3 (dL/2)^3 dL: the integer cube exactly (i below
+// 2^17), the factor once at the end.
 template <int STAGE>
 __device__ __forceinline__ double fwd_stage(const double* in, const double* old, double* out, int N, int r0, int r1,
                                             double c1, double src, double d1)
 {
     const int lane = threadIdx.x & 31;
     double hcur = face_value<true>(in[32 * r0 + lane], in[32 * r0 + lane + 1], in[32 * r0 + lane + 2]);
-    double x = (32 * r0 + lane + 0.5) * d1, m3 = 0.0;
+    double m3 = 0.0;
     for (int r = r0; r < r1; ++r) {
         const int fn = 32 * (r + 1) + lane;
         const double hnext = face_value<true>(in[fn], in[fn + 1], in[fn + 2]);
@@ -98,12 +106,13 @@ __device__ __forceinline__ double fwd_stage(const double* in, const double* old,
             if (i == 0) v += src;
             if (STAGE == 2) v = 0.5 * old[i + 2] + 0.5 * v;
             out[i + 2] = v;
-            m3 += x * x * x * (v * d1);
+            const long long w1 = 2LL * i + 1;
+            m3 = fma(exact_int_double(w1 * w1 * w1), v, m3);
         }
         hcur = hnext;
-        x += 32.0 * d1;
     }
-    return m3;
+    const double hd = 0.5 * d1;
+    return m3 * (((hd * hd) * hd) * d1);
 }
 
 // adjoint of one stage by the team.  nt: stage input (cell i at [i+2]);
@@ -119,13 +128,17 @@ __device__ __forceinline__ void adj_stage(const double* nt, const double* lam, c
     constexpr int NT = 32 * W;
     const int tid = threadIdx.x;
     const double invd = 1.0 / d1;   // once per stage
-    // effective lambda with zero ghosts
+    // effective lambda with zero ghosts; the pending weights sum_k p_k x^k dL
+    // as a polynomial in the exact integer 2i+1 (x = (2i+1) dL/2), its
+    // coefficients p_k (dL/2)^k dL formed once per stage
+    const double hd = 0.5 * d1, q0 = p[0] * d1, q1 = p[1] * (hd * d1), q2 = p[2] * ((hd * hd) * d1),
+                 q3 = p[3] * (((hd * hd) * hd) * d1);
     for (int k = tid; k < 32 * (R + 1) + 3; k += NT) {
         const int i = k - 2;
         double v = 0.0;
         if (i >= 0 && i < N) {
-            const double x = (i + 0.5) * d1;
-            v = s * (lam[k] + (p[0] + x * (p[1] + x * (p[2] + x * p[3]))) * d1);
+            const double w = exact_int_double(2LL * i + 1);
+            v = s * (lam[k] + (q0 + w * (q1 + w * (q2 + w * q3))));
         }
         leff[k] = v;
     }
@@ -212,9 +225,13 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
         s.C = C0s[id];
         s.t = t0s[id];
         {
-            double m3 = 0.0, x = (tid + 0.5) * d1;
-            for (int i = tid; i < N; i += NT, x += NT * d1) m3 += x * x * x * (nb[i + 2] * d1);
-            s.V0 = tm.sum(m3);
+            double m3 = 0.0;   // the volume moment with fwd_stage's weights
+            for (int i = tid; i < N; i += NT) {
+                const long long w1 = 2LL * i + 1;
+                m3 = fma(exact_int_double(w1 * w1 * w1), nb[i + 2], m3);
+            }
+            const double hd = 0.5 * d1;
+            s.V0 = tm.sum(m3 * (((hd * hd) * hd) * d1));
         }
         int out_idx = 0;
         const bool row0 = n_out > 0 && t_out[0] == s.t;
