@@ -318,12 +318,16 @@ __device__ __forceinline__ void poly_growth_warp(const Kin& K, double s, double 
 // (optional, 3 values) s dG_1/ds, s dG_2/ds and s of the polynomial growth
 // law (0 otherwise).  POLY false: a caller that never sees the polynomial law
 // (the fused solve kernel; its register budget sets its occupancy).
+// rec (optional, 2 values): d = C - c* and 1/d (0, 0 when S <= 1 or the
+// rates are fixed), 1/d from lane 3 of the exp, which runs in every lane.
 template <bool POLY = true>
 __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const KinT& tc, double& G1, double& G2,
-                                                double& B, double* Lout = nullptr, double* sGout = nullptr)
+                                                double& B, double* Lout = nullptr, double* sGout = nullptr,
+                                                double* rec = nullptr)
 {
     const int lane = threadIdx.x & 31;
     if (Lout) *Lout = 0.0;
+    if (rec) { rec[0] = 0.0; rec[1] = 0.0; }
     if (sGout) { sGout[0] = 0.0; sGout[1] = 0.0; sGout[2] = 0.0; }
     if (K.kind == PBE_KINETICS_FIXED) {
         G1 = K.kg1;
@@ -338,12 +342,16 @@ __device__ __forceinline__ void kinetics_warp_T(const Kin& K, double C, const Ki
         return;
     }
     const double lx = pbe_log_tab(lane == 0 ? d : cs);
-    const double L = __shfl_sync(0xffffffffu, lx, 0) - __shfl_sync(0xffffffffu, lx, 1);
+    const double ld = __shfl_sync(0xffffffffu, lx, 0);
+    const double L = ld - __shfl_sync(0xffffffffu, lx, 1);
     if (Lout) *Lout = L;
     const double p = lane == 0 ? K.g1 : (lane == 1 ? K.g2 : K.b);
     double q = lane == 0 ? K.lkg1 : (lane == 1 ? K.lkg2 : K.lkb);
     if (K.growth_form == 1 && lane < 2) q -= (lane == 0 ? K.ea1 : K.ea2) / (T + 273.15);   // Arrhenius factor
-    const double e = pbe_exp_tab(fma(p, L, q));
+    double arg = fma(p, L, q);
+    if (rec && lane == 3) arg = -ld;
+    const double e = pbe_exp_tab(arg);
+    if (rec) { rec[0] = d; rec[1] = __shfl_sync(0xffffffffu, e, 3); }
     G1 = __shfl_sync(0xffffffffu, e, 0);
     G2 = (K.ndim == 2) ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
     B = __shfl_sync(0xffffffffu, e, 2);

@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(kWNT, 2) k_fused_win(double* n, double* n1, Sc
         inv_u = ldexp(1.0, 52 - E);
     }
     unsigned int gen = 0;
+    // warp 0: the stage-1 chain's evaluation, for the stage-2 chain's series
+    // (in shared memory: the kernel's registers are at the 2-blocks-per-SM limit)
+    __shared__ RateCarry rcs[32];
+    if (warp == 0) rate_carry_init(rcs[lane], K);
     const int t_first = (int)(((long long)blockIdx.x * ntiles) / G);
     const int t_end = (int)(((long long)(blockIdx.x + 1) * ntiles) / G);
     for (;;) {
@@ -191,8 +195,8 @@ __global__ void __launch_bounds__(kWNT, 2) k_fused_win(double* n, double* n1, Sc
                 }
                 __syncwarp();
                 if (!fail) {
-                    const StageCoef c = stage == 1 ? fused_finish1<false>(&s, K, g, msum[VIDX], tpre)
-                                                   : fused_finish2<false>(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre);
+                    const StageCoef c = stage == 1 ? fused_finish1<false, true>(&s, K, g, msum[VIDX], tpre, &rcs[lane])
+                                                   : fused_finish2<false, true>(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre, &rcs[lane]);
                     if (threadIdx.x == 0) scs = c;
                 }
             }
