@@ -352,8 +352,11 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
         inv_u = ldexp(1.0, 52 - E);
     }
     unsigned int gen = 0;
-    RateCarry rc;   // warp 0: the stage-1 chain's evaluation, for the stage-2 chain's series
-    if (warp == 0) rate_carry_init(rc, K);
+    // warp 0: the stage-1 chain's evaluation, for the stage-2 chain's series
+    // (in shared memory: in registers it would cost the one-tile kernels their
+    // second block per SM, which grids of 153-304 tiles need)
+    __shared__ RateCarry rcs[32];
+    if (warp == 0) rate_carry_init(rcs[threadIdx.x], K);
 
     // moment weights of this thread's cells (one tile per block: fixed for the
     // whole solve).  1-D: the four weights of each cell in registers.  2-D
@@ -549,8 +552,8 @@ __global__ void __launch_bounds__(kFNT, 1) k_fused(double* n, double* n1, Scal* 
                 if (!fail) {
                     // the next stage's coefficients, once per block (the divisions of
                     // stage_coef in every thread cost the FP64 pipe ~4k cycles a stage)
-                    const StageCoef c = stage == 1 ? fused_finish1<false, true>(&s, K, g, msum[VIDX], tpre, &rc)
-                                                   : fused_finish2<false, true>(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre, &rc);
+                    const StageCoef c = stage == 1 ? fused_finish1<false, true>(&s, K, g, msum[VIDX], tpre, &rcs[threadIdx.x & 31])
+                                                   : fused_finish2<false, true>(&s, K, g, t_out, my_rows, msum, NM, VIDX, tpre, &rcs[threadIdx.x & 31]);
                     if (threadIdx.x == 0) scs = c;
                 }
             } else if (warp <= kFaceWarps) {
