@@ -730,7 +730,10 @@ static cudaError_t fused_config(pbe_grid* g)
         int occ2 = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fn_multi, kFNT, 0);
         if (e != cudaSuccess) return e;
-        G = std::min(ntiles, occ2 * sms);
+        // at most two blocks per SM: measured on GB300, 1-D 2^20 cells 31.2 / 28.0 /
+        // 29.1 ms and 2^19 9.3 / 8.3 / 8.6 ms at one / two / three blocks per SM
+        // (three add barrier arrivals and pile more tiles on the busiest SM)
+        G = std::min(ntiles, std::min(occ2, 2) * sms);
         if (2 * G > g->max_blocks) G = g->max_blocks / 2;
         if (g->block_limit > 0 && G > g->block_limit) G = g->block_limit;
         if (G < 1) G = 1;
