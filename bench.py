@@ -56,7 +56,7 @@ BYTES_PER_CELL_STEP_PAPER = 16
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64 (2 FMA/clk/SM x 152 SMs x ~2.07 GHz)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_fused launch on the
 # 256 x 256 solve, from one ncu capture of the current kernel (the state stays in L2)
-FUSED_DRAM_BYTES_PER_LAUNCH = 604416
+FUSED_DRAM_BYTES_PER_LAUNCH = 605440
 L2_FLUSH_BYTES = 256 << 20
 
 
