@@ -27,6 +27,7 @@
 #include <tuple>
 #include <vector>
 
+#include "pbe_chain.cuh"
 #include "pbe_internal.h"
 #include "pbe_tiles.cuh"
 
@@ -297,6 +298,12 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
     s.V0 = m[3];
     double M0 = m[0];   // mu0 of the current state (the closure's input ratio V / mu0)
     double* my_rows = rows + (size_t)id * n_out * 6;
+    // power law: the stage-1 chain's evaluation, for the series of the next
+    // step's rates (both at the step's end time t_new), and that time's
+    // temperature and solubility
+    RateCarry rc;
+    KinT tc{0.0, 0.0};
+    if (!MLP) rate_carry_init(rc, K);
     if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(s.C)) {
         s.status = PBE_ENONFINITE;
         s.done = 1;
@@ -325,7 +332,14 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
         const double C1 = fma(-K.kappa, V1 - s.V0, s.C);
         {
             double G1, B;
-            batch_rates<MLP>(K, C1, s.t_new, MLP ? V1 / m[0] : 0.0, G1, B);
+            if (MLP) {
+                batch_rates<MLP>(K, C1, s.t_new, V1 / m[0], G1, B);
+            } else {   // power law: the step's end time once, the evaluation kept for the series
+                tc = kin_temperature(K, s.t_new);
+                double G2, L, rec[2];
+                kinetics_warp_T<false>(K, C1, tc, G1, G2, B, &L, nullptr, rec);
+                rate_carry_keep(rc, K, G1, G2, B, L, rec);
+            }
             s.G1b = G1; s.Bb = B;
             if (!isfinite(V1) || !isfinite(G1) || !isfinite(B)) { s.status = PBE_ENONFINITE; s.done = 1; break; }
         }
@@ -350,7 +364,12 @@ __device__ __forceinline__ void run_instance(int id, const BatchInst* __restrict
         if (s.out_idx >= n_out) { s.done = 1; break; }
         if (s.steps >= max_steps) { s.status = PBE_ETIMEOUT; s.done = 1; break; }
         double G1, B, dt, t_new;
-        batch_rates<MLP>(K, s.C, s.t, MLP ? s.V0 / M0 : 0.0, G1, B);
+        if (MLP) {
+            batch_rates<MLP>(K, s.C, s.t, s.V0 / M0, G1, B);
+        } else {   // the same time as the stage-1 evaluation: the series where it applies
+            double G2, L;
+            if (!rates_by_series(rc, s.C, tc.cs, 1, G1, G2, B, L)) kinetics_warp_T<false>(K, s.C, tc, G1, G2, B);
+        }
         s.clipped = timestep_fast(K, g, G1, 0.0, s.t, t_out[s.out_idx], dt, t_new);
         s.G1a = G1; s.Ba = B; s.dt = dt; s.t_new = t_new;
         if (!isfinite(G1) || !isfinite(B) || !isfinite(dt)) { s.status = PBE_ENONFINITE; s.done = 1; }

@@ -52,6 +52,40 @@ __device__ __forceinline__ void rate_carry_init(RateCarry& rc, const Kin& K)
 // kinetics start at once, lane 0's bookkeeping is stores at the end, and the
 // coefficients of the next stage come from registers.  tc: temperature and
 // solubility at the step's end time.
+// Keep a full evaluation (kinetics_warp_T with rec) in rc for the series.
+__device__ __forceinline__ void rate_carry_keep(RateCarry& rc, const Kin& K, double G1, double G2, double B, double L,
+                                                const double (&rec)[2])
+{
+    const int lane = threadIdx.x & 31;
+    const double r = lane == 0 ? G1 : (lane == 1 ? G2 : B);
+    rc.a = lane == 3 ? 1.0 : r;
+    rc.b = lane == 3 ? L : r;
+    rc.d0 = rec[0];
+    rc.inv_d0 = rec[1];
+    rc.ok = K.kind == PBE_KINETICS_POWER_LAW && K.growth_form != 2 && finite_nonzero_bits(rec[1]);
+}
+
+// The rates at (C, c*) by the series from the evaluation kept in rc (at the
+// same time: the same c* and Arrhenius factor); false, with nothing set,
+// where it does not apply (then the caller evaluates the kinetics).
+__device__ __forceinline__ bool rates_by_series(const RateCarry& rc, double C, double cs, int ndim, double& G1,
+                                                double& G2, double& B, double& L)
+{
+    if (!rc.ok) return false;
+    const double dd = C - cs, delta = (dd - rc.d0) * rc.inv_d0;
+    if (!(dd > 0.0 && fabs(delta) <= 0x1p-10)) return false;
+    double P = fma(rc.c[4], delta, rc.c[3]);
+    P = fma(P, delta, rc.c[2]);
+    P = fma(P, delta, rc.c[1]);
+    P = fma(P, delta, rc.c[0]);
+    const double e = fma(rc.a, P * delta, rc.b);
+    G1 = __shfl_sync(0xffffffffu, e, 0);
+    G2 = ndim == 2 ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
+    B = __shfl_sync(0xffffffffu, e, 2);
+    L = __shfl_sync(0xffffffffu, e, 3);
+    return true;
+}
+
 // TAYLOR (with rc): keep this evaluation for the stage-2 chain's series.
 template <bool POLY = true, bool TAYLOR = false>
 __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const Geom& g, double V1, const KinT& tc,
@@ -63,14 +97,7 @@ __device__ __forceinline__ StageCoef fused_finish1(Scal* S, const Kin& K, const 
     const int clipped = S->clipped;
     double G1, G2, B, L, sG[3], rec[2];
     kinetics_warp_T<POLY>(K, C1, tc, G1, G2, B, &L, sG, TAYLOR ? rec : nullptr);
-    if (TAYLOR) {
-        const double r = lane == 0 ? G1 : (lane == 1 ? G2 : B);
-        rc->a = lane == 3 ? 1.0 : r;
-        rc->b = lane == 3 ? L : r;
-        rc->d0 = rec[0];
-        rc->inv_d0 = rec[1];
-        rc->ok = K.kind == PBE_KINETICS_POWER_LAW && K.growth_form != 2 && finite_nonzero_bits(rec[1]);
-    }
+    if (TAYLOR) rate_carry_keep(*rc, K, G1, G2, B, L, rec);
     if (lane == 0) {
         S->C1 = C1;
         S->V1 = V1;
@@ -111,22 +138,7 @@ __device__ __forceinline__ StageCoef fused_finish2(Scal* S, const Kin& K, const 
     double G1 = 0.0, G2 = 0.0, B = 0.0, dt = 0.0, t_new = t, L = 0.0, sG[3] = {0.0, 0.0, 0.0};
     int clip2 = 0;
     if (!done) {   // the next step: kinetics at (C, t), CFL step to the next output time
-        bool series = false;
-        if (TAYLOR && rc->ok) {
-            const double dd = C - tc.cs, delta = (dd - rc->d0) * rc->inv_d0;
-            if (dd > 0.0 && fabs(delta) <= 0x1p-10) {
-                double P = fma(rc->c[4], delta, rc->c[3]);
-                P = fma(P, delta, rc->c[2]);
-                P = fma(P, delta, rc->c[1]);
-                P = fma(P, delta, rc->c[0]);
-                const double e = fma(rc->a, P * delta, rc->b);
-                G1 = __shfl_sync(0xffffffffu, e, 0);
-                G2 = g.ndim == 2 ? __shfl_sync(0xffffffffu, e, 1) : 0.0;
-                B = __shfl_sync(0xffffffffu, e, 2);
-                L = __shfl_sync(0xffffffffu, e, 3);
-                series = true;
-            }
-        }
+        const bool series = TAYLOR && rates_by_series(*rc, C, tc.cs, g.ndim, G1, G2, B, L);
         if (!series) kinetics_warp_T<POLY>(K, C, tc, G1, G2, B, &L, sG);
         clip2 = timestep_fast(K, g, G1, G2, t, t_out[oi], dt, t_new);
     }
