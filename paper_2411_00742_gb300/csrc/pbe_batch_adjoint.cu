@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pbe_adjoint.cuh"
+#include "pbe_chain.cuh"
 #include "pbe_internal.h"
 #include "pbe_tiles.cuh"
 
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
     extern __shared__ double smem[];
     __shared__ double red[2 * W];
     __shared__ double chs[6];   // chain values handed from warp 0 to the team
+    __shared__ RateCarry rcs[32];   // warp 0: a step's stage-2 evaluation, for the next step's rates (the same time)
     __shared__ double pcs[4], pus[4];   // pending moment-weight coefficients of the stage adjoints
     __shared__ int s_idx;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -234,6 +236,9 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
             s.V0 = tm.sum(m3 * (((hd * hd) * hd) * d1));
         }
         int out_idx = 0;
+        // the chain's last stage-2 evaluation (time and solubility) for the series
+        double rct = __longlong_as_double(0x7ff8000000000000LL), rccs = 0.0;
+        if (W == 1 || warp == 0) rate_carry_init(rcs[tid & 31], Kn);
         const bool row0 = n_out > 0 && t_out[0] == s.t;
         while (out_idx < n_out && t_out[out_idx] == s.t) ++out_idx;
         long long total = 0;
@@ -245,7 +250,9 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
             double G1, G2, B, dt, tn, L;
             int clipped = 0;
             if (W == 1 || warp == 0) {
-                kinetics_warp<false>(Kn, r.C, r.t, G1, G2, B, &L);
+                // at the time of the last stage-2 evaluation: the series from it
+                if (!(r.t == rct && rates_by_series(rcs[tid & 31], r.C, rccs, 1, G1, G2, B, L)))
+                    kinetics_warp<false>(Kn, r.C, r.t, G1, G2, B, &L);
                 clipped = timestep_fast(Kn, g, G1, G2, r.t, t_out[out_idx], dt, tn);
             }
             if (W > 1) {
@@ -259,7 +266,14 @@ __global__ void __launch_bounds__(W * 32) k_batch_vjp(const BatchInst* __restric
         };
         auto stage2_rates = [&](StepRec1& r) {
             double G1, G2, B, L;
-            if (W == 1 || warp == 0) kinetics_warp<false>(Kn, r.C1, r.t_new, G1, G2, B, &L);
+            if (W == 1 || warp == 0) {
+                const KinT tc = kin_temperature(Kn, r.t_new);
+                double rec[2];
+                kinetics_warp_T<false>(Kn, r.C1, tc, G1, G2, B, &L, nullptr, rec);
+                rate_carry_keep(rcs[tid & 31], Kn, G1, G2, B, L, rec);
+                rct = r.t_new;
+                rccs = tc.cs;
+            }
             if (W > 1) {
                 if (tid == 0) { chs[0] = G1; chs[1] = B; chs[2] = L; }
                 __syncthreads();
