@@ -12,7 +12,8 @@
 // registers), so between stages only its halo comes from L2.  While thread 0
 // waits at the barrier, warps 1-6 compute the next stage's faces that read
 // only the tile's own cells and warp 7 reduces the output moments of output
-// steps (summed into the rows after the solve).  After the barrier warp 0
+// steps (2-D: the threads' column sums S_p = sum x1^p n, weighted by x2^q dA;
+// summed into the rows after the solve).  After the barrier warp 0
 // advances the block's private copy of the scalar chain (solute balance,
 // kinetics, CFL step, the next stage's coefficients - identical in every
 // block) and hands the halo over to warps 1-6 through a named barrier; they
@@ -20,13 +21,17 @@
 // Newton-Raphson quotient (psi_quot_fast).
 //
 // GB300 FP64 notes that shape this kernel: a warp-wide FP64 instruction
-// occupies the SM's FP64 pipe for ~16 cycles whatever its active lanes, and
-// a dependent FP64 operation takes ~65 cycles, so the scalar chain between
-// stages (the critical path on small grids) is kept short: the moment
-// weights of each thread's cells are computed once, the cross-block sum
-// costs no round trip beyond the barrier's own (fixed-point warp sums), the
-// stage coefficients are computed once per block from registers, the
-// temperature once per step, and the kinetics use table-driven exp and log.
+// occupies the SM's FP64 pipe for ~16-18 cycles whatever its active lanes,
+// and one warp issues about one FP64 instruction per ~64 cycles whether or
+// not they depend on each other, so the scalar chain between stages (the
+// critical path on small grids) costs about 64 cycles per FP64 instruction
+// and is kept short: the moment weights of each thread's cells are computed
+// once, the cross-block sum costs no round trip beyond the barrier's own
+// (fixed-point warp sums), the stage coefficients are computed once per
+// block from registers, the temperature once per step, the kinetics use
+// table-driven exp and log, and the second rate evaluation of a step is a
+// short series from the first (RateCarry).  The 2-D output moments are
+// separable column sums, combined by the moment warp.
 //
 // Every wait is bounded: a barrier that does not complete within about one
 // second sets PBE_ETIMEOUT and the kernel returns.
