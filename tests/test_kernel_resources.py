@@ -24,22 +24,26 @@ def _ptxas_report(unit):
            "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", os.path.join(CSRC, unit), "-o", os.devnull]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
-    # entry name -> (registers, spill store bytes)
-    out, name = {}, None
+    # entry name -> (registers, spill store bytes); an entry's report is its
+    # "Function properties for <entry>" block and the "Used ... registers"
+    # line after it (device functions have properties blocks of their own)
+    out, entry, cur = {}, None, None
     for line in r.stderr.splitlines():
         m = re.search(r"Compiling entry function '(\S+)'", line)
         if m:
-            name = m.group(1)
+            entry = cur = m.group(1)
+            out[entry] = [None, 0]
             continue
-        if "Function properties for" in line:   # a device function's report, not the entry's
-            name = None
+        m = re.search(r"Function properties for (\S+)", line)
+        if m:
+            cur = m.group(1)
             continue
         m = re.search(r"(\d+) bytes spill stores", line)
-        if m and name:
-            out.setdefault(name, [None, 0])[1] = int(m.group(1))
+        if m and entry and cur == entry:
+            out[entry][1] = int(m.group(1))
         m = re.search(r"Used (\d+) registers", line)
-        if m and name:
-            out.setdefault(name, [None, 0])[0] = int(m.group(1))
+        if m and entry:
+            out[entry][0] = int(m.group(1))
     return out
 
 
