@@ -74,13 +74,6 @@ __device__ __forceinline__ double allsum2_split(double a, double b)
     return v;
 }
 
-// The integer w as a double, exactly, for 0 <= w < 2^52: w in the low
-// mantissa bits of 2^52, minus 2^52 (one FP64 addition).
-__device__ __forceinline__ double exact_int_double(long long w)
-{
-    return __longlong_as_double(0x4330000000000000LL | w) - 4503599627370496.0;
-}
-
 // The moment weights are x_i^k = (2i + 1)^k (dL/2)^k: the integer powers are
 // formed in integer arithmetic (exact: (2 kMaxBatchCells)^3 < 2^52) and
 // converted by one addition each, the factor (dL/2)^k dL applied to the

@@ -78,12 +78,6 @@ struct Team {
     }
 };
 
-// The integer w as a double, exactly, for 0 <= w < 2^52 (one FP64 addition).
-__device__ __forceinline__ double exact_int_double(long long w)
-{
-    return __longlong_as_double(0x4330000000000000LL | w) - 4503599627370496.0;
-}
-
 // forward stage over the rows [r0, r1) of this warp (fused-path quotient),
 // as in pbe_batch.cu; returns this lane's partial of the volume moment.  The
 // weights x_i^3 dL = (2i+1)^3 (dL/2)^3 dL: the integer cube exactly (i below

@@ -35,6 +35,13 @@ struct Kin {
 constexpr int kMlpH = 64;
 constexpr int kMlpNW = kMlpH * 3 + kMlpH + kMlpH * kMlpH + kMlpH + 3 * kMlpH + 3;  // flat weight count
 
+// The integer w as a double, exactly, for 0 <= w < 2^52: w in the low
+// mantissa bits of 2^52, minus 2^52 (one FP64 addition, no conversion).
+__device__ __forceinline__ double exact_int_double(long long w)
+{
+    return __longlong_as_double(0x4330000000000000LL | w) - 4503599627370496.0;
+}
+
 struct Geom {
     int ndim;
     int N1, N2;      // cells along L1 and L2 (N2 = 1 in 1-D)
